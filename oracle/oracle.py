@@ -1,0 +1,344 @@
+"""ctypes wrapper of the FP64 CPU oracle (smc2_oracle.c).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` load it.  The CUDA library never imports,
+links or calls anything here, and nothing here imports the CUDA package.
+
+Every function is a thin marshalling layer over the C oracle; the arithmetic
+is all in ``smc2_oracle.c``, which follows the paper section by section.
+Arrays cross the boundary as numpy arrays; the population layout on this side
+is row-major ``theta[N][D]``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+from concurrent.futures import ThreadPoolExecutor
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "smc2_oracle.c")
+_LIB_DIR = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_LIB_DIR, "liboracle.so")
+
+LG, SEIR = 0, 1
+LK_FORWARD, LK_GAUSS = 0, 1
+MAX_D = 8
+TAG_THETA_INIT, TAG_PROPOSE, TAG_OUTER_RES = 1, 2, 3
+TAG_PF_INIT, TAG_PF_PROP, TAG_PF_RES = 4, 5, 6
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with plain gcc (no fast-math, no FMA contraction)."""
+    os.makedirs(_LIB_DIR, exist_ok=True)
+    hdr = os.path.join(_HERE, "smc2_oracle.h")
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= max(os.path.getmtime(_SRC), os.path.getmtime(hdr))):
+        return _LIB
+    tmp = _LIB + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off",
+           "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
+    subprocess.check_call(cmd)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+class OracleCfg(C.Structure):
+    _fields_ = [
+        ("model", C.c_int), ("D", C.c_int), ("N", C.c_int), ("M", C.c_int), ("T", C.c_int),
+        ("lkernel", C.c_int), ("dataset", C.c_int),
+        ("rw_scale", C.c_double), ("ess_frac", C.c_double), ("seed", C.c_uint64),
+        ("prior_mean", C.c_double * MAX_D), ("prior_sd", C.c_double * MAX_D),
+        ("npop", C.c_double), ("e0", C.c_double), ("i0", C.c_double),
+        ("lambda_floor", C.c_double), ("n_sub", C.c_int),
+    ]
+
+
+class OracleStats(C.Structure):
+    _fields_ = [
+        ("k", C.c_int), ("resampled", C.c_int), ("lk_fallback", C.c_int), ("pad", C.c_int),
+        ("lse", C.c_double), ("lse2", C.c_double), ("ess", C.c_double), ("logz", C.c_double),
+        ("est", C.c_double * MAX_D),
+    ]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = C.CDLL(build())
+            _declare(_lib)
+    return _lib
+
+
+def _p(a, ct):
+    return a.ctypes.data_as(C.POINTER(ct)) if a is not None else None
+
+
+def _declare(L):
+    dp, ip, up = C.POINTER(C.c_double), C.POINTER(C.c_int32), C.POINTER(C.c_uint32)
+    u64p = C.POINTER(C.c_uint64)
+    L.oracle_philox4x32_10.argtypes = [up, up, up]
+    L.oracle_uniform23.argtypes = [C.c_uint32]
+    L.oracle_uniform23.restype = C.c_double
+    L.oracle_normals4.argtypes = [C.c_uint64] + [C.c_uint32] * 4 + [dp]
+    L.oracle_kalman_loglik.argtypes = [C.c_double, C.c_double, C.c_double, dp, C.c_int]
+    L.oracle_kalman_loglik.restype = C.c_double
+    L.oracle_fixed_point_bits.argtypes = [C.c_int]
+    L.oracle_fixed_point_bits.restype = C.c_int
+    L.oracle_quantise.argtypes = [dp, C.c_int, u64p]
+    L.oracle_quantise.restype = C.c_int
+    L.oracle_systematic_from_q.argtypes = [u64p, C.c_int, C.c_uint32, ip, ip]
+    L.oracle_systematic_from_q.restype = C.c_int
+    L.oracle_log_obs.argtypes = [C.POINTER(OracleCfg), dp, dp, C.c_double]
+    L.oracle_log_obs.restype = C.c_double
+    L.oracle_pf_loglik.argtypes = [C.POINTER(OracleCfg), dp, dp, C.c_uint32, C.c_uint32, dp, ip]
+    L.oracle_pf_loglik.restype = C.c_double
+    L.oracle_log_prior.argtypes = [C.POINTER(OracleCfg), dp]
+    L.oracle_log_prior.restype = C.c_double
+    L.oracle_lkernel_fit.argtypes = [C.c_int, C.c_int, dp, dp, dp, dp, dp, dp, dp, dp]
+    L.oracle_lkernel_fit.restype = C.c_int
+    L.oracle_gauss_lkernel_logpdf.argtypes = [C.c_int, dp, dp, dp, C.c_double, dp, dp]
+    L.oracle_gauss_lkernel_logpdf.restype = C.c_double
+    L.oracle_smc2_step.argtypes = [C.POINTER(OracleCfg), dp, C.c_int, dp, dp, dp, dp,
+                                   C.POINTER(OracleStats)]
+    L.oracle_smc2_step.restype = C.c_int
+    L.oracle_recycle.argtypes = [C.c_int, C.c_int, C.POINTER(OracleStats), dp, dp]
+
+
+# --------------------------------------------------------------------------
+# configuration
+# --------------------------------------------------------------------------
+
+@dataclass
+class Config:
+    """Plain description of one SMC^2 problem, as the oracle sees it."""
+    model: int
+    D: int
+    N: int
+    M: int
+    T: int
+    K: int = 1
+    lkernel: int = LK_GAUSS
+    dataset: int = 0
+    rw_scale: float = 0.1
+    ess_frac: float = 0.5
+    seed: int = 1
+    prior_mean: list = field(default_factory=list)
+    prior_sd: list = field(default_factory=list)
+    npop: float = 0.0
+    e0: float = 0.0
+    i0: float = 0.0
+    lambda_floor: float = 1e-3
+    n_sub: int = 2
+
+    def ctype(self) -> OracleCfg:
+        c = OracleCfg()
+        c.model, c.D, c.N, c.M, c.T = self.model, self.D, self.N, self.M, self.T
+        c.lkernel, c.dataset = self.lkernel, self.dataset
+        c.rw_scale, c.ess_frac, c.seed = self.rw_scale, self.ess_frac, self.seed
+        for d in range(self.D):
+            c.prior_mean[d] = self.prior_mean[d]
+            c.prior_sd[d] = self.prior_sd[d]
+        c.npop, c.e0, c.i0 = self.npop, self.e0, self.i0
+        c.lambda_floor, c.n_sub = self.lambda_floor, self.n_sub
+        return c
+
+
+def config_from(w, **over) -> Config:
+    """Build a Config from any object with the workload's attribute names."""
+    keys = Config.__dataclass_fields__.keys()
+    kw = {k: getattr(w, k) for k in keys if hasattr(w, k)}
+    kw.update(over)
+    return Config(**kw)
+
+
+# --------------------------------------------------------------------------
+# primitives
+# --------------------------------------------------------------------------
+
+def philox(ctr, key) -> np.ndarray:
+    c = np.asarray(ctr, dtype=np.uint32).copy()
+    k = np.asarray(key, dtype=np.uint32).copy()
+    out = np.zeros(4, dtype=np.uint32)
+    lib().oracle_philox4x32_10(_p(c, C.c_uint32), _p(k, C.c_uint32), _p(out, C.c_uint32))
+    return out
+
+
+def uniform23(w: int) -> float:
+    return lib().oracle_uniform23(int(w))
+
+
+def normals4(seed, c0, c1, c2, c3) -> np.ndarray:
+    z = np.zeros(4)
+    lib().oracle_normals4(int(seed), int(c0), int(c1), int(c2), int(c3), _p(z, C.c_double))
+    return z
+
+
+def kalman_loglik(phi, sx, sy, y) -> float:
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    return lib().oracle_kalman_loglik(float(phi), float(sx), float(sy), _p(y, C.c_double), len(y))
+
+
+def fixed_point_bits(n: int) -> int:
+    return lib().oracle_fixed_point_bits(int(n))
+
+
+def quantise(logw):
+    logw = np.ascontiguousarray(logw, dtype=np.float64)
+    q = np.zeros(len(logw), dtype=np.uint64)
+    B = lib().oracle_quantise(_p(logw, C.c_double), len(logw), _p(q, C.c_uint64))
+    return q, B
+
+
+def systematic_from_q(q, U):
+    q = np.ascontiguousarray(q, dtype=np.uint64)
+    n = len(q)
+    nc = np.zeros(n, dtype=np.int32)
+    anc = np.zeros(n, dtype=np.int32)
+    rc = lib().oracle_systematic_from_q(_p(q, C.c_uint64), n, int(U), _p(nc, C.c_int32),
+                                        _p(anc, C.c_int32))
+    if rc != 0:
+        raise ValueError("systematic resampling: no positive weight")
+    return nc, anc
+
+
+def log_obs(cfg: Config, theta, x, y) -> float:
+    c = cfg.ctype()
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    xs = np.zeros(5)
+    xs[:len(x)] = x
+    return lib().oracle_log_obs(C.byref(c), _p(th, C.c_double), _p(xs, C.c_double), float(y))
+
+
+def pf_loglik(cfg: Config, theta, y, k: int, i: int, trace: bool = False):
+    """log p^(y_{1:T} | theta) of filter i at iteration k (with the trace if asked)."""
+    c = cfg.ctype()
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    yy = np.ascontiguousarray(y, dtype=np.float64)
+    delta = np.zeros(cfg.T) if trace else None
+    anc = np.zeros((max(cfg.T - 1, 0), cfg.M), dtype=np.int32) if trace else None
+    ll = lib().oracle_pf_loglik(C.byref(c), _p(th, C.c_double), _p(yy, C.c_double), int(k), int(i),
+                                _p(delta, C.c_double), _p(anc, C.c_int32))
+    return (ll, delta, anc) if trace else ll
+
+
+def pf_loglik_many(cfg: Config, thetas, y, k: int, i0: int = 0, threads: int = 1) -> np.ndarray:
+    """PF log-likelihoods of theta rows i0, i0+1, ... (embarrassingly parallel over theta).
+
+    The C calls release the GIL, so a thread pool uses several host cores."""
+    thetas = np.ascontiguousarray(thetas, dtype=np.float64)
+    n = thetas.shape[0]
+    out = np.zeros(n)
+
+    def run(lo, hi):
+        for r in range(lo, hi):
+            out[r] = pf_loglik(cfg, thetas[r], y, k, i0 + r)
+
+    if threads <= 1:
+        run(0, n)
+    else:
+        chunks = np.linspace(0, n, threads + 1).astype(int)
+        with ThreadPoolExecutor(threads) as ex:
+            list(ex.map(lambda a: run(*a), zip(chunks[:-1], chunks[1:])))
+    return out
+
+
+def log_prior(cfg: Config, theta) -> float:
+    c = cfg.ctype()
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    return lib().oracle_log_prior(C.byref(c), _p(th, C.c_double))
+
+
+def lkernel_fit(theta_prev, theta_new, wn_prev):
+    a = np.ascontiguousarray(theta_prev, dtype=np.float64)
+    b = np.ascontiguousarray(theta_new, dtype=np.float64)
+    w = np.ascontiguousarray(wn_prev, dtype=np.float64)
+    N, D = a.shape
+    mu = np.zeros(2 * D)
+    sigma = np.zeros((2 * D, 2 * D))
+    A = np.zeros((D, D))
+    Lc = np.zeros((D, D))
+    ld = C.c_double(0.0)
+    rc = lib().oracle_lkernel_fit(D, N, _p(a, C.c_double), _p(b, C.c_double), _p(w, C.c_double),
+                                  _p(mu, C.c_double), _p(sigma, C.c_double), _p(A, C.c_double),
+                                  _p(Lc, C.c_double), C.byref(ld))
+    return {"fallback": rc, "mu": mu, "sigma": sigma, "A": A, "Lc": Lc, "logdet": ld.value}
+
+
+def lkernel_logpdf(fit, a, b) -> float:
+    D = fit["A"].shape[0]
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    return lib().oracle_gauss_lkernel_logpdf(D, _p(fit["mu"], C.c_double), _p(fit["A"], C.c_double),
+                                             _p(fit["Lc"], C.c_double), fit["logdet"],
+                                             _p(a, C.c_double), _p(b, C.c_double))
+
+
+# --------------------------------------------------------------------------
+# the SMC^2 sampler
+# --------------------------------------------------------------------------
+
+def _stats_dict(s: OracleStats, D: int) -> dict:
+    return {"k": s.k, "resampled": s.resampled, "lk_fallback": s.lk_fallback, "lse": s.lse,
+            "lse2": s.lse2, "ess": s.ess, "logz": s.logz, "est": np.array(s.est[:D])}
+
+
+class SMC2:
+    """The oracle sampler: state held in numpy arrays, one C call per iteration."""
+
+    def __init__(self, cfg: Config, y):
+        self.cfg = cfg
+        self.y = np.ascontiguousarray(y, dtype=np.float64)
+        N, D = cfg.N, cfg.D
+        self.theta = np.zeros((N, D))
+        self.logprior = np.zeros(N)
+        self.loglik = np.zeros(N)
+        self.logw = np.zeros(N)
+        self.k = 0
+        self.stats: list[dict] = []
+        self._raw: list[OracleStats] = []
+        self._c = cfg.ctype()
+
+    def set_state(self, k, theta, logprior, loglik, logw):
+        self.k = int(k)
+        self.theta[:] = theta
+        self.logprior[:] = logprior
+        self.loglik[:] = loglik
+        self.logw[:] = logw
+
+    def step(self) -> dict:
+        st = OracleStats()
+        k = self.k + 1
+        rc = lib().oracle_smc2_step(C.byref(self._c), _p(self.y, C.c_double), k,
+                                    _p(self.theta, C.c_double), _p(self.logprior, C.c_double),
+                                    _p(self.loglik, C.c_double), _p(self.logw, C.c_double),
+                                    C.byref(st))
+        if rc != 0:
+            raise FloatingPointError(f"oracle SMC2 iteration {k}: status {rc}")
+        self.k = k
+        self._raw.append(st)
+        d = _stats_dict(st, self.cfg.D)
+        self.stats.append(d)
+        return d
+
+    def run(self, K=None) -> "SMC2":
+        for _ in range((K or self.cfg.K) - self.k):
+            self.step()
+        return self
+
+    def recycled(self):
+        K = len(self._raw)
+        arr = (OracleStats * K)(*self._raw)
+        est = np.zeros(self.cfg.D)
+        ck = np.zeros(K)
+        lib().oracle_recycle(K, self.cfg.D, arr, _p(est, C.c_double), _p(ck, C.c_double))
+        return est, ck

@@ -1,0 +1,590 @@
+/*
+ * smc2_oracle.c -- plain, slow, FP64 CPU oracle of the SMC^2 hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the
+ * CPU-baseline leg of the benchmark may load it; the CUDA library never
+ * does.  Every function follows the paper (Rosato, Varsi, Murphy, Maskell,
+ * "An O(log2 N) SMC^2 algorithm on distributed memory with an approx.
+ * optimal L-kernel") step by step, in its order and notation, with no
+ * blocking, fusion or reordering.  Readings of passages that are garbled or
+ * silent are stated where they are used.  The random-number and
+ * fixed-point conventions are described in smc2_oracle.h.
+ */
+#include "smc2_oracle.h"
+
+#include <float.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define LOG_2PI 1.8378770664093454835606594728112
+
+typedef __int128 i128;
+typedef unsigned __int128 u128;
+
+/* ------------------------------------------------------------------ */
+/* Random numbers                                                      */
+/* ------------------------------------------------------------------ */
+
+/* Philox4x32-10 as published by Salmon et al. (SC'11): ten rounds of the
+ * Philox S-box on a 4-word counter; each round multiplies words 0 and 2 by
+ * the two round multipliers, and the key is bumped by the two Weyl
+ * constants between rounds. */
+void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  const uint32_t mult0 = 0xD2511F53u, mult1 = 0xCD9E8D57u;
+  const uint32_t weyl0 = 0x9E3779B9u, weyl1 = 0xBB67AE85u;
+  uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+  uint32_t k0 = key[0], k1 = key[1];
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) {
+      k0 += weyl0;
+      k1 += weyl1;
+    }
+    uint64_t p0 = (uint64_t)mult0 * (uint64_t)x0;
+    uint64_t p1 = (uint64_t)mult1 * (uint64_t)x2;
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t y0 = hi1 ^ x1 ^ k0;
+    uint32_t y1 = lo1;
+    uint32_t y2 = hi0 ^ x3 ^ k1;
+    uint32_t y3 = lo0;
+    x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+  }
+  out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* The 23 high bits of a word, centred in their cell: a uniform on (0,1)
+ * that float32 and float64 both hold exactly. */
+double oracle_uniform23(uint32_t w) { return ((double)(w >> 9) + 0.5) * (1.0 / 8388608.0); }
+
+/* Four standard normals by the Box-Muller transform of the four uniforms. */
+void oracle_normals4(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, double z[4]) {
+  uint32_t ctr[4] = {c0, c1, c2, c3};
+  uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+  uint32_t w[4];
+  oracle_philox4x32_10(ctr, key, w);
+  for (int pair = 0; pair < 2; ++pair) {
+    double ua = oracle_uniform23(w[2 * pair]);
+    double ub = oracle_uniform23(w[2 * pair + 1]);
+    double r = sqrt(-2.0 * log(ua));
+    z[2 * pair] = r * cos(2.0 * M_PI * ub);
+    z[2 * pair + 1] = r * sin(2.0 * M_PI * ub);
+  }
+}
+
+static uint32_t oracle_word0(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3) {
+  uint32_t ctr[4] = {c0, c1, c2, c3};
+  uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+  uint32_t w[4];
+  oracle_philox4x32_10(ctr, key, w);
+  return w[0];
+}
+
+/* ------------------------------------------------------------------ */
+/* Exact likelihood of the linear-Gaussian AR(1) model (Kalman filter)  */
+/* ------------------------------------------------------------------ */
+
+/* x_0 ~ N(0,1), x_t = phi x_{t-1} + sx e_t, y_t = x_t + sy n_t, t = 1..T.
+ * Returns log p(y_{1:T}) by the prediction-error decomposition. */
+double oracle_kalman_loglik(double phi, double sx, double sy, const double* y, int T) {
+  double mean = 0.0, var = 1.0, ll = 0.0;
+  for (int t = 0; t < T; ++t) {
+    mean = phi * mean;
+    var = phi * phi * var + sx * sx;
+    double s = var + sy * sy;
+    double v = y[t] - mean;
+    ll += -0.5 * (LOG_2PI + log(s) + v * v / s);
+    double gain = var / s;
+    mean = mean + gain * v;
+    var = (1.0 - gain) * var;
+  }
+  return ll;
+}
+
+/* ------------------------------------------------------------------ */
+/* Systematic resampling: Sec. IV-B, Eqs. (26)-(28), Algorithm 1        */
+/* ------------------------------------------------------------------ */
+
+/* Fixed-point precision: the largest B <= 52 with n * 2^B < 2^64. */
+int oracle_fixed_point_bits(int n) {
+  int c = 0;
+  while (((int64_t)1 << c) < (int64_t)n) ++c;
+  int b = 63 - c;
+  return b < 52 ? b : 52;
+}
+
+/* q_i = floor(exp(l_i - max l) 2^B): the normalised weights of Eq. (11) up
+ * to the common factor 2^B / max w.  Non-finite log-weights get q = 0.
+ * Returns B, or -1 when no weight is positive. */
+int oracle_quantise(const double* logw, int n, uint64_t* q) {
+  double m = -INFINITY;
+  for (int i = 0; i < n; ++i)
+    if (!isnan(logw[i]) && logw[i] > m) m = logw[i];
+  if (!(m > -INFINITY) || isinf(m)) return -1;
+  int B = oracle_fixed_point_bits(n);
+  for (int i = 0; i < n; ++i) {
+    if (isnan(logw[i]) || isinf(logw[i])) {
+      q[i] = 0;
+    } else {
+      double e = ldexp(exp(logw[i] - m), B);
+      q[i] = (uint64_t)floor(e);
+    }
+  }
+  return B;
+}
+
+static i128 oracle_ceil_div(i128 x, i128 d) { /* d > 0 */
+  if (x >= 0) return (x + d - 1) / d;
+  return -((-x) / d);
+}
+
+/* Choice (Eqs. 26-27) and Redistribution (Algorithm 1).
+ * cdf^i = n C_i / S is the cumulative sum of Eq. (26) on the quantised
+ * weights; u = (2U+1)/2^33.  The printed Eq. (27) reads
+ * ncopies^i = ceil(cdf^{i+1} - u) - ceil(cdf^i - u); with the inclusive
+ * cdf of Eq. (26) its indices are one apart, so the oracle takes
+ * ncopies^i = ceil(cdf^i - u) - ceil(cdf^{i-1} - u), cdf^{-1} = 0.
+ * Each ceil is evaluated exactly as ceil((n C 2^33 - (2U+1) S) / (2^33 S)).
+ * Returns 0, or -1 when S = 0 or the counts break Eq. (28). */
+int oracle_systematic_from_q(const uint64_t* q, int n, uint32_t U, int32_t* ncopies, int32_t* anc) {
+  uint64_t S = 0;
+  for (int i = 0; i < n; ++i) S += q[i];
+  if (S == 0) return -1;
+  const i128 two33 = (i128)1 << 33;
+  const i128 den = two33 * (i128)S;
+  const i128 uS = (2 * (i128)U + 1) * (i128)S;
+  uint64_t C = 0; /* C_{-1} = 0 */
+  i128 prev = oracle_ceil_div((i128)n * (i128)C * two33 - uS, den);
+  int total = 0;
+  for (int i = 0; i < n; ++i) {
+    C += q[i];
+    i128 cur = oracle_ceil_div((i128)n * (i128)C * two33 - uS, den);
+    int nc = (int)(cur - prev);
+    if (nc < 0 || nc > n) return -1; /* Eq. (28a) */
+    ncopies[i] = nc;
+    total += nc;
+    prev = cur;
+  }
+  if (total != n) return -1; /* Eq. (28b) */
+  /* Algorithm 1 (S-R): copy item j ncopies^j times, in order of j. */
+  int slot = 0;
+  for (int j = 0; j < n; ++j)
+    for (int copy = 1; copy <= ncopies[j]; ++copy) anc[slot++] = j;
+  return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* State-space models: Sec. II, Eqs. (1)-(2)                            */
+/* ------------------------------------------------------------------ */
+
+/* Linear-Gaussian AR(1): theta = (phi, log sx, log sy).
+ * SEIR-type: theta = (log beta0, log sigma_rw, log kappa, log gamma); the
+ * state is (S, E, I, log beta_t, lambda_t) with R = Npop - S - E - I and
+ * lambda_t the day's incidence (the E -> I flow), observed as Poisson. */
+
+static void oracle_initial_state(const oracle_cfg* c, const double* theta, uint32_t k, uint32_t c2,
+                                 int j, double* x) {
+  if (c->model == ORACLE_LG) {
+    double z[4];
+    oracle_normals4(c->seed, (uint32_t)j, 0, c2, ORACLE_TAG_PF_INIT | (k << 4), z);
+    x[0] = z[0];
+  } else {
+    x[0] = c->npop - c->e0 - c->i0;
+    x[1] = c->e0;
+    x[2] = c->i0;
+    x[3] = theta[0];
+    x[4] = 0.0;
+  }
+}
+
+/* One draw of Eq. (1), the bootstrap proposal q = f. */
+static void oracle_propagate(const oracle_cfg* c, const double* theta, double z, double* x) {
+  if (c->model == ORACLE_LG) {
+    x[0] = theta[0] * x[0] + exp(theta[1]) * z;
+  } else {
+    double logbeta = x[3] + exp(theta[1]) * z;
+    double beta = exp(logbeta), kappa = exp(theta[2]), gamma = exp(theta[3]);
+    double dt = 1.0 / (double)c->n_sub;
+    double S = x[0], E = x[1], I = x[2], lambda = 0.0;
+    for (int s = 0; s < c->n_sub; ++s) {
+      double infection = beta * S * I / c->npop;
+      double onset = kappa * E;
+      double recovery = gamma * I;
+      lambda += dt * onset;
+      S = fmax(S - dt * infection, 0.0);
+      E = fmax(E + dt * (infection - onset), 0.0);
+      I = fmax(I + dt * (onset - recovery), 0.0);
+    }
+    x[0] = S; x[1] = E; x[2] = I; x[3] = logbeta;
+    x[4] = fmax(lambda, c->lambda_floor);
+  }
+}
+
+/* log g(y_t | x_t, theta), Eq. (2). */
+double oracle_log_obs(const oracle_cfg* c, const double* theta, const double* x, double y) {
+  if (c->model == ORACLE_LG) {
+    double sy = exp(theta[2]);
+    double r = (y - x[0]) / sy;
+    return -0.5 * LOG_2PI - log(sy) - 0.5 * r * r;
+  } else {
+    double lambda = x[4];
+    return (y > 0.0 ? y * log(lambda) : 0.0) - lambda - lgamma(y + 1.0);
+  }
+}
+
+/* ------------------------------------------------------------------ */
+/* Bootstrap particle filter: Sec. II                                   */
+/* ------------------------------------------------------------------ */
+
+/* Returns log p^(y_{1:T} | theta), Eq. (8), for filter i of iteration k.
+ * The unnormalised weight of particle j is carried as exp(L + lw_j): L is
+ * the log of the common weight given to every particle at the last reset
+ * (Eq. 13), lw_j the log of the product of the Eq. (5) factors since then
+ * (with q = f the factor is g(y_t | x_t)).  Resampling is systematic after
+ * every step t < T.  delta_out (T entries) receives
+ * log p^(y_{1:t}) - log p^(y_{1:t-1}); anc_out ((T-1) x M) the ancestors. */
+double oracle_pf_loglik(const oracle_cfg* c, const double* theta, const double* y, uint32_t k,
+                        uint32_t i, double* delta_out, int32_t* anc_out) {
+  const int M = c->M, T = c->T, SD = 5;
+  const uint32_t c2 = i | ((uint32_t)c->dataset << 20);
+  double* x = (double*)malloc(sizeof(double) * M * SD);
+  double* xn = (double*)malloc(sizeof(double) * M * SD);
+  double* lw = (double*)malloc(sizeof(double) * M);
+  uint64_t* q = (uint64_t*)malloc(sizeof(uint64_t) * M);
+  int32_t* ncop = (int32_t*)malloc(sizeof(int32_t) * M);
+  int32_t* anc = (int32_t*)malloc(sizeof(int32_t) * M);
+  for (int j = 0; j < M; ++j) {
+    oracle_initial_state(c, theta, k, c2, j, x + SD * j);
+    lw[j] = 0.0;
+  }
+  double L = 0.0; /* log of the common weight: w_0 = 1 */
+  double loglik = 0.0;
+  for (int t = 1; t <= T; ++t) {
+    for (int j = 0; j < M; ++j) {
+      double z[4];
+      oracle_normals4(c->seed, (uint32_t)j, (uint32_t)((t - 1) >> 2), c2,
+                      ORACLE_TAG_PF_PROP | (k << 4), z);
+      oracle_propagate(c, theta, z[(t - 1) & 3], x + SD * j);
+      double ell = oracle_log_obs(c, theta, x + SD * j, y[t - 1]);
+      if (isnan(ell)) ell = -INFINITY;
+      lw[j] = lw[j] + ell; /* Eq. (5) in logs */
+    }
+    double m = -INFINITY;
+    for (int j = 0; j < M; ++j)
+      if (lw[j] > m) m = lw[j];
+    if (!(m > -INFINITY)) { /* every weight is zero: p^ = 0 */
+      for (int s = t; s <= T; ++s)
+        if (delta_out) delta_out[s - 1] = -INFINITY;
+      loglik = -INFINITY;
+      goto done;
+    }
+    double sum = 0.0;
+    for (int j = 0; j < M; ++j) sum += exp(lw[j] - m);
+    /* Eq. (8): log of (1/M) sum_j exp(L + lw_j). */
+    double logp = L + m + log(sum) - log((double)M);
+    if (delta_out) delta_out[t - 1] = logp - L;
+    loglik = logp;
+    if (t < T) {
+      uint32_t U = oracle_word0(c->seed, 0, (uint32_t)t, c2, ORACLE_TAG_PF_RES | (k << 4));
+      oracle_quantise(lw, M, q);
+      oracle_systematic_from_q(q, M, U, ncop, anc);
+      for (int j = 0; j < M; ++j) memcpy(xn + SD * j, x + SD * anc[j], sizeof(double) * SD);
+      double* tmp = x; x = xn; xn = tmp;
+      if (anc_out) memcpy(anc_out + (size_t)(t - 1) * M, anc, sizeof(int32_t) * M);
+      /* Eq. (13): every particle now carries the mean weight. */
+      L = logp;
+      for (int j = 0; j < M; ++j) lw[j] = 0.0;
+    }
+  }
+done:
+  free(x); free(xn); free(lw); free(q); free(ncop); free(anc);
+  return loglik;
+}
+
+/* ------------------------------------------------------------------ */
+/* SMC^2 outer sampler: Sec. IV                                         */
+/* ------------------------------------------------------------------ */
+
+/* log p(theta): independent Gaussians in the unconstrained coordinates. */
+double oracle_log_prior(const oracle_cfg* c, const double* theta) {
+  double lp = 0.0;
+  for (int d = 0; d < c->D; ++d) {
+    double r = (theta[d] - c->prior_mean[d]) / c->prior_sd[d];
+    lp += -0.5 * LOG_2PI - log(c->prior_sd[d]) - 0.5 * r * r;
+  }
+  return lp;
+}
+
+static double oracle_gauss_iso_logpdf(int D, const double* x, const double* mean, double sd) {
+  double ss = 0.0;
+  for (int d = 0; d < D; ++d) {
+    double r = (x[d] - mean[d]) / sd;
+    ss += r * r;
+  }
+  return -0.5 * D * LOG_2PI - D * log(sd) - 0.5 * ss;
+}
+
+/* Lower Cholesky factor of the n x n matrix a (row-major).  A pivot counts
+ * as zero (return -1) unless it exceeds 1e-12 (a_jj + mean_j^2): below that
+ * the fitted variance is rounding noise of the second moment. */
+static int oracle_cholesky(int n, const double* a, const double* mean, double* l) {
+  memset(l, 0, sizeof(double) * n * n);
+  for (int j = 0; j < n; ++j) {
+    double s = a[j * n + j];
+    for (int p = 0; p < j; ++p) s -= l[j * n + p] * l[j * n + p];
+    double floor_j = 1e-12 * (a[j * n + j] + mean[j] * mean[j]);
+    if (!(s > floor_j) || !isfinite(s)) return -1;
+    l[j * n + j] = sqrt(s);
+    for (int r = j + 1; r < n; ++r) {
+      double v = a[r * n + j];
+      for (int p = 0; p < j; ++p) v -= l[r * n + p] * l[j * n + p];
+      l[r * n + j] = v / l[j * n + j];
+    }
+  }
+  return 0;
+}
+
+/* Approximately optimal L-kernel, Sec. IV-D, Eqs. (32)-(35).
+ * a = theta_{k-1} (parents), b = theta_k (their proposals), weighted by the
+ * normalised parent weights.  Eq. (32): fit a joint Gaussian to (a, b)
+ * (weighted mean and covariance, normalised by the weight sum).
+ * Eqs. (33)-(35) print the conditional with its factors transposed and the
+ * density argument as theta_k; the oracle takes the Gaussian conditional of
+ * a given b:
+ *   mu_{a|b}(b) = mu_a + S_ab S_bb^{-1} (b - mu_b),
+ *   S_{a|b}     = S_aa - S_ab S_bb^{-1} S_ba,
+ *   L(a | b)    = N(a; mu_{a|b}(b), S_{a|b}).
+ * Outputs: mu (2D), sigma (2D x 2D), A = S_ab S_bb^{-1} (D x D), Lc =
+ * chol(S_{a|b}) and log det S_{a|b}.  Returns 0, or 1 when S_bb or S_{a|b}
+ * is numerically singular (the caller then uses the forward kernel, Eq. 30). */
+int oracle_lkernel_fit(int D, int N, const double* theta_prev, const double* theta_new,
+                       const double* wn_prev, double* mu, double* sigma, double* A, double* Lc,
+                       double* logdet_c) {
+  const int D2 = 2 * D;
+  double wsum = 0.0;
+  for (int i = 0; i < N; ++i) wsum += wn_prev[i];
+  for (int r = 0; r < D2; ++r) {
+    double s = 0.0;
+    for (int i = 0; i < N; ++i) {
+      double z = r < D ? theta_prev[i * D + r] : theta_new[i * D + (r - D)];
+      s += wn_prev[i] * z;
+    }
+    mu[r] = s / wsum;
+  }
+  for (int r = 0; r < D2; ++r) {
+    for (int s = 0; s < D2; ++s) {
+      double acc = 0.0;
+      for (int i = 0; i < N; ++i) {
+        double zr = r < D ? theta_prev[i * D + r] : theta_new[i * D + (r - D)];
+        double zs = s < D ? theta_prev[i * D + s] : theta_new[i * D + (s - D)];
+        acc += wn_prev[i] * (zr - mu[r]) * (zs - mu[s]);
+      }
+      sigma[r * D2 + s] = acc / wsum;
+    }
+  }
+  double saa[ORACLE_MAX_D * ORACLE_MAX_D], sab[ORACLE_MAX_D * ORACLE_MAX_D];
+  double sbb[ORACLE_MAX_D * ORACLE_MAX_D], lb[ORACLE_MAX_D * ORACLE_MAX_D];
+  for (int r = 0; r < D; ++r)
+    for (int s = 0; s < D; ++s) {
+      saa[r * D + s] = sigma[r * D2 + s];
+      sab[r * D + s] = sigma[r * D2 + (D + s)];
+      sbb[r * D + s] = sigma[(D + r) * D2 + (D + s)];
+    }
+  if (oracle_cholesky(D, sbb, mu + D, lb) != 0) return 1;
+  /* A = S_ab S_bb^{-1}: solve S_bb X = S_ba (= S_ab^T) column by column, A = X^T. */
+  for (int col = 0; col < D; ++col) {
+    double rhs[ORACLE_MAX_D], tmp[ORACLE_MAX_D], sol[ORACLE_MAX_D];
+    for (int r = 0; r < D; ++r) rhs[r] = sab[col * D + r]; /* column col of S_ba */
+    for (int r = 0; r < D; ++r) {                          /* forward: lb tmp = rhs */
+      double v = rhs[r];
+      for (int p = 0; p < r; ++p) v -= lb[r * D + p] * tmp[p];
+      tmp[r] = v / lb[r * D + r];
+    }
+    for (int r = D - 1; r >= 0; --r) { /* backward: lb^T sol = tmp */
+      double v = tmp[r];
+      for (int p = r + 1; p < D; ++p) v -= lb[p * D + r] * sol[p];
+      sol[r] = v / lb[r * D + r];
+    }
+    for (int r = 0; r < D; ++r) A[col * D + r] = sol[r]; /* row col of A */
+  }
+  double sc[ORACLE_MAX_D * ORACLE_MAX_D];
+  for (int r = 0; r < D; ++r)
+    for (int s = 0; s < D; ++s) {
+      double v = saa[r * D + s];
+      for (int p = 0; p < D; ++p) v -= A[r * D + p] * sab[s * D + p]; /* (A S_ba)_{rs} */
+      sc[r * D + s] = v;
+    }
+  if (oracle_cholesky(D, sc, mu, Lc) != 0) return 1;
+  double ld = 0.0;
+  for (int r = 0; r < D; ++r) ld += 2.0 * log(Lc[r * D + r]);
+  *logdet_c = ld;
+  return 0;
+}
+
+/* log N(a; mu_a + A (b - mu_b), Lc Lc^T), Eq. (33) under the reading above. */
+double oracle_gauss_lkernel_logpdf(int D, const double* mu, const double* A, const double* Lc,
+                                   double logdet_c, const double* a, const double* b) {
+  double r[ORACLE_MAX_D], v[ORACLE_MAX_D];
+  for (int p = 0; p < D; ++p) {
+    double m = mu[p];
+    for (int s = 0; s < D; ++s) m += A[p * D + s] * (b[s] - mu[D + s]);
+    r[p] = a[p] - m;
+  }
+  double ss = 0.0;
+  for (int p = 0; p < D; ++p) {
+    double s = r[p];
+    for (int l = 0; l < p; ++l) s -= Lc[p * D + l] * v[l];
+    v[p] = s / Lc[p * D + p];
+    ss += v[p] * v[p];
+  }
+  return -0.5 * D * LOG_2PI - 0.5 * logdet_c - 0.5 * ss;
+}
+
+/* Eqs. (22), (21), (24), (25): normalise, estimate, recycling constant,
+ * ESS, and the evidence estimate log Z_k = log((1/N) sum_i w_k^i). */
+static int oracle_normalise(const oracle_cfg* c, const double* theta, const double* logw,
+                            oracle_stats* st) {
+  const int N = c->N, D = c->D;
+  double m = -INFINITY;
+  for (int i = 0; i < N; ++i)
+    if (logw[i] > m) m = logw[i];
+  if (!(m > -INFINITY) || isinf(m)) return 4;
+  double sw = 0.0, sw2 = 0.0;
+  for (int i = 0; i < N; ++i) {
+    double w = exp(logw[i] - m);
+    sw += w;
+    sw2 += w * w;
+  }
+  st->lse = m + log(sw);
+  st->lse2 = 2.0 * m + log(sw2);
+  double sum_wn2 = 0.0;
+  for (int d = 0; d < D; ++d) st->est[d] = 0.0;
+  for (int i = 0; i < N; ++i) {
+    double wn = exp(logw[i] - m) / sw; /* Eq. (22) */
+    sum_wn2 += wn * wn;
+    for (int d = 0; d < D; ++d) st->est[d] += wn * theta[i * D + d]; /* Eq. (21) */
+  }
+  st->ess = 1.0 / sum_wn2; /* Eq. (25); equals l_k of Eq. (24) */
+  st->logz = st->lse - log((double)N);
+  return 0;
+}
+
+/* One SMC^2 iteration k (1-based) in place on the population (row-major
+ * theta[N][D], logprior, loglik, logw).  On entry the arrays hold the
+ * population after iteration k-1 (ignored for k = 1); on exit they hold
+ * iteration k after the resampling decision.  Returns 0, or 4 when every
+ * outer weight is zero. */
+int oracle_smc2_step(const oracle_cfg* c, const double* y, int k, double* theta, double* logprior,
+                     double* loglik, double* logw, oracle_stats* st) {
+  const int N = c->N, D = c->D;
+  const uint32_t ds = (uint32_t)c->dataset << 20;
+  memset(st, 0, sizeof(*st));
+  st->k = k;
+  double* th_new = (double*)malloc(sizeof(double) * N * D);
+  double* lp_new = (double*)malloc(sizeof(double) * N);
+  double* ll_new = (double*)malloc(sizeof(double) * N);
+  double* lw_new = (double*)malloc(sizeof(double) * N);
+  int rc = 0;
+  if (k == 1) {
+    /* Eq. (16): theta_1^i ~ q_1 = prior; Eq. (17): w_1 = pi / q_1. */
+    for (int i = 0; i < N; ++i) {
+      for (int g = 0; g * 4 < D; ++g) {
+        double z[4];
+        oracle_normals4(c->seed, (uint32_t)g, 0, (uint32_t)i | ds,
+                        ORACLE_TAG_THETA_INIT | ((uint32_t)k << 4), z);
+        for (int r = 0; r < 4 && 4 * g + r < D; ++r) {
+          int d = 4 * g + r;
+          th_new[i * D + d] = c->prior_mean[d] + c->prior_sd[d] * z[r];
+        }
+      }
+      lp_new[i] = oracle_log_prior(c, th_new + i * D);
+      ll_new[i] = oracle_pf_loglik(c, th_new + i * D, y, (uint32_t)k, (uint32_t)i, NULL, NULL);
+      double logq1 = oracle_log_prior(c, th_new + i * D);
+      lw_new[i] = (lp_new[i] + ll_new[i]) - logq1;
+    }
+  } else {
+    /* Normalised parent weights (Eq. 22 at k-1) for the L-kernel fit. */
+    double m = -INFINITY, sw = 0.0;
+    for (int i = 0; i < N; ++i)
+      if (logw[i] > m) m = logw[i];
+    double* wn = (double*)malloc(sizeof(double) * N);
+    for (int i = 0; i < N; ++i) sw += exp(logw[i] - m);
+    for (int i = 0; i < N; ++i) wn[i] = exp(logw[i] - m) / sw;
+    /* Eqs. (18)-(19): theta_k^i ~ N(theta_{k-1}^i, rw_scale^2 I). */
+    double* logq = (double*)malloc(sizeof(double) * N);
+    for (int i = 0; i < N; ++i) {
+      for (int g = 0; g * 4 < D; ++g) {
+        double z[4];
+        oracle_normals4(c->seed, (uint32_t)g, 0, (uint32_t)i | ds,
+                        ORACLE_TAG_PROPOSE | ((uint32_t)k << 4), z);
+        for (int r = 0; r < 4 && 4 * g + r < D; ++r) {
+          int d = 4 * g + r;
+          th_new[i * D + d] = theta[i * D + d] + c->rw_scale * z[r];
+        }
+      }
+      logq[i] = oracle_gauss_iso_logpdf(D, th_new + i * D, theta + i * D, c->rw_scale);
+      lp_new[i] = oracle_log_prior(c, th_new + i * D);
+      ll_new[i] = oracle_pf_loglik(c, th_new + i * D, y, (uint32_t)k, (uint32_t)i, NULL, NULL);
+    }
+    /* L-kernel (Sec. IV-D). */
+    double mu[2 * ORACLE_MAX_D], sigma[4 * ORACLE_MAX_D * ORACLE_MAX_D];
+    double A[ORACLE_MAX_D * ORACLE_MAX_D], Lc[ORACLE_MAX_D * ORACLE_MAX_D], logdet_c = 0.0;
+    int fallback = 1;
+    if (c->lkernel == ORACLE_LK_GAUSS)
+      fallback = oracle_lkernel_fit(D, N, theta, th_new, wn, mu, sigma, A, Lc, &logdet_c);
+    st->lk_fallback = (c->lkernel == ORACLE_LK_GAUSS) ? fallback : 0;
+    for (int i = 0; i < N; ++i) {
+      double logL;
+      if (fallback) /* Eq. (30): L(a | b) = q(a | b) */
+        logL = oracle_gauss_iso_logpdf(D, theta + i * D, th_new + i * D, c->rw_scale);
+      else
+        logL = oracle_gauss_lkernel_logpdf(D, mu, A, Lc, logdet_c, theta + i * D, th_new + i * D);
+      /* Eq. (20) in logs. */
+      lw_new[i] = logw[i] + (lp_new[i] + ll_new[i]) - (logprior[i] + loglik[i]) + logL - logq[i];
+      if (isnan(lw_new[i])) lw_new[i] = -INFINITY;
+    }
+    free(wn);
+    free(logq);
+  }
+  memcpy(theta, th_new, sizeof(double) * N * D);
+  memcpy(logprior, lp_new, sizeof(double) * N);
+  memcpy(loglik, ll_new, sizeof(double) * N);
+  memcpy(logw, lw_new, sizeof(double) * N);
+  rc = oracle_normalise(c, theta, logw, st);
+  if (rc != 0) goto out;
+  /* Sec. IV-B: resample when N_eff < ess_frac N (the paper uses N/2). */
+  if (st->ess < c->ess_frac * (double)N) {
+    uint64_t* q = (uint64_t*)malloc(sizeof(uint64_t) * N);
+    int32_t* ncop = (int32_t*)malloc(sizeof(int32_t) * N);
+    int32_t* anc = (int32_t*)malloc(sizeof(int32_t) * N);
+    uint32_t U = oracle_word0(c->seed, 0, 0, ds, ORACLE_TAG_OUTER_RES | ((uint32_t)k << 4));
+    oracle_quantise(logw, N, q);
+    oracle_systematic_from_q(q, N, U, ncop, anc);
+    for (int j = 0; j < N; ++j) {
+      memcpy(theta + j * D, th_new + anc[j] * D, sizeof(double) * D);
+      logprior[j] = lp_new[anc[j]];
+      loglik[j] = ll_new[anc[j]];
+    }
+    /* Reset: every normalised weight becomes 1/N; the unnormalised weight
+     * is the mean (1/N) sum_i w_k^i, which keeps the evidence estimate. */
+    for (int j = 0; j < N; ++j) logw[j] = st->lse - log((double)N);
+    st->resampled = 1;
+    free(q); free(ncop); free(anc);
+  }
+out:
+  free(th_new); free(lp_new); free(ll_new); free(lw_new);
+  return rc;
+}
+
+/* Recycling, Sec. IV-C and Eqs. (23)-(24), (29): c_k = l_k / sum_k l_k and
+ * f~ = sum_k c_k f~_k, with l_k the ESS of iteration k. */
+void oracle_recycle(int K, int D, const oracle_stats* st, double* est_out, double* c_out) {
+  double lsum = 0.0;
+  for (int k = 0; k < K; ++k) lsum += st[k].ess;
+  for (int d = 0; d < D; ++d) est_out[d] = 0.0;
+  for (int k = 0; k < K; ++k) {
+    double ck = st[k].ess / lsum;
+    if (c_out) c_out[k] = ck;
+    for (int d = 0; d < D; ++d) est_out[d] += ck * st[k].est[d];
+  }
+}

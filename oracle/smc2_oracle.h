@@ -1,0 +1,100 @@
+/*
+ * smc2_oracle.h -- plain, slow, FP64 CPU oracle of the SMC^2 hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the
+ * CPU-baseline leg of the benchmark may load this code.  It shares no code,
+ * header, table or helper with the CUDA library; the two meet only through
+ * the seeded synthetic inputs and the random-number definition below, which
+ * each side implements on its own from its published description.
+ *
+ * Conventions (the numerics definition both sides are written from):
+ *
+ *  Random numbers.  Philox4x32-10 (Salmon, Moraes, Dror and Shaw, "Parallel
+ *  random numbers: as easy as 1, 2, 3", SC'11), key = (seed low 32 bits,
+ *  seed high 32 bits), counter = (c0, c1, c2, c3) with
+ *     c2 = theta index i | dataset << 20,   c3 = tag | iteration k << 4.
+ *  A 32-bit word w becomes the uniform u = ((w >> 9) + 0.5) * 2^-23 in (0,1)
+ *  (exact in float and double);
+ *  words (w0,w1) and (w2,w3) become two Box-Muller pairs
+ *     r = sqrt(-2 ln u_a),  (r cos 2 pi u_b, r sin 2 pi u_b).
+ *  Tags and the meaning of c0, c1:
+ *     1 THETA_INIT   c0 = coordinate group g (coordinates 4g..4g+3), c1 = 0
+ *     2 PROPOSE      same layout as THETA_INIT
+ *     3 OUTER_RES    c0 = c1 = 0, c2 = dataset << 20; word 0 is U
+ *     4 PF_INIT      c0 = particle j, c1 = 0; normal 0 is the initial draw
+ *     5 PF_PROP      c0 = particle j, c1 = (t-1) >> 2; step t uses normal (t-1) & 3
+ *     6 PF_RES       c0 = 0, c1 = t; word 0 is U for the resampling after step t
+ *
+ *  Systematic resampling in integers.  For log-weights l_0..l_{n-1} with
+ *  maximum m, q_i = floor(exp(l_i - m) * 2^B) with B = min(52, 63 - ceil(log2 n)),
+ *  C_i = q_0 + ... + q_i, S = C_{n-1}, u = (2U + 1) / 2^33, and
+ *     cdf^i = n C_i / S,   ncopies^i = ceil(cdf^i - u) - ceil(cdf^{i-1} - u),
+ *  evaluated exactly in 128-bit integers, then Algorithm 1 (sequential
+ *  redistribution) lays the copies out in index order.
+ */
+#ifndef SMC2_ORACLE_H
+#define SMC2_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { ORACLE_LG = 0, ORACLE_SEIR = 1 };
+enum { ORACLE_LK_FORWARD = 0, ORACLE_LK_GAUSS = 1 };
+enum {
+  ORACLE_TAG_THETA_INIT = 1, ORACLE_TAG_PROPOSE = 2, ORACLE_TAG_OUTER_RES = 3,
+  ORACLE_TAG_PF_INIT = 4, ORACLE_TAG_PF_PROP = 5, ORACLE_TAG_PF_RES = 6
+};
+#define ORACLE_MAX_D 8
+
+typedef struct {
+  int model;             /* ORACLE_LG or ORACLE_SEIR */
+  int D, N, M, T;        /* dim theta, theta samples, PF particles, time steps */
+  int lkernel;           /* ORACLE_LK_FORWARD or ORACLE_LK_GAUSS */
+  int dataset;           /* dataset index (random-stream key only) */
+  double rw_scale;       /* random-walk proposal standard deviation */
+  double ess_frac;       /* outer resampling when ESS < ess_frac * N */
+  uint64_t seed;
+  double prior_mean[ORACLE_MAX_D], prior_sd[ORACLE_MAX_D];
+  /* SEIR constants: population, E0, I0, Euler substeps per day, incidence floor */
+  double npop, e0, i0, lambda_floor;
+  int n_sub;
+} oracle_cfg;
+
+typedef struct {
+  int k, resampled, lk_fallback, pad;
+  double lse, lse2, ess, logz;   /* LSE(log w), LSE(2 log w), ESS = l_k, log Z_k */
+  double est[ORACLE_MAX_D];      /* f~_k = sum_i w~_k^i theta_k^i */
+} oracle_stats;
+
+void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+double oracle_uniform23(uint32_t w);
+void oracle_normals4(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, double z[4]);
+
+double oracle_kalman_loglik(double phi, double sx, double sy, const double* y, int T);
+
+int oracle_fixed_point_bits(int n);
+int oracle_quantise(const double* logw, int n, uint64_t* q);
+int oracle_systematic_from_q(const uint64_t* q, int n, uint32_t U, int32_t* ncopies, int32_t* anc);
+
+double oracle_log_obs(const oracle_cfg* c, const double* theta, const double* x, double y);
+double oracle_pf_loglik(const oracle_cfg* c, const double* theta, const double* y, uint32_t k,
+                        uint32_t i, double* delta_out, int32_t* anc_out);
+
+double oracle_log_prior(const oracle_cfg* c, const double* theta);
+int oracle_lkernel_fit(int D, int N, const double* theta_prev, const double* theta_new,
+                       const double* wn_prev, double* mu, double* sigma, double* A,
+                       double* Lc, double* logdet_c);
+double oracle_gauss_lkernel_logpdf(int D, const double* mu, const double* A, const double* Lc,
+                                   double logdet_c, const double* a, const double* b);
+
+int oracle_smc2_step(const oracle_cfg* c, const double* y, int k, double* theta, double* logprior,
+                     double* loglik, double* logw, oracle_stats* st);
+void oracle_recycle(int K, int D, const oracle_stats* st, double* est_out, double* c_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
