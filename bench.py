@@ -1,0 +1,326 @@
+"""Benchmark of the SMC^2 hot path on one GB300 (or N replicas under torchrun).
+
+One step = one complete SMC^2 run of the workload: K iterations, each scoring
+N parameter samples with an M-particle filter over T observations, plus the
+L-kernel weights, ESS, outer resampling and recycling.  Inputs (observations)
+are resident on the device for `value`; `e2e` repeats the step through the C
+ABI with host buffers (observations copied in, recycled estimate copied out).
+
+Default workload: SEIR-type model, population 1e6, T=100, N=1024, M=512,
+K=20, FP32 particles with FP64 outer arithmetic.  `--impl reference` times
+the CPU oracle on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PF particle-steps/s and SMC² ESS/s vs plain FP64 GPU form; % of roofline"
+UNIT = "particle-steps/s"
+
+# Algorithmic lane operations per particle-step of the particle-filter kernel,
+# counted from the kernel source by category ("Roofline").
+ALG_OPS_PER_PARTICLE_STEP = {
+    0: 122.0,   # linear-Gaussian AR(1)
+    1: 150.0,   # SEIR-type
+}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="seir_t100_n1024")
+    p.add_argument("--no-fp64-form", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (getattr(self, "out", "") or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks() -> dict:
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def alu_peak_ops(sm_count: int, sm_mhz: float) -> float:
+    """Lane-operation issue peak: 4 schedulers x 32 lanes per SM per clock."""
+    return sm_count * 4 * 32 * sm_mhz * 1e6
+
+
+def cpu_baseline(w, seconds: float = 12.0) -> dict:
+    """The oracle particle filter (>= 99.9% of the method's work) on a bounded
+    sample of the workload's filters, all host cores, as it stands."""
+    import numpy as np
+    from oracle import oracle as O
+    from paper_2311_12973_gb300 import inputs as I
+    cores = os.cpu_count() or 1
+    cfg = O.config_from(w)
+    per_chunk = cores * 2
+    th = I.theta_near_prior(w, per_chunk * 64, seed=17, spread=0.3)
+    done, t0, chunk = 0, time.perf_counter(), 0
+    while True:
+        rows = th[(chunk * per_chunk) % len(th):][:per_chunk]
+        O.pf_loglik_many(cfg, rows, w.y, k=1, i0=chunk * per_chunk, threads=cores)
+        done += len(rows)
+        chunk += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return {"value": done * w.M * w.T / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{done} particle filters of the workload (M={w.M}, T={w.T}), FP64 oracle, "
+                      f"{cores} threads, {el:.1f} s"}
+
+
+def run_reference(args, w, rank, world):
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    from paper_2311_12973_gb300 import inputs as I
+    cores = os.cpu_count() or 1
+    cfg = O.config_from(w)
+    per_step = cores * 4
+    th = I.theta_near_prior(w, per_step, seed=17, spread=0.3)
+    for _ in range(args.warmup):
+        O.pf_loglik_many(cfg, th[:cores], w.y, k=1, threads=cores)
+    times = []
+    for s in range(args.steps):
+        t0 = time.perf_counter()
+        O.pf_loglik_many(cfg, th, w.y, k=1 + s, threads=cores)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = per_step * w.M * w.T * args.steps / total
+    sample = f"{per_step} particle filters per step (M={w.M}, T={w.T}), FP64 oracle, {cores} threads"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_config(w, "fp64 oracle"),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def workload_config(w, precision: str) -> dict:
+    return {"workload": w.name, "model": "SEIR-type" if w.model == 1 else "LG-AR(1)", "N": w.N,
+            "M": w.M, "T": w.T, "K": w.K, "precision": precision, "proposal": "random walk",
+            "lkernel": "approx. optimal Gaussian",
+            "l2": "flushed between timed steps (256 MiB write outside the step events)"}
+
+
+def time_runs(S, torch, ctx, w, steps, warmup, flush, rank_sync):
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        ctx.reset(w.seed)
+        ctx.run(w.K, stats=False)
+    torch.cuda.synchronize()
+    ctx.timing(reset=True)
+    ctx.set_timing(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    ess_sums = []
+    rank_sync()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    for s in range(steps):
+        flush.zero_()
+        ev[s][0].record(stream)
+        ctx.reset(w.seed)
+        ctx.run(w.K, stats=False)
+        ev[s][1].record(stream)
+        _, _, ess = ctx.estimate()
+        ess_sums.append(ess)
+    torch.cuda.synchronize()
+    rank_sync()
+    wall = time.perf_counter() - t_wall
+    ctx.set_timing(False)
+    ms = [a.elapsed_time(b) for a, b in ev]
+    pf_ms, pf_n, launches = ctx.timing(reset=True)
+    return ms, ess_sums, pf_ms, pf_n, launches, wall
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    from paper_2311_12973_gb300 import inputs as I
+    w = I.workload(args.workload)
+    if args.impl == "reference":
+        run_reference(args, w, rank, world)
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def rank_sync():
+        if dist is not None:
+            dist.barrier()
+
+    def reduce_max(x: float) -> float:
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    from paper_2311_12973_gb300 import build as B
+    B.build()
+    from paper_2311_12973_gb300 import smc2 as S
+
+    # each rank runs an independent replica (its own seed): weak scaling
+    wr = w.with_(seed=w.seed + 1000 * rank)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    ctx = S.SMC2(S.make_config(wr), wr.y)
+    props = torch.cuda.get_device_properties(local)
+
+    with ClockSampler(local) as clk:
+        ms, ess_sums, pf_ms, pf_n, launches, wall = time_runs(S, torch, ctx, wr, args.steps, args.warmup,
+                                                              flush, rank_sync)
+    clocks = clk.summary()
+    step_ms = reduce_max(sum(ms) / len(ms))
+    units_per_step = wr.N * wr.M * wr.T * wr.K
+    value = units_per_step * world / (step_ms * 1e-3)
+    ess_per_s = statistics.mean(ess_sums) * world / (step_ms * 1e-3)
+
+    # end to end through the C ABI with host buffers
+    import numpy as np
+    y_host = torch.tensor(wr.y, dtype=torch.float64).pin_memory()
+    stream = torch.cuda.current_stream()
+    e2e_ms = []
+    for s in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctx.set_observations(y_host)
+        ctx.reset(wr.seed)
+        ctx.run(wr.K, stats=False)
+        mean, logz, ess = ctx.estimate()
+        b.record(stream)
+        b.synchronize()
+        if s >= args.warmup:
+            e2e_ms.append(a.elapsed_time(b))
+    e2e_step = reduce_max(sum(e2e_ms) / len(e2e_ms))
+    d2h = 8 * wr.D + 112 + 8 + 4
+
+    # plain FP64 GPU form of the same workload
+    fp64 = None
+    if not args.no_fp64_form:
+        w64 = wr.with_(precision=I.PREC_FP64)
+        ctx64 = S.SMC2(S.make_config(w64), w64.y)
+        ms64, ess64, _, _, _, _ = time_runs(S, torch, ctx64, w64, max(2, args.steps // 3), 1, flush,
+                                            rank_sync)
+        st64 = reduce_max(sum(ms64) / len(ms64))
+        fp64 = {"value": units_per_step * world / (st64 * 1e-3), "unit": UNIT,
+                "ess_per_s": statistics.mean(ess64) * world / (st64 * 1e-3), "ms_per_step": st64}
+        ctx64.close()
+
+    if rank != 0:
+        return
+    peaks = measured_peaks()
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    pf_avg_ms = pf_ms / max(pf_n, 1)
+    ops = ALG_OPS_PER_PARTICLE_STEP[wr.model] * wr.N * wr.M * wr.T
+    achieved = ops / (pf_avg_ms * 1e-3)
+    peak = alu_peak_ops(props.multi_processor_count, sm_mhz)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 particles, f64 outer", "data": "synthetic",
+        "config": workload_config(wr, "mixed"),
+        "ess_per_s": ess_per_s,
+        "fp64_form": fp64,
+        "speedup_vs_fp64_form": (value / fp64["value"]) if fp64 else None,
+        "ess_speedup_vs_fp64_form": (ess_per_s / fp64["ess_per_s"]) if fp64 else None,
+        "roofline": {"kernel": "pf_kernel<float,SEIR>", "bound": "alu", "achieved": achieved / 1e9,
+                     "peak": peak / 1e9, "unit": "Gop/s", "frac": achieved / peak, "traffic": None,
+                     "ops_per_particle_step": ALG_OPS_PER_PARTICLE_STEP[wr.model],
+                     "pf_ms_per_launch": pf_avg_ms, "pf_launches": pf_n,
+                     "pf_share_of_step": pf_ms / max(sum(ms), 1e-9),
+                     "peak_basis": f"{props.multi_processor_count} SMs x 128 lanes x {sm_mhz:.0f} MHz "
+                                   "(max SM clock of MEASURED_PEAKS.json)"},
+        "e2e": {"value": units_per_step * world / (e2e_step * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": 8 * wr.T, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_step},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "wall_s": wall,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(wr)
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,233 @@
+/*
+ * smc2.h -- C ABI of the GB300 SMC^2 library (libsmc2.so).
+ *
+ * The library runs the data-parallel hot path of SMC^2 (Rosato, Varsi,
+ * Murphy, Maskell, "An O(log2 N) SMC^2 algorithm on distributed memory with
+ * an approx. optimal L-kernel"): N parameter samples theta, each scored by a
+ * bootstrap particle filter (Sec. II) of M particles over T observations,
+ * importance-weighted with an L-kernel (Sec. IV-A, IV-D), resampled with
+ * systematic resampling (Sec. IV-B) and recycled across iterations
+ * (Sec. IV-C).  Every step runs in the library's own CUDA kernels on one
+ * GPU (sm_103a); the host side only validates arguments, owns a small device
+ * workspace and enqueues work.
+ *
+ * General conventions
+ *  - Every call returns an smc2_status; no exception or signal crosses the
+ *    ABI.  SMC2_EINVAL is returned before any GPU work is enqueued.
+ *  - Pointers marked "device" must be device (or managed) memory of the
+ *    current CUDA device; "host" pointers are plain host memory (pinned or
+ *    pageable).  "host or device" pointers may be either (unified addressing).
+ *  - All GPU work of a context is enqueued on the CUDA stream given to
+ *    smc2_init (NULL = the legacy default stream) and is asynchronous unless
+ *    the call says it synchronises.  Caller buffers must stay valid until the
+ *    work that uses them has completed on that stream.
+ *  - Device-side errors (a non-finite outer weight set, an exhausted bounded
+ *    wait, an index out of range) are recorded in a device status word and
+ *    reported by the next synchronising call; the first error is sticky until
+ *    smc2_destroy or smc2_reset.
+ *  - Parameters theta are in unconstrained coordinates:
+ *      SMC2_MODEL_LG_AR1: (phi, log sigma_x, log sigma_y), D = 3;
+ *      SMC2_MODEL_SEIR:   (log beta0, log sigma_rw, log kappa, log gamma), D = 4.
+ *    Device theta arrays are structure-of-arrays, theta[d * ld + i].
+ *  - Random numbers come from Philox4x32-10 (Salmon et al., SC'11) keyed by
+ *    the seed, with counters (c0, c1, i | dataset << 20, tag | k << 4), so a
+ *    run is a deterministic function of its configuration and seed.
+ */
+#ifndef SMC2_H
+#define SMC2_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SMC2_OK = 0,
+  SMC2_EINVAL = 1,     /* invalid argument or configuration */
+  SMC2_ENOMEM = 2,     /* device or host allocation failed */
+  SMC2_ECUDA = 3,      /* a CUDA runtime call failed */
+  SMC2_ENONFINITE = 4, /* every outer importance weight is zero or NaN */
+  SMC2_ECHOL = 5,      /* reserved: L-kernel factorisation failures fall back, see smc2_iter_stats */
+  SMC2_ETIMEOUT = 6,   /* a bounded device-side wait gave up */
+  SMC2_EBOUNDS = 7,    /* a device-side index check failed */
+  SMC2_ESTATE = 8      /* call not valid in the context's current state */
+} smc2_status;
+
+enum { SMC2_MODEL_LG_AR1 = 0, SMC2_MODEL_SEIR = 1 };
+enum { SMC2_PREC_FP64 = 0, SMC2_PREC_MIXED = 1 };   /* MIXED: FP32 particles, FP64 outer */
+enum { SMC2_PROP_RW = 0, SMC2_PROP_MLP = 1 };
+enum { SMC2_LK_FORWARD = 0, SMC2_LK_GAUSS_OPT = 1 };
+
+#define SMC2_MAX_D 8
+#define SMC2_MAX_M 4096
+#define SMC2_MAX_N 16384
+#define SMC2_MAX_DATASETS 4096
+
+typedef struct smc2_ctx smc2_ctx; /* opaque; owns its device workspace */
+
+/* Sampler configuration (host memory, read during smc2_init only).
+ * model, precision, proposal, lkernel: the enums above.
+ * D: dimension of theta (3 for LG_AR1, 4 for SEIR).
+ * N, M, T: theta samples, particles per filter, observations; used when
+ *   n_datasets <= 1, otherwise taken per dataset from ds_N, ds_M, ds_T.
+ * K: iterations the context will run (sizes the statistics history).
+ * rw_scale: standard deviation of the Gaussian random-walk proposal in every
+ *   unconstrained coordinate (Sec. IV-A, Eq. 19: Sigma = rw_scale^2 I).
+ * ess_frac: outer resampling when ESS < ess_frac * N (Sec. IV-B uses 1/2).
+ * seed: key of the random stream.
+ * prior_mean, prior_sd: independent Gaussian prior (= q_1 of Eq. 16) in the
+ *   unconstrained coordinates, first D entries used.
+ * npop, e0, i0, n_sub, lambda_floor: SEIR constants (population, initial
+ *   exposed and infectious, Euler substeps per day, floor of the Poisson mean).
+ * ppt: particles per thread of the particle-filter kernel (0 = pick by the
+ *   built-in tuner; otherwise 1, 2, 4 or 8).
+ * n_datasets: number of independent datasets run together (<= 1: one).
+ * ds_N, ds_M, ds_T: host arrays of n_datasets sizes (NULL when n_datasets <= 1). */
+typedef struct {
+  int model, precision, proposal, lkernel;
+  int D, N, M, T, K;
+  double rw_scale, ess_frac;
+  uint64_t seed;
+  double prior_mean[SMC2_MAX_D], prior_sd[SMC2_MAX_D];
+  double npop, e0, i0, lambda_floor;
+  int n_sub;
+  int ppt;
+  int n_datasets;
+  const int* ds_N;
+  const int* ds_M;
+  const int* ds_T;
+} smc2_config;
+
+/* Statistics of one iteration k of one dataset (Sec. IV-A, IV-B):
+ * ess = N_eff of Eq. (25) = l_k of Eq. (24); lse = log sum_i w_k^i;
+ * lse2 = log sum_i (w_k^i)^2; logz = lse - log N, the evidence estimate;
+ * est = f~_k of Eq. (21) with f(theta) = theta (before resampling);
+ * resampled = 1 when ESS < ess_frac N; lk_fallback = 1 when the Gaussian
+ * L-kernel was numerically singular and the forward kernel (Eq. 30) was used. */
+typedef struct {
+  int k, resampled, lk_fallback, dataset;
+  double ess, lse, lse2, logz;
+  double est[SMC2_MAX_D];
+} smc2_iter_stats;
+
+/* Create a context: validate cfg, allocate the device workspace, copy the
+ * observations y (host or device, the concatenation over datasets of T_d
+ * doubles; SEIR counts are non-negative integers stored as doubles) and
+ * precompute the per-step observation terms on the device.  stream is a
+ * cudaStream_t (NULL: legacy default stream).  Synchronises the stream.
+ * Errors: EINVAL (bad configuration; *out untouched), ENOMEM, ECUDA. */
+smc2_status smc2_init(const smc2_config* cfg, const double* y, void* stream, smc2_ctx** out);
+
+/* Replace the observations of every dataset (same layout as smc2_init; host
+ * or device) and recompute the observation terms.  Asynchronous on the
+ * context stream: a host y must stay valid until the stream reaches it. */
+smc2_status smc2_set_observations(smc2_ctx* ctx, const double* y);
+
+/* Rewind the sampler to k = 0 with a new seed and clear the sticky error
+ * and the statistics history.  Asynchronous. */
+smc2_status smc2_reset(smc2_ctx* ctx, uint64_t seed);
+
+/* Bootstrap particle filter log-likelihood estimates (Sec. II, Eq. 8):
+ * loglik[i] = log p^(y_{1:T} | theta_i) for i < n, with theta_dev device SoA
+ * [D][n], loglik_dev device [n], the random stream of filter i at iteration
+ * `iteration` of dataset `dataset` (uses that dataset's M, T and y).  Every
+ * step propagates with the state equation (Eq. 1), weights with the
+ * observation density (Eq. 2, bootstrap form of Eq. 5), adds
+ * log((1/M) sum w_t) and resamples systematically (Eqs. 26-27, Algorithm 1)
+ * after every step t < T.  A filter whose weights all vanish returns -inf.
+ * Asynchronous.  Errors: EINVAL (n < 1 or n > SMC2_MAX_N, bad dataset). */
+smc2_status smc2_pf_loglik(smc2_ctx* ctx, const double* theta_dev, int n, int iteration,
+                           int dataset, double* loglik_dev);
+
+/* As smc2_pf_loglik, and also writes the per-step increments
+ * delta_dev[i * T + t] = log p^(y_{1:t+1}) - log p^(y_{1:t}) and the
+ * ancestors anc_dev[(i * (T-1) + t) * M + j] of slot j after step t+1
+ * (either may be NULL).  Diagnostic path for checking the filter. */
+smc2_status smc2_pf_trace(smc2_ctx* ctx, const double* theta_dev, int n, int iteration,
+                          int dataset, double* loglik_dev, double* delta_dev, int32_t* anc_dev);
+
+/* One SMC^2 iteration of every dataset (Sec. IV):
+ *  k = 1: draw theta ~ q_1 = prior (Eq. 16), weight w = pi / q_1 (Eq. 17);
+ *  k > 1: propose theta_k ~ N(theta_{k-1}, rw_scale^2 I) (Eqs. 18-19),
+ *         fit the L-kernel (Eqs. 32-35) and weight by Eq. (20);
+ * then normalise (Eq. 22), estimate (Eq. 21), ESS and l_k (Eqs. 24-25),
+ * evidence, and when ESS < ess_frac N resample (Eqs. 26-27), redistribute
+ * (Algorithm 1's output order) and reset the weights (Sec. IV-B).
+ * stats_host (host, n_datasets entries, may be NULL): if given, the call
+ * synchronises and fills it.  Errors: ESTATE (K iterations already run),
+ * ENONFINITE (reported when synchronising). */
+smc2_status smc2_iterate(smc2_ctx* ctx, smc2_iter_stats* stats_host);
+
+/* n_iter iterations back to back without host synchronisation (captured
+ * once as a CUDA graph and replayed).  stats_host (may be NULL) receives
+ * n_iter * n_datasets entries, iteration-major, and makes the call
+ * synchronise.  Errors: ESTATE when fewer than n_iter iterations remain. */
+smc2_status smc2_run(smc2_ctx* ctx, int n_iter, smc2_iter_stats* stats_host);
+
+/* Recycled estimate after the iterations run so far (Sec. IV-C, Eq. 29 with
+ * the constants of Eqs. 23-24): mean_host[D] = sum_k c_k f~_k; the latest
+ * evidence estimate log Z_k; ess_sum = sum_k l_k, the ESS of the recycled
+ * estimator.  Any output pointer may be NULL.  Synchronises; returns the
+ * sticky device status. */
+smc2_status smc2_estimate(smc2_ctx* ctx, int dataset, double* mean_host,
+                          double* log_evidence_host, double* ess_sum_host);
+
+/* Copy the statistics of iterations 1..k of a dataset to host (k entries;
+ * *k_out receives k).  Synchronises. */
+smc2_status smc2_get_history(smc2_ctx* ctx, int dataset, smc2_iter_stats* hist_host, int cap,
+                             int* k_out);
+
+/* Checkpoint / resume of a dataset's population after iteration k: theta
+ * (host, row-major [N][D]), log prior, PF log-likelihood estimate and
+ * unnormalised log weight (host, N each).  get synchronises; set is
+ * asynchronous and, for dataset 0, sets the context's iteration counter
+ * to k (all datasets share it).  The recycling accumulators and history are
+ * part of the state through smc2_get_history / smc2_set_history. */
+smc2_status smc2_get_state(smc2_ctx* ctx, int dataset, int* k_out, double* theta_host,
+                           double* logprior_host, double* loglik_host, double* logw_host);
+smc2_status smc2_set_state(smc2_ctx* ctx, int dataset, int k, const double* theta_host,
+                           const double* logprior_host, const double* loglik_host,
+                           const double* logw_host);
+smc2_status smc2_set_history(smc2_ctx* ctx, int dataset, const smc2_iter_stats* hist_host, int k);
+
+/* Systematic resampling primitive (Sec. IV-B, Eqs. 26-27 and Algorithm 1's
+ * output order) on quantised weights: q_dev (device, n unsigned 64-bit
+ * integers with sum S, 0 < S < 2^64), U a 32-bit random word, u = (2U+1)/2^33.
+ * anc_dev (device, n) receives a_j = min{i : C_i > floor((j + u) S / n)},
+ * C the inclusive prefix sum of q.  Exact integer arithmetic.  Enqueued on
+ * `stream`.  Errors: EINVAL (n < 1 or n > SMC2_MAX_N). */
+smc2_status smc2_resample_systematic(const uint64_t* q_dev, int n, uint32_t U, int32_t* anc_dev,
+                                     void* stream);
+
+/* The library's random stream, for checking: for each of n counters
+ * ctr_dev[4r .. 4r+3] (device), words_dev[4r..] (device, may be NULL)
+ * receive Philox4x32-10 of (counter, seed) and z_dev[4r..] (device, may be
+ * NULL) the four Box-Muller normals made from them, in double (precision
+ * SMC2_PREC_FP64) or float arithmetic widened to double (SMC2_PREC_MIXED). */
+smc2_status smc2_philox_normals(uint64_t seed, const uint32_t* ctr_dev, int n, int precision,
+                                uint32_t* words_dev, double* z_dev, void* stream);
+
+/* Wait for the context stream and return the sticky device status. */
+smc2_status smc2_sync(smc2_ctx* ctx);
+
+/* Device timing of the particle-filter kernel: when enabled, CUDA events
+ * bracket every particle-filter launch on the context stream; smc2_get_timing
+ * synchronises and returns the summed milliseconds and launch count since
+ * the last reset of the counters, plus the number of kernels this context
+ * has launched (graph replays count their kernel nodes). */
+smc2_status smc2_set_timing(smc2_ctx* ctx, int enable);
+smc2_status smc2_get_timing(smc2_ctx* ctx, double* pf_ms, int64_t* pf_launches,
+                            int64_t* kernel_launches, int reset);
+
+/* Release the context and its device workspace (synchronises its stream). */
+void smc2_destroy(smc2_ctx* ctx);
+
+/* Human-readable name of a status code (static storage). */
+const char* smc2_status_string(smc2_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SMC2_H */

@@ -1,0 +1,649 @@
+// api.cu -- the C ABI declared in include/smc2.h.
+//
+// Host responsibilities only: validate, own one device arena per context,
+// build the particle-filter work list, enqueue kernels on the context stream
+// and capture iterations into CUDA graphs.  No step of the sampler runs here.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+using namespace smc2;
+
+namespace {
+
+struct GraphKey {
+  int n_iter, timing;
+  bool operator<(const GraphKey& o) const {
+    return n_iter != o.n_iter ? n_iter < o.n_iter : timing < o.timing;
+  }
+};
+
+struct TimedGraph {
+  cudaGraphExec_t exec = nullptr;
+  std::vector<cudaEvent_t> ev;  // pairs around each PF launch
+};
+
+}  // namespace
+
+struct smc2_ctx {
+  smc2_config cfg{};
+  int n_ds = 1, D = 0, K = 0, precision = 0, model = 0;
+  std::vector<int> N, M, T, nblk;
+  std::vector<size_t> yoff;
+  size_t ytot = 0;
+  int max_N = 0, max_nblk = 0;
+  cudaStream_t stream = nullptr, cap_stream = nullptr;
+  int device = 0, sms = 0;
+  char* arena = nullptr;
+  size_t arena_bytes = 0;
+  double* d_y = nullptr;
+  std::vector<void*> d_obs;
+  std::vector<DSDev> h_ds;
+  DSDev* d_ds = nullptr;
+  PFJob* d_jobs = nullptr;
+  int4* d_wus = nullptr;
+  int n_wus = 0;
+  int* d_wu_counter = nullptr;
+  int* d_k = nullptr;
+  int* d_status = nullptr;
+  unsigned* d_grid_ticket = nullptr;
+  int ppt = 4, pf_block = 256, pf_grid = 1;
+  size_t pf_smem = 0;
+  int k_host = 0;
+  std::map<GraphKey, TimedGraph> graphs;
+  bool timing = false;
+  double pf_ms = 0.0;
+  int64_t pf_launches = 0, kernel_launches = 0;
+  OuterParams op{};
+  PFLaunch pl{};
+};
+
+namespace {
+
+smc2_status map_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return SMC2_OK;
+  if (e == cudaErrorMemoryAllocation) return SMC2_ENOMEM;
+  return SMC2_ECUDA;
+}
+
+#define SMC2_TRY(expr)                                      \
+  do {                                                      \
+    cudaError_t _e = (expr);                                \
+    if (_e != cudaSuccess) return map_cuda(_e);             \
+  } while (0)
+
+smc2_status status_from_bits(int bits) {
+  if (bits & ST_NONFINITE) return SMC2_ENONFINITE;
+  if (bits & ST_TIMEOUT) return SMC2_ETIMEOUT;
+  if (bits & ST_BOUNDS) return SMC2_EBOUNDS;
+  return SMC2_OK;
+}
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+smc2_status validate(const smc2_config* c) {
+  if (!c) return SMC2_EINVAL;
+  if (c->model != SMC2_MODEL_LG_AR1 && c->model != SMC2_MODEL_SEIR) return SMC2_EINVAL;
+  if (c->precision != SMC2_PREC_FP64 && c->precision != SMC2_PREC_MIXED) return SMC2_EINVAL;
+  if (c->proposal != SMC2_PROP_RW) return SMC2_EINVAL;
+  if (c->lkernel != SMC2_LK_FORWARD && c->lkernel != SMC2_LK_GAUSS_OPT) return SMC2_EINVAL;
+  if (c->D != (c->model == SMC2_MODEL_LG_AR1 ? 3 : 4)) return SMC2_EINVAL;
+  if (c->K < 1 || c->K > (1 << 27)) return SMC2_EINVAL;
+  if (!finite_pos(c->rw_scale) || !std::isfinite(c->ess_frac) || c->ess_frac < 0.0) return SMC2_EINVAL;
+  for (int d = 0; d < c->D; ++d)
+    if (!std::isfinite(c->prior_mean[d]) || !finite_pos(c->prior_sd[d])) return SMC2_EINVAL;
+  if (c->model == SMC2_MODEL_SEIR) {
+    if (!finite_pos(c->npop) || !std::isfinite(c->e0) || !std::isfinite(c->i0) || c->e0 < 0 ||
+        c->i0 < 0 || c->e0 + c->i0 > c->npop || c->n_sub < 1 || c->n_sub > 64 ||
+        !finite_pos(c->lambda_floor))
+      return SMC2_EINVAL;
+  }
+  if (c->ppt != 0 && c->ppt != 1 && c->ppt != 2 && c->ppt != 4 && c->ppt != 8) return SMC2_EINVAL;
+  const int nd = c->n_datasets <= 1 ? 1 : c->n_datasets;
+  if (nd > SMC2_MAX_DATASETS) return SMC2_EINVAL;
+  if (c->n_datasets > 1 && (!c->ds_N || !c->ds_M || !c->ds_T)) return SMC2_EINVAL;
+  for (int d = 0; d < nd; ++d) {
+    const int n = c->n_datasets > 1 ? c->ds_N[d] : c->N;
+    const int m = c->n_datasets > 1 ? c->ds_M[d] : c->M;
+    const int t = c->n_datasets > 1 ? c->ds_T[d] : c->T;
+    if (n < 1 || n > SMC2_MAX_N || m < 1 || m > SMC2_MAX_M || t < 1 || t > (1 << 24))
+      return SMC2_EINVAL;
+  }
+  return SMC2_OK;
+}
+
+int default_ppt(const smc2_ctx* c) {
+  if (c->cfg.ppt) return c->cfg.ppt;
+  int mx = 0;
+  for (int m : c->M) mx = std::max(mx, m);
+  // four particles per thread keeps a 1024-particle filter in one 256-thread CTA
+  int ppt = 4;
+  while (pf_group_threads(ppt, mx) > 1024 && ppt < 8) ppt *= 2;
+  return ppt;
+}
+
+template <typename Tp>
+Tp* carve(char*& p, size_t count) {
+  p = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(p) + 255) & ~uintptr_t(255));
+  Tp* r = reinterpret_cast<Tp*>(p);
+  p += count * sizeof(Tp);
+  return r;
+}
+
+size_t obs_bytes(const smc2_ctx* c, int d) {
+  return (size_t)c->T[d] * 4 * (c->precision == SMC2_PREC_FP64 ? 8 : 4);
+}
+
+// Lay out (or size, when base == nullptr) the arena.
+size_t layout(smc2_ctx* c, char* base) {
+  char* p = base ? base : reinterpret_cast<char*>(uintptr_t(256));
+  char* start = p;
+  const int D = c->D;
+  c->d_y = carve<double>(p, c->ytot);
+  c->d_k = carve<int>(p, 4);
+  c->d_status = carve<int>(p, 4);
+  c->d_grid_ticket = carve<unsigned>(p, 4);
+  c->d_wu_counter = carve<int>(p, 4);
+  c->d_obs.assign(c->n_ds, nullptr);
+  c->h_ds.assign(c->n_ds, DSDev{});
+  for (int d = 0; d < c->n_ds; ++d) {
+    DSDev& s = c->h_ds[d];
+    const int N = c->N[d];
+    s.N = N;
+    s.M = c->M[d];
+    s.T = c->T[d];
+    s.nblk = c->nblk[d];
+    s.thA = carve<double>(p, (size_t)D * N);
+    s.thB = carve<double>(p, (size_t)D * N);
+    s.lpA = carve<double>(p, N);
+    s.lpB = carve<double>(p, N);
+    s.llA = carve<double>(p, N);
+    s.llB = carve<double>(p, N);
+    s.logw = carve<double>(p, N);
+    s.logq = carve<double>(p, N);
+    s.q = carve<uint64_t>(p, N);
+    s.part = carve<double>(p, (size_t)s.nblk * kPartStride);
+    s.part_st = carve<double>(p, (size_t)s.nblk * kStatStride);
+    s.tickets = carve<unsigned>(p, 4);
+    s.lk = carve<LKParams>(p, 1);
+    s.cur = carve<IterCur>(p, 1);
+    s.hist = carve<smc2_iter_stats>(p, c->K);
+    s.rec = carve<double>(p, 1 + D);
+    s.est_rec = carve<double>(p, D);
+    c->d_obs[d] = carve<char>(p, obs_bytes(c, d));
+    s.obs = c->d_obs[d];
+    s.c2hi = (uint32_t)d << 20;
+  }
+  c->d_ds = carve<DSDev>(p, c->n_ds);
+  c->d_jobs = carve<PFJob>(p, c->n_ds);
+  c->d_wus = carve<int4>(p, std::max(c->n_wus, 1));
+  return (size_t)(p - start) + 256;
+}
+
+void build_work_units(smc2_ctx* c, std::vector<int4>& wus) {
+  wus.clear();
+  for (int d = 0; d < c->n_ds; ++d) {
+    const int gt = pf_group_threads(c->ppt, c->M[d]);
+    const int fpc = std::max(1, c->pf_block / gt);
+    for (int f = 0; f < c->N[d]; f += fpc) wus.push_back(make_int4(d, f, std::min(fpc, c->N[d] - f), 0));
+  }
+  // longest processing time first: cost ~ T * M * filters
+  std::stable_sort(wus.begin(), wus.end(), [&](const int4& a, const int4& b) {
+    const double ca = (double)c->T[a.x] * c->M[a.x] * a.z, cb = (double)c->T[b.x] * c->M[b.x] * b.z;
+    return ca > cb;
+  });
+}
+
+smc2_status clear_run_state(smc2_ctx* c) {
+  cudaStream_t s = c->stream;
+  SMC2_TRY(cudaMemsetAsync(c->d_k, 0, 4 * sizeof(int), s));
+  SMC2_TRY(cudaMemsetAsync(c->d_status, 0, 4 * sizeof(int), s));
+  SMC2_TRY(cudaMemsetAsync(c->d_grid_ticket, 0, 4 * sizeof(unsigned), s));
+  for (int d = 0; d < c->n_ds; ++d) {
+    const DSDev& ds = c->h_ds[d];
+    SMC2_TRY(cudaMemsetAsync(ds.tickets, 0, 4 * sizeof(unsigned), s));
+    SMC2_TRY(cudaMemsetAsync(ds.hist, 0, (size_t)c->K * sizeof(smc2_iter_stats), s));
+    SMC2_TRY(cudaMemsetAsync(ds.rec, 0, (size_t)(1 + c->D) * sizeof(double), s));
+    SMC2_TRY(cudaMemsetAsync(ds.est_rec, 0, (size_t)c->D * sizeof(double), s));
+    SMC2_TRY(cudaMemsetAsync(ds.cur, 0, sizeof(IterCur), s));
+    SMC2_TRY(cudaMemsetAsync(ds.lk, 0, sizeof(LKParams), s));
+  }
+  c->k_host = 0;
+  return SMC2_OK;
+}
+
+smc2_status compute_obs(smc2_ctx* c, cudaStream_t s) {
+  for (int d = 0; d < c->n_ds; ++d) {
+    SMC2_TRY(outer_obs_terms(c->precision, c->model, c->d_y + c->yoff[d], c->T[d], c->d_obs[d], s));
+    c->kernel_launches++;
+  }
+  return SMC2_OK;
+}
+
+void fill_params(smc2_ctx* c) {
+  OuterParams& P = c->op;
+  P.ds = c->d_ds;
+  P.n_ds = c->n_ds;
+  P.D = c->D;
+  P.lkernel = c->cfg.lkernel == SMC2_LK_GAUSS_OPT ? LK_GAUSS : LK_FORWARD;
+  P.K = c->K;
+  P.rw_scale = c->cfg.rw_scale;
+  P.ess_frac = c->cfg.ess_frac;
+  for (int d = 0; d < 8; ++d) {
+    P.prior_mean[d] = c->cfg.prior_mean[d];
+    P.prior_sd[d] = c->cfg.prior_sd[d];
+  }
+  P.seed = c->cfg.seed;
+  P.k_done = c->d_k;
+  P.status = c->d_status;
+  P.grid_ticket = c->d_grid_ticket;
+
+  PFLaunch& L = c->pl;
+  L.jobs = c->d_jobs;
+  L.wus = c->d_wus;
+  L.n_wu = c->n_wus;
+  L.fpc_single = 0;
+  L.wu_counter = c->d_wu_counter;
+  L.seed = c->cfg.seed;
+  L.k_done = c->d_k;
+  L.k_imm = 0;
+  L.status = c->d_status;
+  L.mdl.npop = c->cfg.npop;
+  L.mdl.e0 = c->cfg.e0;
+  L.mdl.i0 = c->cfg.i0;
+  L.mdl.lambda_floor = c->cfg.lambda_floor;
+  L.mdl.n_sub = c->cfg.n_sub;
+}
+
+// One iteration of every dataset, enqueued on s.
+smc2_status enqueue_iteration(smc2_ctx* c, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1) {
+  SMC2_TRY(outer_propose(c->op, c->max_nblk, s));
+  SMC2_TRY(cudaMemsetAsync(c->d_wu_counter, 0, sizeof(int), s));
+  if (ev0) SMC2_TRY(cudaEventRecord(ev0, s));
+  SMC2_TRY(pf_launch(c->precision, c->model, c->ppt, c->pf_grid, c->pf_block, c->pf_smem, c->pl, s));
+  if (ev1) SMC2_TRY(cudaEventRecord(ev1, s));
+  SMC2_TRY(outer_weights(c->op, c->max_nblk, s));
+  SMC2_TRY(outer_quantise(c->op, c->max_nblk, s));
+  SMC2_TRY(outer_resample(c->op, c->max_nblk, c->max_N, s));
+  return SMC2_OK;
+}
+
+constexpr int kLaunchesPerIter = 5;
+
+smc2_status get_graph(smc2_ctx* c, int n_iter, TimedGraph** out) {
+  const GraphKey key{n_iter, c->timing ? 1 : 0};
+  auto it = c->graphs.find(key);
+  if (it != c->graphs.end()) {
+    *out = &it->second;
+    return SMC2_OK;
+  }
+  TimedGraph g;
+  if (c->timing) {
+    g.ev.resize(2 * (size_t)n_iter);
+    for (auto& e : g.ev) SMC2_TRY(cudaEventCreate(&e));
+  }
+  SMC2_TRY(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+  smc2_status st = SMC2_OK;
+  for (int it2 = 0; it2 < n_iter && st == SMC2_OK; ++it2)
+    st = enqueue_iteration(c, c->cap_stream, c->timing ? g.ev[2 * it2] : nullptr,
+                           c->timing ? g.ev[2 * it2 + 1] : nullptr);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
+  if (st != SMC2_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  SMC2_TRY(e);
+  e = cudaGraphInstantiate(&g.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  SMC2_TRY(e);
+  auto ins = c->graphs.emplace(key, std::move(g));
+  *out = &ins.first->second;
+  return SMC2_OK;
+}
+
+void drop_graphs(smc2_ctx* c) {
+  for (auto& kv : c->graphs) {
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    for (auto e : kv.second.ev) cudaEventDestroy(e);
+  }
+  c->graphs.clear();
+}
+
+smc2_status sticky(smc2_ctx* c) {
+  int bits = 0;
+  SMC2_TRY(cudaMemcpyAsync(&bits, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  SMC2_TRY(cudaStreamSynchronize(c->stream));
+  return status_from_bits(bits);
+}
+
+bool bad_ds(const smc2_ctx* c, int d) { return !c || d < 0 || d >= c->n_ds; }
+
+}  // namespace
+
+extern "C" {
+
+const char* smc2_status_string(smc2_status s) {
+  switch (s) {
+    case SMC2_OK: return "ok";
+    case SMC2_EINVAL: return "invalid argument";
+    case SMC2_ENOMEM: return "out of memory";
+    case SMC2_ECUDA: return "CUDA runtime error";
+    case SMC2_ENONFINITE: return "every importance weight is zero or not finite";
+    case SMC2_ECHOL: return "covariance factorisation failed";
+    case SMC2_ETIMEOUT: return "bounded device wait expired";
+    case SMC2_EBOUNDS: return "device index out of range";
+    case SMC2_ESTATE: return "call not valid in the current state";
+  }
+  return "unknown status";
+}
+
+smc2_status smc2_init(const smc2_config* cfg, const double* y, void* stream, smc2_ctx** out) {
+  if (!out || !y) return SMC2_EINVAL;
+  smc2_status st = validate(cfg);
+  if (st != SMC2_OK) return st;
+  smc2_ctx* c = new (std::nothrow) smc2_ctx();
+  if (!c) return SMC2_ENOMEM;
+  c->cfg = *cfg;
+  c->n_ds = cfg->n_datasets <= 1 ? 1 : cfg->n_datasets;
+  c->D = cfg->D;
+  c->K = cfg->K;
+  c->precision = cfg->precision;
+  c->model = cfg->model == SMC2_MODEL_LG_AR1 ? MODEL_LG : MODEL_SEIR;
+  for (int d = 0; d < c->n_ds; ++d) {
+    c->N.push_back(cfg->n_datasets > 1 ? cfg->ds_N[d] : cfg->N);
+    c->M.push_back(cfg->n_datasets > 1 ? cfg->ds_M[d] : cfg->M);
+    c->T.push_back(cfg->n_datasets > 1 ? cfg->ds_T[d] : cfg->T);
+    c->nblk.push_back((c->N[d] + kOuterBlock - 1) / kOuterBlock);
+    c->yoff.push_back(c->ytot);
+    c->ytot += c->T[d];
+    c->max_N = std::max(c->max_N, c->N[d]);
+    c->max_nblk = std::max(c->max_nblk, c->nblk[d]);
+  }
+  c->cfg.ds_N = c->cfg.ds_M = c->cfg.ds_T = nullptr;
+  c->stream = static_cast<cudaStream_t>(stream);
+  auto fail = [&](smc2_status s) {
+    smc2_destroy(c);
+    return s;
+  };
+  if (cudaGetDevice(&c->device) != cudaSuccess) return fail(SMC2_ECUDA);
+  if (cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess)
+    return fail(SMC2_ECUDA);
+  if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return fail(SMC2_ECUDA);
+
+  // particle-filter launch shape
+  c->ppt = default_ppt(c);
+  int max_gt = 32;
+  for (int m : c->M) max_gt = std::max(max_gt, pf_group_threads(c->ppt, m));
+  if (max_gt > 1024) return fail(SMC2_EINVAL);
+  c->pf_block = std::max(256, max_gt);
+  size_t smem = 0;
+  for (int m : c->M) smem = std::max(smem, pf_smem_bytes(c->precision, c->model, c->ppt, c->pf_block, m));
+  c->pf_smem = smem;
+  if (pf_configure(c->precision, c->model, c->ppt, smem) != cudaSuccess) return fail(SMC2_EINVAL);
+  std::vector<int4> wus;
+  build_work_units(c, wus);
+  c->n_wus = (int)wus.size();
+  const int occ = std::max(1, pf_occupancy(c->precision, c->model, c->ppt, c->pf_block, smem));
+  c->pf_grid = std::min(c->n_wus, occ * c->sms);
+
+  c->arena_bytes = layout(c, nullptr);
+  if (cudaMalloc(&c->arena, c->arena_bytes) != cudaSuccess) return fail(SMC2_ENOMEM);
+  layout(c, c->arena);
+
+  std::vector<PFJob> jobs(c->n_ds);
+  for (int d = 0; d < c->n_ds; ++d) {
+    PFJob& j = jobs[d];
+    j.theta = c->h_ds[d].thB;
+    j.ld = c->N[d];
+    j.n = c->N[d];
+    j.M = c->M[d];
+    j.T = c->T[d];
+    j.loglik = c->h_ds[d].llB;
+    j.delta = nullptr;
+    j.anc = nullptr;
+    j.obs = c->d_obs[d];
+    j.c2hi = c->h_ds[d].c2hi;
+  }
+  cudaStream_t s = c->stream;
+  if (cudaMemcpyAsync(c->d_y, y, c->ytot * sizeof(double), cudaMemcpyDefault, s) != cudaSuccess ||
+      cudaMemcpyAsync(c->d_ds, c->h_ds.data(), c->n_ds * sizeof(DSDev), cudaMemcpyHostToDevice, s) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(c->d_jobs, jobs.data(), c->n_ds * sizeof(PFJob), cudaMemcpyHostToDevice, s) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(c->d_wus, wus.data(), wus.size() * sizeof(int4), cudaMemcpyHostToDevice, s) !=
+          cudaSuccess)
+    return fail(SMC2_ECUDA);
+  if ((st = clear_run_state(c)) != SMC2_OK) return fail(st);
+  if ((st = compute_obs(c, s)) != SMC2_OK) return fail(st);
+  fill_params(c);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return fail(SMC2_ECUDA);
+  *out = c;
+  return SMC2_OK;
+}
+
+smc2_status smc2_set_observations(smc2_ctx* c, const double* y) {
+  if (!c || !y) return SMC2_EINVAL;
+  SMC2_TRY(cudaMemcpyAsync(c->d_y, y, c->ytot * sizeof(double), cudaMemcpyDefault, c->stream));
+  return compute_obs(c, c->stream);
+}
+
+smc2_status smc2_reset(smc2_ctx* c, uint64_t seed) {
+  if (!c) return SMC2_EINVAL;
+  if (seed != c->cfg.seed) {
+    drop_graphs(c);
+    c->cfg.seed = seed;
+    fill_params(c);
+  }
+  return clear_run_state(c);
+}
+
+static smc2_status pf_standalone(smc2_ctx* c, const double* theta, int n, int iteration, int dataset,
+                                 double* loglik, double* delta, int32_t* anc) {
+  if (!c || !theta || !loglik || n < 1 || n > SMC2_MAX_N || bad_ds(c, dataset) || iteration < 0 ||
+      iteration >= (1 << 28))
+    return SMC2_EINVAL;
+  PFJob job{};
+  job.theta = theta;
+  job.ld = n;
+  job.n = n;
+  job.M = c->M[dataset];
+  job.T = c->T[dataset];
+  job.loglik = loglik;
+  job.delta = delta;
+  job.anc = anc;
+  job.obs = c->d_obs[dataset];
+  job.c2hi = (uint32_t)dataset << 20;
+  // the job travels inside the kernel's parameter block
+  PFLaunch L = c->pl;
+  L.jobs = nullptr;
+  L.job0 = job;
+  const int gt = pf_group_threads(c->ppt, job.M);
+  L.fpc_single = std::max(1, c->pf_block / gt);
+  L.wus = nullptr;
+  L.n_wu = (n + L.fpc_single - 1) / L.fpc_single;
+  L.wu_counter = nullptr;
+  L.k_done = nullptr;
+  L.k_imm = iteration;
+  const int occ = std::max(1, pf_occupancy(c->precision, c->model, c->ppt, c->pf_block, c->pf_smem));
+  const int grid = std::min(L.n_wu, occ * c->sms);
+  SMC2_TRY(pf_launch(c->precision, c->model, c->ppt, grid, c->pf_block, c->pf_smem, L, c->stream));
+  c->kernel_launches++;
+  return SMC2_OK;
+}
+
+smc2_status smc2_pf_loglik(smc2_ctx* c, const double* theta, int n, int iteration, int dataset,
+                           double* loglik) {
+  return pf_standalone(c, theta, n, iteration, dataset, loglik, nullptr, nullptr);
+}
+
+smc2_status smc2_pf_trace(smc2_ctx* c, const double* theta, int n, int iteration, int dataset,
+                          double* loglik, double* delta, int32_t* anc) {
+  return pf_standalone(c, theta, n, iteration, dataset, loglik, delta, anc);
+}
+
+smc2_status smc2_run(smc2_ctx* c, int n_iter, smc2_iter_stats* stats_host) {
+  if (!c || n_iter < 1) return SMC2_EINVAL;
+  if (c->k_host + n_iter > c->K) return SMC2_ESTATE;
+  TimedGraph* g = nullptr;
+  smc2_status st = get_graph(c, n_iter, &g);
+  if (st != SMC2_OK) return st;
+  SMC2_TRY(cudaGraphLaunch(g->exec, c->stream));
+  const int k0 = c->k_host;
+  c->k_host += n_iter;
+  c->kernel_launches += (int64_t)kLaunchesPerIter * n_iter;
+  if (c->timing) {
+    SMC2_TRY(cudaStreamSynchronize(c->stream));
+    for (int i = 0; i < n_iter; ++i) {
+      float ms = 0.f;
+      SMC2_TRY(cudaEventElapsedTime(&ms, g->ev[2 * i], g->ev[2 * i + 1]));
+      c->pf_ms += ms;
+      c->pf_launches++;
+    }
+  }
+  if (stats_host) {
+    for (int d = 0; d < c->n_ds; ++d)
+      for (int i = 0; i < n_iter; ++i)
+        SMC2_TRY(cudaMemcpyAsync(stats_host + (size_t)i * c->n_ds + d, c->h_ds[d].hist + k0 + i,
+                                 sizeof(smc2_iter_stats), cudaMemcpyDeviceToHost, c->stream));
+    return sticky(c);
+  }
+  return SMC2_OK;
+}
+
+smc2_status smc2_iterate(smc2_ctx* c, smc2_iter_stats* stats_host) {
+  return smc2_run(c, 1, stats_host);
+}
+
+smc2_status smc2_estimate(smc2_ctx* c, int dataset, double* mean_host, double* logz_host,
+                          double* ess_sum_host) {
+  if (bad_ds(c, dataset)) return SMC2_EINVAL;
+  if (c->k_host < 1) return SMC2_ESTATE;
+  const DSDev& s = c->h_ds[dataset];
+  smc2_iter_stats last;
+  double rec0 = 0.0;
+  if (mean_host)
+    SMC2_TRY(cudaMemcpyAsync(mean_host, s.est_rec, c->D * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  SMC2_TRY(cudaMemcpyAsync(&last, s.hist + (c->k_host - 1), sizeof(last), cudaMemcpyDeviceToHost, c->stream));
+  SMC2_TRY(cudaMemcpyAsync(&rec0, s.rec, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  smc2_status st = sticky(c);
+  if (logz_host) *logz_host = last.logz;
+  if (ess_sum_host) *ess_sum_host = rec0;
+  return st;
+}
+
+smc2_status smc2_get_history(smc2_ctx* c, int dataset, smc2_iter_stats* hist, int cap, int* k_out) {
+  if (bad_ds(c, dataset) || !hist || cap < 0) return SMC2_EINVAL;
+  const int k = std::min(c->k_host, cap);
+  if (k > 0)
+    SMC2_TRY(cudaMemcpyAsync(hist, c->h_ds[dataset].hist, (size_t)k * sizeof(smc2_iter_stats),
+                             cudaMemcpyDeviceToHost, c->stream));
+  if (k_out) *k_out = c->k_host;
+  return sticky(c);
+}
+
+smc2_status smc2_get_state(smc2_ctx* c, int dataset, int* k_out, double* theta, double* lp,
+                           double* ll, double* lw) {
+  if (bad_ds(c, dataset)) return SMC2_EINVAL;
+  const DSDev& s = c->h_ds[dataset];
+  const int N = s.N, D = c->D;
+  std::vector<double> soa((size_t)D * N);
+  SMC2_TRY(cudaMemcpyAsync(soa.data(), s.thA, soa.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  if (lp) SMC2_TRY(cudaMemcpyAsync(lp, s.lpA, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  if (ll) SMC2_TRY(cudaMemcpyAsync(ll, s.llA, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  if (lw) SMC2_TRY(cudaMemcpyAsync(lw, s.logw, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  smc2_status st = sticky(c);
+  if (theta)
+    for (int i = 0; i < N; ++i)
+      for (int d = 0; d < D; ++d) theta[(size_t)i * D + d] = soa[(size_t)d * N + i];
+  if (k_out) *k_out = c->k_host;
+  return st;
+}
+
+smc2_status smc2_set_state(smc2_ctx* c, int dataset, int k, const double* theta, const double* lp,
+                           const double* ll, const double* lw) {
+  if (bad_ds(c, dataset) || !theta || !lp || !ll || !lw || k < 0 || k > c->K) return SMC2_EINVAL;
+  DSDev& s = c->h_ds[dataset];
+  const int N = s.N, D = c->D;
+  std::vector<double> soa((size_t)D * N);
+  for (int i = 0; i < N; ++i)
+    for (int d = 0; d < D; ++d) soa[(size_t)d * N + i] = theta[(size_t)i * D + d];
+  cudaStream_t st = c->stream;
+  SMC2_TRY(cudaMemcpyAsync(s.thA, soa.data(), soa.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+  SMC2_TRY(cudaMemcpyAsync(s.lpA, lp, N * sizeof(double), cudaMemcpyHostToDevice, st));
+  SMC2_TRY(cudaMemcpyAsync(s.llA, ll, N * sizeof(double), cudaMemcpyHostToDevice, st));
+  SMC2_TRY(cudaMemcpyAsync(s.logw, lw, N * sizeof(double), cudaMemcpyHostToDevice, st));
+  SMC2_TRY(outer_parent_reference(c->op, dataset, st));
+  c->kernel_launches++;
+  if (dataset == 0) {
+    SMC2_TRY(cudaMemcpyAsync(c->d_k, &k, sizeof(int), cudaMemcpyHostToDevice, st));
+    c->k_host = k;
+  }
+  return cudaStreamSynchronize(st) == cudaSuccess ? SMC2_OK : SMC2_ECUDA;
+}
+
+smc2_status smc2_set_history(smc2_ctx* c, int dataset, const smc2_iter_stats* hist, int k) {
+  if (bad_ds(c, dataset) || k < 0 || k > c->K || (k > 0 && !hist)) return SMC2_EINVAL;
+  const DSDev& s = c->h_ds[dataset];
+  if (k > 0)
+    SMC2_TRY(cudaMemcpyAsync(s.hist, hist, (size_t)k * sizeof(smc2_iter_stats), cudaMemcpyHostToDevice,
+                             c->stream));
+  SMC2_TRY(outer_rebuild_recycling(c->op, dataset, k, c->stream));
+  c->kernel_launches++;
+  return cudaStreamSynchronize(c->stream) == cudaSuccess ? SMC2_OK : SMC2_ECUDA;
+}
+
+smc2_status smc2_resample_systematic(const uint64_t* q, int n, uint32_t U, int32_t* anc, void* stream) {
+  if (!q || !anc || n < 1 || n > SMC2_MAX_N) return SMC2_EINVAL;
+  return map_cuda(resample_systematic_launch(q, n, U, anc, static_cast<cudaStream_t>(stream)));
+}
+
+smc2_status smc2_philox_normals(uint64_t seed, const uint32_t* ctr, int n, int precision,
+                                uint32_t* words, double* z, void* stream) {
+  if (!ctr || n < 1 || (precision != SMC2_PREC_FP64 && precision != SMC2_PREC_MIXED)) return SMC2_EINVAL;
+  return map_cuda(philox_normals_launch(seed, ctr, n, precision, words, z, static_cast<cudaStream_t>(stream)));
+}
+
+smc2_status smc2_sync(smc2_ctx* c) {
+  if (!c) return SMC2_EINVAL;
+  return sticky(c);
+}
+
+smc2_status smc2_set_timing(smc2_ctx* c, int enable) {
+  if (!c) return SMC2_EINVAL;
+  c->timing = enable != 0;
+  return SMC2_OK;
+}
+
+smc2_status smc2_get_timing(smc2_ctx* c, double* pf_ms, int64_t* pf_launches, int64_t* kernel_launches,
+                            int reset) {
+  if (!c) return SMC2_EINVAL;
+  SMC2_TRY(cudaStreamSynchronize(c->stream));
+  if (pf_ms) *pf_ms = c->pf_ms;
+  if (pf_launches) *pf_launches = c->pf_launches;
+  if (kernel_launches) *kernel_launches = c->kernel_launches;
+  if (reset) {
+    c->pf_ms = 0.0;
+    c->pf_launches = 0;
+    c->kernel_launches = 0;
+  }
+  return SMC2_OK;
+}
+
+void smc2_destroy(smc2_ctx* c) {
+  if (!c) return;
+  if (c->stream || c->arena) cudaStreamSynchronize(c->stream);
+  drop_graphs(c);
+  if (c->arena) cudaFree(c->arena);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,124 @@
+// internal.h -- descriptors shared by the library's translation units.
+//
+// Device memory layout (per dataset d, all arrays in one arena):
+//   thA, thB   double SoA [D][N]  current population / proposals
+//   lpA, lpB   double [N]         log prior of A / B
+//   llA, llB   double [N]         PF log-likelihood estimate of A / B
+//   logw       double [N]         unnormalised log weight (index-aligned with A and B)
+//   logq       double [N]         log proposal density of B given A
+//   q          uint64 [N]         quantised weights for outer resampling
+//   part       double [nblk][kPartStride]  per-block partial sums
+//   obs        R4 [T]             per-step observation terms in the PF precision
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/smc2.h"
+
+namespace smc2 {
+
+constexpr int kOuterBlock = 256;                       // threads of the outer kernels
+constexpr int kPartStride = 160;                       // >= 1 + 2D + 2D(2D+1)/2 for D <= 8
+constexpr int kStatStride = 16;                        // >= 3 + D
+
+struct LKParams {
+  double mu[2 * 8];    // (mu_a, mu_b)
+  double A[8 * 8];     // S_ab S_bb^{-1}, row-major D x D
+  double Lc[8 * 8];    // lower Cholesky factor of S_{a|b}
+  double logdet;       // log det S_{a|b}
+  int fallback;        // 1: forward kernel used this iteration
+  int pad;
+};
+
+struct IterCur {       // working scalars of the current iteration of one dataset
+  double m;            // max log w (quantisation reference)
+  double lse;          // log sum w
+  double m_par;        // max parent log weight for the next iteration's L-kernel fit
+  int resample;
+  int pad;
+};
+
+struct DSDev {
+  int N, M, T, nblk;
+  double *thA, *thB, *lpA, *lpB, *llA, *llB, *logw, *logq;
+  uint64_t* q;
+  double* part;        // [nblk][kPartStride]
+  double* part_st;     // [nblk][kStatStride]
+  unsigned* tickets;   // [4]
+  LKParams* lk;
+  IterCur* cur;
+  smc2_iter_stats* hist;  // [K]
+  double* rec;         // [1 + D]: sum l_k, sum l_k f~_k
+  double* est_rec;     // [D]: recycled estimate
+  const void* obs;     // PF observation terms (R4 per step)
+  uint32_t c2hi;       // dataset << 20
+  int pad;
+};
+
+struct OuterParams {
+  const DSDev* ds;
+  int n_ds, D, lkernel, K;
+  double rw_scale, ess_frac;
+  double prior_mean[8], prior_sd[8];
+  uint64_t seed;
+  int* k_done;         // completed iterations; the running iteration is k_done + 1
+  int* status;
+  unsigned* grid_ticket;
+};
+
+// One particle-filter job: n filters of one dataset.
+struct PFJob {
+  const double* theta; // SoA [D][ld]
+  int ld, n, M, T;
+  double* loglik;      // [n]
+  double* delta;       // optional [n][T]
+  int32_t* anc;        // optional [n][T-1][M]
+  const void* obs;     // R4 per step
+  uint32_t c2hi;
+  int pad;
+};
+
+struct PFModel {
+  double npop, e0, i0, lambda_floor;
+  int n_sub;
+  int pad;
+};
+
+struct PFLaunch {
+  const PFJob* jobs;   // NULL: the single job job0
+  const int4* wus;     // (job, first filter, count, -); NULL: one job, unit w = filters [w*fpc, ...)
+  int n_wu;
+  int fpc_single;      // filters per unit when wus == NULL
+  int* wu_counter;     // dynamic scheduling when not NULL
+  uint64_t seed;
+  const int* k_done;   // iteration = *k_done + 1 when not NULL
+  int k_imm;
+  int* status;
+  PFModel mdl;
+  PFJob job0;
+};
+
+// Launch-shape helpers (pf.cu).
+size_t pf_smem_bytes(int precision, int model, int ppt, int block, int M);
+int pf_group_threads(int ppt, int M);
+cudaError_t pf_launch(int precision, int model, int ppt, int grid, int block, size_t smem,
+                      const PFLaunch& L, cudaStream_t s);
+cudaError_t pf_configure(int precision, int model, int ppt, size_t smem);
+int pf_occupancy(int precision, int model, int ppt, int block, size_t smem);
+
+// Outer kernels (outer.cu).
+cudaError_t outer_obs_terms(int precision, int model, const double* y, int T, void* obs,
+                            cudaStream_t s);
+cudaError_t outer_propose(const OuterParams& P, int max_nblk, cudaStream_t s);
+cudaError_t outer_weights(const OuterParams& P, int max_nblk, cudaStream_t s);
+cudaError_t outer_quantise(const OuterParams& P, int max_nblk, cudaStream_t s);
+cudaError_t outer_resample(const OuterParams& P, int max_nblk, int max_N, cudaStream_t s);
+cudaError_t outer_parent_reference(const OuterParams& P, int dataset, cudaStream_t s);
+cudaError_t outer_rebuild_recycling(const OuterParams& P, int dataset, int k, cudaStream_t s);
+cudaError_t resample_systematic_launch(const uint64_t* q, int n, uint32_t U, int32_t* anc,
+                                       cudaStream_t s);
+cudaError_t philox_normals_launch(uint64_t seed, const uint32_t* ctr, int n, int precision,
+                                  uint32_t* words, double* z, cudaStream_t s);
+
+}  // namespace smc2

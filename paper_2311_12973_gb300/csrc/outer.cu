@@ -1,0 +1,597 @@
+// outer.cu -- the SMC^2 outer step (Sec. IV of the paper), in FP64.
+//
+// One iteration is four launches over a (block, dataset) grid:
+//   propose   k = 1: theta ~ q_1 = prior (Eq. 16); k > 1: Gaussian random walk
+//             (Eqs. 18-19) and, for the Gaussian L-kernel, per-block weighted
+//             moments of the pairs (theta_{k-1}, theta_k); the last block to
+//             finish fits the joint Gaussian and conditions it (Eqs. 32-35).
+//   weights   Eq. (17) at k = 1, Eq. (20) after; per-block max / sums; the last
+//             block forms log sum w, log sum w^2, ESS (Eqs. 24-25), the estimate
+//             (Eq. 21), the evidence and the recycling sums (Eqs. 23, 29).
+//   quantise  q_i = floor(exp(log w_i - max) 2^B) when ESS < ess_frac N.
+//   resample  every block scans all q into shared memory and redistributes its
+//             own slots (Eq. 27 counts, Algorithm 1 order), or copies when no
+//             resampling was triggered; weights reset to the mean (Sec. IV-B).
+// The "last block" steps use an atomic ticket; their sums run in block order,
+// so results do not depend on scheduling.
+#include <cfloat>
+#include <cmath>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace smc2 {
+
+constexpr int kWarps = kOuterBlock / 32;
+
+__device__ __forceinline__ double block_max(double v, double* sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v = warp_max(v);
+  __syncthreads();
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  double r = sh[0];
+  for (int w = 1; w < kWarps; ++w) r = fmax(r, sh[w]);
+  return r;
+}
+
+// Sum of NV values per thread over the block, written in warp order to out[0..NV).
+template <int NV>
+__device__ __forceinline__ void block_sums(const double (&v)[NV], double* sh /*[kWarps][NV]*/,
+                                           double* out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+#pragma unroll
+  for (int a = 0; a < NV; ++a) {
+    const double s = warp_sum(v[a]);
+    if (lane == 0) sh[warp * NV + a] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    double s = 0.0;
+    for (int w = 0; w < kWarps; ++w) s += sh[w * NV + threadIdx.x];
+    out[threadIdx.x] = s;
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ double log_prior(const OuterParams& P, const double* th) {
+  double lp = 0.0;
+  for (int d = 0; d < P.D; ++d) {
+    const double r = (th[d] - P.prior_mean[d]) / P.prior_sd[d];
+    lp += -0.5 * kLog2Pi - log(P.prior_sd[d]) - 0.5 * r * r;
+  }
+  return lp;
+}
+
+// log N(x; mean, sd^2 I)
+__device__ __forceinline__ double iso_logpdf(int D, const double* x, const double* mean, double sd) {
+  double ss = 0.0;
+  for (int d = 0; d < D; ++d) {
+    const double r = (x[d] - mean[d]) / sd;
+    ss += r * r;
+  }
+  return -0.5 * D * kLog2Pi - D * log(sd) - 0.5 * ss;
+}
+
+// log N(a; mu_a + A (b - mu_b), Lc Lc^T)
+__device__ __forceinline__ double lk_logpdf(int D, const LKParams& L, const double* a, const double* b) {
+  double r[kMaxD], v[kMaxD];
+  for (int p = 0; p < D; ++p) {
+    double m = L.mu[p];
+    for (int s = 0; s < D; ++s) m += L.A[p * D + s] * (b[s] - L.mu[D + s]);
+    r[p] = a[p] - m;
+  }
+  double ss = 0.0;
+  for (int p = 0; p < D; ++p) {
+    double s = r[p];
+    for (int l = 0; l < p; ++l) s -= L.Lc[p * D + l] * v[l];
+    v[p] = s / L.Lc[p * D + p];
+    ss += v[p] * v[p];
+  }
+  return -0.5 * D * kLog2Pi - 0.5 * L.logdet - 0.5 * ss;
+}
+
+// Cholesky with the pivot floor 1e-12 (a_jj + mean_j^2); 0 on success.
+__device__ int chol_floor(int n, const double* a, const double* mean, double* l) {
+  for (int e = 0; e < n * n; ++e) l[e] = 0.0;
+  for (int j = 0; j < n; ++j) {
+    double s = a[j * n + j];
+    for (int p = 0; p < j; ++p) s -= l[j * n + p] * l[j * n + p];
+    const double floor_j = 1e-12 * (a[j * n + j] + mean[j] * mean[j]);
+    if (!(s > floor_j) || !isfinite(s)) return -1;
+    l[j * n + j] = sqrt(s);
+    for (int r = j + 1; r < n; ++r) {
+      double v = a[r * n + j];
+      for (int p = 0; p < j; ++p) v -= l[r * n + p] * l[j * n + p];
+      l[r * n + j] = v / l[j * n + j];
+    }
+  }
+  return 0;
+}
+
+// Moment slots: 0 = sum w; 1..2D = sum w z_r; then sum w z_r z_s for r <= s.
+__device__ __forceinline__ int n_moments(int D) { return 1 + 2 * D + D * (2 * D + 1); }
+
+__device__ void lk_fit(int D, const double* tot, const double* shift, LKParams* out) {
+  const int D2 = 2 * D;
+  double m1[2 * kMaxD], mu[2 * kMaxD], sig[4 * kMaxD * kMaxD];
+  const double W = tot[0];
+  for (int r = 0; r < D2; ++r) {
+    m1[r] = tot[1 + r] / W;
+    mu[r] = shift[r] + m1[r];
+  }
+  int slot = 1 + D2;
+  for (int r = 0; r < D2; ++r)
+    for (int s = r; s < D2; ++s, ++slot) {
+      const double c = tot[slot] / W - m1[r] * m1[s];
+      sig[r * D2 + s] = c;
+      sig[s * D2 + r] = c;
+    }
+  double saa[kMaxD * kMaxD], sab[kMaxD * kMaxD], sbb[kMaxD * kMaxD], lb[kMaxD * kMaxD];
+  for (int r = 0; r < D; ++r)
+    for (int s = 0; s < D; ++s) {
+      saa[r * D + s] = sig[r * D2 + s];
+      sab[r * D + s] = sig[r * D2 + (D + s)];
+      sbb[r * D + s] = sig[(D + r) * D2 + (D + s)];
+    }
+  for (int r = 0; r < D2; ++r) out->mu[r] = mu[r];
+  out->fallback = 1;
+  if (chol_floor(D, sbb, mu + D, lb) != 0) return;
+  // A = S_ab S_bb^{-1}: solve S_bb x = (row c of S_ab)^T for each row c
+  for (int c = 0; c < D; ++c) {
+    double tmp[kMaxD], sol[kMaxD];
+    for (int r = 0; r < D; ++r) {
+      double v = sab[c * D + r];
+      for (int p = 0; p < r; ++p) v -= lb[r * D + p] * tmp[p];
+      tmp[r] = v / lb[r * D + r];
+    }
+    for (int r = D - 1; r >= 0; --r) {
+      double v = tmp[r];
+      for (int p = r + 1; p < D; ++p) v -= lb[p * D + r] * sol[p];
+      sol[r] = v / lb[r * D + r];
+    }
+    for (int r = 0; r < D; ++r) out->A[c * D + r] = sol[r];
+  }
+  double sc[kMaxD * kMaxD];
+  for (int r = 0; r < D; ++r)
+    for (int s = 0; s < D; ++s) {
+      double v = saa[r * D + s];
+      for (int p = 0; p < D; ++p) v -= out->A[r * D + p] * sab[s * D + p];
+      sc[r * D + s] = v;
+    }
+  if (chol_floor(D, sc, mu, out->Lc) != 0) return;
+  double ld = 0.0;
+  for (int r = 0; r < D; ++r) ld += 2.0 * log(out->Lc[r * D + r]);
+  out->logdet = ld;
+  out->fallback = 0;
+}
+
+// ---------------------------------------------------------------------------
+// propose (+ L-kernel fit)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kOuterBlock) propose_kernel(OuterParams P) {
+  const DSDev& S = P.ds[blockIdx.y];
+  if ((int)blockIdx.x >= S.nblk) return;
+  __shared__ double zs[2 * kMaxD][kOuterBlock];
+  __shared__ double ws[kOuterBlock];
+  __shared__ double shift[2 * kMaxD];
+  __shared__ double tot[kPartStride];
+  __shared__ int s_last;
+  const int N = S.N, D = P.D, tid = threadIdx.x;
+  const int i = blockIdx.x * kOuterBlock + tid;
+  const uint32_t k = (uint32_t)(*P.k_done + 1);
+  const bool act = i < N;
+  const uint2 key = seed_key(P.seed);
+  double a[kMaxD], b[kMaxD];
+  if (act) {
+    const uint32_t c2 = counter_c2((uint32_t)i, S.c2hi);
+    for (int g = 0; g * 4 < D; ++g) {
+      double z[4];
+      normals4<double>(make_uint4((uint32_t)g, 0u, c2,
+                                  counter_c3(k == 1 ? TAG_THETA_INIT : TAG_PROPOSE, k)),
+                       key, z);
+      for (int r = 0; r < 4 && 4 * g + r < D; ++r) {
+        const int d = 4 * g + r;
+        if (k == 1) {
+          b[d] = P.prior_mean[d] + P.prior_sd[d] * z[r];
+        } else {
+          a[d] = S.thA[(size_t)d * N + i];
+          b[d] = a[d] + P.rw_scale * z[r];
+        }
+      }
+    }
+    for (int d = 0; d < D; ++d) S.thB[(size_t)d * N + i] = b[d];
+    const double lp = log_prior(P, b);
+    S.lpB[i] = lp;
+    S.logq[i] = (k == 1) ? log_prior(P, b) : iso_logpdf(D, b, a, P.rw_scale);
+  }
+  if (k == 1 || P.lkernel != LK_GAUSS) return;
+
+  // per-block weighted moments of z = (theta_{k-1}, theta_k) - shift
+  if (tid < D) {
+    shift[tid] = S.thA[(size_t)tid * N];
+    shift[D + tid] = S.thA[(size_t)tid * N];
+  }
+  __syncthreads();
+  const double w = act ? exp(S.logw[i] - S.cur->m_par) : 0.0;
+  ws[tid] = w;
+  for (int r = 0; r < 2 * D; ++r)
+    zs[r][tid] = act ? ((r < D ? a[r] : b[r - D]) - shift[r]) : 0.0;
+  __syncthreads();
+  const int NM = n_moments(D);
+  if (tid < NM) {
+    int kind, r = 0, s = 0;
+    if (tid == 0) {
+      kind = 0;
+    } else if (tid <= 2 * D) {
+      kind = 1;
+      r = tid - 1;
+    } else {
+      kind = 2;
+      int slot = tid - 1 - 2 * D;
+      r = 0;
+      while (slot >= 2 * D - r) {
+        slot -= 2 * D - r;
+        ++r;
+      }
+      s = r + slot;
+    }
+    double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;
+    for (int e = 0; e < kOuterBlock; e += 4) {
+      double v0 = ws[e], v1 = ws[e + 1], v2 = ws[e + 2], v3 = ws[e + 3];
+      if (kind >= 1) {
+        v0 *= zs[r][e];
+        v1 *= zs[r][e + 1];
+        v2 *= zs[r][e + 2];
+        v3 *= zs[r][e + 3];
+      }
+      if (kind == 2) {
+        v0 *= zs[s][e];
+        v1 *= zs[s][e + 1];
+        v2 *= zs[s][e + 2];
+        v3 *= zs[s][e + 3];
+      }
+      acc0 += v0;
+      acc1 += v1;
+      acc2 += v2;
+      acc3 += v3;
+    }
+    S.part[(size_t)blockIdx.x * kPartStride + tid] = (acc0 + acc1) + (acc2 + acc3);
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) s_last = (atomicAdd(&S.tickets[0], 1u) == (unsigned)(S.nblk - 1));
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (tid < NM) {
+    double t = 0.0;
+    for (int bb = 0; bb < S.nblk; ++bb) t += __ldcg(&S.part[(size_t)bb * kPartStride + tid]);
+    tot[tid] = t;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    lk_fit(D, tot, shift, S.lk);
+    S.tickets[0] = 0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// weights + normalisation statistics
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void accumulate_recycling(double* rec, double* est_rec, double ess,
+                                                     const double* est, int D) {
+  rec[0] += ess;
+  for (int d = 0; d < D; ++d) rec[1 + d] += ess * est[d];
+  for (int d = 0; d < D; ++d) est_rec[d] = rec[1 + d] / rec[0];
+}
+
+__global__ void __launch_bounds__(kOuterBlock) weights_kernel(OuterParams P) {
+  const DSDev& S = P.ds[blockIdx.y];
+  if ((int)blockIdx.x >= S.nblk) return;
+  __shared__ double shm[kWarps * (2 + kMaxD)];
+  __shared__ double sums[2 + kMaxD];
+  __shared__ int s_last;
+  const int N = S.N, D = P.D, tid = threadIdx.x;
+  const int i = blockIdx.x * kOuterBlock + tid;
+  const uint32_t k = (uint32_t)(*P.k_done + 1);
+  const bool act = i < N;
+  double lw = -HUGE_VAL, b[kMaxD];
+  if (act) {
+    for (int d = 0; d < D; ++d) b[d] = S.thB[(size_t)d * N + i];
+    const double lpB = S.lpB[i], llB = S.llB[i], lq = S.logq[i];
+    if (k == 1) {
+      lw = (lpB + llB) - lq;  // Eq. (17)
+    } else {
+      double a[kMaxD];
+      for (int d = 0; d < D; ++d) a[d] = S.thA[(size_t)d * N + i];
+      const bool gauss = P.lkernel == LK_GAUSS && !S.lk->fallback;
+      const double logL = gauss ? lk_logpdf(D, *S.lk, a, b) : iso_logpdf(D, a, b, P.rw_scale);
+      lw = S.logw[i] + (lpB + llB) - (S.lpA[i] + S.llA[i]) + logL - lq;  // Eq. (20)
+    }
+    if (isnan(lw)) lw = -HUGE_VAL;
+    S.logw[i] = lw;
+  }
+  const double mb = block_max(lw, shm);
+  double v[2 + kMaxD];
+  const double e = (act && lw > -HUGE_VAL) ? exp(lw - mb) : 0.0;
+  v[0] = e;
+  v[1] = e * e;
+  for (int d = 0; d < kMaxD; ++d) v[2 + d] = (d < D && act) ? e * b[d] : 0.0;
+  block_sums<2 + kMaxD>(v, shm, sums);
+  if (tid == 0) {
+    double* ps = S.part_st + (size_t)blockIdx.x * kStatStride;
+    ps[0] = mb;
+    for (int a = 0; a < 2 + D; ++a) ps[1 + a] = sums[a];
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) s_last = (atomicAdd(&S.tickets[1], 1u) == (unsigned)(S.nblk - 1));
+  __syncthreads();
+  if (!s_last || tid != 0) return;
+  __threadfence();
+  double m = -HUGE_VAL;
+  for (int bb = 0; bb < S.nblk; ++bb) m = fmax(m, __ldcg(&S.part_st[(size_t)bb * kStatStride]));
+  smc2_iter_stats st;
+  st.k = (int)k;
+  st.dataset = (int)blockIdx.y;
+  st.lk_fallback = (k > 1 && P.lkernel == LK_GAUSS) ? S.lk->fallback : 0;
+  IterCur* cur = S.cur;
+  if (!(m > -HUGE_VAL) || isinf(m) || isnan(m)) {
+    raise_status(P.status, ST_NONFINITE);
+    st.resampled = 0;
+    st.ess = st.lse = st.lse2 = st.logz = NAN;
+    for (int d = 0; d < kMaxD; ++d) st.est[d] = NAN;
+    cur->resample = 0;
+  } else {
+    double s1 = 0.0, s2 = 0.0, sth[kMaxD];
+    for (int d = 0; d < D; ++d) sth[d] = 0.0;
+    for (int bb = 0; bb < S.nblk; ++bb) {
+      const double* ps = S.part_st + (size_t)bb * kStatStride;
+      const double mbb = __ldcg(ps);
+      if (!(mbb > -HUGE_VAL)) continue;
+      const double f = exp(mbb - m);
+      s1 += __ldcg(ps + 1) * f;
+      s2 += __ldcg(ps + 2) * (f * f);
+      for (int d = 0; d < D; ++d) sth[d] += __ldcg(ps + 3 + d) * f;
+    }
+    st.lse = m + log(s1);
+    st.lse2 = 2.0 * m + log(s2);
+    st.ess = (s1 * s1) / s2;
+    st.logz = st.lse - log((double)N);
+    for (int d = 0; d < kMaxD; ++d) st.est[d] = d < D ? sth[d] / s1 : 0.0;
+    st.resampled = st.ess < P.ess_frac * (double)N;
+    cur->m = m;
+    cur->lse = st.lse;
+    cur->resample = st.resampled;
+    cur->m_par = st.resampled ? st.lse - log((double)N) : m;
+    accumulate_recycling(S.rec, S.est_rec, st.ess, st.est, D);
+  }
+  if ((int)k <= P.K) S.hist[k - 1] = st;
+  S.tickets[1] = 0;
+}
+
+// ---------------------------------------------------------------------------
+// quantise
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kOuterBlock) quantise_kernel(OuterParams P) {
+  const DSDev& S = P.ds[blockIdx.y];
+  if ((int)blockIdx.x >= S.nblk || !S.cur->resample) return;
+  const int i = blockIdx.x * kOuterBlock + threadIdx.x;
+  if (i >= S.N) return;
+  const double lw = S.logw[i];
+  const double scale = ldexp(1.0, fixed_point_bits(S.N));
+  S.q[i] = (lw > -HUGE_VAL && !isnan(lw)) ? __double2ull_rz(exp(lw - S.cur->m) * scale) : 0ull;
+}
+
+// ---------------------------------------------------------------------------
+// resample: block-wide inclusive scan of all q into shared memory, then the
+// block's own slots; both this kernel and the standalone primitive use it.
+// ---------------------------------------------------------------------------
+__device__ uint64_t scan_all_to_smem(const uint64_t* q, int n, uint64_t* C) {
+  __shared__ uint64_t wt[kWarps];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint64_t carry = 0;
+  for (int base = 0; base < n; base += kOuterBlock) {
+    const int idx = base + threadIdx.x;
+    const uint64_t v = idx < n ? q[idx] : 0ull;
+    const uint64_t incl = warp_incl_scan_u64(v, lane);
+    if (lane == 31) wt[warp] = incl;
+    __syncthreads();
+    uint64_t off = 0, total = 0;
+    for (int w = 0; w < kWarps; ++w) {
+      const uint64_t tw = wt[w];
+      if (w < warp) off += tw;
+      total += tw;
+    }
+    if (idx < n) C[idx] = carry + off + incl;
+    carry += total;
+    __syncthreads();
+  }
+  return carry;
+}
+
+__device__ __forceinline__ int search_first_greater(const uint64_t* C, int n, uint64_t tau) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (C[mid] > tau)
+      hi = mid;
+    else
+      lo = mid + 1;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(kOuterBlock) resample_kernel(OuterParams P) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  uint64_t* C = reinterpret_cast<uint64_t*>(smem_raw);
+  const DSDev& S = P.ds[blockIdx.y];
+  const int N = S.N, D = P.D, tid = threadIdx.x;
+  const uint32_t k = (uint32_t)(*P.k_done + 1);
+  if ((int)blockIdx.x < S.nblk) {
+    const int j = blockIdx.x * kOuterBlock + tid;
+    if (S.cur->resample) {
+      const uint64_t total = scan_all_to_smem(S.q, N, C);
+      const uint32_t U =
+          philox4x32_10(make_uint4(0u, 0u, S.c2hi, counter_c3(TAG_OUTER_RES, k)), seed_key(P.seed)).x;
+      const int log2n = ((N & (N - 1)) == 0) ? (__ffs(N) - 1) : -1;
+      if (j < N) {
+        const uint64_t tau = slot_threshold((uint32_t)j, U, total, N, log2n);
+        const int a = search_first_greater(C, N, tau);
+        for (int d = 0; d < D; ++d) S.thA[(size_t)d * N + j] = S.thB[(size_t)d * N + a];
+        S.lpA[j] = S.lpB[a];
+        S.llA[j] = S.llB[a];
+        S.logw[j] = S.cur->lse - log((double)N);
+      }
+    } else if (j < N) {
+      for (int d = 0; d < D; ++d) S.thA[(size_t)d * N + j] = S.thB[(size_t)d * N + j];
+      S.lpA[j] = S.lpB[j];
+      S.llA[j] = S.llB[j];
+    }
+  }
+  // the last block of the whole grid advances the iteration counter
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    const unsigned nb = gridDim.x * gridDim.y;
+    if (atomicAdd(P.grid_ticket, 1u) == nb - 1) {
+      *P.k_done = (int)k;
+      *P.grid_ticket = 0;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kOuterBlock)
+    resample_primitive_kernel(const uint64_t* q, int n, uint32_t U, int32_t* anc) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  uint64_t* C = reinterpret_cast<uint64_t*>(smem_raw);
+  const uint64_t total = scan_all_to_smem(q, n, C);
+  const int log2n = ((n & (n - 1)) == 0) ? (__ffs(n) - 1) : -1;
+  const int j = blockIdx.x * kOuterBlock + threadIdx.x;
+  if (j < n && total > 0) anc[j] = search_first_greater(C, n, slot_threshold((uint32_t)j, U, total, n, log2n));
+}
+
+__global__ void philox_normals_kernel(uint64_t seed, const uint32_t* ctr, int n, int precision,
+                                      uint32_t* words, double* z) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const uint4 c = make_uint4(ctr[4 * r], ctr[4 * r + 1], ctr[4 * r + 2], ctr[4 * r + 3]);
+  const uint2 key = seed_key(seed);
+  if (words) {
+    const uint4 w = philox4x32_10(c, key);
+    words[4 * r] = w.x;
+    words[4 * r + 1] = w.y;
+    words[4 * r + 2] = w.z;
+    words[4 * r + 3] = w.w;
+  }
+  if (z) {
+    if (precision == SMC2_PREC_FP64) {
+      double v[4];
+      normals4<double>(c, key, v);
+      for (int a = 0; a < 4; ++a) z[4 * r + a] = v[a];
+    } else {
+      float v[4];
+      normals4<float>(c, key, v);
+      for (int a = 0; a < 4; ++a) z[4 * r + a] = (double)v[a];
+    }
+  }
+}
+
+template <typename R>
+__global__ void obs_terms_kernel(int model, const double* y, int T, R* obs) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= T) return;
+  const double v = y[t];
+  double inv = 0.0, c = 0.0;
+  if (model == MODEL_SEIR && v > 0.0) {
+    inv = 1.0 / v;
+    c = -lgamma(v + 1.0) + v * log(v) - v;
+  }
+  obs[4 * t] = (R)v;
+  obs[4 * t + 1] = (R)inv;
+  obs[4 * t + 2] = (R)c;
+  obs[4 * t + 3] = (R)0;
+}
+
+// Parent reference after a restored state: m_par = max_i log w_i of one dataset.
+__global__ void __launch_bounds__(kOuterBlock) parent_reference_kernel(OuterParams P, int dataset) {
+  __shared__ double shm[kWarps];
+  const DSDev& S = P.ds[dataset];
+  double m = -HUGE_VAL;
+  for (int i = threadIdx.x; i < S.N; i += kOuterBlock) m = fmax(m, S.logw[i]);
+  m = block_max(m, shm);
+  if (threadIdx.x == 0) S.cur->m_par = m;
+}
+
+// Recycling sums rebuilt from a restored history, in iteration order, with the
+// same accumulation as the weights kernel.
+__global__ void rebuild_recycling_kernel(OuterParams P, int dataset, int k) {
+  const DSDev& S = P.ds[dataset];
+  for (int a = 0; a <= P.D; ++a) S.rec[a] = 0.0;
+  for (int d = 0; d < P.D; ++d) S.est_rec[d] = 0.0;
+  for (int e = 0; e < k; ++e) {
+    const smc2_iter_stats st = S.hist[e];
+    if (isfinite(st.ess)) accumulate_recycling(S.rec, S.est_rec, st.ess, st.est, P.D);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+cudaError_t outer_obs_terms(int precision, int model, const double* y, int T, void* obs,
+                            cudaStream_t s) {
+  const int blk = 128, grid = (T + blk - 1) / blk;
+  if (precision == SMC2_PREC_FP64)
+    obs_terms_kernel<double><<<grid, blk, 0, s>>>(model, y, T, static_cast<double*>(obs));
+  else
+    obs_terms_kernel<float><<<grid, blk, 0, s>>>(model, y, T, static_cast<float*>(obs));
+  return cudaGetLastError();
+}
+
+cudaError_t outer_propose(const OuterParams& P, int max_nblk, cudaStream_t s) {
+  propose_kernel<<<dim3(max_nblk, P.n_ds), kOuterBlock, 0, s>>>(P);
+  return cudaGetLastError();
+}
+cudaError_t outer_weights(const OuterParams& P, int max_nblk, cudaStream_t s) {
+  weights_kernel<<<dim3(max_nblk, P.n_ds), kOuterBlock, 0, s>>>(P);
+  return cudaGetLastError();
+}
+cudaError_t outer_quantise(const OuterParams& P, int max_nblk, cudaStream_t s) {
+  quantise_kernel<<<dim3(max_nblk, P.n_ds), kOuterBlock, 0, s>>>(P);
+  return cudaGetLastError();
+}
+cudaError_t outer_resample(const OuterParams& P, int max_nblk, int max_N, cudaStream_t s) {
+  const size_t smem = (size_t)max_N * sizeof(uint64_t);
+  cudaError_t e = cudaFuncSetAttribute(resample_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  resample_kernel<<<dim3(max_nblk, P.n_ds), kOuterBlock, smem, s>>>(P);
+  return cudaGetLastError();
+}
+cudaError_t outer_parent_reference(const OuterParams& P, int dataset, cudaStream_t s) {
+  parent_reference_kernel<<<1, kOuterBlock, 0, s>>>(P, dataset);
+  return cudaGetLastError();
+}
+cudaError_t outer_rebuild_recycling(const OuterParams& P, int dataset, int k, cudaStream_t s) {
+  rebuild_recycling_kernel<<<1, 1, 0, s>>>(P, dataset, k);
+  return cudaGetLastError();
+}
+cudaError_t resample_systematic_launch(const uint64_t* q, int n, uint32_t U, int32_t* anc,
+                                       cudaStream_t s) {
+  const size_t smem = (size_t)n * sizeof(uint64_t);
+  cudaError_t e = cudaFuncSetAttribute(resample_primitive_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  resample_primitive_kernel<<<(n + kOuterBlock - 1) / kOuterBlock, kOuterBlock, smem, s>>>(q, n, U,
+                                                                                          anc);
+  return cudaGetLastError();
+}
+cudaError_t philox_normals_launch(uint64_t seed, const uint32_t* ctr, int n, int precision,
+                                  uint32_t* words, double* z, cudaStream_t s) {
+  philox_normals_kernel<<<(n + 127) / 128, 128, 0, s>>>(seed, ctr, n, precision, words, z);
+  return cudaGetLastError();
+}
+
+}  // namespace smc2

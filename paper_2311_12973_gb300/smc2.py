@@ -1,0 +1,281 @@
+"""Python binding of libsmc2.so: the C ABI of include/smc2.h, argument marshalling only.
+
+Device buffers are torch CUDA tensors (passed as raw pointers); streams are
+torch CUDA streams.  Every computation happens in the library's CUDA kernels;
+importing this module fails loudly when the library has not been built, and no
+call falls back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+MAX_D = 8
+OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ECHOL, ETIMEOUT, EBOUNDS, ESTATE = range(9)
+MODEL_LG_AR1, MODEL_SEIR = 0, 1
+PREC_FP64, PREC_MIXED = 0, 1
+PROP_RW, PROP_MLP = 0, 1
+LK_FORWARD, LK_GAUSS_OPT = 0, 1
+
+
+class Config(C.Structure):
+    _fields_ = [
+        ("model", C.c_int), ("precision", C.c_int), ("proposal", C.c_int), ("lkernel", C.c_int),
+        ("D", C.c_int), ("N", C.c_int), ("M", C.c_int), ("T", C.c_int), ("K", C.c_int),
+        ("rw_scale", C.c_double), ("ess_frac", C.c_double), ("seed", C.c_uint64),
+        ("prior_mean", C.c_double * MAX_D), ("prior_sd", C.c_double * MAX_D),
+        ("npop", C.c_double), ("e0", C.c_double), ("i0", C.c_double), ("lambda_floor", C.c_double),
+        ("n_sub", C.c_int), ("ppt", C.c_int), ("n_datasets", C.c_int),
+        ("ds_N", C.POINTER(C.c_int)), ("ds_M", C.POINTER(C.c_int)), ("ds_T", C.POINTER(C.c_int)),
+    ]
+
+
+class IterStats(C.Structure):
+    _fields_ = [
+        ("k", C.c_int), ("resampled", C.c_int), ("lk_fallback", C.c_int), ("dataset", C.c_int),
+        ("ess", C.c_double), ("lse", C.c_double), ("lse2", C.c_double), ("logz", C.c_double),
+        ("est", C.c_double * MAX_D),
+    ]
+
+    def as_dict(self, D: int) -> dict:
+        return {"k": self.k, "resampled": self.resampled, "lk_fallback": self.lk_fallback,
+                "dataset": self.dataset, "ess": self.ess, "lse": self.lse, "lse2": self.lse2,
+                "logz": self.logz, "est": np.array(self.est[:D])}
+
+
+class SMC2Error(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)} ({status})")
+
+
+def _load() -> C.CDLL:
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise ImportError(f"libsmc2.so is not built ({path}); run __graft_entry__.build()")
+    lib = C.CDLL(path)
+    vp, dp, i32p, u32p, u64p = C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p
+    st = C.c_int
+    ctx = C.c_void_p
+    sig = {
+        "smc2_init": ([C.POINTER(Config), dp, vp, C.POINTER(ctx)], st),
+        "smc2_set_observations": ([ctx, dp], st),
+        "smc2_reset": ([ctx, C.c_uint64], st),
+        "smc2_pf_loglik": ([ctx, dp, C.c_int, C.c_int, C.c_int, dp], st),
+        "smc2_pf_trace": ([ctx, dp, C.c_int, C.c_int, C.c_int, dp, dp, i32p], st),
+        "smc2_iterate": ([ctx, C.POINTER(IterStats)], st),
+        "smc2_run": ([ctx, C.c_int, C.POINTER(IterStats)], st),
+        "smc2_estimate": ([ctx, C.c_int, dp, dp, dp], st),
+        "smc2_get_history": ([ctx, C.c_int, C.POINTER(IterStats), C.c_int, C.POINTER(C.c_int)], st),
+        "smc2_get_state": ([ctx, C.c_int, C.POINTER(C.c_int), dp, dp, dp, dp], st),
+        "smc2_set_state": ([ctx, C.c_int, C.c_int, dp, dp, dp, dp], st),
+        "smc2_set_history": ([ctx, C.c_int, C.POINTER(IterStats), C.c_int], st),
+        "smc2_resample_systematic": ([u64p, C.c_int, C.c_uint32, i32p, vp], st),
+        "smc2_philox_normals": ([C.c_uint64, u32p, C.c_int, C.c_int, u32p, dp, vp], st),
+        "smc2_sync": ([ctx], st),
+        "smc2_set_timing": ([ctx, C.c_int], st),
+        "smc2_get_timing": ([ctx, C.POINTER(C.c_double), C.POINTER(C.c_int64),
+                             C.POINTER(C.c_int64), C.c_int], st),
+        "smc2_destroy": ([ctx], None),
+        "smc2_status_string": ([st], C.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    return lib
+
+
+lib = _load()
+
+
+def status_string(s: int) -> str:
+    return lib.smc2_status_string(int(s)).decode()
+
+
+def _check(status: int, what: str):
+    if status != OK:
+        raise SMC2Error(status, what)
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        return t.data_ptr()
+    return t.ctypes.data
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+def make_config(w, **over) -> Config:
+    """smc2_config from a workload description (attributes named as in the config)."""
+    c = Config()
+    get = lambda k, d=None: over.get(k, getattr(w, k, d))
+    c.model, c.precision = get("model"), get("precision", PREC_FP64)
+    c.proposal, c.lkernel = get("proposal", PROP_RW), get("lkernel", LK_GAUSS_OPT)
+    c.D, c.N, c.M, c.T, c.K = get("D"), get("N"), get("M"), get("T"), get("K")
+    c.rw_scale, c.ess_frac, c.seed = get("rw_scale"), get("ess_frac"), get("seed")
+    for d in range(c.D):
+        c.prior_mean[d] = get("prior_mean")[d]
+        c.prior_sd[d] = get("prior_sd")[d]
+    c.npop, c.e0, c.i0 = get("npop", 0.0), get("e0", 0.0), get("i0", 0.0)
+    c.lambda_floor, c.n_sub = get("lambda_floor", 1e-3), get("n_sub", 1)
+    c.ppt = get("ppt", 0)
+    c.n_datasets = 0
+    return c
+
+
+class SMC2:
+    """One sampler context (smc2_ctx) on the current CUDA device and stream."""
+
+    def __init__(self, cfg: Config, y, stream=None, datasets=None):
+        self.cfg = cfg
+        self.D = cfg.D
+        self._keep = []
+        if datasets is not None:   # list of (N, M, T)
+            n = len(datasets)
+            arrs = [np.ascontiguousarray([d[a] for d in datasets], dtype=np.int32) for a in range(3)]
+            self._keep += arrs
+            cfg.n_datasets = n
+            cfg.ds_N, cfg.ds_M, cfg.ds_T = (a.ctypes.data_as(C.POINTER(C.c_int)) for a in arrs)
+        self.n_ds = max(1, cfg.n_datasets)
+        self.Ns = [d[0] for d in datasets] if datasets is not None else [cfg.N]
+        self.stream = _stream_handle(stream)
+        y = self._host_or_device(y)
+        self._ctx = C.c_void_p()
+        _check(lib.smc2_init(C.byref(cfg), _ptr(y), self.stream, C.byref(self._ctx)), "smc2_init")
+
+    @staticmethod
+    def _host_or_device(y):
+        if hasattr(y, "data_ptr"):
+            return y.contiguous()
+        return np.ascontiguousarray(y, dtype=np.float64)
+
+    def close(self):
+        if self._ctx:
+            lib.smc2_destroy(self._ctx)
+            self._ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- sampler ----------------------------------------------------------
+    def run(self, n_iter: int, stats: bool = True):
+        if not stats:
+            _check(lib.smc2_run(self._ctx, int(n_iter), None), "smc2_run")
+            return None
+        arr = (IterStats * (n_iter * self.n_ds))()
+        _check(lib.smc2_run(self._ctx, int(n_iter), arr), "smc2_run")
+        return [[arr[i * self.n_ds + d].as_dict(self.D) for d in range(self.n_ds)] for i in range(n_iter)]
+
+    def iterate(self):
+        return self.run(1)[0]
+
+    def estimate(self, dataset: int = 0):
+        mean = np.zeros(self.D)
+        logz, ess = C.c_double(), C.c_double()
+        _check(lib.smc2_estimate(self._ctx, dataset, mean.ctypes.data, C.byref(logz), C.byref(ess)),
+               "smc2_estimate")
+        return mean, logz.value, ess.value
+
+    def history(self, dataset: int = 0, cap: int | None = None):
+        cap = cap or self.cfg.K
+        arr = (IterStats * cap)()
+        k = C.c_int()
+        _check(lib.smc2_get_history(self._ctx, dataset, arr, cap, C.byref(k)), "smc2_get_history")
+        return [arr[i].as_dict(self.D) for i in range(min(k.value, cap))]
+
+    def raw_history(self, dataset: int = 0):
+        cap = self.cfg.K
+        arr = (IterStats * cap)()
+        k = C.c_int()
+        _check(lib.smc2_get_history(self._ctx, dataset, arr, cap, C.byref(k)), "smc2_get_history")
+        return arr, k.value
+
+    def set_history(self, arr, k: int, dataset: int = 0):
+        _check(lib.smc2_set_history(self._ctx, dataset, arr, int(k)), "smc2_set_history")
+
+    def get_state(self, dataset: int = 0):
+        N = self.Ns[dataset]
+        th, lp, ll, lw = np.zeros((N, self.D)), np.zeros(N), np.zeros(N), np.zeros(N)
+        k = C.c_int()
+        _check(lib.smc2_get_state(self._ctx, dataset, C.byref(k), th.ctypes.data, lp.ctypes.data,
+                                  ll.ctypes.data, lw.ctypes.data), "smc2_get_state")
+        return k.value, th, lp, ll, lw
+
+    def set_state(self, k, theta, logprior, loglik, logw, dataset: int = 0):
+        arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (theta, logprior, loglik, logw)]
+        _check(lib.smc2_set_state(self._ctx, dataset, int(k), *(a.ctypes.data for a in arrs)),
+               "smc2_set_state")
+
+    def reset(self, seed: int):
+        _check(lib.smc2_reset(self._ctx, int(seed)), "smc2_reset")
+
+    def set_observations(self, y):
+        y = self._host_or_device(y)
+        self._keep_y = y
+        _check(lib.smc2_set_observations(self._ctx, _ptr(y)), "smc2_set_observations")
+
+    def sync(self):
+        _check(lib.smc2_sync(self._ctx), "smc2_sync")
+
+    # -- particle filter ---------------------------------------------------
+    def pf_loglik(self, theta_soa, iteration: int, dataset: int = 0, out=None):
+        """theta_soa: CUDA float64 tensor [D][n]; returns CUDA float64 [n]."""
+        import torch
+        n = theta_soa.shape[1]
+        out = out if out is not None else torch.empty(n, dtype=torch.float64, device=theta_soa.device)
+        _check(lib.smc2_pf_loglik(self._ctx, _ptr(theta_soa), n, int(iteration), dataset, _ptr(out)),
+               "smc2_pf_loglik")
+        return out
+
+    def pf_trace(self, theta_soa, iteration: int, dataset: int = 0, M: int | None = None,
+                 T: int | None = None):
+        import torch
+        n = theta_soa.shape[1]
+        M = M or self.cfg.M
+        T = T or self.cfg.T
+        dev = theta_soa.device
+        ll = torch.empty(n, dtype=torch.float64, device=dev)
+        delta = torch.empty((n, T), dtype=torch.float64, device=dev)
+        anc = torch.empty((n, max(T - 1, 0), M), dtype=torch.int32, device=dev)
+        _check(lib.smc2_pf_trace(self._ctx, _ptr(theta_soa), n, int(iteration), dataset, _ptr(ll),
+                                 _ptr(delta), _ptr(anc)), "smc2_pf_trace")
+        return ll, delta, anc
+
+    # -- timing -------------------------------------------------------------
+    def set_timing(self, on: bool):
+        _check(lib.smc2_set_timing(self._ctx, int(bool(on))), "smc2_set_timing")
+
+    def timing(self, reset: bool = False):
+        ms, n, kl = C.c_double(), C.c_int64(), C.c_int64()
+        _check(lib.smc2_get_timing(self._ctx, C.byref(ms), C.byref(n), C.byref(kl), int(reset)),
+               "smc2_get_timing")
+        return ms.value, n.value, kl.value
+
+
+def resample_systematic(q, U: int, anc, stream=None):
+    """q: CUDA uint64 (int64 storage) [n]; anc: CUDA int32 [n]."""
+    _check(lib.smc2_resample_systematic(_ptr(q), q.numel(), int(U) & 0xFFFFFFFF, _ptr(anc),
+                                        _stream_handle(stream)), "smc2_resample_systematic")
+    return anc
+
+
+def philox_normals(seed: int, ctr, precision: int, words=None, z=None, stream=None):
+    """ctr: CUDA int32 [n][4] holding uint32 counters."""
+    n = ctr.shape[0]
+    _check(lib.smc2_philox_normals(int(seed), _ptr(ctr), n, int(precision), _ptr(words), _ptr(z),
+                                   _stream_handle(stream)), "smc2_philox_normals")

@@ -1,0 +1,87 @@
+"""The C-ABI library loads without a GPU, exports every entry point that
+include/smc2.h declares, and rejects invalid arguments before touching the GPU."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", h)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(smc2_[a-z0-9_]+)\s*\(", text))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def S():
+    from paper_2311_12973_gb300 import build
+    build.build()
+    from paper_2311_12973_gb300 import smc2
+    return smc2
+
+
+def test_every_declared_symbol_is_exported(S):
+    names = declared_symbols()
+    assert len(names) >= 19
+    for n in names:
+        assert hasattr(S.lib, n), n
+
+
+def test_status_strings(S):
+    for code in range(9):
+        assert S.status_string(code) not in ("", "unknown status")
+    assert S.status_string(99) == "unknown status"
+
+
+def _cfg(S, **over):
+    from paper_2311_12973_gb300 import inputs as I
+    cfg = S.make_config(I.workload("lg_t50_n64"))
+    for k, v in over.items():
+        setattr(cfg, k, v)
+    return cfg
+
+
+@pytest.mark.parametrize("over", [
+    {"model": 7}, {"precision": 3}, {"proposal": 5}, {"lkernel": 9}, {"D": 4}, {"N": 0},
+    {"N": 16385}, {"M": 0}, {"M": 4097}, {"T": 0}, {"K": 0}, {"rw_scale": 0.0},
+    {"rw_scale": float("nan")}, {"ess_frac": -1.0}, {"ppt": 3},
+])
+def test_invalid_configs_rejected_before_gpu_work(S, over):
+    import numpy as np
+    cfg = _cfg(S, **over)
+    y = np.zeros(64)
+    ctx = C.c_void_p()
+    assert S.lib.smc2_init(C.byref(cfg), y.ctypes.data, None, C.byref(ctx)) == S.EINVAL
+    assert not ctx.value
+
+
+def test_invalid_prior_and_seir_constants(S):
+    import numpy as np
+    from paper_2311_12973_gb300 import inputs as I
+    y = np.zeros(200)
+    ctx = C.c_void_p()
+    cfg = _cfg(S)
+    cfg.prior_sd[1] = 0.0
+    assert S.lib.smc2_init(C.byref(cfg), y.ctypes.data, None, C.byref(ctx)) == S.EINVAL
+    w = I.workload("seir_t100_n1024")
+    for over in ({"npop": 0.0}, {"n_sub": 0}, {"lambda_floor": 0.0}, {"i0": 2e6}):
+        cfg = S.make_config(w, **over)
+        assert S.lib.smc2_init(C.byref(cfg), y.ctypes.data, None, C.byref(ctx)) == S.EINVAL
+    assert S.lib.smc2_init(None, y.ctypes.data, None, C.byref(ctx)) == S.EINVAL
+    assert S.lib.smc2_init(C.byref(cfg), None, None, C.byref(ctx)) == S.EINVAL
+
+
+def test_null_context_calls_rejected(S):
+    assert S.lib.smc2_run(None, 1, None) == S.EINVAL
+    assert S.lib.smc2_sync(None) == S.EINVAL
+    assert S.lib.smc2_pf_loglik(None, None, 1, 1, 0, None) == S.EINVAL
+    assert S.lib.smc2_resample_systematic(None, 4, 0, None, None) == S.EINVAL
+    assert S.lib.smc2_philox_normals(1, None, 4, 0, None, None, None) == S.EINVAL
+    S.lib.smc2_destroy(None)

@@ -1,0 +1,120 @@
+"""Particle-filter kernel against the oracle (Sec. II).
+
+FP64: per-step likelihood increments within 1e-12 relative (to the
+magnitude of the per-step log-weight terms) and ancestors bit-exact.
+FP32 particles: the first step (identical inputs: the initial particle
+states are exact in float) within 2e-5; until the first ancestor that differs
+(a quantised weight on the other side of a threshold), increments within the
+drift FP32 state propagation allows (stated in the test)."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2311_12973_gb300 import inputs as I
+
+from gpu_util import rel_err, soa
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def S():
+    from paper_2311_12973_gb300 import smc2
+    return smc2
+
+
+def _run(S, w, thetas, k, ppt=0):
+    ctx = S.SMC2(S.make_config(w, ppt=ppt), w.y)
+    ll, delta, anc = ctx.pf_trace(soa(thetas), iteration=k)
+    out = ll.cpu().numpy(), delta.cpu().numpy(), anc.cpu().numpy()
+    ctx.close()
+    ref = [O.pf_loglik(O.config_from(w), thetas[i], w.y, k, i, trace=True) for i in range(len(thetas))]
+    return out, ref
+
+
+def _obs_scale(w):
+    """Magnitude of the per-step log-weight terms (y log lambda, lambda, log y!)."""
+    if w.model == I.LG:
+        return 10.0
+    y = np.maximum(w.y, 1.0)
+    return float(np.max(y * np.log(y) + y + np.array([math.lgamma(v + 1) for v in y])))
+
+
+@pytest.mark.parametrize("M,n,ppt", [(128, 37, 0), (100, 13, 0), (1, 5, 0), (1024, 9, 0),
+                                     (4096, 3, 0), (256, 11, 1), (256, 11, 2), (512, 7, 8)])
+def test_lg_fp64_bit_exact_ancestors(S, M, n, ppt):
+    w = I.workload("lg_t50_n64", M=M, N=n)
+    th = I.theta_near_prior(w, n, seed=M + n)
+    (ll, delta, anc), ref = _run(S, w, th, k=3, ppt=ppt)
+    for i in range(n):
+        r_ll, r_delta, r_anc = ref[i]
+        assert np.array_equal(anc[i], r_anc), f"filter {i}: ancestors differ"
+        assert rel_err(delta[i], r_delta, 10.0) < 1e-12
+        assert rel_err(ll[i], r_ll, 10.0 * w.T) < 1e-12
+
+
+@pytest.mark.parametrize("M,n,T", [(512, 9, 100), (200, 5, 60), (128, 17, 40)])
+def test_seir_fp64_bit_exact_ancestors(S, M, n, T):
+    w = I.workload("seir_t100_n1024", M=M, N=n, T=T, precision=I.PREC_FP64)
+    th = I.theta_near_prior(w, n, seed=M + n, spread=0.3)
+    (ll, delta, anc), ref = _run(S, w, th, k=2)
+    sc = _obs_scale(w)
+    for i in range(n):
+        r_ll, r_delta, r_anc = ref[i]
+        assert np.array_equal(anc[i], r_anc), f"filter {i}: ancestors differ"
+        assert rel_err(delta[i], r_delta, sc) < 1e-12
+        assert rel_err(ll[i], r_ll, sc * T) < 1e-12
+
+
+def _first_divergence(anc, r_anc):
+    rows = np.flatnonzero(np.any(anc != r_anc, axis=1))
+    return int(rows[0]) if rows.size else anc.shape[0]
+
+
+@pytest.mark.parametrize("model", ["lg", "seir"])
+def test_fp32_particles(S, model):
+    if model == "lg":
+        w = I.workload("lg_t50_n64", M=512, N=24, precision=I.PREC_MIXED)
+        th = I.theta_near_prior(w, 24, seed=5)
+    else:
+        w = I.workload("seir_t100_n1024", M=512, N=24, T=60)
+        th = I.theta_near_prior(w, 24, seed=5, spread=0.3)
+    (ll, delta, anc), ref = _run(S, w, th, k=1)
+    sc = _obs_scale(w)
+    same = 0
+    for i in range(24):
+        r_ll, r_delta, r_anc = ref[i]
+        # step 1: identical inputs, one step of FP32 arithmetic
+        assert rel_err(delta[i, :1], r_delta[:1], max(1.0, abs(r_delta[0]))) < 2e-5
+        t_div = _first_divergence(anc[i], r_anc)
+        # before the first differing ancestor: FP32 state drift, relative 1e-6 per step
+        # of the observation-term magnitude at most
+        upto = t_div + 1
+        drift = 1e-6 * np.arange(1, upto + 1) * (sc if model == "seir" else 10.0)
+        assert np.all(np.abs(delta[i, :upto] - r_delta[:upto]) <= drift + 2e-5)
+        same += t_div == anc.shape[1]
+    # quantised-weight flips are rare (about M 2^-23 per slot and step)
+    assert same >= 12, same
+
+
+def test_degenerate_filter_returns_minus_inf(S):
+    w = I.workload("lg_t50_n64", M=64, N=3)
+    th = np.array([[0.5, 0.0, np.nan], [0.5, 0.0, 0.0], [np.nan, 0.0, 0.0]])
+    ctx = S.SMC2(S.make_config(w), w.y)
+    ll = ctx.pf_loglik(soa(th), iteration=1).cpu().numpy()
+    assert ll[0] == -np.inf and ll[2] == -np.inf and np.isfinite(ll[1])
+    ctx.sync()
+
+
+def test_frozen_beta_seir_exact_in_fp32(S):
+    # sigma_rw = 0: all particles identical, log p = sum_t log Poisson(y_t; lambda_t)
+    w = I.workload("seir_t100_n1024", M=256, N=2, T=50)
+    th = np.array([[math.log(0.55), -np.inf, math.log(0.22), math.log(0.21)]] * 2)
+    ctx = S.SMC2(S.make_config(w), w.y)
+    ll = ctx.pf_loglik(soa(th), iteration=1).cpu().numpy()
+    ref = O.pf_loglik(O.config_from(w), th[0], w.y, 1, 0)
+    assert abs(ll[0] - ref) <= 1e-4 * abs(ref)
+    assert ll[0] == ll[1]

@@ -1,0 +1,137 @@
+"""Whole SMC^2 iterations on the device against the oracle (Sec. IV).
+
+FP64 runs follow the oracle's random stream, so the resampling decisions and
+indices agree exactly and every statistic agrees to rounding: relative 1e-12
+on log-weight-like quantities (scaled by their magnitude, 1e-12 |log w| being
+the rounding floor of sums of logs), and the ESS and estimates within the
+error that this absolute log-weight error induces."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2311_12973_gb300 import inputs as I
+
+from gpu_util import rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def S():
+    from paper_2311_12973_gb300 import smc2
+    return smc2
+
+
+def _compare_stats(g, o, scale):
+    assert g["k"] == o["k"] and g["resampled"] == o["resampled"], (g, o)
+    assert g["lk_fallback"] == o["lk_fallback"], (g, o)
+    for key in ("lse", "lse2", "logz"):
+        assert rel_err(g[key], o[key], scale) < 1e-12, (key, g[key], o[key])
+    assert rel_err(g["ess"], o["ess"]) < 1e-9, (g["ess"], o["ess"])
+    assert rel_err(g["est"], o["est"], 1.0) < 1e-9, (g["est"], o["est"])
+
+
+def _compare_state(S_ctx, ref, scale):
+    k, th, lp, ll, lw = S_ctx.get_state()
+    assert k == ref.k
+    assert rel_err(th, ref.theta, 1.0) < 1e-10
+    assert rel_err(lp, ref.logprior, 10.0) < 1e-12
+    assert rel_err(ll, ref.loglik, scale) < 1e-12
+    assert rel_err(lw, ref.logw, scale) < 1e-12
+
+
+CASES = {
+    "lg_cfg1": dict(name="lg_t50_n64"),
+    "lg_forward": dict(name="lg_t50_n64", lkernel=I.LK_FORWARD, N=96, K=6),
+    "lg_ragged": dict(name="lg_t50_n64", N=300, M=100, T=20, K=4),
+    "seir_fp64": dict(name="seir_t100_n1024", N=64, M=128, T=40, K=5, precision=I.PREC_FP64),
+    "lg_tiny": dict(name="lg_t50_n64", N=1, M=1, T=1, K=3),
+}
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_fp64_run_matches_oracle(S, case):
+    kw = dict(CASES[case])
+    w = I.workload(kw.pop("name"), **kw)
+    ctx = S.SMC2(S.make_config(w), w.y)
+    stats = ctx.run(w.K)
+    ref = O.SMC2(O.config_from(w), w.y).run(w.K)
+    scale = max(10.0, float(np.max(np.abs(ref.logw[np.isfinite(ref.logw)]))))
+    for k in range(w.K):
+        _compare_stats(stats[k][0], ref.stats[k], scale)
+    _compare_state(ctx, ref, scale)
+    mean, logz, ess_sum = ctx.estimate()
+    ref_mean, _ = ref.recycled()
+    assert rel_err(mean, ref_mean, 1.0) < 1e-9
+    assert rel_err(logz, ref.stats[-1]["logz"], scale) < 1e-12
+    assert rel_err(ess_sum, sum(s["ess"] for s in ref.stats)) < 1e-9
+    ctx.close()
+
+
+@pytest.mark.parametrize("lk", [I.LK_GAUSS, I.LK_FORWARD])
+@pytest.mark.parametrize("name", ["lg_t50_n64", "seir_t100_n1024"])
+def test_stagewise_iteration_from_oracle_state(S, name, lk):
+    """The oracle's population after iteration k is loaded into the context;
+    one device iteration must equal the oracle's iteration k+1."""
+    kw = dict(N=128, M=64, T=30, K=4, lkernel=lk, precision=I.PREC_FP64)
+    w = I.workload(name, **kw)
+    ref = O.SMC2(O.config_from(w, ess_frac=0.3), w.y).run(2)
+    ctx = S.SMC2(S.make_config(w, ess_frac=0.3), w.y)
+    ctx.set_state(ref.k, ref.theta, ref.logprior, ref.loglik, ref.logw)
+    g = ctx.run(1)[0][0]
+    o = ref.step()
+    scale = max(10.0, float(np.max(np.abs(ref.logw[np.isfinite(ref.logw)]))))
+    _compare_stats(g, o, scale)
+    _compare_state(ctx, ref, scale)
+    ctx.close()
+
+
+def test_checkpoint_resume_is_bit_identical(S):
+    w = I.workload("lg_t50_n64", N=128, K=8)
+    a = S.SMC2(S.make_config(w), w.y)
+    full = a.run(w.K)
+    mean_a, logz_a, ess_a = a.estimate()
+    b = S.SMC2(S.make_config(w), w.y)
+    b.run(5)
+    k, th, lp, ll, lw = b.get_state()
+    hist, kh = b.raw_history()
+    b.close()
+    c = S.SMC2(S.make_config(w), w.y)
+    c.set_state(k, th, lp, ll, lw)
+    c.set_history(hist, kh)
+    rest = c.run(w.K - 5)
+    for i in range(w.K - 5):
+        assert rest[i][0]["lse"] == full[5 + i][0]["lse"]
+        assert np.array_equal(rest[i][0]["est"], full[5 + i][0]["est"])
+    mean_c, logz_c, ess_c = c.estimate()
+    assert np.array_equal(mean_a, mean_c) and logz_a == logz_c and ess_a == ess_c
+    sa, sc = a.get_state(), c.get_state()
+    for x, y in zip(sa[1:], sc[1:]):
+        assert np.array_equal(x, y)
+
+
+def test_run_state_errors(S):
+    w = I.workload("lg_t50_n64", N=16, M=16, T=5, K=2)
+    ctx = S.SMC2(S.make_config(w), w.y)
+    ctx.run(2)
+    with pytest.raises(S.SMC2Error) as e:
+        ctx.run(1)
+    assert e.value.status == S.ESTATE
+    ctx.reset(w.seed)
+    again = ctx.run(2)
+    ctx.reset(w.seed + 1)
+    other = ctx.run(2)
+    assert again[1][0]["lse"] != other[1][0]["lse"]
+
+
+def test_nonfinite_outer_weights_reported(S):
+    # every observation impossible under every theta: y = nan makes all PF weights vanish
+    w = I.workload("lg_t50_n64", N=16, M=16, T=5, K=1)
+    y = np.full(5, np.nan)
+    ctx = S.SMC2(S.make_config(w), y)
+    with pytest.raises(S.SMC2Error) as e:
+        ctx.run(1)
+    assert e.value.status == S.ENONFINITE
