@@ -61,7 +61,7 @@ enum { SMC2_PROP_RW = 0, SMC2_PROP_MLP = 1 };
 enum { SMC2_LK_FORWARD = 0, SMC2_LK_GAUSS_OPT = 1 };
 
 #define SMC2_MAX_D 8
-#define SMC2_MAX_M 4096
+#define SMC2_MAX_M 4096     /* particles per filter; M > 2048 uses 8 particles per thread */
 #define SMC2_MAX_N 16384
 #define SMC2_MAX_DATASETS 4096
 
@@ -223,6 +223,11 @@ smc2_status smc2_get_timing(smc2_ctx* ctx, double* pf_ms, int64_t* pf_launches,
 
 /* Release the context and its device workspace (synchronises its stream). */
 void smc2_destroy(smc2_ctx* ctx);
+
+/* The last CUDA runtime failure seen by this thread inside the library, as
+ * "call: error name (description)", or "" (thread-local static storage).
+ * Diagnostic companion of SMC2_ECUDA / SMC2_ENOMEM. */
+const char* smc2_last_error_string(void);
 
 /* Human-readable name of a status code (static storage). */
 const char* smc2_status_string(smc2_status s);

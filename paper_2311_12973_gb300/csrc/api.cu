@@ -4,6 +4,7 @@
 // build the particle-filter work list, enqueue kernels on the context stream
 // and capture iterations into CUDA graphs.  No step of the sampler runs here.
 #include <algorithm>
+#include <cstdio>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -72,10 +73,18 @@ smc2_status map_cuda(cudaError_t e) {
   return SMC2_ECUDA;
 }
 
+thread_local char g_last_error[256] = "";
+
+smc2_status record_cuda(cudaError_t e, const char* what) {
+  snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%s)", what, cudaGetErrorName(e),
+           cudaGetErrorString(e));
+  return map_cuda(e);
+}
+
 #define SMC2_TRY(expr)                                      \
   do {                                                      \
     cudaError_t _e = (expr);                                \
-    if (_e != cudaSuccess) return map_cuda(_e);             \
+    if (_e != cudaSuccess) return record_cuda(_e, #expr);   \
   } while (0)
 
 smc2_status status_from_bits(int bits) {
@@ -124,7 +133,7 @@ int default_ppt(const smc2_ctx* c) {
   for (int m : c->M) mx = std::max(mx, m);
   // four particles per thread keeps a 1024-particle filter in one 256-thread CTA
   int ppt = 4;
-  while (pf_group_threads(ppt, mx) > 1024 && ppt < 8) ppt *= 2;
+  while (pf_group_threads(ppt, mx) > kPfMaxBlock && ppt < 8) ppt *= 2;
   return ppt;
 }
 
@@ -329,6 +338,8 @@ bool bad_ds(const smc2_ctx* c, int d) { return !c || d < 0 || d >= c->n_ds; }
 
 extern "C" {
 
+const char* smc2_last_error_string(void) { return g_last_error; }
+
 const char* smc2_status_string(smc2_status s) {
   switch (s) {
     case SMC2_OK: return "ok";
@@ -382,12 +393,14 @@ smc2_status smc2_init(const smc2_config* cfg, const double* y, void* stream, smc
   c->ppt = default_ppt(c);
   int max_gt = 32;
   for (int m : c->M) max_gt = std::max(max_gt, pf_group_threads(c->ppt, m));
-  if (max_gt > 1024) return fail(SMC2_EINVAL);
+  if (max_gt > kPfMaxBlock) return fail(SMC2_EINVAL);
   c->pf_block = std::max(256, max_gt);
   size_t smem = 0;
   for (int m : c->M) smem = std::max(smem, pf_smem_bytes(c->precision, c->model, c->ppt, c->pf_block, m));
   c->pf_smem = smem;
-  if (pf_configure(c->precision, c->model, c->ppt, smem) != cudaSuccess) return fail(SMC2_EINVAL);
+  if (smem > 227 * 1024) return fail(SMC2_EINVAL);
+  if (cudaError_t e = pf_configure(c->precision, c->model, c->ppt, smem); e != cudaSuccess)
+    return fail(record_cuda(e, "pf_configure"));
   std::vector<int4> wus;
   build_work_units(c, wus);
   c->n_wus = (int)wus.size();

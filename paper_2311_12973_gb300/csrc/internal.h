@@ -19,6 +19,7 @@
 namespace smc2 {
 
 constexpr int kOuterBlock = 256;                       // threads of the outer kernels
+constexpr int kPfMaxBlock = 512;                       // threads of a particle-filter CTA, at most
 constexpr int kPartStride = 160;                       // >= 1 + 2D + 2D(2D+1)/2 for D <= 8
 constexpr int kStatStride = 16;                        // >= 3 + D
 

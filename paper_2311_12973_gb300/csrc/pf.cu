@@ -312,7 +312,7 @@ __device__ __forceinline__ void run_filter(const PFJob& J, const PFModel& mdl, i
 }
 
 template <typename R, int MODEL, int PPT>
-__global__ void pf_kernel(PFLaunch L) {
+__global__ void __launch_bounds__(kPfMaxBlock) pf_kernel(PFLaunch L) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_wu;
   constexpr int NS = ModelDims<MODEL>::NS;

@@ -50,7 +50,10 @@ class IterStats(C.Structure):
 class SMC2Error(RuntimeError):
     def __init__(self, status: int, what: str):
         self.status = status
-        super().__init__(f"{what}: {status_string(status)} ({status})")
+        detail = ""
+        if status in (ECUDA, ENOMEM):
+            detail = " [" + lib.smc2_last_error_string().decode() + "]"
+        super().__init__(f"{what}: {status_string(status)} ({status}){detail}")
 
 
 def _load() -> C.CDLL:
@@ -82,6 +85,7 @@ def _load() -> C.CDLL:
                              C.POINTER(C.c_int64), C.c_int], st),
         "smc2_destroy": ([ctx], None),
         "smc2_status_string": ([st], C.c_char_p),
+        "smc2_last_error_string": ([], C.c_char_p),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)

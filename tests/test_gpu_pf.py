@@ -46,8 +46,12 @@ def _obs_scale(w):
 @pytest.mark.parametrize("M,n,ppt", [(128, 37, 0), (100, 13, 0), (1, 5, 0), (1024, 9, 0),
                                      (4096, 3, 0), (256, 11, 1), (256, 11, 2), (512, 7, 8)])
 def test_lg_fp64_bit_exact_ancestors(S, M, n, ppt):
+    # |phi| < 1: a stationary model.  With |phi| > 1 the state grows like |phi|^t
+    # and one-ulp differences between libm and CUDA (FMA contraction, exp/log)
+    # are amplified by the same factor, so no fixed tolerance applies there.
     w = I.workload("lg_t50_n64", M=M, N=n)
     th = I.theta_near_prior(w, n, seed=M + n)
+    th[:, 0] = np.clip(th[:, 0], -0.95, 0.95)
     (ll, delta, anc), ref = _run(S, w, th, k=3, ppt=ppt)
     for i in range(n):
         r_ll, r_delta, r_anc = ref[i]
@@ -84,7 +88,7 @@ def test_fp32_particles(S, model):
         th = I.theta_near_prior(w, 24, seed=5, spread=0.3)
     (ll, delta, anc), ref = _run(S, w, th, k=1)
     sc = _obs_scale(w)
-    same = 0
+    diffs = []
     for i in range(24):
         r_ll, r_delta, r_anc = ref[i]
         # step 1: identical inputs, one step of FP32 arithmetic
@@ -95,9 +99,12 @@ def test_fp32_particles(S, model):
         upto = t_div + 1
         drift = 1e-6 * np.arange(1, upto + 1) * (sc if model == "seir" else 10.0)
         assert np.all(np.abs(delta[i, :upto] - r_delta[:upto]) <= drift + 2e-5)
-        same += t_div == anc.shape[1]
-    # quantised-weight flips are rare (about M 2^-23 per slot and step)
-    assert same >= 12, same
+        diffs.append(ll[i] - r_ll)
+    # After the first differing ancestor (FP32 quantised weights put a threshold
+    # on the other side about M^2 T 2^-23 times per filter) the two filters are
+    # independent estimates of the same likelihood: no systematic offset.
+    d = np.array(diffs)
+    assert abs(d.mean()) <= 4.0 * d.std() / np.sqrt(len(d)) + 1e-6, (d.mean(), d.std())
 
 
 def test_degenerate_filter_returns_minus_inf(S):
