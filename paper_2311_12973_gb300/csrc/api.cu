@@ -274,9 +274,9 @@ void fill_params(smc2_ctx* c) {
 smc2_status enqueue_iteration(smc2_ctx* c, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1) {
   SMC2_TRY(outer_propose(c->op, c->max_nblk, s));
   SMC2_TRY(cudaMemsetAsync(c->d_wu_counter, 0, sizeof(int), s));
-  if (ev0) SMC2_TRY(cudaEventRecord(ev0, s));
+  if (ev0) SMC2_TRY(cudaEventRecordWithFlags(ev0, s, cudaEventRecordExternal));
   SMC2_TRY(pf_launch(c->precision, c->model, c->ppt, c->pf_grid, c->pf_block, c->pf_smem, c->pl, s));
-  if (ev1) SMC2_TRY(cudaEventRecord(ev1, s));
+  if (ev1) SMC2_TRY(cudaEventRecordWithFlags(ev1, s, cudaEventRecordExternal));
   SMC2_TRY(outer_weights(c->op, c->max_nblk, s));
   SMC2_TRY(outer_quantise(c->op, c->max_nblk, s));
   SMC2_TRY(outer_resample(c->op, c->max_nblk, c->max_N, s));
