@@ -241,6 +241,7 @@ def main():
     wr = w.with_(seed=w.seed + 1000 * rank)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     ctx = S.SMC2(S.make_config(wr), wr.y)
+    shape = ctx.launch_shape()
     props = torch.cuda.get_device_properties(local)
 
     with ClockSampler(local) as clk:
@@ -306,6 +307,7 @@ def main():
                      "ops_per_particle_step": ALG_OPS_PER_PARTICLE_STEP[wr.model],
                      "pf_ms_per_launch": pf_avg_ms, "pf_launches": pf_n,
                      "pf_share_of_step": pf_ms / max(sum(ms), 1e-9),
+                     "launch_shape": shape,
                      "peak_basis": f"{props.multi_processor_count} SMs x 128 lanes x {sm_mhz:.0f} MHz "
                                    "(max SM clock of MEASURED_PEAKS.json)"},
         "e2e": {"value": units_per_step * world / (e2e_step * 1e-3), "unit": UNIT,

@@ -83,6 +83,10 @@ typedef struct smc2_ctx smc2_ctx; /* opaque; owns its device workspace */
  *   exposed and infectious, Euler substeps per day, floor of the Poisson mean).
  * ppt: particles per thread of the particle-filter kernel (0 = pick by the
  *   built-in tuner; otherwise 1, 2, 4 or 8).
+ * cta_threads: threads per particle-filter CTA (0 = pick by the tuner;
+ *   otherwise a multiple of 32 up to 512 that holds whole filter groups).
+ *   The tuner times every valid (ppt, cta_threads) pair on the context's own
+ *   work list, prior draws of theta and min(T, 16) steps, during smc2_init.
  * n_datasets: number of independent datasets run together (<= 1: one).
  * ds_N, ds_M, ds_T: host arrays of n_datasets sizes (NULL when n_datasets <= 1). */
 typedef struct {
@@ -94,6 +98,7 @@ typedef struct {
   double npop, e0, i0, lambda_floor;
   int n_sub;
   int ppt;
+  int cta_threads;
   int n_datasets;
   const int* ds_N;
   const int* ds_M;
@@ -220,6 +225,10 @@ smc2_status smc2_sync(smc2_ctx* ctx);
 smc2_status smc2_set_timing(smc2_ctx* ctx, int enable);
 smc2_status smc2_get_timing(smc2_ctx* ctx, double* pf_ms, int64_t* pf_launches,
                             int64_t* kernel_launches, int reset);
+
+/* The particle-filter launch shape in use: particles per thread, threads per
+ * CTA, CTAs per launch (host outputs, any may be NULL). */
+smc2_status smc2_get_launch_shape(smc2_ctx* ctx, int* ppt, int* cta_threads, int* grid);
 
 /* Release the context and its device workspace (synchronises its stream). */
 void smc2_destroy(smc2_ctx* ctx);

@@ -35,10 +35,10 @@ struct TimedGraph {
 struct smc2_ctx {
   smc2_config cfg{};
   int n_ds = 1, D = 0, K = 0, precision = 0, model = 0;
-  std::vector<int> N, M, T, nblk;
+  std::vector<int> N, M, T, nblk, nblk_res;
   std::vector<size_t> yoff;
   size_t ytot = 0;
-  int max_N = 0, max_nblk = 0;
+  int max_N = 0, max_nblk = 0, max_nblk_res = 0;
   cudaStream_t stream = nullptr, cap_stream = nullptr;
   int device = 0, sms = 0;
   char* arena = nullptr;
@@ -114,6 +114,8 @@ smc2_status validate(const smc2_config* c) {
       return SMC2_EINVAL;
   }
   if (c->ppt != 0 && c->ppt != 1 && c->ppt != 2 && c->ppt != 4 && c->ppt != 8) return SMC2_EINVAL;
+  if (c->cta_threads != 0 && (c->cta_threads < 32 || c->cta_threads > kPfMaxBlock || c->cta_threads % 32))
+    return SMC2_EINVAL;
   const int nd = c->n_datasets <= 1 ? 1 : c->n_datasets;
   if (nd > SMC2_MAX_DATASETS) return SMC2_EINVAL;
   if (c->n_datasets > 1 && (!c->ds_N || !c->ds_M || !c->ds_T)) return SMC2_EINVAL;
@@ -123,18 +125,10 @@ smc2_status validate(const smc2_config* c) {
     const int t = c->n_datasets > 1 ? c->ds_T[d] : c->T;
     if (n < 1 || n > SMC2_MAX_N || m < 1 || m > SMC2_MAX_M || t < 1 || t > (1 << 24))
       return SMC2_EINVAL;
+    const int gt = pf_group_threads(c->ppt ? c->ppt : 8, m);
+    if (gt > (c->cta_threads ? c->cta_threads : kPfMaxBlock)) return SMC2_EINVAL;
   }
   return SMC2_OK;
-}
-
-int default_ppt(const smc2_ctx* c) {
-  if (c->cfg.ppt) return c->cfg.ppt;
-  int mx = 0;
-  for (int m : c->M) mx = std::max(mx, m);
-  // four particles per thread keeps a 1024-particle filter in one 256-thread CTA
-  int ppt = 4;
-  while (pf_group_threads(ppt, mx) > kPfMaxBlock && ppt < 8) ppt *= 2;
-  return ppt;
 }
 
 template <typename Tp>
@@ -168,6 +162,8 @@ size_t layout(smc2_ctx* c, char* base) {
     s.M = c->M[d];
     s.T = c->T[d];
     s.nblk = c->nblk[d];
+    s.nblk_res = c->nblk_res[d];
+    s.logN = std::log((double)N);
     s.thA = carve<double>(p, (size_t)D * N);
     s.thB = carve<double>(p, (size_t)D * N);
     s.lpA = carve<double>(p, N);
@@ -191,8 +187,21 @@ size_t layout(smc2_ctx* c, char* base) {
   }
   c->d_ds = carve<DSDev>(p, c->n_ds);
   c->d_jobs = carve<PFJob>(p, c->n_ds);
-  c->d_wus = carve<int4>(p, std::max(c->n_wus, 1));
+  size_t wu_cap = 0;
+  for (int n : c->N) wu_cap += (size_t)n;
+  c->d_wus = carve<int4>(p, wu_cap);
   return (size_t)(p - start) + 256;
+}
+
+// A launch shape is valid when every dataset's filter group fits the CTA and,
+// for groups wider than a warp, at most 15 groups share it (named barriers 1..15).
+bool shape_valid(const smc2_ctx* c, int ppt, int block) {
+  for (int m : c->M) {
+    const int gt = pf_group_threads(ppt, m);
+    if (gt > block) return false;
+    if (gt > 32 && block / gt > 15) return false;
+  }
+  return true;
 }
 
 void build_work_units(smc2_ctx* c, std::vector<int4>& wus) {
@@ -207,6 +216,74 @@ void build_work_units(smc2_ctx* c, std::vector<int4>& wus) {
     const double ca = (double)c->T[a.x] * c->M[a.x] * a.z, cb = (double)c->T[b.x] * c->M[b.x] * b.z;
     return ca > cb;
   });
+}
+
+smc2_status apply_shape(smc2_ctx* c, int ppt, int block, bool upload) {
+  c->ppt = ppt;
+  c->pf_block = block;
+  size_t smem = 0;
+  for (int m : c->M) smem = std::max(smem, pf_smem_bytes(c->precision, c->model, ppt, block, m));
+  if (smem > 227 * 1024) return SMC2_EINVAL;
+  c->pf_smem = smem;
+  SMC2_TRY(pf_configure(c->precision, c->model, ppt, smem));
+  std::vector<int4> wus;
+  build_work_units(c, wus);
+  c->n_wus = (int)wus.size();
+  const int occ = pf_occupancy(c->precision, c->model, ppt, block, smem);
+  if (occ < 1) return SMC2_EINVAL;
+  c->pf_grid = std::min(c->n_wus, occ * c->sms);
+  c->pl.n_wu = c->n_wus;
+  if (upload)
+    SMC2_TRY(cudaMemcpyAsync(c->d_wus, wus.data(), wus.size() * sizeof(int4), cudaMemcpyHostToDevice,
+                             c->stream));
+  return SMC2_OK;
+}
+
+// Launch-shape tuner: time every valid (particles per thread, CTA threads) pair
+// on the context's own work list (prior draws of theta, min(T, 16) steps).
+smc2_status choose_launch_shape(smc2_ctx* c) {
+  std::vector<std::pair<int, int>> cand;
+  for (int ppt : {1, 2, 4, 8}) {
+    if (c->cfg.ppt && ppt != c->cfg.ppt) continue;
+    for (int block = 32; block <= kPfMaxBlock; block += 32) {
+      if (c->cfg.cta_threads && block != c->cfg.cta_threads) continue;
+      if (!c->cfg.cta_threads && (block & (block - 1))) continue;  // powers of two when tuning
+      if (shape_valid(c, ppt, block)) cand.push_back({ppt, block});
+    }
+  }
+  if (cand.empty()) return SMC2_EINVAL;
+  if (cand.size() == 1) return apply_shape(c, cand[0].first, cand[0].second, true);
+  cudaStream_t s = c->stream;
+  SMC2_TRY(outer_propose(c->op, c->max_nblk, s));  // k = 1: prior draws into the proposal buffers
+  cudaEvent_t e0, e1;
+  SMC2_TRY(cudaEventCreate(&e0));
+  SMC2_TRY(cudaEventCreate(&e1));
+  float best = 1e30f;
+  std::pair<int, int> pick = cand[0];
+  for (const auto& cb : cand) {
+    if (apply_shape(c, cb.first, cb.second, true) != SMC2_OK) continue;
+    PFLaunch L = c->pl;
+    float ms = 0.f;
+    bool ok = true;
+    for (int rep = 0; rep < 2 && ok; ++rep) {
+      L.t_cap = rep == 0 ? 4 : 16;
+      ok = cudaMemsetAsync(c->d_wu_counter, 0, sizeof(int), s) == cudaSuccess &&
+           cudaEventRecord(e0, s) == cudaSuccess &&
+           pf_launch(c->precision, c->model, c->ppt, c->pf_grid, c->pf_block, c->pf_smem, L, s) ==
+               cudaSuccess &&
+           cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+           cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+      c->kernel_launches++;
+    }
+    if (ok && ms < best) {
+      best = ms;
+      pick = cb;
+    }
+    cudaGetLastError();
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return apply_shape(c, pick.first, pick.second, true);
 }
 
 smc2_status clear_run_state(smc2_ctx* c) {
@@ -247,7 +324,11 @@ void fill_params(smc2_ctx* c) {
   for (int d = 0; d < 8; ++d) {
     P.prior_mean[d] = c->cfg.prior_mean[d];
     P.prior_sd[d] = c->cfg.prior_sd[d];
+    P.inv_prior_sd[d] = d < c->D ? 1.0 / c->cfg.prior_sd[d] : 0.0;
+    P.log_prior_sd[d] = d < c->D ? std::log(c->cfg.prior_sd[d]) : 0.0;
   }
+  P.inv_rw = 1.0 / c->cfg.rw_scale;
+  P.log_rw = std::log(c->cfg.rw_scale);
   P.seed = c->cfg.seed;
   P.k_done = c->d_k;
   P.status = c->d_status;
@@ -279,7 +360,7 @@ smc2_status enqueue_iteration(smc2_ctx* c, cudaStream_t s, cudaEvent_t ev0, cuda
   if (ev1) SMC2_TRY(cudaEventRecordWithFlags(ev1, s, cudaEventRecordExternal));
   SMC2_TRY(outer_weights(c->op, c->max_nblk, s));
   SMC2_TRY(outer_quantise(c->op, c->max_nblk, s));
-  SMC2_TRY(outer_resample(c->op, c->max_nblk, c->max_N, s));
+  SMC2_TRY(outer_resample(c->op, c->max_nblk_res, c->max_N, s));
   return SMC2_OK;
 }
 
@@ -372,6 +453,8 @@ smc2_status smc2_init(const smc2_config* cfg, const double* y, void* stream, smc
     c->M.push_back(cfg->n_datasets > 1 ? cfg->ds_M[d] : cfg->M);
     c->T.push_back(cfg->n_datasets > 1 ? cfg->ds_T[d] : cfg->T);
     c->nblk.push_back((c->N[d] + kOuterBlock - 1) / kOuterBlock);
+    c->nblk_res.push_back((c->N[d] + kResBlock - 1) / kResBlock);
+    c->max_nblk_res = std::max(c->max_nblk_res, c->nblk_res[d]);
     c->yoff.push_back(c->ytot);
     c->ytot += c->T[d];
     c->max_N = std::max(c->max_N, c->N[d]);
@@ -389,29 +472,12 @@ smc2_status smc2_init(const smc2_config* cfg, const double* y, void* stream, smc
   if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
     return fail(SMC2_ECUDA);
 
-  // particle-filter launch shape
-  c->ppt = default_ppt(c);
-  int max_gt = 32;
-  for (int m : c->M) max_gt = std::max(max_gt, pf_group_threads(c->ppt, m));
-  if (max_gt > kPfMaxBlock) return fail(SMC2_EINVAL);
-  c->pf_block = std::max(256, max_gt);
-  size_t smem = 0;
-  for (int m : c->M) smem = std::max(smem, pf_smem_bytes(c->precision, c->model, c->ppt, c->pf_block, m));
-  c->pf_smem = smem;
-  if (smem > 227 * 1024) return fail(SMC2_EINVAL);
-  if (cudaError_t e = pf_configure(c->precision, c->model, c->ppt, smem); e != cudaSuccess)
-    return fail(record_cuda(e, "pf_configure"));
-  std::vector<int4> wus;
-  build_work_units(c, wus);
-  c->n_wus = (int)wus.size();
-  const int occ = std::max(1, pf_occupancy(c->precision, c->model, c->ppt, c->pf_block, smem));
-  c->pf_grid = std::min(c->n_wus, occ * c->sms);
-
   c->arena_bytes = layout(c, nullptr);
   if (cudaMalloc(&c->arena, c->arena_bytes) != cudaSuccess) return fail(SMC2_ENOMEM);
   layout(c, c->arena);
 
   std::vector<PFJob> jobs(c->n_ds);
+  c->n_wus = 0;
   for (int d = 0; d < c->n_ds; ++d) {
     PFJob& j = jobs[d];
     j.theta = c->h_ds[d].thB;
@@ -430,13 +496,13 @@ smc2_status smc2_init(const smc2_config* cfg, const double* y, void* stream, smc
       cudaMemcpyAsync(c->d_ds, c->h_ds.data(), c->n_ds * sizeof(DSDev), cudaMemcpyHostToDevice, s) !=
           cudaSuccess ||
       cudaMemcpyAsync(c->d_jobs, jobs.data(), c->n_ds * sizeof(PFJob), cudaMemcpyHostToDevice, s) !=
-          cudaSuccess ||
-      cudaMemcpyAsync(c->d_wus, wus.data(), wus.size() * sizeof(int4), cudaMemcpyHostToDevice, s) !=
           cudaSuccess)
     return fail(SMC2_ECUDA);
   if ((st = clear_run_state(c)) != SMC2_OK) return fail(st);
   if ((st = compute_obs(c, s)) != SMC2_OK) return fail(st);
   fill_params(c);
+  if ((st = choose_launch_shape(c)) != SMC2_OK) return fail(st);
+  if ((st = clear_run_state(c)) != SMC2_OK) return fail(st);
   if (cudaStreamSynchronize(s) != cudaSuccess) return fail(SMC2_ECUDA);
   *out = c;
   return SMC2_OK;
@@ -627,6 +693,14 @@ smc2_status smc2_philox_normals(uint64_t seed, const uint32_t* ctr, int n, int p
 smc2_status smc2_sync(smc2_ctx* c) {
   if (!c) return SMC2_EINVAL;
   return sticky(c);
+}
+
+smc2_status smc2_get_launch_shape(smc2_ctx* c, int* ppt, int* cta_threads, int* grid) {
+  if (!c) return SMC2_EINVAL;
+  if (ppt) *ppt = c->ppt;
+  if (cta_threads) *cta_threads = c->pf_block;
+  if (grid) *grid = c->pf_grid;
+  return SMC2_OK;
 }
 
 smc2_status smc2_set_timing(smc2_ctx* c, int enable) {

@@ -18,7 +18,8 @@
 
 namespace smc2 {
 
-constexpr int kOuterBlock = 256;                       // threads of the outer kernels
+constexpr int kOuterBlock = 32;                        // threads of the per-sample outer kernels (one warp)
+constexpr int kResBlock = 256;                         // threads of the resampling kernel
 constexpr int kPfMaxBlock = 512;                       // threads of a particle-filter CTA, at most
 constexpr int kPartStride = 160;                       // >= 1 + 2D + 2D(2D+1)/2 for D <= 8
 constexpr int kStatStride = 16;                        // >= 3 + D
@@ -41,7 +42,9 @@ struct IterCur {       // working scalars of the current iteration of one datase
 };
 
 struct DSDev {
-  int N, M, T, nblk;
+  int N, M, T, nblk;   // nblk: blocks of kOuterBlock samples
+  int nblk_res;        // blocks of kResBlock slots
+  double logN;
   double *thA, *thB, *lpA, *lpB, *llA, *llB, *logw, *logq;
   uint64_t* q;
   double* part;        // [nblk][kPartStride]
@@ -62,6 +65,8 @@ struct OuterParams {
   int n_ds, D, lkernel, K;
   double rw_scale, ess_frac;
   double prior_mean[8], prior_sd[8];
+  double inv_prior_sd[8], log_prior_sd[8];   // configuration constants
+  double inv_rw, log_rw;
   uint64_t seed;
   int* k_done;         // completed iterations; the running iteration is k_done + 1
   int* status;
@@ -97,6 +102,8 @@ struct PFLaunch {
   int k_imm;
   int* status;
   PFModel mdl;
+  int t_cap;           // > 0: run at most t_cap steps (launch-shape tuning)
+  int pad;
   PFJob job0;
 };
 
@@ -114,7 +121,7 @@ cudaError_t outer_obs_terms(int precision, int model, const double* y, int T, vo
 cudaError_t outer_propose(const OuterParams& P, int max_nblk, cudaStream_t s);
 cudaError_t outer_weights(const OuterParams& P, int max_nblk, cudaStream_t s);
 cudaError_t outer_quantise(const OuterParams& P, int max_nblk, cudaStream_t s);
-cudaError_t outer_resample(const OuterParams& P, int max_nblk, int max_N, cudaStream_t s);
+cudaError_t outer_resample(const OuterParams& P, int max_nblk_res, int max_N, cudaStream_t s);
 cudaError_t outer_parent_reference(const OuterParams& P, int dataset, cudaStream_t s);
 cudaError_t outer_rebuild_recycling(const OuterParams& P, int dataset, int k, cudaStream_t s);
 cudaError_t resample_systematic_launch(const uint64_t* q, int n, uint32_t U, int32_t* anc,

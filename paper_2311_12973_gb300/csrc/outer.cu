@@ -22,56 +22,26 @@
 
 namespace smc2 {
 
-constexpr int kWarps = kOuterBlock / 32;
-
-__device__ __forceinline__ double block_max(double v, double* sh) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  v = warp_max(v);
-  __syncthreads();
-  if (lane == 0) sh[warp] = v;
-  __syncthreads();
-  double r = sh[0];
-  for (int w = 1; w < kWarps; ++w) r = fmax(r, sh[w]);
-  return r;
-}
-
-// Sum of NV values per thread over the block, written in warp order to out[0..NV).
-template <int NV>
-__device__ __forceinline__ void block_sums(const double (&v)[NV], double* sh /*[kWarps][NV]*/,
-                                           double* out) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  __syncthreads();
-#pragma unroll
-  for (int a = 0; a < NV; ++a) {
-    const double s = warp_sum(v[a]);
-    if (lane == 0) sh[warp * NV + a] = s;
-  }
-  __syncthreads();
-  if (threadIdx.x < NV) {
-    double s = 0.0;
-    for (int w = 0; w < kWarps; ++w) s += sh[w * NV + threadIdx.x];
-    out[threadIdx.x] = s;
-  }
-  __syncthreads();
-}
+constexpr int kResWarps = kResBlock / 32;
+static_assert(kOuterBlock == 32, "the per-sample outer kernels are one warp per block");
 
 __device__ __forceinline__ double log_prior(const OuterParams& P, const double* th) {
   double lp = 0.0;
   for (int d = 0; d < P.D; ++d) {
-    const double r = (th[d] - P.prior_mean[d]) / P.prior_sd[d];
-    lp += -0.5 * kLog2Pi - log(P.prior_sd[d]) - 0.5 * r * r;
+    const double r = (th[d] - P.prior_mean[d]) * P.inv_prior_sd[d];
+    lp += -0.5 * kLog2Pi - P.log_prior_sd[d] - 0.5 * r * r;
   }
   return lp;
 }
 
-// log N(x; mean, sd^2 I)
-__device__ __forceinline__ double iso_logpdf(int D, const double* x, const double* mean, double sd) {
+// log N(x; mean, rw_scale^2 I)
+__device__ __forceinline__ double rw_logpdf(const OuterParams& P, const double* x, const double* mean) {
   double ss = 0.0;
-  for (int d = 0; d < D; ++d) {
-    const double r = (x[d] - mean[d]) / sd;
+  for (int d = 0; d < P.D; ++d) {
+    const double r = (x[d] - mean[d]) * P.inv_rw;
     ss += r * r;
   }
-  return -0.5 * D * kLog2Pi - D * log(sd) - 0.5 * ss;
+  return -0.5 * P.D * kLog2Pi - P.D * P.log_rw - 0.5 * ss;
 }
 
 // log N(a; mu_a + A (b - mu_b), Lc Lc^T)
@@ -173,13 +143,11 @@ __device__ void lk_fit(int D, const double* tot, const double* shift, LKParams* 
 __global__ void __launch_bounds__(kOuterBlock) propose_kernel(OuterParams P) {
   const DSDev& S = P.ds[blockIdx.y];
   if ((int)blockIdx.x >= S.nblk) return;
-  __shared__ double zs[2 * kMaxD][kOuterBlock];
+  __shared__ double zs[kOuterBlock][2 * kMaxD];
   __shared__ double ws[kOuterBlock];
-  __shared__ double shift[2 * kMaxD];
   __shared__ double tot[kPartStride];
-  __shared__ int s_last;
-  const int N = S.N, D = P.D, tid = threadIdx.x;
-  const int i = blockIdx.x * kOuterBlock + tid;
+  const int N = S.N, D = P.D, lane = threadIdx.x;
+  const int i = blockIdx.x * kOuterBlock + lane;
   const uint32_t k = (uint32_t)(*P.k_done + 1);
   const bool act = i < N;
   const uint2 key = seed_key(P.seed);
@@ -204,75 +172,57 @@ __global__ void __launch_bounds__(kOuterBlock) propose_kernel(OuterParams P) {
     for (int d = 0; d < D; ++d) S.thB[(size_t)d * N + i] = b[d];
     const double lp = log_prior(P, b);
     S.lpB[i] = lp;
-    S.logq[i] = (k == 1) ? log_prior(P, b) : iso_logpdf(D, b, a, P.rw_scale);
+    S.logq[i] = (k == 1) ? lp : rw_logpdf(P, b, a);
   }
   if (k == 1 || P.lkernel != LK_GAUSS) return;
 
-  // per-block weighted moments of z = (theta_{k-1}, theta_k) - shift
-  if (tid < D) {
-    shift[tid] = S.thA[(size_t)tid * N];
-    shift[D + tid] = S.thA[(size_t)tid * N];
-  }
-  __syncthreads();
-  const double w = act ? exp(S.logw[i] - S.cur->m_par) : 0.0;
-  ws[tid] = w;
-  for (int r = 0; r < 2 * D; ++r)
-    zs[r][tid] = act ? ((r < D ? a[r] : b[r - D]) - shift[r]) : 0.0;
-  __syncthreads();
+  // weighted moments of z = (theta_{k-1}, theta_k) - shift over this block's samples;
+  // the shift (sample 0's parent) keeps the one-pass covariance well conditioned
+  double shift[kMaxD];
+  for (int d = 0; d < D; ++d) shift[d] = S.thA[(size_t)d * N];
+  ws[lane] = act ? exp(S.logw[i] - S.cur->m_par) : 0.0;
+  for (int r = 0; r < 2 * D; ++r) zs[lane][r] = act ? ((r < D ? a[r] : b[r - D]) - shift[r % D]) : 0.0;
+  __syncwarp();
   const int NM = n_moments(D);
-  if (tid < NM) {
-    int kind, r = 0, s = 0;
-    if (tid == 0) {
-      kind = 0;
-    } else if (tid <= 2 * D) {
-      kind = 1;
-      r = tid - 1;
-    } else {
-      kind = 2;
-      int slot = tid - 1 - 2 * D;
+  for (int mo = lane; mo < NM; mo += 32) {
+    int r = -1, q = -1;
+    if (mo >= 1 && mo <= 2 * D) {
+      r = mo - 1;
+    } else if (mo > 2 * D) {
+      int slot = mo - 1 - 2 * D;
       r = 0;
       while (slot >= 2 * D - r) {
         slot -= 2 * D - r;
         ++r;
       }
-      s = r + slot;
+      q = r + slot;
     }
-    double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;
-    for (int e = 0; e < kOuterBlock; e += 4) {
-      double v0 = ws[e], v1 = ws[e + 1], v2 = ws[e + 2], v3 = ws[e + 3];
-      if (kind >= 1) {
-        v0 *= zs[r][e];
-        v1 *= zs[r][e + 1];
-        v2 *= zs[r][e + 2];
-        v3 *= zs[r][e + 3];
-      }
-      if (kind == 2) {
-        v0 *= zs[s][e];
-        v1 *= zs[s][e + 1];
-        v2 *= zs[s][e + 2];
-        v3 *= zs[s][e + 3];
-      }
-      acc0 += v0;
-      acc1 += v1;
-      acc2 += v2;
-      acc3 += v3;
+    double acc = 0.0;
+    for (int e = 0; e < kOuterBlock; ++e) {
+      double v = ws[e];
+      if (r >= 0) v *= zs[e][r];
+      if (q >= 0) v *= zs[e][q];
+      acc += v;
     }
-    S.part[(size_t)blockIdx.x * kPartStride + tid] = (acc0 + acc1) + (acc2 + acc3);
+    S.part[(size_t)blockIdx.x * kPartStride + mo] = acc;
   }
   __threadfence();
-  __syncthreads();
-  if (tid == 0) s_last = (atomicAdd(&S.tickets[0], 1u) == (unsigned)(S.nblk - 1));
-  __syncthreads();
-  if (!s_last) return;
+  __syncwarp();
+  unsigned ticket = 0;
+  if (lane == 0) ticket = atomicAdd(&S.tickets[0], 1u);
+  ticket = __shfl_sync(0xffffffffu, ticket, 0);
+  if (ticket != (unsigned)(S.nblk - 1)) return;
   __threadfence();
-  if (tid < NM) {
+  for (int mo = lane; mo < NM; mo += 32) {
     double t = 0.0;
-    for (int bb = 0; bb < S.nblk; ++bb) t += __ldcg(&S.part[(size_t)bb * kPartStride + tid]);
-    tot[tid] = t;
+    for (int bb = 0; bb < S.nblk; ++bb) t += __ldcg(&S.part[(size_t)bb * kPartStride + mo]);
+    tot[mo] = t;
   }
-  __syncthreads();
-  if (tid == 0) {
-    lk_fit(D, tot, shift, S.lk);
+  __syncwarp();
+  if (lane == 0) {
+    double sh2[2 * kMaxD];
+    for (int r = 0; r < 2 * D; ++r) sh2[r] = shift[r % D];
+    lk_fit(D, tot, sh2, S.lk);
     S.tickets[0] = 0;
   }
 }
@@ -290,11 +240,8 @@ __device__ __forceinline__ void accumulate_recycling(double* rec, double* est_re
 __global__ void __launch_bounds__(kOuterBlock) weights_kernel(OuterParams P) {
   const DSDev& S = P.ds[blockIdx.y];
   if ((int)blockIdx.x >= S.nblk) return;
-  __shared__ double shm[kWarps * (2 + kMaxD)];
-  __shared__ double sums[2 + kMaxD];
-  __shared__ int s_last;
-  const int N = S.N, D = P.D, tid = threadIdx.x;
-  const int i = blockIdx.x * kOuterBlock + tid;
+  const int N = S.N, D = P.D, lane = threadIdx.x;
+  const int i = blockIdx.x * kOuterBlock + lane;
   const uint32_t k = (uint32_t)(*P.k_done + 1);
   const bool act = i < N;
   double lw = -HUGE_VAL, b[kMaxD];
@@ -307,67 +254,81 @@ __global__ void __launch_bounds__(kOuterBlock) weights_kernel(OuterParams P) {
       double a[kMaxD];
       for (int d = 0; d < D; ++d) a[d] = S.thA[(size_t)d * N + i];
       const bool gauss = P.lkernel == LK_GAUSS && !S.lk->fallback;
-      const double logL = gauss ? lk_logpdf(D, *S.lk, a, b) : iso_logpdf(D, a, b, P.rw_scale);
+      const double logL = gauss ? lk_logpdf(D, *S.lk, a, b) : rw_logpdf(P, a, b);
       lw = S.logw[i] + (lpB + llB) - (S.lpA[i] + S.llA[i]) + logL - lq;  // Eq. (20)
     }
     if (isnan(lw)) lw = -HUGE_VAL;
     S.logw[i] = lw;
   }
-  const double mb = block_max(lw, shm);
-  double v[2 + kMaxD];
+  const double mb = warp_max(lw);
   const double e = (act && lw > -HUGE_VAL) ? exp(lw - mb) : 0.0;
-  v[0] = e;
-  v[1] = e * e;
-  for (int d = 0; d < kMaxD; ++d) v[2 + d] = (d < D && act) ? e * b[d] : 0.0;
-  block_sums<2 + kMaxD>(v, shm, sums);
-  if (tid == 0) {
-    double* ps = S.part_st + (size_t)blockIdx.x * kStatStride;
-    ps[0] = mb;
-    for (int a = 0; a < 2 + D; ++a) ps[1 + a] = sums[a];
+  double* ps = S.part_st + (size_t)blockIdx.x * kStatStride;
+  {
+    const double s1 = warp_sum(e), s2 = warp_sum(e * e);
+    if (lane == 0) {
+      ps[0] = mb;
+      ps[1] = s1;
+      ps[2] = s2;
+    }
+    for (int d = 0; d < D; ++d) {
+      const double sd = warp_sum(act ? e * b[d] : 0.0);
+      if (lane == 0) ps[3 + d] = sd;
+    }
   }
   __threadfence();
-  __syncthreads();
-  if (tid == 0) s_last = (atomicAdd(&S.tickets[1], 1u) == (unsigned)(S.nblk - 1));
-  __syncthreads();
-  if (!s_last || tid != 0) return;
+  __syncwarp();
+  unsigned ticket = 0;
+  if (lane == 0) ticket = atomicAdd(&S.tickets[1], 1u);
+  ticket = __shfl_sync(0xffffffffu, ticket, 0);
+  if (ticket != (unsigned)(S.nblk - 1)) return;
   __threadfence();
+  // combine the block partials: lane l takes blocks l, l+32, ... in order, then a fixed shuffle tree
   double m = -HUGE_VAL;
-  for (int bb = 0; bb < S.nblk; ++bb) m = fmax(m, __ldcg(&S.part_st[(size_t)bb * kStatStride]));
+  for (int bb = lane; bb < S.nblk; bb += 32) m = fmax(m, __ldcg(&S.part_st[(size_t)bb * kStatStride]));
+  m = warp_max(m);
   smc2_iter_stats st;
   st.k = (int)k;
   st.dataset = (int)blockIdx.y;
   st.lk_fallback = (k > 1 && P.lkernel == LK_GAUSS) ? S.lk->fallback : 0;
   IterCur* cur = S.cur;
   if (!(m > -HUGE_VAL) || isinf(m) || isnan(m)) {
-    raise_status(P.status, ST_NONFINITE);
-    st.resampled = 0;
-    st.ess = st.lse = st.lse2 = st.logz = NAN;
-    for (int d = 0; d < kMaxD; ++d) st.est[d] = NAN;
-    cur->resample = 0;
-  } else {
-    double s1 = 0.0, s2 = 0.0, sth[kMaxD];
-    for (int d = 0; d < D; ++d) sth[d] = 0.0;
-    for (int bb = 0; bb < S.nblk; ++bb) {
-      const double* ps = S.part_st + (size_t)bb * kStatStride;
-      const double mbb = __ldcg(ps);
-      if (!(mbb > -HUGE_VAL)) continue;
-      const double f = exp(mbb - m);
-      s1 += __ldcg(ps + 1) * f;
-      s2 += __ldcg(ps + 2) * (f * f);
-      for (int d = 0; d < D; ++d) sth[d] += __ldcg(ps + 3 + d) * f;
+    if (lane == 0) {
+      raise_status(P.status, ST_NONFINITE);
+      st.resampled = 0;
+      st.ess = st.lse = st.lse2 = st.logz = NAN;
+      for (int d = 0; d < kMaxD; ++d) st.est[d] = NAN;
+      cur->resample = 0;
+      if ((int)k <= P.K) S.hist[k - 1] = st;
+      S.tickets[1] = 0;
     }
-    st.lse = m + log(s1);
-    st.lse2 = 2.0 * m + log(s2);
-    st.ess = (s1 * s1) / s2;
-    st.logz = st.lse - log((double)N);
-    for (int d = 0; d < kMaxD; ++d) st.est[d] = d < D ? sth[d] / s1 : 0.0;
-    st.resampled = st.ess < P.ess_frac * (double)N;
-    cur->m = m;
-    cur->lse = st.lse;
-    cur->resample = st.resampled;
-    cur->m_par = st.resampled ? st.lse - log((double)N) : m;
-    accumulate_recycling(S.rec, S.est_rec, st.ess, st.est, D);
+    return;
   }
+  double s1 = 0.0, s2 = 0.0, sth[kMaxD];
+  for (int d = 0; d < D; ++d) sth[d] = 0.0;
+  for (int bb = lane; bb < S.nblk; bb += 32) {
+    const double* pb = S.part_st + (size_t)bb * kStatStride;
+    const double mbb = __ldcg(pb);
+    if (!(mbb > -HUGE_VAL)) continue;
+    const double f = exp(mbb - m);
+    s1 += __ldcg(pb + 1) * f;
+    s2 += __ldcg(pb + 2) * (f * f);
+    for (int d = 0; d < D; ++d) sth[d] += __ldcg(pb + 3 + d) * f;
+  }
+  s1 = warp_sum(s1);
+  s2 = warp_sum(s2);
+  for (int d = 0; d < D; ++d) sth[d] = warp_sum(sth[d]);
+  if (lane != 0) return;
+  st.lse = m + log(s1);
+  st.lse2 = 2.0 * m + log(s2);
+  st.ess = (s1 * s1) / s2;
+  st.logz = st.lse - S.logN;
+  for (int d = 0; d < kMaxD; ++d) st.est[d] = d < D ? sth[d] / s1 : 0.0;
+  st.resampled = st.ess < P.ess_frac * (double)N;
+  cur->m = m;
+  cur->lse = st.lse;
+  cur->resample = st.resampled;
+  cur->m_par = st.resampled ? st.lse - S.logN : m;
+  accumulate_recycling(S.rec, S.est_rec, st.ess, st.est, D);
   if ((int)k <= P.K) S.hist[k - 1] = st;
   S.tickets[1] = 0;
 }
@@ -390,17 +351,17 @@ __global__ void __launch_bounds__(kOuterBlock) quantise_kernel(OuterParams P) {
 // block's own slots; both this kernel and the standalone primitive use it.
 // ---------------------------------------------------------------------------
 __device__ uint64_t scan_all_to_smem(const uint64_t* q, int n, uint64_t* C) {
-  __shared__ uint64_t wt[kWarps];
+  __shared__ uint64_t wt[kResWarps];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint64_t carry = 0;
-  for (int base = 0; base < n; base += kOuterBlock) {
+  for (int base = 0; base < n; base += kResBlock) {
     const int idx = base + threadIdx.x;
     const uint64_t v = idx < n ? q[idx] : 0ull;
     const uint64_t incl = warp_incl_scan_u64(v, lane);
     if (lane == 31) wt[warp] = incl;
     __syncthreads();
     uint64_t off = 0, total = 0;
-    for (int w = 0; w < kWarps; ++w) {
+    for (int w = 0; w < kResWarps; ++w) {
       const uint64_t tw = wt[w];
       if (w < warp) off += tw;
       total += tw;
@@ -424,14 +385,14 @@ __device__ __forceinline__ int search_first_greater(const uint64_t* C, int n, ui
   return lo;
 }
 
-__global__ void __launch_bounds__(kOuterBlock) resample_kernel(OuterParams P) {
+__global__ void __launch_bounds__(kResBlock) resample_kernel(OuterParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   uint64_t* C = reinterpret_cast<uint64_t*>(smem_raw);
   const DSDev& S = P.ds[blockIdx.y];
   const int N = S.N, D = P.D, tid = threadIdx.x;
   const uint32_t k = (uint32_t)(*P.k_done + 1);
-  if ((int)blockIdx.x < S.nblk) {
-    const int j = blockIdx.x * kOuterBlock + tid;
+  if ((int)blockIdx.x < S.nblk_res) {
+    const int j = blockIdx.x * kResBlock + tid;
     if (S.cur->resample) {
       const uint64_t total = scan_all_to_smem(S.q, N, C);
       const uint32_t U =
@@ -443,7 +404,7 @@ __global__ void __launch_bounds__(kOuterBlock) resample_kernel(OuterParams P) {
         for (int d = 0; d < D; ++d) S.thA[(size_t)d * N + j] = S.thB[(size_t)d * N + a];
         S.lpA[j] = S.lpB[a];
         S.llA[j] = S.llB[a];
-        S.logw[j] = S.cur->lse - log((double)N);
+        S.logw[j] = S.cur->lse - S.logN;
       }
     } else if (j < N) {
       for (int d = 0; d < D; ++d) S.thA[(size_t)d * N + j] = S.thB[(size_t)d * N + j];
@@ -463,13 +424,13 @@ __global__ void __launch_bounds__(kOuterBlock) resample_kernel(OuterParams P) {
   }
 }
 
-__global__ void __launch_bounds__(kOuterBlock)
+__global__ void __launch_bounds__(kResBlock)
     resample_primitive_kernel(const uint64_t* q, int n, uint32_t U, int32_t* anc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   uint64_t* C = reinterpret_cast<uint64_t*>(smem_raw);
   const uint64_t total = scan_all_to_smem(q, n, C);
   const int log2n = ((n & (n - 1)) == 0) ? (__ffs(n) - 1) : -1;
-  const int j = blockIdx.x * kOuterBlock + threadIdx.x;
+  const int j = blockIdx.x * kResBlock + threadIdx.x;
   if (j < n && total > 0) anc[j] = search_first_greater(C, n, slot_threshold((uint32_t)j, U, total, n, log2n));
 }
 
@@ -516,12 +477,11 @@ __global__ void obs_terms_kernel(int model, const double* y, int T, R* obs) {
 }
 
 // Parent reference after a restored state: m_par = max_i log w_i of one dataset.
-__global__ void __launch_bounds__(kOuterBlock) parent_reference_kernel(OuterParams P, int dataset) {
-  __shared__ double shm[kWarps];
+__global__ void parent_reference_kernel(OuterParams P, int dataset) {
   const DSDev& S = P.ds[dataset];
   double m = -HUGE_VAL;
-  for (int i = threadIdx.x; i < S.N; i += kOuterBlock) m = fmax(m, S.logw[i]);
-  m = block_max(m, shm);
+  for (int i = threadIdx.x; i < S.N; i += 32) m = fmax(m, S.logw[i]);
+  m = warp_max(m);
   if (threadIdx.x == 0) S.cur->m_par = m;
 }
 
@@ -562,16 +522,16 @@ cudaError_t outer_quantise(const OuterParams& P, int max_nblk, cudaStream_t s) {
   quantise_kernel<<<dim3(max_nblk, P.n_ds), kOuterBlock, 0, s>>>(P);
   return cudaGetLastError();
 }
-cudaError_t outer_resample(const OuterParams& P, int max_nblk, int max_N, cudaStream_t s) {
+cudaError_t outer_resample(const OuterParams& P, int max_nblk_res, int max_N, cudaStream_t s) {
   const size_t smem = (size_t)max_N * sizeof(uint64_t);
   cudaError_t e = cudaFuncSetAttribute(resample_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  resample_kernel<<<dim3(max_nblk, P.n_ds), kOuterBlock, smem, s>>>(P);
+  resample_kernel<<<dim3(max_nblk_res, P.n_ds), kResBlock, smem, s>>>(P);
   return cudaGetLastError();
 }
 cudaError_t outer_parent_reference(const OuterParams& P, int dataset, cudaStream_t s) {
-  parent_reference_kernel<<<1, kOuterBlock, 0, s>>>(P, dataset);
+  parent_reference_kernel<<<1, 32, 0, s>>>(P, dataset);
   return cudaGetLastError();
 }
 cudaError_t outer_rebuild_recycling(const OuterParams& P, int dataset, int k, cudaStream_t s) {
@@ -584,8 +544,7 @@ cudaError_t resample_systematic_launch(const uint64_t* q, int n, uint32_t U, int
   cudaError_t e = cudaFuncSetAttribute(resample_primitive_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  resample_primitive_kernel<<<(n + kOuterBlock - 1) / kOuterBlock, kOuterBlock, smem, s>>>(q, n, U,
-                                                                                          anc);
+  resample_primitive_kernel<<<(n + kResBlock - 1) / kResBlock, kResBlock, smem, s>>>(q, n, U, anc);
   return cudaGetLastError();
 }
 cudaError_t philox_normals_launch(uint64_t seed, const uint32_t* ctr, int n, int precision,

@@ -55,10 +55,59 @@ __host__ __device__ inline int group_threads_for(int ppt, int M) {
   return (t + 31) & ~31;
 }
 
+// Shared memory of one filter group (Mp = particles incl. padding, nw warps):
+//   P  u64 [Mp]      warp-local inclusive prefix of the quantised weights
+//   X  R   [Mp][ns]  particle states, one vector per particle
+//   Z  R   [4][Mp]   the four normals of the current Philox counter of every particle
+//   wsum u64 [nw], wmax 8 B [nw], sU u32 [8] (resampling words of two groups of four steps)
 __host__ __device__ inline size_t region_bytes(int Mp, int nw, int ns, int rsize) {
-  size_t b = (size_t)Mp * 8 + (size_t)ns * Mp * rsize + (size_t)nw * 8 + (size_t)nw * rsize + 8;
+  size_t b = (size_t)Mp * 8 + (size_t)ns * Mp * rsize + (size_t)4 * Mp * rsize + (size_t)nw * 16 + 32;
   return (b + 15) & ~(size_t)15;
 }
+
+// Register budget per variant (threads x registers must fit the SM at the
+// shapes the tuner tries); beyond it the compiler spills to local memory.
+template <typename R, int PPT>
+struct RegCap {
+  static constexpr int value = sizeof(R) == 4 ? (PPT <= 2 ? 64 : (PPT == 4 ? 80 : 128))
+                                              : (PPT == 1 ? 80 : (PPT == 2 ? 96 : 128));
+};
+
+template <typename R, int NS>
+struct StateVec;
+template <typename R>
+struct StateVec<R, 1> {
+  __device__ __forceinline__ static void store(R* X, int j, const R* x) { X[j] = x[0]; }
+  __device__ __forceinline__ static void load(const R* X, int j, R* x) { x[0] = X[j]; }
+};
+template <>
+struct StateVec<float, 4> {
+  __device__ __forceinline__ static void store(float* X, int j, const float* x) {
+    reinterpret_cast<float4*>(X)[j] = make_float4(x[0], x[1], x[2], x[3]);
+  }
+  __device__ __forceinline__ static void load(const float* X, int j, float* x) {
+    const float4 v = reinterpret_cast<const float4*>(X)[j];
+    x[0] = v.x;
+    x[1] = v.y;
+    x[2] = v.z;
+    x[3] = v.w;
+  }
+};
+template <>
+struct StateVec<double, 4> {
+  __device__ __forceinline__ static void store(double* X, int j, const double* x) {
+    reinterpret_cast<double2*>(X)[2 * j] = make_double2(x[0], x[1]);
+    reinterpret_cast<double2*>(X)[2 * j + 1] = make_double2(x[2], x[3]);
+  }
+  __device__ __forceinline__ static void load(const double* X, int j, double* x) {
+    const double2 a = reinterpret_cast<const double2*>(X)[2 * j];
+    const double2 b = reinterpret_cast<const double2*>(X)[2 * j + 1];
+    x[0] = a.x;
+    x[1] = a.y;
+    x[2] = b.x;
+    x[3] = b.y;
+  }
+};
 
 template <typename R>
 __device__ __forceinline__ R neg_inf();
@@ -155,21 +204,23 @@ struct FilterParams<R, MODEL_SEIR> {
 
 template <typename R, int MODEL, int PPT>
 __device__ __forceinline__ void run_filter(const PFJob& J, const PFModel& mdl, int i, int g, int lt,
-                                           int gt, unsigned char* region, uint2 key, uint32_t k) {
+                                           int gt, unsigned char* region, uint2 key, uint32_t k,
+                                           int t_cap) {
   constexpr int NS = ModelDims<MODEL>::NS;
   constexpr int D = ModelDims<MODEL>::D;
   using R4 = typename R4Of<R>::type;
-  const int M = J.M, T = J.T;
+  const int M = J.M, T = t_cap > 0 ? min(J.T, t_cap) : J.T;
   const int Mp = gt * PPT;
   const int nw = gt >> 5;
   const int lane = lt & 31, warp = lt >> 5;
   const int seg = 32 * PPT;  // particles per warp
 
   uint64_t* P = reinterpret_cast<uint64_t*>(region);   // [Mp] warp-local inclusive prefix of q
-  R* X = reinterpret_cast<R*>(P + Mp);                  // [NS][Mp] particle states
-  uint64_t* wsum = reinterpret_cast<uint64_t*>(X + (size_t)NS * Mp);  // [nw] warp totals
-  R* wmax = reinterpret_cast<R*>(wsum + nw);            // [nw] warp maxima
-  uint32_t* sU = reinterpret_cast<uint32_t*>(wmax + nw);  // [2] resampling words, by step parity
+  R* X = reinterpret_cast<R*>(P + Mp);                  // [Mp][NS] particle states
+  R* Z = X + (size_t)NS * Mp;                           // [4][Mp] cached normals
+  uint64_t* wsum = reinterpret_cast<uint64_t*>(Z + (size_t)4 * Mp);  // [nw] warp totals
+  R* wmax = reinterpret_cast<R*>(wsum + nw);            // [nw] warp maxima (8-byte slots)
+  uint32_t* sU = reinterpret_cast<uint32_t*>(wsum + 2 * nw);  // [8] resampling words
 
   auto group_sync = [&]() {
     if (nw == 1)
@@ -206,93 +257,103 @@ __device__ __forceinline__ void run_filter(const PFJob& J, const PFModel& mdl, i
   }
 
   double loglik = 0.0;
-  bool dead = false;
-  for (int t0 = 1; t0 <= T && !dead; t0 += 4) {
-    R zc[PPT][4];
-#pragma unroll
-    for (int r = 0; r < PPT; ++r)
-      normals4<R>(make_uint4((uint32_t)(lt * PPT + r), (uint32_t)((t0 - 1) >> 2), c2, c3prop), key,
-                  zc[r]);
-#pragma unroll
-    for (int tm = 0; tm < 4; ++tm) {
-      const int t = t0 + tm;
-      if (t > T || dead) break;
-      if (lt == 0 && t < T) sU[t & 1] = philox4x32_10(make_uint4(0u, (uint32_t)t, c2, c3res), key).x;
-      const R4 ob = obs[t - 1];
-      R ell[PPT];
-      R lmax = neg_inf<R>();
+  for (int t = 1; t <= T; ++t) {
+    const int tm = (t - 1) & 3;
+    if (tm == 0) {  // one Philox call per particle every four steps; normals kept in shared memory
 #pragma unroll
       for (int r = 0; r < PPT; ++r) {
-        fp.propagate(x[r], zc[r][tm]);
-        R l;
-        if constexpr (MODEL == MODEL_LG) {
-          l = fp.log_obs(x[r], ob);
-        } else {
-          const R lam = fp.day(x[r]);
-          l = fp.log_pois(lam, ob);
-        }
-        if (isnan(l) || lt * PPT + r >= M) l = neg_inf<R>();
-        ell[r] = l;
-        lmax = fmax(lmax, l);
+        R z4[4];
+        normals4<R>(make_uint4((uint32_t)(lt * PPT + r), (uint32_t)((t - 1) >> 2), c2, c3prop), key,
+                    z4);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) Z[e * Mp + lt * PPT + r] = z4[e];
       }
-      // (3) group maximum
-      lmax = warp_max(lmax);
-      if (nw > 1 && lane == 0) wmax[warp] = lmax;
-      group_sync();
-      if (nw > 1) {
-        lmax = wmax[0];
-        for (int w = 1; w < nw; ++w) lmax = fmax(lmax, wmax[w]);
+    }
+    // resampling words of steps t..t+3, one lane each, double-buffered by step group
+    uint32_t* sUg = sU + 4 * (((t - 1) >> 2) & 1);
+    if (tm == 0 && lt < 4 && t + lt < T)
+      sUg[lt] = philox4x32_10(make_uint4(0u, (uint32_t)(t + lt), c2, c3res), key).x;
+    const R4 ob = obs[t - 1];
+    R ell[PPT];
+    R lmax = neg_inf<R>();
+#pragma unroll
+    for (int r = 0; r < PPT; ++r) {
+      fp.propagate(x[r], Z[tm * Mp + lt * PPT + r]);
+      R l;
+      if constexpr (MODEL == MODEL_LG) {
+        l = fp.log_obs(x[r], ob);
+      } else {
+        const R lam = fp.day(x[r]);
+        l = fp.log_pois(lam, ob);
       }
-      const R m = lmax;
-      if (!(m > neg_inf<R>())) {  // every weight vanished: the estimate is zero
-        dead = true;
-        loglik = -HUGE_VAL;
-        if (lt == 0 && J.delta)
-          for (int s = t; s <= T; ++s) J.delta[(size_t)i * T + (s - 1)] = -HUGE_VAL;
-        break;
-      }
-      // (4) quantise and scan
-      uint64_t run = 0, c[PPT];
+      if (isnan(l) || lt * PPT + r >= M) l = neg_inf<R>();
+      ell[r] = l;
+      lmax = fmax(lmax, l);
+    }
+    // (3) group maximum
+    lmax = warp_max(lmax);
+    if (nw > 1 && lane == 0) wmax[warp] = lmax;
+    group_sync();
+    if (nw > 1) {
+      lmax = wmax[0];
+      for (int w = 1; w < nw; ++w) lmax = fmax(lmax, wmax[w]);
+    }
+    const R m = lmax;
+    if (!(m > neg_inf<R>())) {  // every weight vanished: the estimate is zero
+      loglik = -HUGE_VAL;
+      if (lt == 0 && J.delta)
+        for (int s = t; s <= T; ++s) J.delta[(size_t)i * T + (s - 1)] = -HUGE_VAL;
+      break;
+    }
+    // (4) quantise and scan (warp-local inclusive prefix in P, warp totals in wsum)
+    uint64_t run = 0, c[PPT];
+#pragma unroll
+    for (int r = 0; r < PPT; ++r) {
+      const uint64_t qv = (ell[r] > neg_inf<R>()) ? to_u64_rz(exp(ell[r] - m) * scaleB) : 0ull;
+      run += qv;
+      c[r] = run;
+    }
+    const uint64_t incl = warp_incl_scan_u64(run, lane);
+    const uint64_t excl = incl - run;
+#pragma unroll
+    for (int r = 0; r < PPT; ++r) {
+      P[lt * PPT + r] = excl + c[r];
+      StateVec<R, NS>::store(X, lt * PPT + r, x[r]);
+    }
+    if (lane == 31) wsum[warp] = incl;
+    group_sync();
+    uint64_t S = 0;
+    for (int w = 0; w < nw; ++w) S += wsum[w];
+    // (5) log-likelihood increment: log S from its binary exponent and mantissa
+    if (lt == 0) {
+      const int e = 63 - __clzll((long long)S);
+      const R mant = (R)(e >= 52 ? (S >> (e - 52)) : (S << (52 - e))) * (R)0x1p-52;
+      const double delta = (double)m + ((double)e * kLn2 + (double)log(mant)) + log_norm;
+      loglik += delta;
+      if (J.delta) J.delta[(size_t)i * T + (t - 1)] = delta;
+    }
+    // (6) systematic resampling and ancestor gather.  The thread's slots are
+    // consecutive and their ancestors non-decreasing: the first is found by a
+    // search over the warp totals and a binary search inside one warp's prefix,
+    // the others by galloping forward from the previous ancestor.
+    if (t < T) {
+      const uint32_t U = sUg[tm];
+      int w = 0, a = 0;
+      uint64_t base = 0;
 #pragma unroll
       for (int r = 0; r < PPT; ++r) {
-        const uint64_t qv = (ell[r] > neg_inf<R>()) ? to_u64_rz(exp(ell[r] - m) * scaleB) : 0ull;
-        run += qv;
-        c[r] = run;
-      }
-      const uint64_t incl = warp_incl_scan_u64(run, lane);
-      const uint64_t excl = incl - run;
-#pragma unroll
-      for (int r = 0; r < PPT; ++r) {
-        P[lt * PPT + r] = excl + c[r];
-#pragma unroll
-        for (int s = 0; s < NS; ++s) X[s * Mp + lt * PPT + r] = x[r][s];
-      }
-      if (lane == 31) wsum[warp] = incl;
-      group_sync();
-      uint64_t S = 0;
-      for (int w = 0; w < nw; ++w) S += wsum[w];
-      // (5) log-likelihood increment
-      if (lt == 0) {
-        const double delta = (double)m + log((double)S) + log_norm;
-        loglik += delta;
-        if (J.delta) J.delta[(size_t)i * T + (t - 1)] = delta;
-      }
-      // (6) systematic resampling and ancestor gather
-      if (t < T) {
-        const uint32_t U = sU[t & 1];
-#pragma unroll
-        for (int r = 0; r < PPT; ++r) {
-          const int j = lt * PPT + r;
-          if (j < M) {
-            const uint64_t tau = slot_threshold((uint32_t)j, U, S, M, log2M);
-            uint64_t base = 0;
-            int w = 0;
-            while (w < nw - 1 && base + wsum[w] <= tau) {
-              base += wsum[w];
-              ++w;
-            }
-            const uint64_t tl = tau - base;
-            int lo = w * seg, hi = lo + seg - 1;
+        const int j = lt * PPT + r;
+        if (j < M) {
+          const uint64_t tau = slot_threshold((uint32_t)j, U, S, M, log2M);
+          while (w < nw - 1 && base + wsum[w] <= tau) {  // answer lies in a later warp
+            base += wsum[w];
+            ++w;
+            a = w * seg;
+          }
+          const uint64_t tl = tau - base;
+          const int seg_end = w * seg + seg - 1;  // P[seg_end] = wsum[w] > tl
+          if (r == 0) {
+            int lo = w * seg, hi = seg_end;
             while (lo < hi) {
               const int mid = (lo + hi) >> 1;
               if (P[mid] > tl)
@@ -300,10 +361,25 @@ __device__ __forceinline__ void run_filter(const PFJob& J, const PFModel& mdl, i
               else
                 lo = mid + 1;
             }
-#pragma unroll
-            for (int s = 0; s < NS; ++s) x[r][s] = X[s * Mp + lo];
-            if (J.anc) J.anc[((size_t)i * (T - 1) + (t - 1)) * M + j] = lo;
+            a = lo;
+          } else if (P[a] <= tl) {
+            int lo = a + 1, step = 1;
+            while (lo + step - 1 < seg_end && P[lo + step - 1] <= tl) {
+              lo += step;
+              step <<= 1;
+            }
+            int hi = min(lo + step - 1, seg_end);
+            while (lo < hi) {
+              const int mid = (lo + hi) >> 1;
+              if (P[mid] > tl)
+                hi = mid;
+              else
+                lo = mid + 1;
+            }
+            a = lo;
           }
+          StateVec<R, NS>::load(X, a, x[r]);
+          if (J.anc) J.anc[((size_t)i * (T - 1) + (t - 1)) * M + j] = a;
         }
       }
     }
@@ -312,7 +388,7 @@ __device__ __forceinline__ void run_filter(const PFJob& J, const PFModel& mdl, i
 }
 
 template <typename R, int MODEL, int PPT>
-__global__ void __launch_bounds__(kPfMaxBlock) pf_kernel(PFLaunch L) {
+__global__ void __maxnreg__((RegCap<R, PPT>::value)) pf_kernel(PFLaunch L) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_wu;
   constexpr int NS = ModelDims<MODEL>::NS;
@@ -345,7 +421,7 @@ __global__ void __launch_bounds__(kPfMaxBlock) pf_kernel(PFLaunch L) {
     const int g = threadIdx.x / gt, lt = threadIdx.x - g * gt;
     const size_t rb = region_bytes(gt * PPT, gt >> 5, NS, (int)sizeof(R));
     if (g < count && (g + 1) * gt <= (int)blockDim.x)
-      run_filter<R, MODEL, PPT>(J, L.mdl, first + g, g, lt, gt, smem + g * rb, key, k);
+      run_filter<R, MODEL, PPT>(J, L.mdl, first + g, g, lt, gt, smem + g * rb, key, k, L.t_cap);
     if (!L.wu_counter) __syncthreads();
   }
 }

@@ -29,7 +29,7 @@ class Config(C.Structure):
         ("rw_scale", C.c_double), ("ess_frac", C.c_double), ("seed", C.c_uint64),
         ("prior_mean", C.c_double * MAX_D), ("prior_sd", C.c_double * MAX_D),
         ("npop", C.c_double), ("e0", C.c_double), ("i0", C.c_double), ("lambda_floor", C.c_double),
-        ("n_sub", C.c_int), ("ppt", C.c_int), ("n_datasets", C.c_int),
+        ("n_sub", C.c_int), ("ppt", C.c_int), ("cta_threads", C.c_int), ("n_datasets", C.c_int),
         ("ds_N", C.POINTER(C.c_int)), ("ds_M", C.POINTER(C.c_int)), ("ds_T", C.POINTER(C.c_int)),
     ]
 
@@ -83,6 +83,7 @@ def _load() -> C.CDLL:
         "smc2_set_timing": ([ctx, C.c_int], st),
         "smc2_get_timing": ([ctx, C.POINTER(C.c_double), C.POINTER(C.c_int64),
                              C.POINTER(C.c_int64), C.c_int], st),
+        "smc2_get_launch_shape": ([ctx, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)], st),
         "smc2_destroy": ([ctx], None),
         "smc2_status_string": ([st], C.c_char_p),
         "smc2_last_error_string": ([], C.c_char_p),
@@ -135,6 +136,7 @@ def make_config(w, **over) -> Config:
     c.npop, c.e0, c.i0 = get("npop", 0.0), get("e0", 0.0), get("i0", 0.0)
     c.lambda_floor, c.n_sub = get("lambda_floor", 1e-3), get("n_sub", 1)
     c.ppt = get("ppt", 0)
+    c.cta_threads = get("cta_threads", 0)
     c.n_datasets = 0
     return c
 
@@ -259,6 +261,12 @@ class SMC2:
         _check(lib.smc2_pf_trace(self._ctx, _ptr(theta_soa), n, int(iteration), dataset, _ptr(ll),
                                  _ptr(delta), _ptr(anc)), "smc2_pf_trace")
         return ll, delta, anc
+
+    def launch_shape(self):
+        a, b, c = C.c_int(), C.c_int(), C.c_int()
+        _check(lib.smc2_get_launch_shape(self._ctx, C.byref(a), C.byref(b), C.byref(c)),
+               "smc2_get_launch_shape")
+        return {"ppt": a.value, "cta_threads": b.value, "grid": c.value}
 
     # -- timing -------------------------------------------------------------
     def set_timing(self, on: bool):

@@ -51,7 +51,8 @@ def _cfg(S, **over):
 @pytest.mark.parametrize("over", [
     {"model": 7}, {"precision": 3}, {"proposal": 5}, {"lkernel": 9}, {"D": 4}, {"N": 0},
     {"N": 16385}, {"M": 0}, {"M": 4097}, {"T": 0}, {"K": 0}, {"rw_scale": 0.0},
-    {"rw_scale": float("nan")}, {"ess_frac": -1.0}, {"ppt": 3},
+    {"rw_scale": float("nan")}, {"ess_frac": -1.0}, {"ppt": 3}, {"cta_threads": 48},
+    {"cta_threads": 1024}, {"ppt": 1, "M": 4096}, {"ppt": 4, "cta_threads": 64, "M": 1024},
 ])
 def test_invalid_configs_rejected_before_gpu_work(S, over):
     import numpy as np
