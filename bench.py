@@ -43,6 +43,8 @@ def parse():
     p.add_argument("--workload", default="seir_t100_n1024")
     p.add_argument("--no-fp64-form", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--ppt", type=int, default=0, help="pin particles per thread (0: tuner)")
+    p.add_argument("--cta", type=int, default=0, help="pin threads per PF CTA (0: tuner)")
     return p.parse_args()
 
 
@@ -238,7 +240,7 @@ def main():
     from paper_2311_12973_gb300 import smc2 as S
 
     # each rank runs an independent replica (its own seed): weak scaling
-    wr = w.with_(seed=w.seed + 1000 * rank)
+    wr = w.with_(seed=w.seed + 1000 * rank, ppt=args.ppt, cta_threads=args.cta)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     ctx = S.SMC2(S.make_config(wr), wr.y)
     shape = ctx.launch_shape()
@@ -276,7 +278,7 @@ def main():
     # plain FP64 GPU form of the same workload
     fp64 = None
     if not args.no_fp64_form:
-        w64 = wr.with_(precision=I.PREC_FP64)
+        w64 = wr.with_(precision=I.PREC_FP64, ppt=0, cta_threads=0)
         ctx64 = S.SMC2(S.make_config(w64), w64.y)
         ms64, ess64, _, _, _, _ = time_runs(S, torch, ctx64, w64, max(2, args.steps // 3), 1, flush,
                                             rank_sync)

@@ -86,7 +86,7 @@ typedef struct smc2_ctx smc2_ctx; /* opaque; owns its device workspace */
  * cta_threads: threads per particle-filter CTA (0 = pick by the tuner;
  *   otherwise a multiple of 32 up to 512 that holds whole filter groups).
  *   The tuner times every valid (ppt, cta_threads) pair on the context's own
- *   work list, prior draws of theta and min(T, 16) steps, during smc2_init.
+ *   work list, prior draws of theta and min(T, 32) steps, during smc2_init.
  * n_datasets: number of independent datasets run together (<= 1: one).
  * ds_N, ds_M, ds_T: host arrays of n_datasets sizes (NULL when n_datasets <= 1). */
 typedef struct {

@@ -240,7 +240,7 @@ smc2_status apply_shape(smc2_ctx* c, int ppt, int block, bool upload) {
 }
 
 // Launch-shape tuner: time every valid (particles per thread, CTA threads) pair
-// on the context's own work list (prior draws of theta, min(T, 16) steps).
+// on the context's own work list (prior draws of theta, min(T, 32) steps).
 smc2_status choose_launch_shape(smc2_ctx* c) {
   std::vector<std::pair<int, int>> cand;
   for (int ppt : {1, 2, 4, 8}) {
@@ -265,8 +265,9 @@ smc2_status choose_launch_shape(smc2_ctx* c) {
     PFLaunch L = c->pl;
     float ms = 0.f;
     bool ok = true;
-    for (int rep = 0; rep < 2 && ok; ++rep) {
-      L.t_cap = rep == 0 ? 4 : 16;
+    float cand_best = 1e30f;
+    for (int rep = 0; rep < 3 && ok; ++rep) {  // one warm-up launch, then the best of two
+      L.t_cap = rep == 0 ? 4 : 32;
       ok = cudaMemsetAsync(c->d_wu_counter, 0, sizeof(int), s) == cudaSuccess &&
            cudaEventRecord(e0, s) == cudaSuccess &&
            pf_launch(c->precision, c->model, c->ppt, c->pf_grid, c->pf_block, c->pf_smem, L, s) ==
@@ -274,9 +275,10 @@ smc2_status choose_launch_shape(smc2_ctx* c) {
            cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
            cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
       c->kernel_launches++;
+      if (ok && rep > 0) cand_best = std::min(cand_best, ms);
     }
-    if (ok && ms < best) {
-      best = ms;
+    if (ok && cand_best < best) {
+      best = cand_best;
       pick = cb;
     }
     cudaGetLastError();

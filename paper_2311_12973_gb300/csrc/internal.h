@@ -28,6 +28,7 @@ struct LKParams {
   double mu[2 * 8];    // (mu_a, mu_b)
   double A[8 * 8];     // S_ab S_bb^{-1}, row-major D x D
   double Lc[8 * 8];    // lower Cholesky factor of S_{a|b}
+  double Lc_inv[8];    // reciprocals of its diagonal
   double logdet;       // log det S_{a|b}
   int fallback;        // 1: forward kernel used this iteration
   int pad;

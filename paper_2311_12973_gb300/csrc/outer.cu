@@ -25,9 +25,11 @@ namespace smc2 {
 constexpr int kResWarps = kResBlock / 32;
 static_assert(kOuterBlock == 32, "the per-sample outer kernels are one warp per block");
 
+template <int D>
 __device__ __forceinline__ double log_prior(const OuterParams& P, const double* th) {
   double lp = 0.0;
-  for (int d = 0; d < P.D; ++d) {
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
     const double r = (th[d] - P.prior_mean[d]) * P.inv_prior_sd[d];
     lp += -0.5 * kLog2Pi - P.log_prior_sd[d] - 0.5 * r * r;
   }
@@ -35,47 +37,69 @@ __device__ __forceinline__ double log_prior(const OuterParams& P, const double* 
 }
 
 // log N(x; mean, rw_scale^2 I)
+template <int D>
 __device__ __forceinline__ double rw_logpdf(const OuterParams& P, const double* x, const double* mean) {
   double ss = 0.0;
-  for (int d = 0; d < P.D; ++d) {
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
     const double r = (x[d] - mean[d]) * P.inv_rw;
     ss += r * r;
   }
-  return -0.5 * P.D * kLog2Pi - P.D * P.log_rw - 0.5 * ss;
+  return -0.5 * D * kLog2Pi - D * P.log_rw - 0.5 * ss;
 }
 
 // log N(a; mu_a + A (b - mu_b), Lc Lc^T)
-__device__ __forceinline__ double lk_logpdf(int D, const LKParams& L, const double* a, const double* b) {
-  double r[kMaxD], v[kMaxD];
+template <int D>
+__device__ __forceinline__ double lk_logpdf(const LKParams& L, const double* a, const double* b) {
+  double r[D], v[D];
+#pragma unroll
   for (int p = 0; p < D; ++p) {
     double m = L.mu[p];
+#pragma unroll
     for (int s = 0; s < D; ++s) m += L.A[p * D + s] * (b[s] - L.mu[D + s]);
     r[p] = a[p] - m;
   }
   double ss = 0.0;
+#pragma unroll
   for (int p = 0; p < D; ++p) {
     double s = r[p];
+#pragma unroll
     for (int l = 0; l < p; ++l) s -= L.Lc[p * D + l] * v[l];
-    v[p] = s / L.Lc[p * D + p];
+    v[p] = s * L.Lc_inv[p];
     ss += v[p] * v[p];
   }
   return -0.5 * D * kLog2Pi - 0.5 * L.logdet - 0.5 * ss;
 }
 
-// Cholesky with the pivot floor 1e-12 (a_jj + mean_j^2); 0 on success.
-__device__ int chol_floor(int n, const double* a, const double* mean, double* l) {
-  for (int e = 0; e < n * n; ++e) l[e] = 0.0;
+// Warp-cooperative Cholesky of the n x n matrix a (shared, row-major) into l
+// (shared), with the pivot floor 1e-12 (a_jj + mean_j^2): column by column,
+// lane 0 forms the pivot and its reciprocal, lanes r > j update row r.
+// Returns 0 on success (same value in every lane).
+__device__ int warp_chol(int n, const double* a, const double* mean, double* l, double* inv_diag) {
+  const int lane = threadIdx.x & 31;
+  for (int e = lane; e < n * n; e += 32) l[e] = 0.0;
+  __syncwarp();
+  int ok = 1;
   for (int j = 0; j < n; ++j) {
-    double s = a[j * n + j];
-    for (int p = 0; p < j; ++p) s -= l[j * n + p] * l[j * n + p];
-    const double floor_j = 1e-12 * (a[j * n + j] + mean[j] * mean[j]);
-    if (!(s > floor_j) || !isfinite(s)) return -1;
-    l[j * n + j] = sqrt(s);
-    for (int r = j + 1; r < n; ++r) {
+    if (lane == 0) {
+      double sj = a[j * n + j];
+      for (int p = 0; p < j; ++p) sj -= l[j * n + p] * l[j * n + p];
+      const double floor_j = 1e-12 * (a[j * n + j] + mean[j] * mean[j]);
+      ok = (sj > floor_j) && isfinite(sj);
+      const double d = ok ? sqrt(sj) : 1.0;
+      l[j * n + j] = d;
+      inv_diag[j] = 1.0 / d;
+    }
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    if (!ok) return -1;
+    __syncwarp();
+    const int r = j + 1 + lane;
+    if (r < n) {
       double v = a[r * n + j];
       for (int p = 0; p < j; ++p) v -= l[r * n + p] * l[j * n + p];
-      l[r * n + j] = v / l[j * n + j];
+      l[r * n + j] = v * inv_diag[j];
     }
+    __syncwarp();
   }
   return 0;
 }
@@ -83,82 +107,100 @@ __device__ int chol_floor(int n, const double* a, const double* mean, double* l)
 // Moment slots: 0 = sum w; 1..2D = sum w z_r; then sum w z_r z_s for r <= s.
 __device__ __forceinline__ int n_moments(int D) { return 1 + 2 * D + D * (2 * D + 1); }
 
-__device__ void lk_fit(int D, const double* tot, const double* shift, LKParams* out) {
-  const int D2 = 2 * D;
-  double m1[2 * kMaxD], mu[2 * kMaxD], sig[4 * kMaxD * kMaxD];
-  const double W = tot[0];
-  for (int r = 0; r < D2; ++r) {
-    m1[r] = tot[1 + r] / W;
-    mu[r] = shift[r] + m1[r];
-  }
-  int slot = 1 + D2;
-  for (int r = 0; r < D2; ++r)
-    for (int s = r; s < D2; ++s, ++slot) {
-      const double c = tot[slot] / W - m1[r] * m1[s];
-      sig[r * D2 + s] = c;
-      sig[s * D2 + r] = c;
-    }
+struct FitScratch {
+  double sig[4 * kMaxD * kMaxD], mu[2 * kMaxD], m1[2 * kMaxD];
   double saa[kMaxD * kMaxD], sab[kMaxD * kMaxD], sbb[kMaxD * kMaxD], lb[kMaxD * kMaxD];
-  for (int r = 0; r < D; ++r)
-    for (int s = 0; s < D; ++s) {
-      saa[r * D + s] = sig[r * D2 + s];
-      sab[r * D + s] = sig[r * D2 + (D + s)];
-      sbb[r * D + s] = sig[(D + r) * D2 + (D + s)];
-    }
-  for (int r = 0; r < D2; ++r) out->mu[r] = mu[r];
-  out->fallback = 1;
-  if (chol_floor(D, sbb, mu + D, lb) != 0) return;
-  // A = S_ab S_bb^{-1}: solve S_bb x = (row c of S_ab)^T for each row c
-  for (int c = 0; c < D; ++c) {
-    double tmp[kMaxD], sol[kMaxD];
+  double sc[kMaxD * kMaxD], inv_b[kMaxD], tmp[kMaxD * kMaxD];
+};
+
+// Gaussian fit of (theta_{k-1}, theta_k) from the weighted moment totals and
+// its conditional a | b (Eqs. 32-35 under the reading in the oracle), by one warp.
+__device__ void lk_fit_warp(int D, const double* tot, const double* shift, FitScratch& F,
+                            LKParams* out) {
+  const int lane = threadIdx.x & 31, D2 = 2 * D;
+  const double W = tot[0];
+  const double invW = 1.0 / W;
+  for (int r = lane; r < D2; r += 32) {
+    F.m1[r] = tot[1 + r] * invW;
+    F.mu[r] = shift[r] + F.m1[r];
+  }
+  __syncwarp();
+  for (int e = lane; e < D2 * D2; e += 32) {
+    const int r = e / D2, q = e % D2;
+    const int lo = r < q ? r : q, hi = r < q ? q : r;
+    const int slot = 1 + D2 + lo * D2 - lo * (lo - 1) / 2 + (hi - lo);
+    F.sig[e] = tot[slot] * invW - F.m1[r] * F.m1[q];
+  }
+  __syncwarp();
+  for (int e = lane; e < D * D; e += 32) {
+    const int r = e / D, q = e % D;
+    F.saa[e] = F.sig[r * D2 + q];
+    F.sab[e] = F.sig[r * D2 + (D + q)];
+    F.sbb[e] = F.sig[(D + r) * D2 + (D + q)];
+  }
+  for (int r = lane; r < D2; r += 32) out->mu[r] = F.mu[r];
+  if (lane == 0) out->fallback = 1;
+  __syncwarp();
+  if (warp_chol(D, F.sbb, F.mu + D, F.lb, F.inv_b) != 0) return;
+  // A = S_ab S_bb^{-1}: lane c solves S_bb x = (row c of S_ab)^T; A's row c = x
+  if (lane < D) {
+    const int c = lane;
+    double* t = F.tmp + c * D;
     for (int r = 0; r < D; ++r) {
-      double v = sab[c * D + r];
-      for (int p = 0; p < r; ++p) v -= lb[r * D + p] * tmp[p];
-      tmp[r] = v / lb[r * D + r];
+      double v = F.sab[c * D + r];
+      for (int p = 0; p < r; ++p) v -= F.lb[r * D + p] * t[p];
+      t[r] = v * F.inv_b[r];
     }
     for (int r = D - 1; r >= 0; --r) {
-      double v = tmp[r];
-      for (int p = r + 1; p < D; ++p) v -= lb[p * D + r] * sol[p];
-      sol[r] = v / lb[r * D + r];
+      double v = t[r];
+      for (int p = r + 1; p < D; ++p) v -= F.lb[p * D + r] * out->A[c * D + p];
+      out->A[c * D + r] = v * F.inv_b[r];
     }
-    for (int r = 0; r < D; ++r) out->A[c * D + r] = sol[r];
   }
-  double sc[kMaxD * kMaxD];
-  for (int r = 0; r < D; ++r)
-    for (int s = 0; s < D; ++s) {
-      double v = saa[r * D + s];
-      for (int p = 0; p < D; ++p) v -= out->A[r * D + p] * sab[s * D + p];
-      sc[r * D + s] = v;
-    }
-  if (chol_floor(D, sc, mu, out->Lc) != 0) return;
-  double ld = 0.0;
-  for (int r = 0; r < D; ++r) ld += 2.0 * log(out->Lc[r * D + r]);
-  out->logdet = ld;
-  out->fallback = 0;
+  __syncwarp();
+  for (int e = lane; e < D * D; e += 32) {
+    const int r = e / D, q = e % D;
+    double v = F.saa[e];
+    for (int p = 0; p < D; ++p) v -= out->A[r * D + p] * F.sab[q * D + p];
+    F.sc[e] = v;
+  }
+  __syncwarp();
+  if (warp_chol(D, F.sc, F.mu, F.tmp, out->Lc_inv) != 0) return;
+  for (int e = lane; e < D * D; e += 32) out->Lc[e] = F.tmp[e];
+  double ld = lane < D ? 2.0 * log(F.tmp[lane * D + lane]) : 0.0;
+  for (int o = 16; o > 0; o >>= 1) ld += __shfl_xor_sync(0xffffffffu, ld, o);
+  if (lane == 0) {
+    out->logdet = ld;
+    out->fallback = 0;
+  }
 }
 
 // ---------------------------------------------------------------------------
 // propose (+ L-kernel fit)
 // ---------------------------------------------------------------------------
+template <int D>
 __global__ void __launch_bounds__(kOuterBlock) propose_kernel(OuterParams P) {
   const DSDev& S = P.ds[blockIdx.y];
   if ((int)blockIdx.x >= S.nblk) return;
   __shared__ double zs[kOuterBlock][2 * kMaxD];
   __shared__ double ws[kOuterBlock];
   __shared__ double tot[kPartStride];
-  const int N = S.N, D = P.D, lane = threadIdx.x;
+  __shared__ FitScratch fit;
+  const int N = S.N, lane = threadIdx.x;
   const int i = blockIdx.x * kOuterBlock + lane;
   const uint32_t k = (uint32_t)(*P.k_done + 1);
   const bool act = i < N;
   const uint2 key = seed_key(P.seed);
-  double a[kMaxD], b[kMaxD];
+  double a[D], b[D];
   if (act) {
     const uint32_t c2 = counter_c2((uint32_t)i, S.c2hi);
+#pragma unroll
     for (int g = 0; g * 4 < D; ++g) {
       double z[4];
       normals4<double>(make_uint4((uint32_t)g, 0u, c2,
                                   counter_c3(k == 1 ? TAG_THETA_INIT : TAG_PROPOSE, k)),
                        key, z);
+#pragma unroll
       for (int r = 0; r < 4 && 4 * g + r < D; ++r) {
         const int d = 4 * g + r;
         if (k == 1) {
@@ -169,19 +211,25 @@ __global__ void __launch_bounds__(kOuterBlock) propose_kernel(OuterParams P) {
         }
       }
     }
+#pragma unroll
     for (int d = 0; d < D; ++d) S.thB[(size_t)d * N + i] = b[d];
-    const double lp = log_prior(P, b);
+    const double lp = log_prior<D>(P, b);
     S.lpB[i] = lp;
-    S.logq[i] = (k == 1) ? lp : rw_logpdf(P, b, a);
+    S.logq[i] = (k == 1) ? lp : rw_logpdf<D>(P, b, a);
   }
   if (k == 1 || P.lkernel != LK_GAUSS) return;
 
   // weighted moments of z = (theta_{k-1}, theta_k) - shift over this block's samples;
   // the shift (sample 0's parent) keeps the one-pass covariance well conditioned
-  double shift[kMaxD];
+  double shift[D];
+#pragma unroll
   for (int d = 0; d < D; ++d) shift[d] = S.thA[(size_t)d * N];
   ws[lane] = act ? exp(S.logw[i] - S.cur->m_par) : 0.0;
-  for (int r = 0; r < 2 * D; ++r) zs[lane][r] = act ? ((r < D ? a[r] : b[r - D]) - shift[r % D]) : 0.0;
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    zs[lane][d] = act ? a[d] - shift[d] : 0.0;
+    zs[lane][D + d] = act ? b[d] - shift[d] : 0.0;
+  }
   __syncwarp();
   const int NM = n_moments(D);
   for (int mo = lane; mo < NM; mo += 32) {
@@ -213,18 +261,19 @@ __global__ void __launch_bounds__(kOuterBlock) propose_kernel(OuterParams P) {
   ticket = __shfl_sync(0xffffffffu, ticket, 0);
   if (ticket != (unsigned)(S.nblk - 1)) return;
   __threadfence();
-  for (int mo = lane; mo < NM; mo += 32) {
+  // totals: lane l takes blocks l, l+32, ... in order, then a fixed shuffle tree
+  for (int mo = 0; mo < NM; ++mo) {
     double t = 0.0;
-    for (int bb = 0; bb < S.nblk; ++bb) t += __ldcg(&S.part[(size_t)bb * kPartStride + mo]);
-    tot[mo] = t;
+    for (int bb = lane; bb < S.nblk; bb += 32) t += __ldcg(&S.part[(size_t)bb * kPartStride + mo]);
+    t = warp_sum(t);
+    if (lane == 0) tot[mo] = t;
   }
   __syncwarp();
-  if (lane == 0) {
-    double sh2[2 * kMaxD];
-    for (int r = 0; r < 2 * D; ++r) sh2[r] = shift[r % D];
-    lk_fit(D, tot, sh2, S.lk);
-    S.tickets[0] = 0;
-  }
+  double sh2[2 * D];
+#pragma unroll
+  for (int r = 0; r < 2 * D; ++r) sh2[r] = shift[r % D];
+  lk_fit_warp(D, tot, sh2, fit, S.lk);
+  if (lane == 0) S.tickets[0] = 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -237,24 +286,27 @@ __device__ __forceinline__ void accumulate_recycling(double* rec, double* est_re
   for (int d = 0; d < D; ++d) est_rec[d] = rec[1 + d] / rec[0];
 }
 
+template <int D>
 __global__ void __launch_bounds__(kOuterBlock) weights_kernel(OuterParams P) {
   const DSDev& S = P.ds[blockIdx.y];
   if ((int)blockIdx.x >= S.nblk) return;
-  const int N = S.N, D = P.D, lane = threadIdx.x;
+  const int N = S.N, lane = threadIdx.x;
   const int i = blockIdx.x * kOuterBlock + lane;
   const uint32_t k = (uint32_t)(*P.k_done + 1);
   const bool act = i < N;
-  double lw = -HUGE_VAL, b[kMaxD];
+  double lw = -HUGE_VAL, b[D];
   if (act) {
+#pragma unroll
     for (int d = 0; d < D; ++d) b[d] = S.thB[(size_t)d * N + i];
     const double lpB = S.lpB[i], llB = S.llB[i], lq = S.logq[i];
     if (k == 1) {
       lw = (lpB + llB) - lq;  // Eq. (17)
     } else {
-      double a[kMaxD];
+      double a[D];
+#pragma unroll
       for (int d = 0; d < D; ++d) a[d] = S.thA[(size_t)d * N + i];
       const bool gauss = P.lkernel == LK_GAUSS && !S.lk->fallback;
-      const double logL = gauss ? lk_logpdf(D, *S.lk, a, b) : rw_logpdf(P, a, b);
+      const double logL = gauss ? lk_logpdf<D>(*S.lk, a, b) : rw_logpdf<D>(P, a, b);
       lw = S.logw[i] + (lpB + llB) - (S.lpA[i] + S.llA[i]) + logL - lq;  // Eq. (20)
     }
     if (isnan(lw)) lw = -HUGE_VAL;
@@ -270,6 +322,7 @@ __global__ void __launch_bounds__(kOuterBlock) weights_kernel(OuterParams P) {
       ps[1] = s1;
       ps[2] = s2;
     }
+#pragma unroll
     for (int d = 0; d < D; ++d) {
       const double sd = warp_sum(act ? e * b[d] : 0.0);
       if (lane == 0) ps[3 + d] = sd;
@@ -303,7 +356,8 @@ __global__ void __launch_bounds__(kOuterBlock) weights_kernel(OuterParams P) {
     }
     return;
   }
-  double s1 = 0.0, s2 = 0.0, sth[kMaxD];
+  double s1 = 0.0, s2 = 0.0, sth[D];
+#pragma unroll
   for (int d = 0; d < D; ++d) sth[d] = 0.0;
   for (int bb = lane; bb < S.nblk; bb += 32) {
     const double* pb = S.part_st + (size_t)bb * kStatStride;
@@ -312,10 +366,12 @@ __global__ void __launch_bounds__(kOuterBlock) weights_kernel(OuterParams P) {
     const double f = exp(mbb - m);
     s1 += __ldcg(pb + 1) * f;
     s2 += __ldcg(pb + 2) * (f * f);
+#pragma unroll
     for (int d = 0; d < D; ++d) sth[d] += __ldcg(pb + 3 + d) * f;
   }
   s1 = warp_sum(s1);
   s2 = warp_sum(s2);
+#pragma unroll
   for (int d = 0; d < D; ++d) sth[d] = warp_sum(sth[d]);
   if (lane != 0) return;
   st.lse = m + log(s1);
@@ -511,11 +567,23 @@ cudaError_t outer_obs_terms(int precision, int model, const double* y, int T, vo
 }
 
 cudaError_t outer_propose(const OuterParams& P, int max_nblk, cudaStream_t s) {
-  propose_kernel<<<dim3(max_nblk, P.n_ds), kOuterBlock, 0, s>>>(P);
+  const dim3 grid(max_nblk, P.n_ds);
+  if (P.D == 3)
+    propose_kernel<3><<<grid, kOuterBlock, 0, s>>>(P);
+  else if (P.D == 4)
+    propose_kernel<4><<<grid, kOuterBlock, 0, s>>>(P);
+  else
+    return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 cudaError_t outer_weights(const OuterParams& P, int max_nblk, cudaStream_t s) {
-  weights_kernel<<<dim3(max_nblk, P.n_ds), kOuterBlock, 0, s>>>(P);
+  const dim3 grid(max_nblk, P.n_ds);
+  if (P.D == 3)
+    weights_kernel<3><<<grid, kOuterBlock, 0, s>>>(P);
+  else if (P.D == 4)
+    weights_kernel<4><<<grid, kOuterBlock, 0, s>>>(P);
+  else
+    return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 cudaError_t outer_quantise(const OuterParams& P, int max_nblk, cudaStream_t s) {

@@ -56,6 +56,8 @@ class Workload:
     i0: float = 0.0
     lambda_floor: float = 1e-3
     n_sub: int = 2
+    ppt: int = 0            # particle-filter launch shape (0: the library's tuner)
+    cta_threads: int = 0
     y: np.ndarray | None = None
 
     @property
