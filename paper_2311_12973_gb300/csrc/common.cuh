@@ -69,14 +69,18 @@ __device__ __forceinline__ double uniform23<double>(uint32_t w) {
 
 template <typename R>
 __device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, R& z0, R& z1);
+// FP32: hardware approximations (lg2, rsqrt, sin, cos; absolute error about
+// 2^-21 on [-pi, pi]).  The angle is taken as 2 pi (u_b - 1/2), inside that
+// range, and the pair is negated back: (cos 2 pi u_b, sin 2 pi u_b).
 template <>
 __device__ __forceinline__ void box_muller<float>(uint32_t wa, uint32_t wb, float& z0, float& z1) {
   const float ua = uniform23<float>(wa), ub = uniform23<float>(wb);
-  const float r = sqrtf(-2.0f * logf(ua));
+  const float e = -2.0f * __logf(ua);
+  const float r = e * rsqrtf(e);
   float s, c;
-  sincospif(2.0f * ub, &s, &c);
-  z0 = r * c;
-  z1 = r * s;
+  __sincosf(6.28318530717958647692f * (ub - 0.5f), &s, &c);
+  z0 = -r * c;
+  z1 = -r * s;
 }
 template <>
 __device__ __forceinline__ void box_muller<double>(uint32_t wa, uint32_t wb, double& z0, double& z1) {

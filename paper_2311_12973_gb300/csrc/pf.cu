@@ -123,6 +123,11 @@ __device__ __forceinline__ double neg_inf<double>() {
 __device__ __forceinline__ uint64_t to_u64_rz(float v) { return __float2ull_rz(v); }
 __device__ __forceinline__ uint64_t to_u64_rz(double v) { return __double2ull_rz(v); }
 
+// exp in the working precision: the FP32 path uses the hardware exp2
+// approximation (relative error about 2^-22), the FP64 path the full-precision exp.
+__device__ __forceinline__ float fast_exp(float x) { return __expf(x); }
+__device__ __forceinline__ double fast_exp(double x) { return exp(x); }
+
 // Per-filter constants of the model in the working precision.
 template <typename R, int MODEL>
 struct FilterParams;
@@ -173,17 +178,23 @@ struct FilterParams<R, MODEL_SEIR> {
   __device__ __forceinline__ void propagate(R* x, R z) const {
     x[3] = x[3] + srw * z;
   }
+  __device__ __forceinline__ void substep(R beta, R& S, R& E, R& I, R& lam) const {
+    const R infection = beta * S * I * inv_npop;
+    const R onset = kappa * E;
+    const R recovery = gamma * I;
+    lam += dt * onset;
+    S = fmax(S - dt * infection, (R)0);
+    E = fmax(E + dt * (infection - onset), (R)0);
+    I = fmax(I + dt * (onset - recovery), (R)0);
+  }
   __device__ __forceinline__ R day(R* x) const {
-    const R beta = exp(x[3]);
+    const R beta = fast_exp(x[3]);
     R S = x[0], E = x[1], I = x[2], lam = (R)0;
-    for (int s = 0; s < n_sub; ++s) {
-      const R infection = beta * S * I * inv_npop;
-      const R onset = kappa * E;
-      const R recovery = gamma * I;
-      lam += dt * onset;
-      S = fmax(S - dt * infection, (R)0);
-      E = fmax(E + dt * (infection - onset), (R)0);
-      I = fmax(I + dt * (onset - recovery), (R)0);
+    if (n_sub == 2) {  // the common case, unrolled
+      substep(beta, S, E, I, lam);
+      substep(beta, S, E, I, lam);
+    } else {
+      for (int s = 0; s < n_sub; ++s) substep(beta, S, E, I, lam);
     }
     x[0] = S;
     x[1] = E;

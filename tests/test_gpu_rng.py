@@ -50,14 +50,15 @@ def test_words_bit_exact(S, seed):
     assert np.array_equal(got, want)
 
 
-@pytest.mark.parametrize("precision,tol", [(0, 1e-13), (1, 2e-6)])
+@pytest.mark.parametrize("precision,tol", [(0, 1e-13), (1, 1e-5)])
 def test_normals(S, precision, tol):
-    # FP64: libm vs CUDA log/sincos, a few ulps; FP32: float log/sqrt/sincospi,
-    # a few float ulps (6e-8) of r <= 5.8
+    # FP64: libm vs CUDA log/sincos, a few ulps.  FP32: hardware lg2, rsqrt,
+    # sin and cos: absolute error about 2^-21 on each factor, times r <= 5.8,
+    # plus the rounding of 2 pi (u - 1/2): |dz| < 1e-5 (1 + |z|).
     c = _counters(4096, 11)
     ctr = torch.tensor(c.view(np.int32), device="cuda")
     z = torch.zeros((4096, 4), dtype=torch.float64, device="cuda")
     S.philox_normals(99, ctr, precision, z=z)
     got = z.cpu().numpy()
     want = np.array([O.normals4(99, *row) for row in c])
-    assert np.max(np.abs(got - want) / np.maximum(1.0, np.abs(want))) < tol
+    assert np.max(np.abs(got - want) / (1.0 + np.abs(want))) < tol
