@@ -120,8 +120,37 @@ __device__ __forceinline__ double neg_inf<double>() {
   return -HUGE_VAL;
 }
 
-__device__ __forceinline__ uint64_t to_u64_rz(float v) { return __float2ull_rz(v); }
-__device__ __forceinline__ uint64_t to_u64_rz(double v) { return __double2ull_rz(v); }
+// floor(e 2^B) for 0 <= e <= 1 from the bit fields of e (integer ops only):
+// e = mant 2^(E - bias - frac_bits), so e 2^B is mant shifted by E - bias - frac_bits + B.
+__device__ __forceinline__ uint64_t fixed_point(float e, int B) {
+  const uint32_t f = __float_as_uint(e);
+  const int E = (int)(f >> 23);
+  if (E == 0) return 0ull;  // zero (or subnormal: below 2^-126, far below one unit)
+  const uint64_t mant = (uint64_t)((f & 0x7fffffu) | 0x800000u);
+  const int sh = E - 150 + B;
+  return sh >= 0 ? (mant << sh) : (sh > -64 ? (mant >> -sh) : 0ull);
+}
+__device__ __forceinline__ uint64_t fixed_point(double e, int B) {
+  const uint64_t f = (uint64_t)__double_as_longlong(e);
+  const int E = (int)(f >> 52);
+  if (E == 0) return 0ull;
+  const uint64_t mant = (f & 0xfffffffffffffull) | 0x10000000000000ull;
+  const int sh = E - 1075 + B;
+  return sh >= 0 ? (mant << sh) : (sh > -64 ? (mant >> -sh) : 0ull);
+}
+
+// A value in [1, 2) holding the leading bits of S (S > 0): S = mant 2^e.
+template <typename R>
+__device__ __forceinline__ R leading_mantissa(uint64_t S, int e);
+template <>
+__device__ __forceinline__ float leading_mantissa<float>(uint64_t S, int e) {
+  return __uint_as_float(0x3f800000u | (uint32_t)(((S << (63 - e)) >> 40) & 0x7fffffull));
+}
+template <>
+__device__ __forceinline__ double leading_mantissa<double>(uint64_t S, int e) {
+  return __longlong_as_double(
+      (long long)(0x3ff0000000000000ull | (((S << (63 - e)) >> 11) & 0xfffffffffffffull)));
+}
 
 // exp in the working precision: the FP32 path uses the hardware exp2
 // approximation (relative error about 2^-22), the FP64 path the full-precision exp.
@@ -251,7 +280,6 @@ __device__ __forceinline__ void run_filter(const PFJob& J, const PFModel& mdl, i
   const uint32_t c3res = counter_c3(TAG_PF_RES, k);
   const int B = fixed_point_bits(M);
   const int log2M = ((M & (M - 1)) == 0) ? (__ffs(M) - 1) : -1;
-  const R scaleB = (R)ldexp(1.0, B);
   const double log_norm = -(double)B * kLn2 - log((double)M);
   const R4* obs = reinterpret_cast<const R4*>(J.obs);
 
@@ -301,14 +329,11 @@ __device__ __forceinline__ void run_filter(const PFJob& J, const PFModel& mdl, i
       ell[r] = l;
       lmax = fmax(lmax, l);
     }
-    // (3) group maximum
+    // (3) group maximum: warp shuffles, then one warp total per lane
     lmax = warp_max(lmax);
     if (nw > 1 && lane == 0) wmax[warp] = lmax;
     group_sync();
-    if (nw > 1) {
-      lmax = wmax[0];
-      for (int w = 1; w < nw; ++w) lmax = fmax(lmax, wmax[w]);
-    }
+    if (nw > 1) lmax = warp_max(lane < nw ? wmax[lane] : neg_inf<R>());
     const R m = lmax;
     if (!(m > neg_inf<R>())) {  // every weight vanished: the estimate is zero
       loglik = -HUGE_VAL;
@@ -320,7 +345,7 @@ __device__ __forceinline__ void run_filter(const PFJob& J, const PFModel& mdl, i
     uint64_t run = 0, c[PPT];
 #pragma unroll
     for (int r = 0; r < PPT; ++r) {
-      const uint64_t qv = (ell[r] > neg_inf<R>()) ? to_u64_rz(exp(ell[r] - m) * scaleB) : 0ull;
+      const uint64_t qv = (ell[r] > neg_inf<R>()) ? fixed_point(fast_exp(ell[r] - m), B) : 0ull;
       run += qv;
       c[r] = run;
     }
@@ -333,12 +358,13 @@ __device__ __forceinline__ void run_filter(const PFJob& J, const PFModel& mdl, i
     }
     if (lane == 31) wsum[warp] = incl;
     group_sync();
-    uint64_t S = 0;
-    for (int w = 0; w < nw; ++w) S += wsum[w];
+    // inclusive prefix of the warp totals, lane w holding warps 0..w
+    const uint64_t wpre = warp_incl_scan_u64(lane < nw ? wsum[lane] : 0ull, lane);
+    const uint64_t S = __shfl_sync(0xffffffffu, wpre, nw - 1);
     // (5) log-likelihood increment: log S from its binary exponent and mantissa
     if (lt == 0) {
       const int e = 63 - __clzll((long long)S);
-      const R mant = (R)(e >= 52 ? (S >> (e - 52)) : (S << (52 - e))) * (R)0x1p-52;
+      const R mant = leading_mantissa<R>(S, e);
       const double delta = (double)m + ((double)e * kLn2 + (double)log(mant)) + log_norm;
       loglik += delta;
       if (J.delta) J.delta[(size_t)i * T + (t - 1)] = delta;
@@ -349,17 +375,34 @@ __device__ __forceinline__ void run_filter(const PFJob& J, const PFModel& mdl, i
     // the others by galloping forward from the previous ancestor.
     if (t < T) {
       const uint32_t U = sUg[tm];
-      int w = 0, a = 0;
-      uint64_t base = 0;
+      // threshold numerators (2^33 j + 2U + 1) S advance by 2^33 S per slot
+      const unsigned __int128 step = (unsigned __int128)S << 33;
+      unsigned __int128 num = ((((unsigned __int128)(lt * PPT)) << 33) + 2ull * U + 1ull) * S;
+      const unsigned __int128 den = (unsigned __int128)M << 33;
+      // warp of the first slot's ancestor: first w with prefix(w) > tau, by a
+      // fixed-length binary search over the shuffled prefixes
+      const uint64_t tau0 = log2M >= 0 ? (uint64_t)(num >> (33 + log2M)) : (uint64_t)(num / den);
+      int w = 0;
+      for (int span = 16; span > 0; span >>= 1) {
+        const int probe = w + span - 1;
+        const uint64_t pv = __shfl_sync(0xffffffffu, wpre, probe < nw ? probe : nw - 1);
+        if (probe < nw - 1 && pv <= tau0) w += span;
+      }
+      uint64_t base = w > 0 ? __shfl_sync(0xffffffffu, wpre, w - 1) : 0ull;
+      if (w == 0) base = 0ull;
+      int a = 0;
 #pragma unroll
       for (int r = 0; r < PPT; ++r) {
         const int j = lt * PPT + r;
+        const uint64_t tau = log2M >= 0 ? (uint64_t)(num >> (33 + log2M)) : (uint64_t)(num / den);
+        num += step;
         if (j < M) {
-          const uint64_t tau = slot_threshold((uint32_t)j, U, S, M, log2M);
-          while (w < nw - 1 && base + wsum[w] <= tau) {  // answer lies in a later warp
-            base += wsum[w];
-            ++w;
-            a = w * seg;
+          if (r > 0) {
+            while (w < nw - 1 && base + wsum[w] <= tau) {  // answer lies in a later warp
+              base += wsum[w];
+              ++w;
+              a = w * seg;
+            }
           }
           const uint64_t tl = tau - base;
           const int seg_end = w * seg + seg - 1;  // P[seg_end] = wsum[w] > tl
@@ -374,12 +417,12 @@ __device__ __forceinline__ void run_filter(const PFJob& J, const PFModel& mdl, i
             }
             a = lo;
           } else if (P[a] <= tl) {
-            int lo = a + 1, step = 1;
-            while (lo + step - 1 < seg_end && P[lo + step - 1] <= tl) {
-              lo += step;
-              step <<= 1;
+            int lo = a + 1, stp = 1;
+            while (lo + stp - 1 < seg_end && P[lo + stp - 1] <= tl) {
+              lo += stp;
+              stp <<= 1;
             }
-            int hi = min(lo + step - 1, seg_end);
+            int hi = min(lo + stp - 1, seg_end);
             while (lo < hi) {
               const int mid = (lo + hi) >> 1;
               if (P[mid] > tl)
