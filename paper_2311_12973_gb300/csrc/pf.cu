@@ -388,8 +388,9 @@ __device__ __forceinline__ void run_filter(const PFJob& J, const PFModel& mdl, i
         const uint64_t pv = __shfl_sync(0xffffffffu, wpre, probe < nw ? probe : nw - 1);
         if (probe < nw - 1 && pv <= tau0) w += span;
       }
-      uint64_t base = w > 0 ? __shfl_sync(0xffffffffu, wpre, w - 1) : 0ull;
-      if (w == 0) base = 0ull;
+      // every lane takes part in the shuffle; only the selection depends on w
+      const uint64_t below = __shfl_sync(0xffffffffu, wpre, w > 0 ? w - 1 : 0);
+      uint64_t base = w > 0 ? below : 0ull;
       int a = 0;
 #pragma unroll
       for (int r = 0; r < PPT; ++r) {
