@@ -82,7 +82,7 @@ typedef struct smc2_ctx smc2_ctx; /* opaque; owns its device workspace */
  * npop, e0, i0, n_sub, lambda_floor: SEIR constants (population, initial
  *   exposed and infectious, Euler substeps per day, floor of the Poisson mean).
  * ppt: particles per thread of the particle-filter kernel (0 = pick by the
- *   built-in tuner; otherwise 1, 2, 4 or 8).
+ *   built-in tuner; otherwise 1, 2, 4, 8 or 16).
  * cta_threads: threads per particle-filter CTA (0 = pick by the tuner;
  *   otherwise a multiple of 32 up to 512 that holds whole filter groups).
  *   The tuner times every valid (ppt, cta_threads) pair on the context's own

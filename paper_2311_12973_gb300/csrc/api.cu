@@ -113,7 +113,8 @@ smc2_status validate(const smc2_config* c) {
         !finite_pos(c->lambda_floor))
       return SMC2_EINVAL;
   }
-  if (c->ppt != 0 && c->ppt != 1 && c->ppt != 2 && c->ppt != 4 && c->ppt != 8) return SMC2_EINVAL;
+  if (c->ppt != 0 && c->ppt != 1 && c->ppt != 2 && c->ppt != 4 && c->ppt != 8 && c->ppt != 16)
+    return SMC2_EINVAL;
   if (c->cta_threads != 0 && (c->cta_threads < 32 || c->cta_threads > kPfMaxBlock || c->cta_threads % 32))
     return SMC2_EINVAL;
   const int nd = c->n_datasets <= 1 ? 1 : c->n_datasets;
@@ -125,7 +126,7 @@ smc2_status validate(const smc2_config* c) {
     const int t = c->n_datasets > 1 ? c->ds_T[d] : c->T;
     if (n < 1 || n > SMC2_MAX_N || m < 1 || m > SMC2_MAX_M || t < 1 || t > (1 << 24))
       return SMC2_EINVAL;
-    const int gt = pf_group_threads(c->ppt ? c->ppt : 8, m);
+    const int gt = pf_group_threads(c->ppt ? c->ppt : 16, m);
     if (gt > (c->cta_threads ? c->cta_threads : kPfMaxBlock)) return SMC2_EINVAL;
   }
   return SMC2_OK;
@@ -243,7 +244,7 @@ smc2_status apply_shape(smc2_ctx* c, int ppt, int block, bool upload) {
 // on the context's own work list (prior draws of theta, min(T, 32) steps).
 smc2_status choose_launch_shape(smc2_ctx* c) {
   std::vector<std::pair<int, int>> cand;
-  for (int ppt : {1, 2, 4, 8}) {
+  for (int ppt : {1, 2, 4, 8, 16}) {
     if (c->cfg.ppt && ppt != c->cfg.ppt) continue;
     for (int block = 32; block <= kPfMaxBlock; block += 32) {
       if (c->cfg.cta_threads && block != c->cfg.cta_threads) continue;

@@ -1,0 +1,494 @@
+// pf_impl.cuh -- bootstrap particle filter kernel (Sec. II of the paper).
+//
+// One group of threads runs one filter over all T steps: each thread holds
+// PPT consecutive particles in registers.  Per step:
+//   1. propagate with the state equation (Eq. 1) using counter-based normals;
+//   2. log-weight with the observation density (Eq. 2; bootstrap form of Eq. 5);
+//   3. group max of the log-weights (warp shuffles, one barrier);
+//   4. quantise q_j = floor(exp(l_j - max) 2^B), warp-local inclusive scan of q
+//      in registers + shuffles, warp totals and particle states to shared memory
+//      (second barrier);
+//   5. log-likelihood increment log((1/M) sum_j w_j) = max + log(S 2^-B) - log M
+//      from the exact integer total S (Eq. 8, with the mean-weight reset of
+//      Eq. 13 every step);
+//   6. systematic resampling (Eqs. 26-27): slot j takes the first particle whose
+//      cumulative weight exceeds floor((j + u) S / M), found by a search over
+//      the warp totals and then a binary search inside one warp's prefix;
+//      the slot's new state is gathered from shared memory.
+// A work unit is `count` filters of one job (dataset); units are taken from an
+// atomic queue so that jobs of uneven length balance over the SMs.
+// With 8 or more particles per thread ("staged"), the log-weights and the
+// thread-local prefixes pass through shared memory instead of registers, which
+// lets a 512-particle filter run in a single warp: the group reductions become
+// warp shuffles and the per-thread costs are shared by 16 particles.
+#pragma once
+#include <cfloat>
+#include <cmath>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace smc2 {
+
+template <typename R>
+struct R4Of;
+template <>
+struct R4Of<float> {
+  using type = float4;
+};
+struct __align__(32) Double4 {
+  double x, y, z, w;
+};
+template <>
+struct R4Of<double> {
+  using type = Double4;
+};
+
+template <int MODEL>
+struct ModelDims;
+template <>
+struct ModelDims<MODEL_LG> {
+  static constexpr int D = 3, NS = 1;
+};
+template <>
+struct ModelDims<MODEL_SEIR> {
+  static constexpr int D = 4, NS = 4;
+};
+
+__host__ __device__ inline int group_threads_for(int ppt, int M) {
+  const int t = (M + ppt - 1) / ppt;
+  return (t + 31) & ~31;
+}
+
+// Shared memory of one filter group (Mp = particles incl. padding, nw warps):
+//   P  u64 [Mp]      warp-local inclusive prefix of the quantised weights
+//   X  R   [Mp][ns]  particle states, one vector per particle
+//   Z  R   [4][Mp]   the four normals of the current Philox counter of every particle
+//   L  R   [Mp]      log-weights (staged path only)
+//   wsum u64 [nw], wmax 8 B [nw], sU u32 [8] (resampling words of two groups of four steps)
+__host__ __device__ constexpr bool is_staged(int ppt) { return ppt >= 8; }
+__host__ __device__ inline size_t region_bytes(int Mp, int nw, int ns, int rsize, bool staged) {
+  size_t b = (size_t)Mp * 8 + (size_t)ns * Mp * rsize + (size_t)4 * Mp * rsize + (size_t)nw * 16 + 32;
+  if (staged) b += (size_t)Mp * rsize;
+  return (b + 15) & ~(size_t)15;
+}
+
+// Register budget per variant (threads x registers must fit the SM at the
+// shapes the tuner tries); beyond it the compiler spills to local memory.
+template <typename R, int PPT>
+struct RegCap {
+  static constexpr int value =
+      sizeof(R) == 4 ? (PPT <= 2 ? 64 : (PPT == 4 ? 80 : (PPT == 8 ? 128 : 168)))
+                     : (PPT == 1 ? 80 : (PPT == 2 ? 96 : (PPT <= 8 ? 128 : 168)));
+  static_assert(PPT == 1 || PPT == 2 || PPT == 4 || PPT == 8 || PPT == 16, "particles per thread");
+};
+
+template <typename R, int NS>
+struct StateVec;
+template <typename R>
+struct StateVec<R, 1> {
+  __device__ __forceinline__ static void store(R* X, int j, const R* x) { X[j] = x[0]; }
+  __device__ __forceinline__ static void load(const R* X, int j, R* x) { x[0] = X[j]; }
+};
+template <>
+struct StateVec<float, 4> {
+  __device__ __forceinline__ static void store(float* X, int j, const float* x) {
+    reinterpret_cast<float4*>(X)[j] = make_float4(x[0], x[1], x[2], x[3]);
+  }
+  __device__ __forceinline__ static void load(const float* X, int j, float* x) {
+    const float4 v = reinterpret_cast<const float4*>(X)[j];
+    x[0] = v.x;
+    x[1] = v.y;
+    x[2] = v.z;
+    x[3] = v.w;
+  }
+};
+template <>
+struct StateVec<double, 4> {
+  __device__ __forceinline__ static void store(double* X, int j, const double* x) {
+    reinterpret_cast<double2*>(X)[2 * j] = make_double2(x[0], x[1]);
+    reinterpret_cast<double2*>(X)[2 * j + 1] = make_double2(x[2], x[3]);
+  }
+  __device__ __forceinline__ static void load(const double* X, int j, double* x) {
+    const double2 a = reinterpret_cast<const double2*>(X)[2 * j];
+    const double2 b = reinterpret_cast<const double2*>(X)[2 * j + 1];
+    x[0] = a.x;
+    x[1] = a.y;
+    x[2] = b.x;
+    x[3] = b.y;
+  }
+};
+
+template <typename R>
+__device__ __forceinline__ R neg_inf();
+template <>
+__device__ __forceinline__ float neg_inf<float>() {
+  return -INFINITY;
+}
+template <>
+__device__ __forceinline__ double neg_inf<double>() {
+  return -HUGE_VAL;
+}
+
+__device__ __forceinline__ uint64_t to_u64_rz(float v) { return __float2ull_rz(v); }
+__device__ __forceinline__ uint64_t to_u64_rz(double v) { return __double2ull_rz(v); }
+
+// exp in the working precision: the FP32 path uses the hardware exp2
+// approximation (relative error about 2^-22), the FP64 path the full-precision exp.
+__device__ __forceinline__ float fast_exp(float x) { return __expf(x); }
+__device__ __forceinline__ double fast_exp(double x) { return exp(x); }
+
+// Per-filter constants of the model in the working precision.
+template <typename R, int MODEL>
+struct FilterParams;
+
+template <typename R>
+struct FilterParams<R, MODEL_LG> {
+  R phi, sx, inv_sy, c_obs;
+  __device__ void load(const double* th, const PFModel&) {
+    const double sy = exp(th[2]);
+    phi = (R)th[0];
+    sx = (R)exp(th[1]);
+    inv_sy = (R)(1.0 / sy);
+    c_obs = (R)(-0.5 * kLog2Pi - th[2]);
+  }
+  __device__ __forceinline__ void init(R* x, R z0, const double*) const { x[0] = z0; }
+  __device__ __forceinline__ void propagate(R* x, R z) const { x[0] = phi * x[0] + sx * z; }
+  template <typename R4>
+  __device__ __forceinline__ R log_obs(const R* x, const R4& ob) const {
+    const R r = (ob.x - x[0]) * inv_sy;
+    return c_obs - (R)0.5 * r * r;
+  }
+};
+
+template <typename R>
+struct FilterParams<R, MODEL_SEIR> {
+  R srw, kappa, gamma, inv_npop, dt, lam_floor, S0, E0, I0, lb0;
+  int n_sub;
+  __device__ void load(const double* th, const PFModel& m) {
+    lb0 = (R)th[0];
+    srw = (R)exp(th[1]);
+    kappa = (R)exp(th[2]);
+    gamma = (R)exp(th[3]);
+    inv_npop = (R)(1.0 / m.npop);
+    dt = (R)(1.0 / m.n_sub);
+    n_sub = m.n_sub;
+    lam_floor = (R)m.lambda_floor;
+    S0 = (R)(m.npop - m.e0 - m.i0);
+    E0 = (R)m.e0;
+    I0 = (R)m.i0;
+  }
+  __device__ __forceinline__ void init(R* x, R, const double*) const {
+    x[0] = S0;
+    x[1] = E0;
+    x[2] = I0;
+    x[3] = lb0;
+  }
+  // x = (S, E, I, log beta); the day's incidence lambda is returned in x[4]'s place
+  __device__ __forceinline__ void propagate(R* x, R z) const {
+    x[3] = x[3] + srw * z;
+  }
+  __device__ __forceinline__ void substep(R beta, R& S, R& E, R& I, R& lam) const {
+    const R infection = beta * S * I * inv_npop;
+    const R onset = kappa * E;
+    const R recovery = gamma * I;
+    lam += dt * onset;
+    S = fmax(S - dt * infection, (R)0);
+    E = fmax(E + dt * (infection - onset), (R)0);
+    I = fmax(I + dt * (onset - recovery), (R)0);
+  }
+  __device__ __forceinline__ R day(R* x) const {
+    const R beta = fast_exp(x[3]);
+    R S = x[0], E = x[1], I = x[2], lam = (R)0;
+    if (n_sub == 2) {  // the common case, unrolled
+      substep(beta, S, E, I, lam);
+      substep(beta, S, E, I, lam);
+    } else {
+      for (int s = 0; s < n_sub; ++s) substep(beta, S, E, I, lam);
+    }
+    x[0] = S;
+    x[1] = E;
+    x[2] = I;
+    return fmax(lam, lam_floor);
+  }
+  // Poisson log-pmf written as y (log1p(d) - d) + c_y with d = (lambda - y) / y and
+  // c_y = y log y - y - log y! precomputed: no cancellation between y log lambda and lambda.
+  template <typename R4>
+  __device__ __forceinline__ R log_pois(R lam, const R4& ob) const {
+    if (ob.x > (R)0) {
+      const R d = (lam - ob.x) * ob.y;
+      return ob.x * (log1p(d) - d) + ob.z;
+    }
+    return -lam;
+  }
+};
+
+template <typename R, int MODEL, int PPT>
+__device__ __forceinline__ void run_filter(const PFJob& J, const PFModel& mdl, int i, int g, int lt,
+                                           int gt, unsigned char* region, uint2 key, uint32_t k,
+                                           int t_cap) {
+  constexpr int NS = ModelDims<MODEL>::NS;
+  constexpr int D = ModelDims<MODEL>::D;
+  using R4 = typename R4Of<R>::type;
+  const int M = J.M, T = t_cap > 0 ? min(J.T, t_cap) : J.T;
+  const int Mp = gt * PPT;
+  const int nw = gt >> 5;
+  const int lane = lt & 31, warp = lt >> 5;
+  const int seg = 32 * PPT;  // particles per warp
+
+  uint64_t* P = reinterpret_cast<uint64_t*>(region);   // [Mp] warp-local inclusive prefix of q
+  R* X = reinterpret_cast<R*>(P + Mp);                  // [Mp][NS] particle states
+  R* Z = X + (size_t)NS * Mp;                           // [4][Mp] cached normals
+  uint64_t* wsum = reinterpret_cast<uint64_t*>(Z + (size_t)4 * Mp);  // [nw] warp totals
+  R* wmax = reinterpret_cast<R*>(wsum + nw);            // [nw] warp maxima (8-byte slots)
+  uint32_t* sU = reinterpret_cast<uint32_t*>(wsum + 2 * nw);  // [8] resampling words
+  R* Lw = reinterpret_cast<R*>(reinterpret_cast<unsigned char*>(sU) + 32);  // [Mp] staged log-weights
+  constexpr bool STAGED = is_staged(PPT);
+
+  auto group_sync = [&]() {
+    if (nw == 1)
+      __syncwarp();
+    else
+      named_barrier(1 + g, gt);
+  };
+
+  double th[D];
+#pragma unroll
+  for (int d = 0; d < D; ++d) th[d] = J.theta[(size_t)d * J.ld + i];
+  FilterParams<R, MODEL> fp;
+  fp.load(th, mdl);
+
+  const uint32_t c2 = counter_c2((uint32_t)i, J.c2hi);
+  const uint32_t c3prop = counter_c3(TAG_PF_PROP, k);
+  const uint32_t c3res = counter_c3(TAG_PF_RES, k);
+  const int B = fixed_point_bits(M);
+  const int log2M = ((M & (M - 1)) == 0) ? (__ffs(M) - 1) : -1;
+  const R scaleB = (R)ldexp(1.0, B);
+  const double log_norm = -(double)B * kLn2 - log((double)M);
+  const R4* obs = reinterpret_cast<const R4*>(J.obs);
+
+  R x[PPT][NS];
+#pragma unroll
+  for (int r = 0; r < PPT; ++r) {
+    R z0 = (R)0;
+    if constexpr (MODEL == MODEL_LG) {
+      R z[4];
+      normals4<R>(make_uint4((uint32_t)(lt * PPT + r), 0u, c2, counter_c3(TAG_PF_INIT, k)), key, z);
+      z0 = z[0];
+    }
+    fp.init(x[r], z0, th);
+  }
+
+  double loglik = 0.0;
+  for (int t = 1; t <= T; ++t) {
+    const int tm = (t - 1) & 3;
+    if (tm == 0) {  // one Philox call per particle every four steps; normals kept in shared memory
+#pragma unroll
+      for (int r = 0; r < PPT; ++r) {
+        R z4[4];
+        normals4<R>(make_uint4((uint32_t)(lt * PPT + r), (uint32_t)((t - 1) >> 2), c2, c3prop), key,
+                    z4);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) Z[e * Mp + lt * PPT + r] = z4[e];
+      }
+    }
+    // resampling words of steps t..t+3, one lane each, double-buffered by step group
+    uint32_t* sUg = sU + 4 * (((t - 1) >> 2) & 1);
+    if (tm == 0 && lt < 4 && t + lt < T)
+      sUg[lt] = philox4x32_10(make_uint4(0u, (uint32_t)(t + lt), c2, c3res), key).x;
+    const R4 ob = obs[t - 1];
+    R ell[STAGED ? 1 : PPT];
+    R lmax = neg_inf<R>();
+#pragma unroll
+    for (int r = 0; r < PPT; ++r) {
+      fp.propagate(x[r], Z[tm * Mp + lt * PPT + r]);
+      R l;
+      if constexpr (MODEL == MODEL_LG) {
+        l = fp.log_obs(x[r], ob);
+      } else {
+        const R lam = fp.day(x[r]);
+        l = fp.log_pois(lam, ob);
+      }
+      if (isnan(l) || lt * PPT + r >= M) l = neg_inf<R>();
+      if constexpr (STAGED)
+        Lw[lt * PPT + r] = l;
+      else
+        ell[r] = l;
+      lmax = fmax(lmax, l);
+    }
+    // (3) group maximum
+    lmax = warp_max(lmax);
+    if (nw > 1 && lane == 0) wmax[warp] = lmax;
+    group_sync();
+    if (nw > 1) lmax = warp_max(lane < nw ? wmax[lane] : neg_inf<R>());
+    const R m = lmax;
+    if (!(m > neg_inf<R>())) {  // every weight vanished: the estimate is zero
+      loglik = -HUGE_VAL;
+      if (lt == 0 && J.delta)
+        for (int s = t; s <= T; ++s) J.delta[(size_t)i * T + (s - 1)] = -HUGE_VAL;
+      break;
+    }
+    // (4) quantise and scan (warp-local inclusive prefix in P, warp totals in wsum)
+    uint64_t run = 0;
+    if constexpr (STAGED) {
+      // thread-local inclusive prefix into P, then the thread's offset added in place
+#pragma unroll
+      for (int r = 0; r < PPT; ++r) {
+        const R l = Lw[lt * PPT + r];
+        run += (l > neg_inf<R>()) ? to_u64_rz(fast_exp(l - m) * scaleB) : 0ull;
+        P[lt * PPT + r] = run;
+        StateVec<R, NS>::store(X, lt * PPT + r, x[r]);
+      }
+    }
+    uint64_t c[STAGED ? 1 : PPT];
+    if constexpr (!STAGED) {
+#pragma unroll
+      for (int r = 0; r < PPT; ++r) {
+        const uint64_t qv = (ell[r] > neg_inf<R>()) ? to_u64_rz(fast_exp(ell[r] - m) * scaleB) : 0ull;
+        run += qv;
+        c[r] = run;
+      }
+    }
+    const uint64_t incl = warp_incl_scan_u64(run, lane);
+    const uint64_t excl = incl - run;
+#pragma unroll
+    for (int r = 0; r < PPT; ++r) {
+      if constexpr (STAGED) {
+        P[lt * PPT + r] += excl;
+      } else {
+        P[lt * PPT + r] = excl + c[r];
+        StateVec<R, NS>::store(X, lt * PPT + r, x[r]);
+      }
+    }
+    if (lane == 31) wsum[warp] = incl;
+    group_sync();
+    uint64_t S = 0;
+    for (int w = 0; w < nw; ++w) S += wsum[w];
+    // (5) log-likelihood increment: log S from its binary exponent and mantissa
+    if (lt == 0) {
+      const int e = 63 - __clzll((long long)S);
+      const R mant = (R)(e >= 52 ? (S >> (e - 52)) : (S << (52 - e))) * (R)0x1p-52;
+      const double delta = (double)m + ((double)e * kLn2 + (double)log(mant)) + log_norm;
+      loglik += delta;
+      if (J.delta) J.delta[(size_t)i * T + (t - 1)] = delta;
+    }
+    // (6) systematic resampling and ancestor gather.  The thread's slots are
+    // consecutive and their ancestors non-decreasing: the first is found by a
+    // search over the warp totals and a binary search inside one warp's prefix,
+    // the others by galloping forward from the previous ancestor.
+    if (t < T) {
+      const uint32_t U = sUg[tm];
+      int w = 0, a = 0;
+      uint64_t base = 0;
+#pragma unroll
+      for (int r = 0; r < PPT; ++r) {
+        const int j = lt * PPT + r;
+        if (j < M) {
+          const uint64_t tau = slot_threshold((uint32_t)j, U, S, M, log2M);
+          while (w < nw - 1 && base + wsum[w] <= tau) {  // answer lies in a later warp
+            base += wsum[w];
+            ++w;
+            a = w * seg;
+          }
+          const uint64_t tl = tau - base;
+          const int seg_end = w * seg + seg - 1;  // P[seg_end] = wsum[w] > tl
+          if (r == 0) {
+            int lo = w * seg, hi = seg_end;
+            while (lo < hi) {
+              const int mid = (lo + hi) >> 1;
+              if (P[mid] > tl)
+                hi = mid;
+              else
+                lo = mid + 1;
+            }
+            a = lo;
+          } else if (P[a] <= tl) {
+            int lo = a + 1, step = 1;
+            while (lo + step - 1 < seg_end && P[lo + step - 1] <= tl) {
+              lo += step;
+              step <<= 1;
+            }
+            int hi = min(lo + step - 1, seg_end);
+            while (lo < hi) {
+              const int mid = (lo + hi) >> 1;
+              if (P[mid] > tl)
+                hi = mid;
+              else
+                lo = mid + 1;
+            }
+            a = lo;
+          }
+          StateVec<R, NS>::load(X, a, x[r]);
+          if (J.anc) J.anc[((size_t)i * (T - 1) + (t - 1)) * M + j] = a;
+        }
+      }
+    }
+  }
+  if (lt == 0) J.loglik[i] = loglik;
+}
+
+template <typename R, int MODEL, int PPT>
+__global__ void __maxnreg__((RegCap<R, PPT>::value)) pf_kernel(PFLaunch L) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_wu;
+  constexpr int NS = ModelDims<MODEL>::NS;
+  const uint32_t k = L.k_done ? (uint32_t)(*L.k_done + 1) : (uint32_t)L.k_imm;
+  const uint2 key = seed_key(L.seed);
+  for (int it = 0;; ++it) {
+    int w;
+    if (L.wu_counter) {
+      __syncthreads();
+      if (threadIdx.x == 0) s_wu = atomicAdd(L.wu_counter, 1);
+      __syncthreads();
+      w = s_wu;
+    } else {
+      w = blockIdx.x + it * gridDim.x;
+    }
+    if (w >= L.n_wu) break;
+    int job, first, count;
+    if (L.wus) {
+      const int4 u = L.wus[w];
+      job = u.x;
+      first = u.y;
+      count = u.z;
+    } else {
+      job = 0;
+      first = w * L.fpc_single;
+      count = min(L.fpc_single, L.job0.n - first);
+    }
+    const PFJob J = L.jobs ? L.jobs[job] : L.job0;
+    const int gt = group_threads_for(PPT, J.M);
+    const int g = threadIdx.x / gt, lt = threadIdx.x - g * gt;
+    const size_t rb = region_bytes(gt * PPT, gt >> 5, NS, (int)sizeof(R), is_staged(PPT));
+    if (g < count && (g + 1) * gt <= (int)blockDim.x)
+      run_filter<R, MODEL, PPT>(J, L.mdl, first + g, g, lt, gt, smem + g * rb, key, k, L.t_cap);
+    if (!L.wu_counter) __syncthreads();
+  }
+}
+
+
+template <typename R, int MODEL, int PPT>
+const void* pf_kernel_ptr() {
+  return reinterpret_cast<const void*>(&pf_kernel<R, MODEL, PPT>);
+}
+
+template <typename R>
+const void* pf_select_precision(int model, int ppt) {
+#define SMC2_PF_CASE(MODEL)                          \
+  switch (ppt) {                                     \
+    case 1: return pf_kernel_ptr<R, MODEL, 1>();     \
+    case 2: return pf_kernel_ptr<R, MODEL, 2>();     \
+    case 4: return pf_kernel_ptr<R, MODEL, 4>();     \
+    case 8: return pf_kernel_ptr<R, MODEL, 8>();     \
+    case 16: return pf_kernel_ptr<R, MODEL, 16>();   \
+    default: return nullptr;                         \
+  }
+  if (model == MODEL_LG) SMC2_PF_CASE(MODEL_LG)
+  SMC2_PF_CASE(MODEL_SEIR)
+#undef SMC2_PF_CASE
+}
+
+const void* pf_select_f32(int model, int ppt);
+const void* pf_select_f64(int model, int ppt);
+
+}  // namespace smc2
