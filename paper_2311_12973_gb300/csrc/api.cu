@@ -55,6 +55,7 @@ struct smc2_ctx {
   int* d_status = nullptr;
   unsigned* d_grid_ticket = nullptr;
   int ppt = 4, pf_block = 256, pf_grid = 1;
+  bool pf_named = false;
   size_t pf_smem = 0;
   int k_host = 0;
   std::map<GraphKey, TimedGraph> graphs;
@@ -196,11 +197,13 @@ size_t layout(smc2_ctx* c, char* base) {
 
 // A launch shape is valid when every dataset's filter group fits the CTA and,
 // for groups wider than a warp, at most 15 groups share it (named barriers 1..15).
-bool shape_valid(const smc2_ctx* c, int ppt, int block) {
+bool shape_valid(const smc2_ctx* c, int ppt, int block, bool named) {
   for (int m : c->M) {
     const int gt = pf_group_threads(ppt, m);
     if (gt > block) return false;
-    if (gt > 32 && block / gt > 15) return false;
+    if (gt == 32) continue;                       // one-warp groups: __syncwarp
+    if (!named && gt != block) return false;      // wide group = the whole CTA
+    if (named && (block / gt > 15 || block % gt)) return false;
   }
   return true;
 }
@@ -219,18 +222,19 @@ void build_work_units(smc2_ctx* c, std::vector<int4>& wus) {
   });
 }
 
-smc2_status apply_shape(smc2_ctx* c, int ppt, int block, bool upload) {
+smc2_status apply_shape(smc2_ctx* c, int ppt, int block, bool named, bool upload) {
   c->ppt = ppt;
   c->pf_block = block;
+  c->pf_named = named;
   size_t smem = 0;
   for (int m : c->M) smem = std::max(smem, pf_smem_bytes(c->precision, c->model, ppt, block, m));
   if (smem > 227 * 1024) return SMC2_EINVAL;
   c->pf_smem = smem;
-  SMC2_TRY(pf_configure(c->precision, c->model, ppt, smem));
+  SMC2_TRY(pf_configure(c->precision, c->model, ppt, named, smem));
   std::vector<int4> wus;
   build_work_units(c, wus);
   c->n_wus = (int)wus.size();
-  const int occ = pf_occupancy(c->precision, c->model, ppt, block, smem);
+  const int occ = pf_occupancy(c->precision, c->model, ppt, named, block, smem);
   if (occ < 1) return SMC2_EINVAL;
   c->pf_grid = std::min(c->n_wus, occ * c->sms);
   c->pl.n_wu = c->n_wus;
@@ -243,26 +247,33 @@ smc2_status apply_shape(smc2_ctx* c, int ppt, int block, bool upload) {
 // Launch-shape tuner: time every valid (particles per thread, CTA threads) pair
 // on the context's own work list (prior draws of theta, min(T, 32) steps).
 smc2_status choose_launch_shape(smc2_ctx* c) {
-  std::vector<std::pair<int, int>> cand;
+  struct Shape {
+    int ppt, block;
+    bool named;
+  };
+  std::vector<Shape> cand;
   for (int ppt : {1, 2, 4, 8, 16}) {
     if (c->cfg.ppt && ppt != c->cfg.ppt) continue;
     for (int block = 32; block <= kPfMaxBlock; block += 32) {
       if (c->cfg.cta_threads && block != c->cfg.cta_threads) continue;
       if (!c->cfg.cta_threads && (block & (block - 1))) continue;  // powers of two when tuning
-      if (shape_valid(c, ppt, block)) cand.push_back({ppt, block});
+      if (shape_valid(c, ppt, block, false))
+        cand.push_back({ppt, block, false});
+      else if (shape_valid(c, ppt, block, true))
+        cand.push_back({ppt, block, true});
     }
   }
   if (cand.empty()) return SMC2_EINVAL;
-  if (cand.size() == 1) return apply_shape(c, cand[0].first, cand[0].second, true);
+  if (cand.size() == 1) return apply_shape(c, cand[0].ppt, cand[0].block, cand[0].named, true);
   cudaStream_t s = c->stream;
   SMC2_TRY(outer_propose(c->op, c->max_nblk, s));  // k = 1: prior draws into the proposal buffers
   cudaEvent_t e0, e1;
   SMC2_TRY(cudaEventCreate(&e0));
   SMC2_TRY(cudaEventCreate(&e1));
   float best = 1e30f;
-  std::pair<int, int> pick = cand[0];
+  Shape pick = cand[0];
   for (const auto& cb : cand) {
-    if (apply_shape(c, cb.first, cb.second, true) != SMC2_OK) continue;
+    if (apply_shape(c, cb.ppt, cb.block, cb.named, true) != SMC2_OK) continue;
     PFLaunch L = c->pl;
     float ms = 0.f;
     bool ok = true;
@@ -271,8 +282,8 @@ smc2_status choose_launch_shape(smc2_ctx* c) {
       L.t_cap = rep == 0 ? 4 : 32;
       ok = cudaMemsetAsync(c->d_wu_counter, 0, sizeof(int), s) == cudaSuccess &&
            cudaEventRecord(e0, s) == cudaSuccess &&
-           pf_launch(c->precision, c->model, c->ppt, c->pf_grid, c->pf_block, c->pf_smem, L, s) ==
-               cudaSuccess &&
+           pf_launch(c->precision, c->model, c->ppt, c->pf_named, c->pf_grid, c->pf_block, c->pf_smem,
+                     L, s) == cudaSuccess &&
            cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
            cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
       c->kernel_launches++;
@@ -286,7 +297,7 @@ smc2_status choose_launch_shape(smc2_ctx* c) {
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  return apply_shape(c, pick.first, pick.second, true);
+  return apply_shape(c, pick.ppt, pick.block, pick.named, true);
 }
 
 smc2_status clear_run_state(smc2_ctx* c) {
@@ -359,7 +370,8 @@ smc2_status enqueue_iteration(smc2_ctx* c, cudaStream_t s, cudaEvent_t ev0, cuda
   SMC2_TRY(outer_propose(c->op, c->max_nblk, s));
   SMC2_TRY(cudaMemsetAsync(c->d_wu_counter, 0, sizeof(int), s));
   if (ev0) SMC2_TRY(cudaEventRecordWithFlags(ev0, s, cudaEventRecordExternal));
-  SMC2_TRY(pf_launch(c->precision, c->model, c->ppt, c->pf_grid, c->pf_block, c->pf_smem, c->pl, s));
+  SMC2_TRY(pf_launch(c->precision, c->model, c->ppt, c->pf_named, c->pf_grid, c->pf_block, c->pf_smem,
+                     c->pl, s));
   if (ev1) SMC2_TRY(cudaEventRecordWithFlags(ev1, s, cudaEventRecordExternal));
   SMC2_TRY(outer_weights(c->op, c->max_nblk, s));
   SMC2_TRY(outer_quantise(c->op, c->max_nblk, s));
@@ -554,9 +566,11 @@ static smc2_status pf_standalone(smc2_ctx* c, const double* theta, int n, int it
   L.wu_counter = nullptr;
   L.k_done = nullptr;
   L.k_imm = iteration;
-  const int occ = std::max(1, pf_occupancy(c->precision, c->model, c->ppt, c->pf_block, c->pf_smem));
+  const int occ =
+      std::max(1, pf_occupancy(c->precision, c->model, c->ppt, c->pf_named, c->pf_block, c->pf_smem));
   const int grid = std::min(L.n_wu, occ * c->sms);
-  SMC2_TRY(pf_launch(c->precision, c->model, c->ppt, grid, c->pf_block, c->pf_smem, L, c->stream));
+  SMC2_TRY(pf_launch(c->precision, c->model, c->ppt, c->pf_named, grid, c->pf_block, c->pf_smem, L,
+                     c->stream));
   c->kernel_launches++;
   return SMC2_OK;
 }

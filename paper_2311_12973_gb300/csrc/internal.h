@@ -111,10 +111,10 @@ struct PFLaunch {
 // Launch-shape helpers (pf.cu).
 size_t pf_smem_bytes(int precision, int model, int ppt, int block, int M);
 int pf_group_threads(int ppt, int M);
-cudaError_t pf_launch(int precision, int model, int ppt, int grid, int block, size_t smem,
+cudaError_t pf_launch(int precision, int model, int ppt, bool named, int grid, int block, size_t smem,
                       const PFLaunch& L, cudaStream_t s);
-cudaError_t pf_configure(int precision, int model, int ppt, size_t smem);
-int pf_occupancy(int precision, int model, int ppt, int block, size_t smem);
+cudaError_t pf_configure(int precision, int model, int ppt, bool named, size_t smem);
+int pf_occupancy(int precision, int model, int ppt, bool named, int block, size_t smem);
 
 // Outer kernels (outer.cu).
 cudaError_t outer_obs_terms(int precision, int model, const double* y, int T, void* obs,

@@ -17,26 +17,27 @@ size_t pf_smem_bytes(int precision, int model, int ppt, int block, int M) {
   return (size_t)fpc * region_bytes(gt * ppt, gt >> 5, ns, rs, is_staged(ppt));
 }
 
-static const void* select_kernel(int precision, int model, int ppt) {
-  return precision == SMC2_PREC_FP64 ? pf_select_f64(model, ppt) : pf_select_f32(model, ppt);
+static const void* select_kernel(int precision, int model, int ppt, bool named) {
+  return precision == SMC2_PREC_FP64 ? pf_select_f64(model, ppt, named)
+                                     : pf_select_f32(model, ppt, named);
 }
 
-cudaError_t pf_configure(int precision, int model, int ppt, size_t smem) {
-  const void* f = select_kernel(precision, model, ppt);
+cudaError_t pf_configure(int precision, int model, int ppt, bool named, size_t smem) {
+  const void* f = select_kernel(precision, model, ppt, named);
   if (!f) return cudaErrorInvalidValue;
   return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-int pf_occupancy(int precision, int model, int ppt, int block, size_t smem) {
-  const void* f = select_kernel(precision, model, ppt);
+int pf_occupancy(int precision, int model, int ppt, bool named, int block, size_t smem) {
+  const void* f = select_kernel(precision, model, ppt, named);
   int n = 0;
   if (!f || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, block, smem) != cudaSuccess) return 0;
   return n;
 }
 
-cudaError_t pf_launch(int precision, int model, int ppt, int grid, int block, size_t smem,
+cudaError_t pf_launch(int precision, int model, int ppt, bool named, int grid, int block, size_t smem,
                       const PFLaunch& L, cudaStream_t s) {
-  const void* f = select_kernel(precision, model, ppt);
+  const void* f = select_kernel(precision, model, ppt, named);
   if (!f) return cudaErrorInvalidValue;
   void* args[] = {const_cast<PFLaunch*>(&L)};
   return cudaLaunchKernel(f, dim3(grid), dim3(block), args, smem, s);

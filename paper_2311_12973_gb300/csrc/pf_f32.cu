@@ -2,5 +2,7 @@
 #include "pf_impl.cuh"
 
 namespace smc2 {
-const void* pf_select_f32(int model, int ppt) { return pf_select_precision<float>(model, ppt); }
+const void* pf_select_f32(int model, int ppt, bool named) {
+  return pf_select_precision<float>(model, ppt, named);
+}
 }  // namespace smc2

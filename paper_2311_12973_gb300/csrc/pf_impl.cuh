@@ -223,7 +223,11 @@ struct FilterParams<R, MODEL_SEIR> {
   }
 };
 
-template <typename R, int MODEL, int PPT>
+// NAMED: groups wider than a warp that share a CTA synchronise on named
+// barriers 1..15 (ptxas then reserves all 16 barriers of the CTA, which limits
+// residency to four CTAs per SM).  Otherwise a wide group is the whole CTA and
+// uses __syncthreads, and a one-warp group uses __syncwarp.
+template <typename R, int MODEL, int PPT, bool NAMED>
 __device__ __forceinline__ void run_filter(const PFJob& J, const PFModel& mdl, int i, int g, int lt,
                                            int gt, unsigned char* region, uint2 key, uint32_t k,
                                            int t_cap) {
@@ -248,8 +252,10 @@ __device__ __forceinline__ void run_filter(const PFJob& J, const PFModel& mdl, i
   auto group_sync = [&]() {
     if (nw == 1)
       __syncwarp();
-    else
+    else if constexpr (NAMED)
       named_barrier(1 + g, gt);
+    else
+      __syncthreads();
   };
 
   double th[D];
@@ -427,7 +433,7 @@ __device__ __forceinline__ void run_filter(const PFJob& J, const PFModel& mdl, i
   if (lt == 0) J.loglik[i] = loglik;
 }
 
-template <typename R, int MODEL, int PPT>
+template <typename R, int MODEL, int PPT, bool NAMED>
 __global__ void __maxnreg__((RegCap<R, PPT>::value)) pf_kernel(PFLaunch L) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_wu;
@@ -461,34 +467,37 @@ __global__ void __maxnreg__((RegCap<R, PPT>::value)) pf_kernel(PFLaunch L) {
     const int g = threadIdx.x / gt, lt = threadIdx.x - g * gt;
     const size_t rb = region_bytes(gt * PPT, gt >> 5, NS, (int)sizeof(R), is_staged(PPT));
     if (g < count && (g + 1) * gt <= (int)blockDim.x)
-      run_filter<R, MODEL, PPT>(J, L.mdl, first + g, g, lt, gt, smem + g * rb, key, k, L.t_cap);
+      run_filter<R, MODEL, PPT, NAMED>(J, L.mdl, first + g, g, lt, gt, smem + g * rb, key, k, L.t_cap);
     if (!L.wu_counter) __syncthreads();
   }
 }
 
 
-template <typename R, int MODEL, int PPT>
+template <typename R, int MODEL, int PPT, bool NAMED>
 const void* pf_kernel_ptr() {
-  return reinterpret_cast<const void*>(&pf_kernel<R, MODEL, PPT>);
+  return reinterpret_cast<const void*>(&pf_kernel<R, MODEL, PPT, NAMED>);
+}
+
+template <typename R, int MODEL, bool NAMED>
+const void* pf_select_ppt(int ppt) {
+  switch (ppt) {
+    case 1: return pf_kernel_ptr<R, MODEL, 1, NAMED>();
+    case 2: return pf_kernel_ptr<R, MODEL, 2, NAMED>();
+    case 4: return pf_kernel_ptr<R, MODEL, 4, NAMED>();
+    case 8: return pf_kernel_ptr<R, MODEL, 8, NAMED>();
+    case 16: return pf_kernel_ptr<R, MODEL, 16, NAMED>();
+    default: return nullptr;
+  }
 }
 
 template <typename R>
-const void* pf_select_precision(int model, int ppt) {
-#define SMC2_PF_CASE(MODEL)                          \
-  switch (ppt) {                                     \
-    case 1: return pf_kernel_ptr<R, MODEL, 1>();     \
-    case 2: return pf_kernel_ptr<R, MODEL, 2>();     \
-    case 4: return pf_kernel_ptr<R, MODEL, 4>();     \
-    case 8: return pf_kernel_ptr<R, MODEL, 8>();     \
-    case 16: return pf_kernel_ptr<R, MODEL, 16>();   \
-    default: return nullptr;                         \
-  }
-  if (model == MODEL_LG) SMC2_PF_CASE(MODEL_LG)
-  SMC2_PF_CASE(MODEL_SEIR)
-#undef SMC2_PF_CASE
+const void* pf_select_precision(int model, int ppt, bool named) {
+  if (model == MODEL_LG)
+    return named ? pf_select_ppt<R, MODEL_LG, true>(ppt) : pf_select_ppt<R, MODEL_LG, false>(ppt);
+  return named ? pf_select_ppt<R, MODEL_SEIR, true>(ppt) : pf_select_ppt<R, MODEL_SEIR, false>(ppt);
 }
 
-const void* pf_select_f32(int model, int ppt);
-const void* pf_select_f64(int model, int ppt);
+const void* pf_select_f32(int model, int ppt, bool named);
+const void* pf_select_f64(int model, int ppt, bool named);
 
 }  // namespace smc2
