@@ -214,6 +214,28 @@ smc2_status smc2_resample_systematic(const uint64_t* q_dev, int n, uint32_t U, i
 smc2_status smc2_philox_normals(uint64_t seed, const uint32_t* ctr_dev, int n, int precision,
                                 uint32_t* words_dev, double* z_dev, void* stream);
 
+/* Particle-filter log-likelihoods that allocate no device memory (the paper
+ * has no counterpart: this is a deployment variant of smc2_pf_loglik).
+ * For callers that cannot allocate once running: a fixed device-memory
+ * budget, a framework whose own pool owns the device memory, or a loop that
+ * cannot afford the implicit synchronisation of cudaMalloc.  It computes
+ * what smc2_pf_loglik computes for dataset 0 of a context made from cfg --
+ * loglik_dev[i] for theta_dev (device SoA [D][n]) with y_dev (device, cfg->T
+ * doubles), the random stream of `iteration` -- but needs no context.  Its
+ * scratch (observation terms and the kernel's work-unit counter) is a 1 MiB
+ * static device array that every GPU loading the library holds until exit.
+ * Limits: cfg->T <= SMC2_NOALLOC_MAX_T and the usual n, M limits; larger
+ * sizes return SMC2_EINVAL before any work is enqueued.  cfg->ppt selects
+ * particles per thread (0: 2).  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) and should come before any
+ * stream capture.  Every call reuses the same array and clears the counter
+ * it needs, so calls that overlap on the GPU (other streams, other threads)
+ * race on it.  Asynchronous on `stream`.  Errors: EINVAL, ECUDA. */
+#define SMC2_NOALLOC_MAX_T 32000
+smc2_status smc2_pf_loglik_noalloc(const smc2_config* cfg, const double* y_dev,
+                                   const double* theta_dev, int n, int iteration,
+                                   double* loglik_dev, void* stream);
+
 /* Wait for the context stream and return the sticky device status. */
 smc2_status smc2_sync(smc2_ctx* ctx);
 

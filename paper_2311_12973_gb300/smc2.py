@@ -84,6 +84,7 @@ def _load() -> C.CDLL:
         "smc2_get_timing": ([ctx, C.POINTER(C.c_double), C.POINTER(C.c_int64),
                              C.POINTER(C.c_int64), C.c_int], st),
         "smc2_get_launch_shape": ([ctx, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)], st),
+        "smc2_pf_loglik_noalloc": ([C.POINTER(Config), dp, dp, C.c_int, C.c_int, dp, vp], st),
         "smc2_destroy": ([ctx], None),
         "smc2_status_string": ([st], C.c_char_p),
         "smc2_last_error_string": ([], C.c_char_p),
@@ -277,6 +278,17 @@ class SMC2:
         _check(lib.smc2_get_timing(self._ctx, C.byref(ms), C.byref(n), C.byref(kl), int(reset)),
                "smc2_get_timing")
         return ms.value, n.value, kl.value
+
+
+def pf_loglik_noalloc(cfg: Config, y_dev, theta_soa, iteration: int, out=None, stream=None):
+    """smc2_pf_loglik_noalloc: no context and no device allocation by the library.
+    y_dev: CUDA float64 [T]; theta_soa: CUDA float64 [D][n]; returns CUDA float64 [n]."""
+    import torch
+    n = theta_soa.shape[1]
+    out = out if out is not None else torch.empty(n, dtype=torch.float64, device=theta_soa.device)
+    _check(lib.smc2_pf_loglik_noalloc(C.byref(cfg), _ptr(y_dev), _ptr(theta_soa), n, int(iteration),
+                                      _ptr(out), _stream_handle(stream)), "smc2_pf_loglik_noalloc")
+    return out
 
 
 def resample_systematic(q, U: int, anc, stream=None):
