@@ -27,11 +27,15 @@ METRIC = "PF particle-steps/s and SMC² ESS/s vs plain FP64 GPU form; % of roofl
 UNIT = "particle-steps/s"
 
 # Algorithmic lane operations per particle-step of the particle-filter kernel,
-# counted from the kernel source by category ("Roofline").
+# counted from the kernel source by category ("Roofline basis").
 ALG_OPS_PER_PARTICLE_STEP = {
-    0: 122.0,   # linear-Gaussian AR(1)
-    1: 150.0,   # SEIR-type
+    0: 67.0,    # linear-Gaussian AR(1)
+    1: 108.0,   # SEIR-type
 }
+# DRAM bytes per particle-filter launch from one ncu capture of the SEIR-type
+# workload (profiles/pf_kernel_seir_t100_n1024.md), valid only for the kernel
+# source it was taken on (sha-256 prefixes of pf_impl.cuh and common.cuh).
+PF_TRAFFIC = {"bytes": 98560.0, "sources": {"pf_impl.cuh": "6ccc98f0284631fa", "common.cuh": "ae3e5d1cb62ab831"}}
 
 
 def parse():
@@ -104,6 +108,15 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def pf_traffic_if_current():
+    import hashlib
+    d = os.path.join(ROOT, "paper_2311_12973_gb300", "csrc")
+    for f, h in PF_TRAFFIC["sources"].items():
+        if hashlib.sha256(open(os.path.join(d, f), "rb").read()).hexdigest()[:16] != h:
+            return None
+    return PF_TRAFFIC["bytes"]
 
 
 def measured_peaks() -> dict:
@@ -305,7 +318,8 @@ def main():
         "speedup_vs_fp64_form": (value / fp64["value"]) if fp64 else None,
         "ess_speedup_vs_fp64_form": (ess_per_s / fp64["ess_per_s"]) if fp64 else None,
         "roofline": {"kernel": "pf_kernel<float,SEIR>", "bound": "alu", "achieved": achieved / 1e9,
-                     "peak": peak / 1e9, "unit": "Gop/s", "frac": achieved / peak, "traffic": None,
+                     "peak": peak / 1e9, "unit": "Gop/s", "frac": achieved / peak,
+                     "traffic": pf_traffic_if_current() if wr.model == 1 else None,
                      "ops_per_particle_step": ALG_OPS_PER_PARTICLE_STEP[wr.model],
                      "pf_ms_per_launch": pf_avg_ms, "pf_launches": pf_n,
                      "pf_share_of_step": pf_ms / max(sum(ms), 1e-9),
