@@ -39,7 +39,8 @@ struct smc2_ctx {
   std::vector<size_t> yoff;
   size_t ytot = 0;
   int max_N = 0, max_nblk = 0, max_nblk_res = 0;
-  cudaStream_t stream = nullptr, cap_stream = nullptr;
+  cudaStream_t stream = nullptr, cap_stream = nullptr, side_stream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int device = 0, sms = 0;
   char* arena = nullptr;
   size_t arena_bytes = 0;
@@ -365,21 +366,27 @@ void fill_params(smc2_ctx* c) {
   L.mdl.n_sub = c->cfg.n_sub;
 }
 
-// One iteration of every dataset, enqueued on s.
+// One iteration of every dataset, enqueued on s; the L-kernel fit runs on the
+// side stream between a fork after the proposal and a join before the weights.
 smc2_status enqueue_iteration(smc2_ctx* c, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1) {
   SMC2_TRY(outer_propose(c->op, c->max_nblk, s));
+  SMC2_TRY(cudaEventRecord(c->ev_fork, s));
+  SMC2_TRY(cudaStreamWaitEvent(c->side_stream, c->ev_fork, 0));
+  SMC2_TRY(outer_lkfit(c->op, c->side_stream));
+  SMC2_TRY(cudaEventRecord(c->ev_join, c->side_stream));
   SMC2_TRY(cudaMemsetAsync(c->d_wu_counter, 0, sizeof(int), s));
   if (ev0) SMC2_TRY(cudaEventRecordWithFlags(ev0, s, cudaEventRecordExternal));
   SMC2_TRY(pf_launch(c->precision, c->model, c->ppt, c->pf_named, c->pf_grid, c->pf_block, c->pf_smem,
                      c->pl, s));
   if (ev1) SMC2_TRY(cudaEventRecordWithFlags(ev1, s, cudaEventRecordExternal));
+  SMC2_TRY(cudaStreamWaitEvent(s, c->ev_join, 0));
   SMC2_TRY(outer_weights(c->op, c->max_nblk, s));
   SMC2_TRY(outer_quantise(c->op, c->max_nblk, s));
   SMC2_TRY(outer_resample(c->op, c->max_nblk_res, c->max_N, s));
   return SMC2_OK;
 }
 
-constexpr int kLaunchesPerIter = 5;
+constexpr int kLaunchesPerIter = 6;
 
 smc2_status get_graph(smc2_ctx* c, int n_iter, TimedGraph** out) {
   const GraphKey key{n_iter, c->timing ? 1 : 0};
@@ -484,7 +491,10 @@ smc2_status smc2_init(const smc2_config* cfg, const double* y, void* stream, smc
   if (cudaGetDevice(&c->device) != cudaSuccess) return fail(SMC2_ECUDA);
   if (cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess)
     return fail(SMC2_ECUDA);
-  if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+  if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess)
     return fail(SMC2_ECUDA);
 
   c->arena_bytes = layout(c, nullptr);
@@ -747,6 +757,9 @@ void smc2_destroy(smc2_ctx* c) {
   drop_graphs(c);
   if (c->arena) cudaFree(c->arena);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->side_stream) cudaStreamDestroy(c->side_stream);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
   delete c;
 }
 

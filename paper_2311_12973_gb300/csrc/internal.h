@@ -120,6 +120,7 @@ int pf_occupancy(int precision, int model, int ppt, bool named, int block, size_
 cudaError_t outer_obs_terms(int precision, int model, const double* y, int T, void* obs,
                             cudaStream_t s);
 cudaError_t outer_propose(const OuterParams& P, int max_nblk, cudaStream_t s);
+cudaError_t outer_lkfit(const OuterParams& P, cudaStream_t s);
 cudaError_t outer_weights(const OuterParams& P, int max_nblk, cudaStream_t s);
 cudaError_t outer_quantise(const OuterParams& P, int max_nblk, cudaStream_t s);
 cudaError_t outer_resample(const OuterParams& P, int max_nblk_res, int max_N, cudaStream_t s);

@@ -1,10 +1,11 @@
 // outer.cu -- the SMC^2 outer step (Sec. IV of the paper), in FP64.
 //
-// One iteration is four launches over a (block, dataset) grid:
+// One iteration is five launches (four over a (block, dataset) grid):
 //   propose   k = 1: theta ~ q_1 = prior (Eq. 16); k > 1: Gaussian random walk
 //             (Eqs. 18-19) and, for the Gaussian L-kernel, per-block weighted
-//             moments of the pairs (theta_{k-1}, theta_k); the last block to
-//             finish fits the joint Gaussian and conditions it (Eqs. 32-35).
+//             moments of the pairs (theta_{k-1}, theta_k).
+//   lkfit     one warp per dataset totals the moments, fits the joint Gaussian
+//             and conditions it (Eqs. 32-35); it runs beside the particle filter.
 //   weights   Eq. (17) at k = 1, Eq. (20) after; per-block max / sums; the last
 //             block forms log sum w, log sum w^2, ESS (Eqs. 24-25), the estimate
 //             (Eq. 21), the evidence and the recycling sums (Eqs. 23, 29).
@@ -184,8 +185,6 @@ __global__ void __launch_bounds__(kOuterBlock) propose_kernel(OuterParams P) {
   if ((int)blockIdx.x >= S.nblk) return;
   __shared__ double zs[kOuterBlock][2 * kMaxD];
   __shared__ double ws[kOuterBlock];
-  __shared__ double tot[kPartStride];
-  __shared__ FitScratch fit;
   const int N = S.N, lane = threadIdx.x;
   const int i = blockIdx.x * kOuterBlock + lane;
   const uint32_t k = (uint32_t)(*P.k_done + 1);
@@ -254,26 +253,32 @@ __global__ void __launch_bounds__(kOuterBlock) propose_kernel(OuterParams P) {
     }
     S.part[(size_t)blockIdx.x * kPartStride + mo] = acc;
   }
-  __threadfence();
-  __syncwarp();
-  unsigned ticket = 0;
-  if (lane == 0) ticket = atomicAdd(&S.tickets[0], 1u);
-  ticket = __shfl_sync(0xffffffffu, ticket, 0);
-  if (ticket != (unsigned)(S.nblk - 1)) return;
-  __threadfence();
+}
+
+// Totals of the block moments and the L-kernel fit of one dataset, by one warp.
+// It needs only the proposal kernel's partial moments, so it runs beside the
+// particle filter (a parallel branch of the iteration graph).
+template <int D>
+__global__ void __launch_bounds__(32) lkfit_kernel(OuterParams P) {
+  const DSDev& S = P.ds[blockIdx.y];
+  const uint32_t k = (uint32_t)(*P.k_done + 1);
+  if (k == 1 || P.lkernel != LK_GAUSS) return;
+  __shared__ double tot[kPartStride];
+  __shared__ FitScratch fit;
+  const int lane = threadIdx.x, N = S.N;
+  const int NM = n_moments(D);
   // totals: lane l takes blocks l, l+32, ... in order, then a fixed shuffle tree
   for (int mo = 0; mo < NM; ++mo) {
     double t = 0.0;
-    for (int bb = lane; bb < S.nblk; bb += 32) t += __ldcg(&S.part[(size_t)bb * kPartStride + mo]);
+    for (int bb = lane; bb < S.nblk; bb += 32) t += S.part[(size_t)bb * kPartStride + mo];
     t = warp_sum(t);
     if (lane == 0) tot[mo] = t;
   }
   __syncwarp();
   double sh2[2 * D];
 #pragma unroll
-  for (int r = 0; r < 2 * D; ++r) sh2[r] = shift[r % D];
+  for (int r = 0; r < 2 * D; ++r) sh2[r] = S.thA[(size_t)(r % D) * N];
   lk_fit_warp(D, tot, sh2, fit, S.lk);
-  if (lane == 0) S.tickets[0] = 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -572,6 +577,16 @@ cudaError_t outer_propose(const OuterParams& P, int max_nblk, cudaStream_t s) {
     propose_kernel<3><<<grid, kOuterBlock, 0, s>>>(P);
   else if (P.D == 4)
     propose_kernel<4><<<grid, kOuterBlock, 0, s>>>(P);
+  else
+    return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+cudaError_t outer_lkfit(const OuterParams& P, cudaStream_t s) {
+  const dim3 grid(1, P.n_ds);
+  if (P.D == 3)
+    lkfit_kernel<3><<<grid, 32, 0, s>>>(P);
+  else if (P.D == 4)
+    lkfit_kernel<4><<<grid, 32, 0, s>>>(P);
   else
     return cudaErrorInvalidValue;
   return cudaGetLastError();
