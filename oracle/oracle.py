@@ -112,6 +112,16 @@ def _declare(L):
                                    C.POINTER(OracleStats)]
     L.oracle_smc2_step.restype = C.c_int
     L.oracle_recycle.argtypes = [C.c_int, C.c_int, C.POINTER(OracleStats), dp, dp]
+    L.oracle_bf16.argtypes = [C.c_double]
+    L.oracle_bf16.restype = C.c_double
+    L.oracle_mlp_nparams.argtypes = [C.c_int, C.c_int]
+    L.oracle_mlp_nparams.restype = C.c_int
+    L.oracle_mlp_forward.argtypes = [C.c_int, C.c_int, dp, dp, C.c_int, C.c_int, dp]
+    L.oracle_mlp_loss_grad.argtypes = [C.c_int, C.c_int, dp, dp, dp, C.c_int, C.c_int, dp]
+    L.oracle_mlp_loss_grad.restype = C.c_double
+    L.oracle_mlp_input_grad.argtypes = [C.c_int, C.c_int, dp, dp, C.c_int, C.c_int, dp, dp]
+    L.oracle_adam_step.argtypes = [C.c_int, dp, dp, dp, dp, C.c_int, C.c_double, C.c_double,
+                                   C.c_double, C.c_double]
 
 
 # --------------------------------------------------------------------------
@@ -342,3 +352,53 @@ class SMC2:
         ck = np.zeros(K)
         lib().oracle_recycle(K, self.cfg.D, arr, _p(est, C.c_double), _p(ck, C.c_double))
         return est, ck
+
+
+# --------------------------------------------------------------------------
+# surrogate network of the learned proposal
+# --------------------------------------------------------------------------
+
+def bf16(v: float) -> float:
+    return lib().oracle_bf16(float(v))
+
+
+def mlp_nparams(D: int, H: int = 64) -> int:
+    return lib().oracle_mlp_nparams(D, H)
+
+
+def mlp_forward(params, x, H: int = 64, bf16_points: bool = False) -> np.ndarray:
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    xx = np.ascontiguousarray(x, dtype=np.float64)
+    R, D = xx.shape
+    out = np.zeros(R)
+    lib().oracle_mlp_forward(D, H, _p(p, C.c_double), _p(xx, C.c_double), R, int(bf16_points),
+                             _p(out, C.c_double))
+    return out
+
+
+def mlp_loss_grad(params, x, y, H: int = 64, bf16_points: bool = False):
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    xx = np.ascontiguousarray(x, dtype=np.float64)
+    yy = np.ascontiguousarray(y, dtype=np.float64)
+    R, D = xx.shape
+    g = np.zeros_like(p)
+    loss = lib().oracle_mlp_loss_grad(D, H, _p(p, C.c_double), _p(xx, C.c_double), _p(yy, C.c_double),
+                                      R, int(bf16_points), _p(g, C.c_double))
+    return loss, g
+
+
+def mlp_input_grad(params, x, H: int = 64, bf16_points: bool = False):
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    xx = np.ascontiguousarray(x, dtype=np.float64)
+    R, D = xx.shape
+    s = np.zeros(R)
+    dx = np.zeros((R, D))
+    lib().oracle_mlp_input_grad(D, H, _p(p, C.c_double), _p(xx, C.c_double), R, int(bf16_points),
+                                _p(s, C.c_double), _p(dx, C.c_double))
+    return s, dx
+
+
+def adam_step(params, grad, m, v, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+    """In place on params, m, v (float64 numpy arrays)."""
+    lib().oracle_adam_step(len(params), _p(params, C.c_double), _p(np.ascontiguousarray(grad), C.c_double),
+                           _p(m, C.c_double), _p(v, C.c_double), int(t), lr, beta1, beta2, eps)

@@ -588,3 +588,134 @@ void oracle_recycle(int K, int D, const oracle_stats* st, double* est_out, doubl
     for (int d = 0; d < D; ++d) est_out[d] += ck * st[k].est[d];
   }
 }
+
+/* ------------------------------------------------------------------ */
+/* Surrogate network of the learned proposal (not in the paper)         */
+/* ------------------------------------------------------------------ */
+
+/* Nearest bfloat16 (8 exponent bits, 7 fraction bits), ties to even,
+ * returned as a double.  Finite inputs only. */
+double oracle_bf16(double v) {
+  float f = (float)v;
+  uint32_t u;
+  memcpy(&u, &f, sizeof(u));
+  uint32_t lsb = (u >> 16) & 1u;
+  u += 0x7fffu + lsb;
+  u &= 0xffff0000u;
+  memcpy(&f, &u, sizeof(f));
+  return (double)f;
+}
+
+int oracle_mlp_nparams(int D, int H) { return D * H + H * H + 3 * H + 1; }
+
+static double oracle_round(double v, int bf16) { return bf16 ? oracle_bf16(v) : v; }
+
+/* One row: z1 = W1^T x + b1, h1 = tanh z1, z2 = W2^T h1 + b2, h2 = tanh z2,
+ * s = w3 . h2 + b3.  h1r, h2r are the values fed to the next product. */
+static double oracle_mlp_row(int D, int H, const double* p, const double* x, int bf16, double* h1,
+                             double* h1r, double* h2, double* h2r) {
+  const double *W1 = p, *b1 = W1 + D * H, *W2 = b1 + H, *b2 = W2 + H * H, *w3 = b2 + H, *b3 = w3 + H;
+  for (int o = 0; o < H; ++o) {
+    double z = b1[o];
+    for (int d = 0; d < D; ++d) z += oracle_round(x[d], bf16) * W1[d * H + o];
+    h1[o] = tanh(z);
+    h1r[o] = oracle_round(h1[o], bf16);
+  }
+  for (int o = 0; o < H; ++o) {
+    double z = b2[o];
+    for (int i = 0; i < H; ++i) z += h1r[i] * W2[i * H + o];
+    h2[o] = tanh(z);
+    h2r[o] = oracle_round(h2[o], bf16);
+  }
+  double sv = b3[0];
+  for (int i = 0; i < H; ++i) sv += h2r[i] * w3[i];
+  return sv;
+}
+
+void oracle_mlp_forward(int D, int H, const double* params, const double* x, int R, int bf16, double* out) {
+  double* buf = (double*)malloc(sizeof(double) * 4 * H);
+  for (int r = 0; r < R; ++r)
+    out[r] = oracle_mlp_row(D, H, params, x + (size_t)r * D, bf16, buf, buf + H, buf + 2 * H, buf + 3 * H);
+  free(buf);
+}
+
+/* Back-propagation of a signal g (ds) through one row; adds the parameter
+ * gradients scaled by g to grad (if not NULL) and writes ds/dx * g to dx
+ * (if not NULL). */
+static void oracle_mlp_back_row(int D, int H, const double* p, const double* x, const double* h1,
+                                const double* h1r, const double* h2, const double* h2r, double g,
+                                int bf16, double* grad, double* dx) {
+  const double *W1 = p, *W2 = W1 + D * H + H, *w3 = W2 + H * H + H;
+  double* dz2 = (double*)malloc(sizeof(double) * 2 * H);
+  double* dz1 = dz2 + H;
+  for (int o = 0; o < H; ++o) dz2[o] = oracle_round(g * w3[o] * (1.0 - h2[o] * h2[o]), bf16);
+  for (int i = 0; i < H; ++i) {
+    double dh = 0.0;
+    for (int o = 0; o < H; ++o) dh += W2[i * H + o] * dz2[o];
+    dz1[i] = oracle_round(dh * (1.0 - h1[i] * h1[i]), bf16);
+  }
+  if (grad) {
+    double *gW1 = grad, *gb1 = gW1 + D * H, *gW2 = gb1 + H, *gb2 = gW2 + H * H, *gw3 = gb2 + H,
+           *gb3 = gw3 + H;
+    for (int d = 0; d < D; ++d)
+      for (int o = 0; o < H; ++o) gW1[d * H + o] += oracle_round(x[d], bf16) * dz1[o];
+    for (int o = 0; o < H; ++o) gb1[o] += dz1[o];
+    for (int i = 0; i < H; ++i)
+      for (int o = 0; o < H; ++o) gW2[i * H + o] += h1r[i] * dz2[o];
+    for (int o = 0; o < H; ++o) gb2[o] += dz2[o];
+    for (int i = 0; i < H; ++i) gw3[i] += h2r[i] * g;
+    gb3[0] += g;
+  }
+  if (dx)
+    for (int d = 0; d < D; ++d) {
+      double v = 0.0;
+      for (int o = 0; o < H; ++o) v += W1[d * H + o] * dz1[o];
+      dx[d] = v;
+    }
+  free(dz2);
+}
+
+/* Mean squared error L = (1/R) sum_r (s(x_r) - y_r)^2 and its gradient. */
+double oracle_mlp_loss_grad(int D, int H, const double* params, const double* x, const double* y, int R,
+                            int bf16, double* grad) {
+  const int P = oracle_mlp_nparams(D, H);
+  double* buf = (double*)malloc(sizeof(double) * 4 * H);
+  for (int q = 0; q < P; ++q) grad[q] = 0.0;
+  double loss = 0.0;
+  for (int r = 0; r < R; ++r) {
+    const double* xr = x + (size_t)r * D;
+    double sv = oracle_mlp_row(D, H, params, xr, bf16, buf, buf + H, buf + 2 * H, buf + 3 * H);
+    double e = sv - y[r];
+    loss += e * e;
+    oracle_mlp_back_row(D, H, params, xr, buf, buf + H, buf + 2 * H, buf + 3 * H, 2.0 * e / R, bf16,
+                        grad, NULL);
+  }
+  free(buf);
+  return loss / R;
+}
+
+/* s(x_r) and ds/dx at every row. */
+void oracle_mlp_input_grad(int D, int H, const double* params, const double* x, int R, int bf16,
+                           double* s_out, double* dx) {
+  double* buf = (double*)malloc(sizeof(double) * 4 * H);
+  for (int r = 0; r < R; ++r) {
+    const double* xr = x + (size_t)r * D;
+    double sv = oracle_mlp_row(D, H, params, xr, bf16, buf, buf + H, buf + 2 * H, buf + 3 * H);
+    if (s_out) s_out[r] = sv;
+    oracle_mlp_back_row(D, H, params, xr, buf, buf + H, buf + 2 * H, buf + 3 * H, 1.0, bf16, NULL,
+                        dx + (size_t)r * D);
+  }
+  free(buf);
+}
+
+/* Adam (Kingma and Ba, 2015): moments with bias correction at step t >= 1. */
+void oracle_adam_step(int n, double* params, const double* grad, double* m, double* v, int t, double lr,
+                      double beta1, double beta2, double eps) {
+  const double c1 = 1.0 - pow(beta1, (double)t), c2 = 1.0 - pow(beta2, (double)t);
+  for (int q = 0; q < n; ++q) {
+    m[q] = beta1 * m[q] + (1.0 - beta1) * grad[q];
+    v[q] = beta2 * v[q] + (1.0 - beta2) * grad[q] * grad[q];
+    const double mh = m[q] / c1, vh = v[q] / c2;
+    params[q] -= lr * mh / (sqrt(vh) + eps);
+  }
+}

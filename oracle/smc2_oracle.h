@@ -92,6 +92,22 @@ double oracle_gauss_lkernel_logpdf(int D, const double* mu, const double* A, con
 
 int oracle_smc2_step(const oracle_cfg* c, const double* y, int k, double* theta, double* logprior,
                      double* loglik, double* logw, oracle_stats* st);
+
+/* Surrogate network of the learned proposal: s(x) = w3 . h2 + b3,
+ * h2 = tanh(W2^T h1 + b2), h1 = tanh(W1^T x + b1), x in R^D, hidden width H.
+ * Parameters, one vector: W1 [D][H], b1 [H], W2 [H][H] (input-major), b2 [H],
+ * w3 [H], b3 -- D H + H H + 3 H + 1 values.  bf16 != 0 rounds, to the nearest
+ * bfloat16 (ties to even), the values the tensor-core kernels feed to their
+ * products: x, h1, h2 and the backward signals dz2 and dz1. */
+double oracle_bf16(double v);
+int oracle_mlp_nparams(int D, int H);
+void oracle_mlp_forward(int D, int H, const double* params, const double* x, int R, int bf16, double* out);
+double oracle_mlp_loss_grad(int D, int H, const double* params, const double* x, const double* y, int R,
+                            int bf16, double* grad);
+void oracle_mlp_input_grad(int D, int H, const double* params, const double* x, int R, int bf16,
+                           double* s_out, double* dx);
+void oracle_adam_step(int n, double* params, const double* grad, double* m, double* v, int t, double lr,
+                      double beta1, double beta2, double eps);
 void oracle_recycle(int K, int D, const oracle_stats* st, double* est_out, double* c_out);
 
 #ifdef __cplusplus
