@@ -236,6 +236,26 @@ smc2_status smc2_pf_loglik_noalloc(const smc2_config* cfg, const double* y_dev,
                                    const double* theta_dev, int n, int iteration,
                                    double* loglik_dev, void* stream);
 
+/* Surrogate network of the learned proposal (not in the paper; it proposes
+ * theta_k in place of the random walk of Sec. IV-A, and the L-kernel weights
+ * of Eq. (20) keep the estimator exact): s(x) = w3.h2 + b3, h2 = tanh(W2^T h1
+ * + b2), h1 = tanh(W1^T x + b1), hidden width 64, x in R^D (D <= 8).
+ * params_dev (device FP32) holds, in order, W1 [D][64], b1 [64], W2 [64][64]
+ * (input-major), b2 [64], w3 [64], b3: 64 D + 4289 values.  The products run
+ * on tensor cores with bfloat16 operands (x, weights, h1, h2 and the backward
+ * signals rounded to the nearest bfloat16) and FP32 accumulation.
+ *
+ * smc2_mlp_loss_grad: mean squared error L = (1/R) sum_r (s(x_r) - y_r)^2 of
+ * R rows x_dev [R][D] (device FP32), y_dev [R], into *loss_dev and its
+ * gradient grad_dev [params] (device FP32).  Allocates its partial sums on
+ * `stream` (stream-ordered).  Errors: EINVAL (D outside 1..8, R < 1).
+ * smc2_mlp_input_grad: s(x_r) into s_dev [R] (may be NULL) and ds/dx into
+ * dx_dev [R][D]. */
+smc2_status smc2_mlp_loss_grad(int D, const float* params_dev, const float* x_dev, const float* y_dev,
+                               int R, float* grad_dev, float* loss_dev, void* stream);
+smc2_status smc2_mlp_input_grad(int D, const float* params_dev, const float* x_dev, int R,
+                                float* s_dev, float* dx_dev, void* stream);
+
 /* Wait for the context stream and return the sticky device status. */
 smc2_status smc2_sync(smc2_ctx* ctx);
 

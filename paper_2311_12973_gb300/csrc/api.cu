@@ -717,6 +717,30 @@ smc2_status smc2_philox_normals(uint64_t seed, const uint32_t* ctr, int n, int p
   return map_cuda(philox_normals_launch(seed, ctr, n, precision, words, z, static_cast<cudaStream_t>(stream)));
 }
 
+smc2_status smc2_mlp_loss_grad(int D, const float* params, const float* x, const float* y, int R,
+                               float* grad, float* loss, void* stream) {
+  if (D < 1 || D > kMlpMaxD || R < 1 || !params || !x || !y || !grad || !loss) return SMC2_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int n_cta = mlp_grad_ctas(R);
+  float* part = nullptr;
+  SMC2_TRY(cudaMallocAsync(reinterpret_cast<void**>(&part),
+                           (size_t)n_cta * (mlp_param_count(D) + 1) * sizeof(float), s));
+  cudaError_t e = mlp_grad_launch(params, D, x, y, R, part, nullptr, s);
+  if (e == cudaSuccess)
+    e = mlp_reduce_launch(const_cast<float*>(params), D, part, n_cta, R, grad, loss, 0, nullptr, nullptr,
+                          nullptr, 0.f, s);
+  cudaFreeAsync(part, s);
+  SMC2_TRY(e);
+  return SMC2_OK;
+}
+
+smc2_status smc2_mlp_input_grad(int D, const float* params, const float* x, int R, float* s_out, float* dx,
+                                void* stream) {
+  if (D < 1 || D > kMlpMaxD || R < 1 || !params || !x || !dx) return SMC2_EINVAL;
+  SMC2_TRY(mlp_input_grad_launch(params, D, x, R, s_out, dx, static_cast<cudaStream_t>(stream)));
+  return SMC2_OK;
+}
+
 smc2_status smc2_sync(smc2_ctx* c) {
   if (!c) return SMC2_EINVAL;
   return sticky(c);

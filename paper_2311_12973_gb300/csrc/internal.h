@@ -21,6 +21,9 @@ namespace smc2 {
 constexpr int kOuterBlock = 32;                        // threads of the per-sample outer kernels (one warp)
 constexpr int kResBlock = 256;                         // threads of the resampling kernel
 constexpr int kPfMaxBlock = 512;                       // threads of a particle-filter CTA, at most
+constexpr int kMlpH = 64;                              // hidden width of the surrogate network
+constexpr int kMlpWarps = 4;                           // warps (16 rows each) per network CTA
+constexpr int kMlpMaxD = 8;                            // input dimension, at most
 constexpr int kPartStride = 160;                       // >= 1 + 2D + 2D(2D+1)/2 for D <= 8
 constexpr int kStatStride = 16;                        // >= 3 + D
 
@@ -128,6 +131,18 @@ cudaError_t outer_parent_reference(const OuterParams& P, int dataset, cudaStream
 cudaError_t outer_rebuild_recycling(const OuterParams& P, int dataset, int k, cudaStream_t s);
 cudaError_t resample_systematic_launch(const uint64_t* q, int n, uint32_t U, int32_t* anc,
                                        cudaStream_t s);
+// Surrogate network (mlp.cu).
+int mlp_param_count(int D);
+int mlp_grad_ctas(int R);
+size_t mlp_grad_smem_bytes();
+cudaError_t mlp_grad_launch(const float* p, int D, const float* x, const float* y, int R, float* part,
+                            int* step, cudaStream_t s);
+cudaError_t mlp_reduce_launch(float* p, int D, const float* part, int n_cta, int R, float* grad,
+                              float* loss, int adam, float* m, float* v, const int* step, float lr,
+                              cudaStream_t s);
+cudaError_t mlp_input_grad_launch(const float* p, int D, const float* x, int R, float* s_out, float* dx,
+                                  cudaStream_t s);
+
 cudaError_t philox_normals_launch(uint64_t seed, const uint32_t* ctr, int n, int precision,
                                   uint32_t* words, double* z, cudaStream_t s);
 

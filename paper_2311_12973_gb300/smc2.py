@@ -85,6 +85,8 @@ def _load() -> C.CDLL:
                              C.POINTER(C.c_int64), C.c_int], st),
         "smc2_get_launch_shape": ([ctx, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)], st),
         "smc2_pf_loglik_noalloc": ([C.POINTER(Config), dp, dp, C.c_int, C.c_int, dp, vp], st),
+        "smc2_mlp_loss_grad": ([C.c_int, dp, dp, dp, C.c_int, dp, dp, vp], st),
+        "smc2_mlp_input_grad": ([C.c_int, dp, dp, C.c_int, dp, dp, vp], st),
         "smc2_destroy": ([ctx], None),
         "smc2_status_string": ([st], C.c_char_p),
         "smc2_last_error_string": ([], C.c_char_p),
@@ -289,6 +291,27 @@ def pf_loglik_noalloc(cfg: Config, y_dev, theta_soa, iteration: int, out=None, s
     _check(lib.smc2_pf_loglik_noalloc(C.byref(cfg), _ptr(y_dev), _ptr(theta_soa), n, int(iteration),
                                       _ptr(out), _stream_handle(stream)), "smc2_pf_loglik_noalloc")
     return out
+
+
+def mlp_loss_grad(params, x, y, stream=None):
+    """params, x [R][D], y: CUDA float32 tensors; returns (loss, grad) as CUDA tensors."""
+    import torch
+    R, D = x.shape
+    grad = torch.empty_like(params)
+    loss = torch.empty(1, dtype=torch.float32, device=params.device)
+    _check(lib.smc2_mlp_loss_grad(D, _ptr(params), _ptr(x), _ptr(y), R, _ptr(grad), _ptr(loss),
+                                  _stream_handle(stream)), "smc2_mlp_loss_grad")
+    return loss, grad
+
+
+def mlp_input_grad(params, x, stream=None):
+    import torch
+    R, D = x.shape
+    s = torch.empty(R, dtype=torch.float32, device=params.device)
+    dx = torch.empty((R, D), dtype=torch.float32, device=params.device)
+    _check(lib.smc2_mlp_input_grad(D, _ptr(params), _ptr(x), R, _ptr(s), _ptr(dx),
+                                   _stream_handle(stream)), "smc2_mlp_input_grad")
+    return s, dx
 
 
 def resample_systematic(q, U: int, anc, stream=None):
