@@ -40,9 +40,11 @@ def test_loss_gradient_against_oracle(S, D, R):
     rel_norm = np.linalg.norm(g_g - g_o) / np.linalg.norm(g_o)
     rel_elem = np.max(np.abs(g_g - g_o) / (np.abs(g_o) + 1e-2 * np.max(np.abs(g_o))))
     print(f"D={D} R={R} loss {loss_g:.8g} vs {loss_o:.8g}  grad rel norm {rel_norm:.3g}  elem {rel_elem:.3g}")
-    assert abs(loss_g - loss_o) <= 1e-3 * abs(loss_o)
-    assert rel_norm < 1e-2
-    assert rel_elem < 5e-2
+    # measured on GB300: loss 4e-6, norm <= 2.4e-5, element <= 1e-3 (one bf16 step of
+    # an activation is 2^-8 = 4e-3 of its contribution; a few flips per R rows)
+    assert abs(loss_g - loss_o) <= 1e-4 * abs(loss_o)
+    assert rel_norm < 2e-4
+    assert rel_elem < 5e-3
 
 
 @pytest.mark.parametrize("D,R", [(4, 300), (3, 64)])
@@ -57,5 +59,5 @@ def test_input_gradient_against_oracle(S, D, R):
     es = np.max(np.abs(s_g - s_o)) / np.max(np.abs(s_o))
     ed = np.linalg.norm(dx_g - dx_o) / np.linalg.norm(dx_o)
     print(f"D={D} R={R} s err {es:.3g}  dx rel norm {ed:.3g}")
-    assert es < 1e-2
-    assert ed < 1e-2
+    assert es < 2e-3   # one bf16 step of an h2 value moves s by up to |w3| 2^-8
+    assert ed < 1e-3
