@@ -83,6 +83,23 @@ typedef struct smc2_ctx smc2_ctx; /* opaque; owns its device workspace */
  *   exposed and infectious, Euler substeps per day, floor of the Poisson mean).
  * ppt: particles per thread of the particle-filter kernel (0 = pick by the
  *   built-in tuner; otherwise 1, 2, 4, 8 or 16).
+ * proposal = SMC2_PROP_MLP (learned proposal; not in the paper): once the
+ *   network explains half the variance of its standardised targets (from
+ *   k = 3 on) and the previous population has ESS >= 2 (D + 1) and a positive
+ *   definite covariance Sigma = L L^T, theta_k = theta_{k-1} + h L (w + z),
+ *   z ~ N(0, I), w = h/2 L^T grad log pi^(theta_{k-1}) clipped to [-3, 3]:
+ *   a Langevin step preconditioned by Sigma (drift h^2/2 Sigma grad log pi^)
+ *   with the gradient of a 64-wide two-layer tanh network trained in the run
+ *   (tensor cores, bfloat16 operands, FP32 accumulation, Adam) on the
+ *   (theta, log pi^) pairs of the last mlp_window iterations; otherwise the
+ *   random walk above.  The network proposing at k was trained on the pairs
+ *   of iterations up to k - 2 (its training overlaps iteration k - 1).  log q
+ *   is the exact Gaussian density, so Eq. (20) with the Gaussian L-kernel
+ *   keeps the weights valid.  Requires lkernel = SMC2_LK_GAUSS_OPT and one
+ *   dataset.
+ * mlp_h, mlp_lr, mlp_steps, mlp_window: step h of the learned proposal, Adam
+ *   learning rate, Adam steps per iteration, iterations of training pairs
+ *   kept (0 selects 1.0, 5e-3, 16, 4; steps <= 256, window <= 16).
  * cta_threads: threads per particle-filter CTA (0 = pick by the tuner;
  *   otherwise a multiple of 32 up to 512 that holds whole filter groups).
  *   The tuner times every valid (ppt, cta_threads) pair on the context's own
@@ -103,6 +120,8 @@ typedef struct {
   const int* ds_N;
   const int* ds_M;
   const int* ds_T;
+  double mlp_h, mlp_lr;
+  int mlp_steps, mlp_window;
 } smc2_config;
 
 /* Statistics of one iteration k of one dataset (Sec. IV-A, IV-B):
@@ -110,11 +129,15 @@ typedef struct {
  * lse2 = log sum_i (w_k^i)^2; logz = lse - log N, the evidence estimate;
  * est = f~_k of Eq. (21) with f(theta) = theta (before resampling);
  * resampled = 1 when ESS < ess_frac N; lk_fallback = 1 when the Gaussian
- * L-kernel was numerically singular and the forward kernel (Eq. 30) was used. */
+ * L-kernel was numerically singular and the forward kernel (Eq. 30) was used.
+ * mlp_used, mlp_loss: see SMC2_PROP_MLP in smc2_config. */
 typedef struct {
   int k, resampled, lk_fallback, dataset;
   double ess, lse, lse2, logz;
   double est[SMC2_MAX_D];
+  int mlp_used;        /* 1: theta_k came from the learned proposal */
+  int pad;
+  double mlp_loss;     /* training loss of the surrogate that proposed (learned proposal) */
 } smc2_iter_stats;
 
 /* Create a context: validate cfg, allocate the device workspace, copy the
@@ -241,20 +264,31 @@ smc2_status smc2_pf_loglik_noalloc(const smc2_config* cfg, const double* y_dev,
  * of Eq. (20) keep the estimator exact): s(x) = w3.h2 + b3, h2 = tanh(W2^T h1
  * + b2), h1 = tanh(W1^T x + b1), hidden width 64, x in R^D (D <= 8).
  * params_dev (device FP32) holds, in order, W1 [D][64], b1 [64], W2 [64][64]
- * (input-major), b2 [64], w3 [64], b3: 64 D + 4289 values.  The products run
- * on tensor cores with bfloat16 operands (x, weights, h1, h2 and the backward
- * signals rounded to the nearest bfloat16) and FP32 accumulation.
+ * (input-major), b2 [64], w3 [64], b3: 64 D + 4289 values, starting on a
+ * 16-byte boundary (it is read as float4).  The products run
+ * on tensor cores with bfloat16 operands (x, the weights W1, W2, w3, h1, h2
+ * and the backward signals rounded to the nearest bfloat16; the biases stay
+ * FP32) and FP32 accumulation.
  *
  * smc2_mlp_loss_grad: mean squared error L = (1/R) sum_r (s(x_r) - y_r)^2 of
  * R rows x_dev [R][D] (device FP32), y_dev [R], into *loss_dev and its
  * gradient grad_dev [params] (device FP32).  Allocates its partial sums on
- * `stream` (stream-ordered).  Errors: EINVAL (D outside 1..8, R < 1).
+ * `stream` (stream-ordered).  Errors: EINVAL (D outside 1..8, R < 1, a NULL
+ * pointer, params_dev not 16-byte aligned).
  * smc2_mlp_input_grad: s(x_r) into s_dev [R] (may be NULL) and ds/dx into
- * dx_dev [R][D]. */
+ * dx_dev [R][D].
+ * smc2_mlp_adam_step: one training step as the sampler takes it: the
+ * gradient of L at params_dev, then Adam (beta1 = 0.9, beta2 = 0.999,
+ * eps = 1e-8, bias-corrected) with learning rate lr at step t = *step_dev + 1
+ * (device int, advanced in place), updating params_dev, m_dev, v_dev (device
+ * FP32, one value per parameter); *loss_dev receives L before the update. */
 smc2_status smc2_mlp_loss_grad(int D, const float* params_dev, const float* x_dev, const float* y_dev,
                                int R, float* grad_dev, float* loss_dev, void* stream);
 smc2_status smc2_mlp_input_grad(int D, const float* params_dev, const float* x_dev, int R,
                                 float* s_dev, float* dx_dev, void* stream);
+smc2_status smc2_mlp_adam_step(int D, float* params_dev, float* m_dev, float* v_dev, int* step_dev,
+                               const float* x_dev, const float* y_dev, int R, float lr, float* loss_dev,
+                               void* stream);
 
 /* Wait for the context stream and return the sticky device status. */
 smc2_status smc2_sync(smc2_ctx* ctx);

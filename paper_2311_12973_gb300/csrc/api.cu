@@ -18,6 +18,13 @@ using namespace smc2;
 
 namespace {
 
+// Learned proposal defaults: step h, Adam rate, Adam steps per iteration,
+// iterations of training pairs kept.
+constexpr double kMlpStep = 1.0;
+constexpr double kMlpLr = 5e-3;
+constexpr int kMlpSteps = 16;
+constexpr int kMlpWindow = 4;
+
 struct GraphKey {
   int n_iter, timing;
   bool operator<(const GraphKey& o) const {
@@ -41,6 +48,9 @@ struct smc2_ctx {
   int max_N = 0, max_nblk = 0, max_nblk_res = 0;
   cudaStream_t stream = nullptr, cap_stream = nullptr, side_stream = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaStream_t train_stream = nullptr;              // learned-proposal training branch
+  cudaEvent_t ev_tfork = nullptr, ev_tjoin = nullptr;
+  bool train_pending = false;                       // while capturing: branch not yet joined
   int device = 0, sms = 0;
   char* arena = nullptr;
   size_t arena_bytes = 0;
@@ -65,6 +75,7 @@ struct smc2_ctx {
   int64_t pf_launches = 0, kernel_launches = 0;
   OuterParams op{};
   PFLaunch pl{};
+  MlpDev mlp{};
 };
 
 namespace {
@@ -102,7 +113,13 @@ smc2_status validate(const smc2_config* c) {
   if (!c) return SMC2_EINVAL;
   if (c->model != SMC2_MODEL_LG_AR1 && c->model != SMC2_MODEL_SEIR) return SMC2_EINVAL;
   if (c->precision != SMC2_PREC_FP64 && c->precision != SMC2_PREC_MIXED) return SMC2_EINVAL;
-  if (c->proposal != SMC2_PROP_RW) return SMC2_EINVAL;
+  if (c->proposal != SMC2_PROP_RW && c->proposal != SMC2_PROP_MLP) return SMC2_EINVAL;
+  if (c->proposal == SMC2_PROP_MLP &&
+      (c->lkernel != SMC2_LK_GAUSS_OPT || c->n_datasets > 1 || c->D > kMlpMaxD))
+    return SMC2_EINVAL;
+  if (!(c->mlp_h >= 0.0 && c->mlp_h < 1e3) || !(c->mlp_lr >= 0.0 && c->mlp_lr < 1.0) ||
+      c->mlp_steps < 0 || c->mlp_steps > 256 || c->mlp_window < 0 || c->mlp_window > 16)
+    return SMC2_EINVAL;
   if (c->lkernel != SMC2_LK_FORWARD && c->lkernel != SMC2_LK_GAUSS_OPT) return SMC2_EINVAL;
   if (c->D != (c->model == SMC2_MODEL_LG_AR1 ? 3 : 4)) return SMC2_EINVAL;
   if (c->K < 1 || c->K > (1 << 27)) return SMC2_EINVAL;
@@ -187,6 +204,31 @@ size_t layout(smc2_ctx* c, char* base) {
     c->d_obs[d] = carve<char>(p, obs_bytes(c, d));
     s.obs = c->d_obs[d];
     s.c2hi = (uint32_t)d << 20;
+  }
+  MlpDev& M = c->mlp;
+  M = MlpDev{};
+  if (c->cfg.proposal == SMC2_PROP_MLP) {
+    const int P = mlp_param_count(D), N0 = c->N[0];
+    M.on = 1;
+    M.W = c->cfg.mlp_window;
+    M.h = c->cfg.mlp_h;
+    const size_t rows = (size_t)M.W * N0;
+    M.p = carve<float>(p, P);
+    M.p_use = carve<float>(p, P);
+    M.norm_use = carve<MlpNorm>(p, 1);
+    M.loss_use = carve<float>(p, 4);
+    M.ring_rows = carve<int>(p, 4);
+    M.m = carve<float>(p, P);
+    M.v = carve<float>(p, P);
+    M.step = carve<int>(p, 4);
+    M.loss = carve<float>(p, 4);
+    M.ring_th = carve<float>(p, rows * D);
+    M.ring_lp = carve<float>(p, rows);
+    M.xs = carve<float>(p, rows * D);
+    M.ys = carve<float>(p, rows);
+    M.norm = carve<MlpNorm>(p, 1);
+    M.score = carve<double>(p, (size_t)D * N0);
+    M.part = carve<float>(p, (size_t)mlp_grad_ctas((int)rows) * (P + 1));
   }
   c->d_ds = carve<DSDev>(p, c->n_ds);
   c->d_jobs = carve<PFJob>(p, c->n_ds);
@@ -315,6 +357,14 @@ smc2_status clear_run_state(smc2_ctx* c) {
     SMC2_TRY(cudaMemsetAsync(ds.cur, 0, sizeof(IterCur), s));
     SMC2_TRY(cudaMemsetAsync(ds.lk, 0, sizeof(LKParams), s));
   }
+  if (c->mlp.on) {
+    SMC2_TRY(mlp_init_launch(c->mlp, c->D, c->cfg.seed, s));
+    for (float* l : {c->mlp.loss, c->mlp.loss_use})  // NaN: no trained network yet
+      SMC2_TRY(cudaMemsetAsync(l, 0xff, 4 * sizeof(float), s));
+    for (MlpNorm* nm : {c->mlp.norm, c->mlp.norm_use}) SMC2_TRY(cudaMemsetAsync(nm, 0, sizeof(MlpNorm), s));
+    SMC2_TRY(cudaMemsetAsync(c->mlp.ring_rows, 0, 4 * sizeof(int), s));
+    c->kernel_launches++;
+  }
   c->k_host = 0;
   return SMC2_OK;
 }
@@ -348,6 +398,8 @@ void fill_params(smc2_ctx* c) {
   P.k_done = c->d_k;
   P.status = c->d_status;
   P.grid_ticket = c->d_grid_ticket;
+  P.mlp = c->mlp;
+  P.ds_N0 = c->N[0];
 
   PFLaunch& L = c->pl;
   L.jobs = c->d_jobs;
@@ -368,7 +420,20 @@ void fill_params(smc2_ctx* c) {
 
 // One iteration of every dataset, enqueued on s; the L-kernel fit runs on the
 // side stream between a fork after the proposal and a join before the weights.
+// With the learned proposal, the network is trained on the train stream from
+// after this iteration's weights to after the next iteration's weights, beside
+// the next proposal and particle filter; the trained state is then published
+// for the iteration after that.  Every iteration therefore proposes with the
+// network trained on the pairs of iterations up to k - 2, however the
+// iterations are grouped into calls.
+cudaError_t join_training(smc2_ctx* c, cudaStream_t s) {
+  const bool pending = c->train_pending;
+  c->train_pending = false;
+  return pending ? cudaStreamWaitEvent(s, c->ev_tjoin, 0) : cudaSuccess;
+}
+
 smc2_status enqueue_iteration(smc2_ctx* c, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1) {
+  if (c->mlp.on) SMC2_TRY(mlp_score_launch(c->op, c->N[0], s));
   SMC2_TRY(outer_propose(c->op, c->max_nblk, s));
   SMC2_TRY(cudaEventRecord(c->ev_fork, s));
   SMC2_TRY(cudaStreamWaitEvent(c->side_stream, c->ev_fork, 0));
@@ -381,12 +446,25 @@ smc2_status enqueue_iteration(smc2_ctx* c, cudaStream_t s, cudaEvent_t ev0, cuda
   if (ev1) SMC2_TRY(cudaEventRecordWithFlags(ev1, s, cudaEventRecordExternal));
   SMC2_TRY(cudaStreamWaitEvent(s, c->ev_join, 0));
   SMC2_TRY(outer_weights(c->op, c->max_nblk, s));
+  if (c->mlp.on) {
+    SMC2_TRY(join_training(c, s));
+    SMC2_TRY(mlp_publish_launch(c->op, s));
+    SMC2_TRY(mlp_append_launch(c->op, c->N[0], s));
+    SMC2_TRY(cudaEventRecord(c->ev_tfork, s));
+    SMC2_TRY(cudaStreamWaitEvent(c->train_stream, c->ev_tfork, 0));
+    SMC2_TRY(mlp_train_launch(c->op, c->cfg.mlp_steps, (float)c->cfg.mlp_lr, c->train_stream));
+    SMC2_TRY(cudaEventRecord(c->ev_tjoin, c->train_stream));
+    c->train_pending = true;
+  }
   SMC2_TRY(outer_quantise(c->op, c->max_nblk, s));
   SMC2_TRY(outer_resample(c->op, c->max_nblk_res, c->max_N, s));
   return SMC2_OK;
 }
 
-constexpr int kLaunchesPerIter = 6;
+int launches_per_iteration(const smc2_ctx* c) {
+  return 6 + (c->mlp.on ? 4 + 2 * c->cfg.mlp_steps : 0);
+}
+
 
 smc2_status get_graph(smc2_ctx* c, int n_iter, TimedGraph** out) {
   const GraphKey key{n_iter, c->timing ? 1 : 0};
@@ -405,6 +483,8 @@ smc2_status get_graph(smc2_ctx* c, int n_iter, TimedGraph** out) {
   for (int it2 = 0; it2 < n_iter && st == SMC2_OK; ++it2)
     st = enqueue_iteration(c, c->cap_stream, c->timing ? g.ev[2 * it2] : nullptr,
                            c->timing ? g.ev[2 * it2 + 1] : nullptr);
+  const cudaError_t ej = join_training(c, c->cap_stream);  // no branch outlives the graph
+  if (st == SMC2_OK && ej != cudaSuccess) st = record_cuda(ej, "join_training");
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
   if (st != SMC2_OK) {
@@ -465,6 +545,10 @@ smc2_status smc2_init(const smc2_config* cfg, const double* y, void* stream, smc
   smc2_ctx* c = new (std::nothrow) smc2_ctx();
   if (!c) return SMC2_ENOMEM;
   c->cfg = *cfg;
+  if (c->cfg.mlp_h == 0.0) c->cfg.mlp_h = kMlpStep;
+  if (c->cfg.mlp_lr == 0.0) c->cfg.mlp_lr = kMlpLr;
+  if (c->cfg.mlp_steps == 0) c->cfg.mlp_steps = kMlpSteps;
+  if (c->cfg.mlp_window == 0) c->cfg.mlp_window = kMlpWindow;
   c->n_ds = cfg->n_datasets <= 1 ? 1 : cfg->n_datasets;
   c->D = cfg->D;
   c->K = cfg->K;
@@ -494,7 +578,10 @@ smc2_status smc2_init(const smc2_config* cfg, const double* y, void* stream, smc
   if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess)
+      cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->train_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_tfork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_tjoin, cudaEventDisableTiming) != cudaSuccess)
     return fail(SMC2_ECUDA);
 
   c->arena_bytes = layout(c, nullptr);
@@ -604,7 +691,7 @@ smc2_status smc2_run(smc2_ctx* c, int n_iter, smc2_iter_stats* stats_host) {
   SMC2_TRY(cudaGraphLaunch(g->exec, c->stream));
   const int k0 = c->k_host;
   c->k_host += n_iter;
-  c->kernel_launches += (int64_t)kLaunchesPerIter * n_iter;
+  c->kernel_launches += (int64_t)launches_per_iteration(c) * n_iter;
   if (c->timing) {
     SMC2_TRY(cudaStreamSynchronize(c->stream));
     for (int i = 0; i < n_iter; ++i) {
@@ -720,15 +807,30 @@ smc2_status smc2_philox_normals(uint64_t seed, const uint32_t* ctr, int n, int p
 smc2_status smc2_mlp_loss_grad(int D, const float* params, const float* x, const float* y, int R,
                                float* grad, float* loss, void* stream) {
   if (D < 1 || D > kMlpMaxD || R < 1 || !params || !x || !y || !grad || !loss) return SMC2_EINVAL;
+  if (reinterpret_cast<uintptr_t>(params) % 16 != 0) return SMC2_EINVAL;  // read as float4
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int n_cta = mlp_grad_ctas(R);
   float* part = nullptr;
   SMC2_TRY(cudaMallocAsync(reinterpret_cast<void**>(&part),
                            (size_t)n_cta * (mlp_param_count(D) + 1) * sizeof(float), s));
-  cudaError_t e = mlp_grad_launch(params, D, x, y, R, part, nullptr, s);
-  if (e == cudaSuccess)
-    e = mlp_reduce_launch(const_cast<float*>(params), D, part, n_cta, R, grad, loss, 0, nullptr, nullptr,
-                          nullptr, 0.f, s);
+  const cudaError_t e = mlp_step_launch(const_cast<float*>(params), D, x, y, R, nullptr, part, grad, loss, 0,
+                                        nullptr, nullptr, nullptr, 0.f, s);
+  cudaFreeAsync(part, s);
+  SMC2_TRY(e);
+  return SMC2_OK;
+}
+
+smc2_status smc2_mlp_adam_step(int D, float* params, float* m, float* v, int* step, const float* x,
+                               const float* y, int R, float lr, float* loss, void* stream) {
+  if (D < 1 || D > kMlpMaxD || R < 1 || !params || !m || !v || !step || !x || !y || !loss ||
+      !(lr >= 0.f && lr < 1.f))
+    return SMC2_EINVAL;
+  if (reinterpret_cast<uintptr_t>(params) % 16 != 0) return SMC2_EINVAL;  // read as float4
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  float* part = nullptr;
+  SMC2_TRY(cudaMallocAsync(reinterpret_cast<void**>(&part),
+                           (size_t)mlp_grad_ctas(R) * (mlp_param_count(D) + 1) * sizeof(float), s));
+  const cudaError_t e = mlp_step_launch(params, D, x, y, R, nullptr, part, nullptr, loss, 1, m, v, step, lr, s);
   cudaFreeAsync(part, s);
   SMC2_TRY(e);
   return SMC2_OK;
@@ -737,6 +839,7 @@ smc2_status smc2_mlp_loss_grad(int D, const float* params, const float* x, const
 smc2_status smc2_mlp_input_grad(int D, const float* params, const float* x, int R, float* s_out, float* dx,
                                 void* stream) {
   if (D < 1 || D > kMlpMaxD || R < 1 || !params || !x || !dx) return SMC2_EINVAL;
+  if (reinterpret_cast<uintptr_t>(params) % 16 != 0) return SMC2_EINVAL;  // read as float4
   SMC2_TRY(mlp_input_grad_launch(params, D, x, R, s_out, dx, static_cast<cudaStream_t>(stream)));
   return SMC2_OK;
 }
@@ -784,6 +887,9 @@ void smc2_destroy(smc2_ctx* c) {
   if (c->side_stream) cudaStreamDestroy(c->side_stream);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->train_stream) cudaStreamDestroy(c->train_stream);
+  if (c->ev_tfork) cudaEventDestroy(c->ev_tfork);
+  if (c->ev_tjoin) cudaEventDestroy(c->ev_tjoin);
   delete c;
 }
 

@@ -25,7 +25,7 @@ constexpr int kMlpH = 64;                              // hidden width of the su
 constexpr int kMlpWarps = 4;                           // warps (16 rows each) per network CTA
 constexpr int kMlpMaxD = 8;                            // input dimension, at most
 constexpr int kPartStride = 160;                       // >= 1 + 2D + 2D(2D+1)/2 for D <= 8
-constexpr int kStatStride = 16;                        // >= 3 + D
+constexpr int kStatStride = 24;                        // >= 3 + D + D (D + 1) / 2
 
 struct LKParams {
   double mu[2 * 8];    // (mu_a, mu_b)
@@ -41,8 +41,40 @@ struct IterCur {       // working scalars of the current iteration of one datase
   double m;            // max log w (quantisation reference)
   double lse;          // log sum w
   double m_par;        // max parent log weight for the next iteration's L-kernel fit
+  double Lpop[64];     // learned proposal: Cholesky factor of the weighted population covariance
+  int pop_ok;          // Lpop usable (positive pivots, ESS >= 2 (D + 1))
   int resample;
-  int pad;
+  int mlp_used;        // 1: this iteration proposes with the learned drift
+  double mlp_loss;     // training loss of the network that proposed
+};
+
+// Learned proposal: standardisation of the training set.
+struct MlpNorm {
+  double mu[8], sd[8];  // input standardisation
+  double ymax, tau;     // z = max((log pi - ymax) / tau, -8)
+  double zmean, zsd;    // y = (z - zmean) / zsd, the training target
+  int rows;             // rows in the training set
+  float var_y;          // variance of the targets (1, or 0 when they are constant)
+};
+
+// Learned proposal: device state (dataset 0 of a context).  Training writes
+// p, norm and loss; the proposal reads the published copies p_use, norm_use,
+// loss_use, so that training can run beside the next iteration.
+struct MlpDev {
+  int on, W;            // enabled; iterations kept in the training ring
+  double h;             // proposal step
+  float *p, *m, *v;     // parameters and Adam moments (FP32)
+  int* step;            // Adam steps taken
+  float* loss;          // latest training loss (mean squared error)
+  float *ring_th, *ring_lp;   // [W N][D], [W N] (theta, log pi^)
+  int* ring_rows;       // rows of the ring filled so far
+  float *xs, *ys;       // standardised training set
+  MlpNorm* norm;
+  float* p_use;         // published parameters, standardisation and loss
+  MlpNorm* norm_use;
+  float* loss_use;
+  double* score;        // [D][N] grad log pi^ at the parents (surrogate)
+  float* part;          // [ctas][params + 1] partial gradients
 };
 
 struct DSDev {
@@ -75,6 +107,8 @@ struct OuterParams {
   int* k_done;         // completed iterations; the running iteration is k_done + 1
   int* status;
   unsigned* grid_ticket;
+  MlpDev mlp;
+  int ds_N0;           // N of dataset 0
 };
 
 // One particle-filter job: n filters of one dataset.
@@ -133,13 +167,16 @@ cudaError_t resample_systematic_launch(const uint64_t* q, int n, uint32_t U, int
                                        cudaStream_t s);
 // Surrogate network (mlp.cu).
 int mlp_param_count(int D);
-int mlp_grad_ctas(int R);
+int mlp_grad_ctas(int R);  // CTAs (and partial-gradient rows) of one training step over R rows
 size_t mlp_grad_smem_bytes();
-cudaError_t mlp_grad_launch(const float* p, int D, const float* x, const float* y, int R, float* part,
-                            int* step, cudaStream_t s);
-cudaError_t mlp_reduce_launch(float* p, int D, const float* part, int n_cta, int R, float* grad,
-                              float* loss, int adam, float* m, float* v, const int* step, float lr,
-                              cudaStream_t s);
+cudaError_t mlp_step_launch(float* p, int D, const float* x, const float* y, int R, const int* R_dev,
+                            float* part, float* grad, float* loss, int adam, float* m, float* v, int* step,
+                            float lr, cudaStream_t s);
+cudaError_t mlp_init_launch(const MlpDev& M, int D, uint64_t seed, cudaStream_t s);
+cudaError_t mlp_append_launch(const OuterParams& P, int N, cudaStream_t s);
+cudaError_t mlp_train_launch(const OuterParams& P, int steps, float lr, cudaStream_t s);
+cudaError_t mlp_publish_launch(const OuterParams& P, cudaStream_t s);
+cudaError_t mlp_score_launch(const OuterParams& P, int N, cudaStream_t s);
 cudaError_t mlp_input_grad_launch(const float* p, int D, const float* x, int R, float* s_out, float* dx,
                                   cudaStream_t s);
 

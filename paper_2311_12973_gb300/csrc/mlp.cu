@@ -57,33 +57,62 @@ struct MlpSmemWeights {
   bf16 w2t[kMlpH * kLd];
   bf16 w2b[kMlpH * kLd];
   bf16 w3b[kMlpH];
-  float b1[kMlpH], b2[kMlpH], w3f[kMlpH];
+  float b1[kMlpH], b2[kMlpH], w3f[kMlpH];  // w3f: the bfloat16 w3 as FP32
   float b3;
 };
 
 // Load the weights from the FP32 parameter vector (bf16-rounded copies).
+// Every thread issues its float4 loads before the first shared-memory store
+// (the vector is 16-byte aligned and every block of it starts at a multiple
+// of four floats), so a CTA waits for about one L2 round trip; the
+// transposes happen in the shared-memory stores.
 __device__ void load_weights(MlpSmemWeights& W, const float* p, int D) {
-  for (int e = threadIdx.x; e < kMlpH * kLd1; e += blockDim.x) {
-    const int o = e / kLd1, d = e % kLd1;
-    W.w1t[e] = __float2bfloat16_rn(d < D ? p[d * kMlpH + o] : 0.f);
+  constexpr int kV = 8;  // float4 loads in flight per thread and round
+  const int nt = blockDim.x, tid = threadIdx.x;
+  for (int e = tid; e < kMlpH * kLd1; e += nt) W.w1t[e] = __float2bfloat16_rn(0.f);
+  for (int e = tid; e < 8 * kLd; e += nt) W.w1b[e] = __float2bfloat16_rn(0.f);
+  __syncthreads();
+  const int n4 = (mlp_nparams(D) - 1) / 4;  // float4 blocks before b3
+  const float4* p4 = reinterpret_cast<const float4*>(p);
+  for (int base = tid; base < n4; base += kV * nt) {
+    float4 v[kV];
+#pragma unroll
+    for (int u = 0; u < kV; ++u) {
+      const int q4 = base + u * nt;
+      v[u] = q4 < n4 ? p4[q4] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < kV; ++u) {
+      const int q4 = base + u * nt;
+      if (q4 >= n4) break;
+      const float vals[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int q = 4 * q4 + c;
+        const float f = vals[c];
+        if (q < off_b1(D)) {  // W1[d][o]
+          const int d = q / kMlpH, o = q % kMlpH;
+          const bf16 h = __float2bfloat16_rn(f);
+          W.w1t[o * kLd1 + d] = h;
+          W.w1b[d * kLd + o] = h;
+        } else if (q < off_W2(D)) {
+          W.b1[q - off_b1(D)] = f;
+        } else if (q < off_b2(D)) {  // W2[i][o]
+          const int r = q - off_W2(D), i = r / kMlpH, o = r % kMlpH;
+          const bf16 h = __float2bfloat16_rn(f);
+          W.w2b[i * kLd + o] = h;
+          W.w2t[o * kLd + i] = h;
+        } else if (q < off_w3(D)) {
+          W.b2[q - off_b2(D)] = f;
+        } else {
+          const bf16 h = __float2bfloat16_rn(f);  // weights are used rounded, biases exact
+          W.w3b[q - off_w3(D)] = h;
+          W.w3f[q - off_w3(D)] = __bfloat162float(h);
+        }
+      }
+    }
   }
-  for (int e = threadIdx.x; e < 8 * kLd; e += blockDim.x) {
-    const int d = e / kLd, o = e % kLd;
-    W.w1b[e] = __float2bfloat16_rn(d < D && o < kMlpH ? p[d * kMlpH + o] : 0.f);
-  }
-  const float* W2 = p + off_W2(D);
-  for (int e = threadIdx.x; e < kMlpH * kLd; e += blockDim.x) {
-    const int r = e / kLd, q = e % kLd;
-    W.w2t[e] = __float2bfloat16_rn(q < kMlpH ? W2[q * kMlpH + r] : 0.f);  // [o][i]
-    W.w2b[e] = __float2bfloat16_rn(q < kMlpH ? W2[r * kMlpH + q] : 0.f);  // [i][o]
-  }
-  for (int e = threadIdx.x; e < kMlpH; e += blockDim.x) {
-    W.w3b[e] = __float2bfloat16_rn(p[off_w3(D) + e]);
-    W.w3f[e] = p[off_w3(D) + e];
-    W.b1[e] = p[off_b1(D) + e];
-    W.b2[e] = p[off_b2(D) + e];
-  }
-  if (threadIdx.x == 0) W.b3 = p[off_b3(D)];
+  if (tid == 0) W.b3 = p[off_b3(D)];
 }
 
 // Forward pass of one warp's 16 rows.  Lane (g, t) = (lane / 4, lane % 4)
@@ -187,163 +216,217 @@ __device__ __forceinline__ float sum_over_g(float v) {
   return v;
 }
 
+constexpr int kGradWarps = 8;                            // warps of a training-step CTA
+constexpr int kGradTiles = 1;                            // 16-row tiles per warp
+constexpr int kRowsGrad = 16 * kGradWarps * kGradTiles;  // rows per CTA
+constexpr int kLdR = kRowsGrad + 8;                      // padded row of the staged [unit][row] tiles
+
 struct MlpGradSmem {
   MlpSmemWeights W;
-  bf16 h1T[kMlpH * kLd];   // [i][row] h1 of the CTA's rows (bf16)
-  bf16 dz2T[kMlpH * kLd];  // [o][row] dz2 of the CTA's rows (bf16)
-  float col[kMlpWarps][3][kMlpH];        // per warp: db1, db2, dw3
-  float w1g[kMlpWarps][kMlpMaxD][kMlpH]; // per warp: dW1
-  float sc[kMlpWarps][2];                // per warp: sum e^2, db3
+  bf16 h1T[kMlpH * kLdR];                   // [i][row] h1 of the CTA's rows (bf16)
+  bf16 dz2T[kMlpH * kLdR];                  // [o][row] dz2 of the CTA's rows (bf16)
+  float col[kGradWarps][3][kMlpH];          // per warp: db1, db2, dw3
+  float w1g[kGradWarps][kMlpMaxD][kMlpH];   // per warp: dW1
+  float sc[kGradWarps][2];                  // per warp: sum e^2, db3
 };
 
 size_t mlp_grad_smem_bytes() { return sizeof(MlpGradSmem); }
 
-// Per-CTA partial gradients of L = (1/R) sum (s(x_r) - y_r)^2 into
-// part[blockIdx.x][0..P) and sum e^2 into part[blockIdx.x][P].
-__global__ void __launch_bounds__(32 * kMlpWarps)
+// Partial gradients of L = (1/R) sum (s(x_r) - y_r)^2: CTA c writes the
+// gradient over its rows (and their sum of e^2) to part[c][0..P].
+__global__ void __launch_bounds__(32 * kGradWarps)
     mlp_grad_kernel(const float* __restrict__ p, int D, const float* __restrict__ x,
-                    const float* __restrict__ y, int R, float* __restrict__ part, int* step) {
+                    const float* __restrict__ y, int R_imm, const int* R_dev, float* __restrict__ part,
+                    int* step) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int R = R_dev ? *R_dev : R_imm;
+  const int n_active = (R + kRowsGrad - 1) / kRowsGrad;
+  const int P = mlp_nparams(D);
   MlpGradSmem& S = *reinterpret_cast<MlpGradSmem*>(smem_raw);
-  load_weights(S.W, p, D);
-  if (step && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(step, 1);
-  __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  const int ra = blockIdx.x * kRowsCta + warp * 16 + g, rb = ra + 8;
-  const bool va = ra < R, vb = rb < R;
-  float xa[4], xb[4];  // input columns 2t, 2t+1 (a0/a1) and 2t+8, 2t+9 (a2/a3)
+  if (step && blockIdx.x == 0 && threadIdx.x == 0) *step += 1;  // the Adam step this gradient feeds
+  if ((int)blockIdx.x < n_active) {
+    load_weights(S.W, p, D);
+    for (int e = threadIdx.x; e < kGradWarps * 3 * kMlpH; e += blockDim.x) (&S.col[0][0][0])[e] = 0.f;
+    for (int e = threadIdx.x; e < kGradWarps * kMlpMaxD * kMlpH; e += blockDim.x) (&S.w1g[0][0][0])[e] = 0.f;
+    __syncthreads();
+    float l_acc = 0.f, d3_acc = 0.f;
+    for (int tile = 0; tile < kGradTiles; ++tile) {
+      const int rl = (warp * kGradTiles + tile) * 16 + g;  // row within the CTA
+      const int ra = blockIdx.x * kRowsGrad + rl, rb = ra + 8;
+      const bool va = ra < R, vb = rb < R;
+      float xa[4], xb[4], xfa[kMlpMaxD], xfb[kMlpMaxD];
 #pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    const int k = 2 * t + (e & 1) + (e >> 1) * 8;
-    xa[e] = (va && k < D) ? x[(size_t)ra * D + k] : 0.f;
-    xb[e] = (vb && k < D) ? x[(size_t)rb * D + k] : 0.f;
-  }
-  WarpForward F;
-  warp_forward(S.W, xa, xb, F);
-  const float ea = va ? F.s_lo - y[ra] : 0.f, eb = vb ? F.s_hi - y[rb] : 0.f;
-  const float ga = 2.f * ea / (float)R, gb = 2.f * eb / (float)R;
-  float dz2[8][4], dz1[8][4];
-  warp_backward(S.W, F, ga, gb, dz2, dz1);
-  // loss and db3: rows counted once, in the t = 0 lanes
-  const float l = warp_sum(t == 0 ? ea * ea + eb * eb : 0.f);
-  const float d3 = warp_sum(t == 0 ? ga + gb : 0.f);
-  if (lane == 0) {
-    S.sc[warp][0] = l;
-    S.sc[warp][1] = d3;
-  }
-  // column sums over the warp's rows: db2, dw3, db1, dW1
-#pragma unroll
-  for (int j = 0; j < 8; ++j) {
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-      const int col = 8 * j + 2 * t + e;
-      const float v_db2 = sum_over_g(dz2[j][e] + dz2[j][2 + e]);
-      const float v_dw3 = sum_over_g(round_bf16(F.h2[j][e]) * ga + round_bf16(F.h2[j][2 + e]) * gb);
-      const float v_db1 = sum_over_g(dz1[j][e] + dz1[j][2 + e]);
-      if (g == 0) {
-        S.col[warp][1][col] = v_db2;
-        S.col[warp][2][col] = v_dw3;
-        S.col[warp][0][col] = v_db1;
+      for (int e = 0; e < 4; ++e) {
+        const int k = 2 * t + (e & 1) + (e >> 1) * 8;
+        xa[e] = (va && k < D) ? x[(size_t)ra * D + k] : 0.f;
+        xb[e] = (vb && k < D) ? x[(size_t)rb * D + k] : 0.f;
       }
-      for (int d = 0; d < D; ++d) {
-        const float xad = va ? round_bf16(x[(size_t)ra * D + d]) : 0.f;
-        const float xbd = vb ? round_bf16(x[(size_t)rb * D + d]) : 0.f;
-        const float v = sum_over_g(xad * dz1[j][e] + xbd * dz1[j][2 + e]);
-        if (g == 0) S.w1g[warp][d][col] = v;
+#pragma unroll
+      for (int d = 0; d < kMlpMaxD; ++d) {
+        xfa[d] = (va && d < D) ? round_bf16(x[(size_t)ra * D + d]) : 0.f;
+        xfb[d] = (vb && d < D) ? round_bf16(x[(size_t)rb * D + d]) : 0.f;
       }
-    }
-  }
-  // stage h1 and dz2 transposed for dW2 = h1^T dz2 over the CTA's rows
-  const int rl = warp * 16 + g;
-#pragma unroll
-  for (int j = 0; j < 8; ++j)
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-      const int c = 8 * j + 2 * t + e;
-      S.h1T[c * kLd + rl] = __float2bfloat16_rn(F.h1[j][e]);
-      S.h1T[c * kLd + rl + 8] = __float2bfloat16_rn(F.h1[j][2 + e]);
-      S.dz2T[c * kLd + rl] = __float2bfloat16_rn(dz2[j][e]);
-      S.dz2T[c * kLd + rl + 8] = __float2bfloat16_rn(dz2[j][2 + e]);
-    }
-  __syncthreads();
-  float* out = part + (size_t)blockIdx.x * (mlp_nparams(D) + 1);
-  {
-    float acc[8][4];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-#pragma unroll
-    for (int kk = 0; kk < 4; ++kk) {  // k = the CTA's rows 16kk..16kk+15
-      const bf16* a = S.h1T + (16 * warp + g) * kLd + 16 * kk + 2 * t;
-      const uint32_t a0 = ld32(a), a1 = ld32(a + 8 * kLd), a2 = ld32(a + 8), a3 = ld32(a + 8 * kLd + 8);
+      WarpForward F;
+      warp_forward(S.W, xa, xb, F);
+      const float ea = va ? F.s_lo - y[ra] : 0.f, eb = vb ? F.s_hi - y[rb] : 0.f;
+      const float ga = 2.f * ea / (float)R, gb = 2.f * eb / (float)R;
+      float dz2[8][4], dz1[8][4];
+      warp_backward(S.W, F, ga, gb, dz2, dz1);
+      // loss and db3: rows counted once, in the t = 0 lanes
+      l_acc += warp_sum(t == 0 ? ea * ea + eb * eb : 0.f);
+      d3_acc += warp_sum(t == 0 ? ga + gb : 0.f);
+      // column sums over the tile's rows: db2, dw3, db1, dW1 (the warp owns its slots)
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
-        const bf16* b = S.dz2T + (8 * j + g) * kLd + 16 * kk + 2 * t;
-        mma_bf16(acc[j], a0, a1, a2, a3, ld32(b), ld32(b + 8));
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const int c = 8 * j + 2 * t + e;
+          const float v_db2 = sum_over_g(dz2[j][e] + dz2[j][2 + e]);
+          const float v_dw3 = sum_over_g(round_bf16(F.h2[j][e]) * ga + round_bf16(F.h2[j][2 + e]) * gb);
+          const float v_db1 = sum_over_g(dz1[j][e] + dz1[j][2 + e]);
+          if (g == 0) {
+            S.col[warp][1][c] += v_db2;
+            S.col[warp][2][c] += v_dw3;
+            S.col[warp][0][c] += v_db1;
+          }
+#pragma unroll
+          for (int d = 0; d < kMlpMaxD; ++d) {
+            if (d >= D) break;
+            const float w = sum_over_g(xfa[d] * dz1[j][e] + xfb[d] * dz1[j][2 + e]);
+            if (g == 0) S.w1g[warp][d][c] += w;
+          }
+        }
+      }
+      // stage h1 and dz2 transposed for dW2 = h1^T dz2 over the CTA's rows
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const int c = 8 * j + 2 * t + e;
+          S.h1T[c * kLdR + rl] = __float2bfloat16_rn(F.h1[j][e]);
+          S.h1T[c * kLdR + rl + 8] = __float2bfloat16_rn(F.h1[j][2 + e]);
+          S.dz2T[c * kLdR + rl] = __float2bfloat16_rn(dz2[j][e]);
+          S.dz2T[c * kLdR + rl + 8] = __float2bfloat16_rn(dz2[j][2 + e]);
+        }
+    }
+    if (lane == 0) {
+      S.sc[warp][0] = l_acc;
+      S.sc[warp][1] = d3_acc;
+    }
+    __syncthreads();
+    float* out = part + (size_t)blockIdx.x * (P + 1);
+    {  // dW2: warp (mt, nh) computes units i of m-tile mt against o of n-tiles 4 nh .. 4 nh + 3
+      const int mt = warp & 3, nh = warp >> 2;
+      float acc[4][4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+#pragma unroll 4
+      for (int kk = 0; kk < kRowsGrad / 16; ++kk) {
+        const bf16* a = S.h1T + (16 * mt + g) * kLdR + 16 * kk + 2 * t;
+        const uint32_t a0 = ld32(a), a1 = ld32(a + 8 * kLdR), a2 = ld32(a + 8), a3 = ld32(a + 8 * kLdR + 8);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const bf16* b = S.dz2T + (8 * (4 * nh + j) + g) * kLdR + 16 * kk + 2 * t;
+          mma_bf16(acc[j], a0, a1, a2, a3, ld32(b), ld32(b + 8));
+        }
+      }
+      float* gW2 = out + off_W2(D);
+      const int i0 = 16 * mt + g;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int o = 8 * (4 * nh + j) + 2 * t;
+        gW2[i0 * kMlpH + o] = acc[j][0];
+        gW2[i0 * kMlpH + o + 1] = acc[j][1];
+        gW2[(i0 + 8) * kMlpH + o] = acc[j][2];
+        gW2[(i0 + 8) * kMlpH + o + 1] = acc[j][3];
       }
     }
-    float* gW2 = out + off_W2(D);
-    const int i0 = 16 * warp + g;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int o = 8 * j + 2 * t;
-      gW2[i0 * kMlpH + o] = acc[j][0];
-      gW2[i0 * kMlpH + o + 1] = acc[j][1];
-      gW2[(i0 + 8) * kMlpH + o] = acc[j][2];
-      gW2[(i0 + 8) * kMlpH + o + 1] = acc[j][3];
+    // the remaining partials: warp sums in warp order
+    for (int e = threadIdx.x; e < kMlpH; e += blockDim.x) {
+      float b1s = 0.f, b2s = 0.f, w3s = 0.f;
+      for (int w = 0; w < kGradWarps; ++w) {
+        b1s += S.col[w][0][e];
+        b2s += S.col[w][1][e];
+        w3s += S.col[w][2][e];
+      }
+      out[off_b1(D) + e] = b1s;
+      out[off_b2(D) + e] = b2s;
+      out[off_w3(D) + e] = w3s;
+      for (int d = 0; d < D; ++d) {
+        float s1 = 0.f;
+        for (int w = 0; w < kGradWarps; ++w) s1 += S.w1g[w][d][e];
+        out[d * kMlpH + e] = s1;
+      }
     }
-  }
-  // the remaining partials: warp sums in warp order
-  for (int e = threadIdx.x; e < kMlpH; e += blockDim.x) {
-    float b1s = 0.f, b2s = 0.f, w3s = 0.f;
-    for (int w = 0; w < kMlpWarps; ++w) {
-      b1s += S.col[w][0][e];
-      b2s += S.col[w][1][e];
-      w3s += S.col[w][2][e];
+    if (threadIdx.x == 0) {
+      float l2 = 0.f, b3s = 0.f;
+      for (int w = 0; w < kGradWarps; ++w) {
+        l2 += S.sc[w][0];
+        b3s += S.sc[w][1];
+      }
+      out[off_b3(D)] = b3s;
+      out[P] = l2;
     }
-    out[off_b1(D) + e] = b1s;
-    out[off_b2(D) + e] = b2s;
-    out[off_w3(D) + e] = w3s;
-    for (int d = 0; d < D; ++d) {
-      float s1 = 0.f;
-      for (int w = 0; w < kMlpWarps; ++w) s1 += S.w1g[w][d][e];
-      out[d * kMlpH + e] = s1;
-    }
-  }
-  if (threadIdx.x == 0) {
-    float l2 = 0.f, b3s = 0.f;
-    for (int w = 0; w < kMlpWarps; ++w) {
-      l2 += S.sc[w][0];
-      b3s += S.sc[w][1];
-    }
-    out[off_b3(D)] = b3s;
-    out[mlp_nparams(D)] = l2;
   }
 }
 
-// Gradient (and mean loss) from the partials, summed over CTAs in order; with
-// adam != 0 also one Adam step on p (moments m, v; step count *step).
-__global__ void mlp_reduce_kernel(float* p, int D, const float* part, int n_cta, int R, float* grad,
-                                  float* loss, int adam, float* m, float* v, const int* step,
-                                  float lr, float beta1, float beta2, float eps) {
+// Sum of the partials over the CTAs in order, then the loss (and the gradient
+// when grad != nullptr) and, with adam != 0, one Adam step on p (moments m, v;
+// *step, already advanced by the gradient kernel, is the step number).
+__global__ void __launch_bounds__(128)
+    mlp_reduce_kernel(float* p, int D, const float* __restrict__ part, int R_imm, const int* R_dev,
+                      float* grad, float* loss, int adam, float* m, float* v, int* step, float lr) {
   const int P = mlp_nparams(D);
+  const int R = R_dev ? *R_dev : R_imm;
+  const int n = (R + kRowsGrad - 1) / kRowsGrad;
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q > P) return;
-  float s = 0.f;
-  for (int c = 0; c < n_cta; ++c) s += part[(size_t)c * (P + 1) + q];
+  float sum = 0.f;
+  for (int c0 = 0; c0 < n; c0 += 16) {
+    float tv[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) tv[u] = c0 + u < n ? __ldcg(part + (size_t)(c0 + u) * (P + 1) + q) : 0.f;
+#pragma unroll
+    for (int u = 0; u < 16; ++u) sum += tv[u];
+  }
   if (q == P) {
-    if (loss) loss[0] = s / (float)R;
+    if (loss) loss[0] = R > 0 ? sum / (float)R : 0.f;
     return;
   }
-  if (grad) grad[q] = s;
+  if (grad) grad[q] = sum;
   if (!adam) return;
-  const int tstep = *step;
-  const float mq = beta1 * m[q] + (1.f - beta1) * s;
-  const float vq = beta2 * v[q] + (1.f - beta2) * s * s;
+  const float beta1 = 0.9f, beta2 = 0.999f, eps = 1e-8f;
+  const float mq = beta1 * m[q] + (1.f - beta1) * sum;
+  const float vq = beta2 * v[q] + (1.f - beta2) * sum * sum;
   m[q] = mq;
   v[q] = vq;
-  const float mh = mq / (1.f - powf(beta1, (float)tstep));
-  const float vh = vq / (1.f - powf(beta2, (float)tstep));
-  p[q] -= lr * mh / (sqrtf(vh) + eps);
+  const float t_step = (float)*step;
+  const float bc1 = 1.f - powf(beta1, t_step), bc2 = 1.f - powf(beta2, t_step);
+  p[q] -= lr * (mq / bc1) / (sqrtf(vq / bc2) + eps);
+}
+
+// s and ds/dx of a warp's rows g and g+8: lane (g, t) returns dx of
+// coordinates 2t and 2t+1 (rows g: dx_lo, g+8: dx_hi).
+__device__ __forceinline__ void warp_input_grad(const MlpSmemWeights& W, const float* xa, const float* xb,
+                                                WarpForward& F, float (&dx_lo)[2], float (&dx_hi)[2]) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  warp_forward(W, xa, xb, F);
+  float dz2[8][4], dz1[8][4];
+  warp_backward(W, F, 1.f, 1.f, dz2, dz1);
+  // dx = dz1 W1^T: k over the hidden units, n over the input coordinates (padded to 8)
+  float c[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int kk = 0; kk < 4; ++kk) {
+    const bf16* w = W.w1b + g * kLd + 16 * kk + 2 * t;
+    mma_bf16(c, pack_bf16(dz1[2 * kk][0], dz1[2 * kk][1]), pack_bf16(dz1[2 * kk][2], dz1[2 * kk][3]),
+             pack_bf16(dz1[2 * kk + 1][0], dz1[2 * kk + 1][1]),
+             pack_bf16(dz1[2 * kk + 1][2], dz1[2 * kk + 1][3]), ld32(w), ld32(w + 8));
+  }
+  dx_lo[0] = c[0];
+  dx_lo[1] = c[1];
+  dx_hi[0] = c[2];
+  dx_hi[1] = c[3];
 }
 
 // s(x) and ds/dx of R rows.
@@ -364,18 +447,8 @@ __global__ void __launch_bounds__(32 * kMlpWarps)
     xb[e] = (vb && k < D) ? x[(size_t)rb * D + k] : 0.f;
   }
   WarpForward F;
-  warp_forward(W, xa, xb, F);
-  float dz2[8][4], dz1[8][4];
-  warp_backward(W, F, 1.f, 1.f, dz2, dz1);
-  // dx = dz1 W1^T: k over the hidden units, n over the input coordinates (padded to 8)
-  float c[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-  for (int kk = 0; kk < 4; ++kk) {
-    const bf16* w = W.w1b + g * kLd + 16 * kk + 2 * t;
-    mma_bf16(c, pack_bf16(dz1[2 * kk][0], dz1[2 * kk][1]), pack_bf16(dz1[2 * kk][2], dz1[2 * kk][3]),
-             pack_bf16(dz1[2 * kk + 1][0], dz1[2 * kk + 1][1]),
-             pack_bf16(dz1[2 * kk + 1][2], dz1[2 * kk + 1][3]), ld32(w), ld32(w + 8));
-  }
+  float dlo[2], dhi[2];
+  warp_input_grad(W, xa, xb, F, dlo, dhi);
   if (t == 0) {
     if (va && s_out) s_out[ra] = F.s_lo;
     if (vb && s_out) s_out[rb] = F.s_hi;
@@ -384,9 +457,207 @@ __global__ void __launch_bounds__(32 * kMlpWarps)
   for (int e = 0; e < 2; ++e) {
     const int d = 2 * t + e;
     if (d < D) {
-      if (va) dx[(size_t)ra * D + d] = c[e];
-      if (vb) dx[(size_t)rb * D + d] = c[2 + e];
+      if (va) dx[(size_t)ra * D + d] = dlo[e];
+      if (vb) dx[(size_t)rb * D + d] = dhi[e];
     }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// the learned proposal inside the sampler (dataset 0)
+// ---------------------------------------------------------------------------
+
+// Xavier-uniform weights and zero biases from the random stream (tag MLP_INIT);
+// Adam moments and step cleared.
+__global__ void mlp_init_kernel(MlpDev M, int D, uint64_t seed) {
+  const int P = mlp_nparams(D);
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q == 0) *M.step = 0;
+  if (q >= P) return;
+  const float u = 2.f * uniform23<float>(philox4x32_10(make_uint4((uint32_t)q, 0u, 0u, TAG_MLP_INIT),
+                                                       seed_key(seed)).x) - 1.f;
+  float a = 0.f;
+  if (q < off_b1(D))
+    a = sqrtf(6.f / (float)(D + kMlpH));
+  else if (q >= off_W2(D) && q < off_b2(D))
+    a = sqrtf(6.f / (float)(2 * kMlpH));
+  else if (q >= off_w3(D) && q < off_b3(D))
+    a = sqrtf(6.f / (float)(kMlpH + 1));
+  M.p[q] = a * u;
+  M.p_use[q] = a * u;
+  M.m[q] = 0.f;
+  M.v[q] = 0.f;
+}
+
+// (theta_k, log pi^(theta_k)) of this iteration's proposals into ring slot (k-1) mod W.
+__global__ void mlp_append_kernel(OuterParams P) {
+  const DSDev& S = P.ds[0];
+  const int k = *P.k_done + 1, N = S.N, D = P.D;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const size_t row = (size_t)((k - 1) % P.mlp.W) * N + i;
+  for (int d = 0; d < D; ++d) P.mlp.ring_th[row * D + d] = (float)S.thB[(size_t)d * N + i];
+  P.mlp.ring_lp[row] = (float)(S.lpB[i] + S.llB[i]);
+  if (i == 0) *P.mlp.ring_rows = min(k, P.mlp.W) * N;
+}
+
+// The trained state becomes the one the proposal reads.
+__global__ void mlp_publish_kernel(MlpDev M, int n_par) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < n_par) M.p_use[q] = M.p[q];
+  if (q == 0) {
+    *M.norm_use = *M.norm;
+    *M.loss_use = *M.loss;
+  }
+}
+
+// Sums of NV values over the 1024 threads of a block, fixed order (shuffle
+// tree in each warp, then the warps in order); every thread gets the totals.
+template <int NV, typename R>
+__device__ void block_sums(R (&v)[NV], R (*red)[32], bool is_max = false) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    v[i] = is_max ? warp_max(v[i]) : warp_sum(v[i]);
+    if (lane == 0) red[i][warp] = v[i];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    R r = red[i][0];
+    for (int w = 1; w < 32; ++w) r = is_max ? fmax(r, red[i][w]) : r + red[i][w];
+    v[i] = r;
+  }
+  __syncthreads();
+}
+
+// Standardised training set of the rows in the ring (one block of 1024
+// threads, FP32, fixed-order sums): z = max((log pi - max log pi) / tau, -8),
+// tau = max(2, D), and the target y = (z - mean z) / sd z; inputs
+// standardised by the mean and sd of the rows above the clip (all rows if too
+// few), the moments taken about ring row 0.
+__global__ void __launch_bounds__(1024) mlp_stats_kernel(OuterParams P) {
+  __shared__ float red[2 * kMlpMaxD + 1][32];
+  const int D = P.D, tid = threadIdx.x;
+  const int rows = *P.mlp.ring_rows;
+  const float tau = D > 2 ? (float)D : 2.f, inv_tau = 1.f / tau;
+  const float* th = P.mlp.ring_th;
+  const float* lpv = P.mlp.ring_lp;
+  float mx[1] = {-INFINITY};
+  for (int r = tid; r < rows; r += 1024) {
+    const float lp = lpv[r];
+    if (isfinite(lp)) mx[0] = fmaxf(mx[0], lp);
+  }
+  block_sums<1, float>(mx, red, true);
+  const float ymax = mx[0];
+  const float cut = ymax - 8.f * tau;
+  float ref[kMlpMaxD], mu[kMlpMaxD], sd[kMlpMaxD];
+#pragma unroll
+  for (int d = 0; d < kMlpMaxD; ++d) ref[d] = (rows > 0 && d < D) ? th[d] : 0.f;
+  for (int pass = 0; pass < 2; ++pass) {  // pass 0: rows above the clip; pass 1: every finite row
+    float acc[2 * kMlpMaxD + 1];
+#pragma unroll
+    for (int i = 0; i < 2 * kMlpMaxD + 1; ++i) acc[i] = 0.f;
+    for (int r = tid; r < rows; r += 1024) {
+      const float lp = lpv[r];
+      if (!isfinite(lp) || (pass == 0 && lp <= cut)) continue;
+      acc[2 * kMlpMaxD] += 1.f;
+#pragma unroll
+      for (int d = 0; d < kMlpMaxD; ++d) {
+        if (d >= D) break;
+        const float c = th[(size_t)r * D + d] - ref[d];
+        acc[d] += c;
+        acc[kMlpMaxD + d] += c * c;
+      }
+    }
+    block_sums<2 * kMlpMaxD + 1, float>(acc, red);
+    const float cnt = acc[2 * kMlpMaxD];
+#pragma unroll
+    for (int d = 0; d < kMlpMaxD; ++d) {
+      const float m1 = cnt > 0.f ? acc[d] / cnt : 0.f;
+      const float m2 = cnt > 0.f ? acc[kMlpMaxD + d] / cnt : 0.f;
+      mu[d] = ref[d] + m1;
+      sd[d] = cnt > 1.f ? sqrtf(fmaxf(m2 - m1 * m1, 0.f)) : 1.f;
+      sd[d] = fmaxf(sd[d], 1e-6f);
+    }
+    if (cnt >= 2.f * D + 2.f) break;
+  }
+  auto z_of = [&](float lp) { return isfinite(lp) ? fmaxf((lp - ymax) * inv_tau, -8.f) : -8.f; };
+  float zs[2] = {0.f, 0.f};
+  for (int r = tid; r < rows; r += 1024) {
+    const float z = z_of(lpv[r]);
+    zs[0] += z;
+    zs[1] += z * z;
+  }
+  block_sums<2, float>(zs, red);
+  const float zmean = rows > 0 ? zs[0] / (float)rows : 0.f;
+  const float zvar = rows > 0 ? fmaxf(zs[1] / (float)rows - zmean * zmean, 0.f) : 0.f;
+  const float zsd = zvar > 1e-8f ? sqrtf(zvar) : 1.f, inv_zsd = 1.f / zsd;
+  float inv_sd[kMlpMaxD];
+#pragma unroll
+  for (int d = 0; d < kMlpMaxD; ++d) inv_sd[d] = 1.f / sd[d];
+  for (int r = tid; r < rows; r += 1024) {
+    P.mlp.ys[r] = (z_of(lpv[r]) - zmean) * inv_zsd;
+#pragma unroll
+    for (int d = 0; d < kMlpMaxD; ++d) {
+      if (d >= D) break;
+      P.mlp.xs[(size_t)r * D + d] = (th[(size_t)r * D + d] - mu[d]) * inv_sd[d];
+    }
+  }
+  if (tid == 0) {
+    MlpNorm& nm = *P.mlp.norm;
+    for (int d = 0; d < D; ++d) {
+      nm.mu[d] = mu[d];
+      nm.sd[d] = 1.0 / (double)inv_sd[d];
+    }
+    nm.ymax = ymax;
+    nm.tau = tau;
+    nm.zmean = zmean;
+    nm.zsd = zsd;
+    nm.rows = rows;
+    nm.var_y = zvar > 1e-8f ? 1.f : 0.f;
+  }
+}
+
+// Score of the surrogate at the parents theta_{k-1}: through the input and
+// target standardisations, d log pi^ / d theta_d = tau zsd (ds/dx)_d / sd_d.
+// Decides whether iteration k proposes with it: from k = 3 on, while the
+// published network explains half the variance of its targets and the
+// population covariance has a usable Cholesky factor.
+__global__ void __launch_bounds__(32 * kMlpWarps) mlp_score_kernel(OuterParams P) {
+  __shared__ MlpSmemWeights W;
+  const DSDev& S = P.ds[0];
+  const int k = *P.k_done + 1, N = S.N, D = P.D;
+  const MlpNorm& nm = *P.mlp.norm_use;
+  const float loss = *P.mlp.loss_use;
+  const bool use = k >= 3 && isfinite(loss) && nm.var_y > 0.f && loss < 0.5f * nm.var_y && S.cur->pop_ok;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    S.cur->mlp_used = use ? 1 : 0;
+    S.cur->mlp_loss = (double)loss;
+  }
+  if (!use) return;
+  load_weights(W, P.mlp.p_use, D);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int ra = blockIdx.x * kRowsCta + warp * 16 + g, rb = ra + 8;
+  const bool va = ra < N, vb = rb < N;
+  float xa[4], xb[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int d = 2 * t + (e & 1) + (e >> 1) * 8;
+    xa[e] = (va && d < D) ? (float)((S.thA[(size_t)d * N + ra] - nm.mu[d]) / nm.sd[d]) : 0.f;
+    xb[e] = (vb && d < D) ? (float)((S.thA[(size_t)d * N + rb] - nm.mu[d]) / nm.sd[d]) : 0.f;
+  }
+  WarpForward F;
+  float dlo[2], dhi[2];
+  warp_input_grad(W, xa, xb, F, dlo, dhi);
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    const int d = 2 * t + e;
+    if (d >= D) continue;
+    const double scale = nm.tau * nm.zsd / nm.sd[d];
+    if (va) P.mlp.score[(size_t)d * N + ra] = scale * dlo[e];
+    if (vb) P.mlp.score[(size_t)d * N + rb] = scale * dhi[e];
   }
 }
 
@@ -394,24 +665,59 @@ __global__ void __launch_bounds__(32 * kMlpWarps)
 // host launchers
 // ---------------------------------------------------------------------------
 int mlp_param_count(int D) { return mlp_nparams(D); }
-int mlp_grad_ctas(int R) { return (R + kRowsCta - 1) / kRowsCta; }
+int mlp_grad_ctas(int R) { return (R + kRowsGrad - 1) / kRowsGrad; }
 
-cudaError_t mlp_grad_launch(const float* p, int D, const float* x, const float* y, int R, float* part,
-                            int* step, cudaStream_t s) {
+// One gradient (and optionally Adam) step over R rows (R_dev, when given, holds
+// the row count; R bounds it and sizes the grid).
+cudaError_t mlp_step_launch(float* p, int D, const float* x, const float* y, int R, const int* R_dev,
+                            float* part, float* grad, float* loss, int adam, float* m, float* v, int* step,
+                            float lr, cudaStream_t s) {
   const size_t smem = sizeof(MlpGradSmem);
   cudaError_t e = cudaFuncSetAttribute(mlp_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  mlp_grad_kernel<<<mlp_grad_ctas(R), 32 * kMlpWarps, smem, s>>>(p, D, x, y, R, part, step);
+  mlp_grad_kernel<<<mlp_grad_ctas(R), 32 * kGradWarps, smem, s>>>(p, D, x, y, R, R_dev, part,
+                                                                  adam ? step : nullptr);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int P = mlp_nparams(D);
+  mlp_reduce_kernel<<<(P + 1 + 127) / 128, 128, 0, s>>>(p, D, part, R, R_dev, grad, loss, adam, m, v, step,
+                                                         lr);
   return cudaGetLastError();
 }
 
-cudaError_t mlp_reduce_launch(float* p, int D, const float* part, int n_cta, int R, float* grad,
-                              float* loss, int adam, float* m, float* v, const int* step, float lr,
-                              cudaStream_t s) {
+cudaError_t mlp_init_launch(const MlpDev& M, int D, uint64_t seed, cudaStream_t s) {
   const int P = mlp_nparams(D);
-  mlp_reduce_kernel<<<(P + 1 + 255) / 256, 256, 0, s>>>(p, D, part, n_cta, R, grad, loss, adam, m, v,
-                                                       step, lr, 0.9f, 0.999f, 1e-8f);
+  mlp_init_kernel<<<(P + 255) / 256, 256, 0, s>>>(M, D, seed);
+  return cudaGetLastError();
+}
+
+// Store this iteration's rows (before resampling moves the population).
+cudaError_t mlp_append_launch(const OuterParams& P, int N, cudaStream_t s) {
+  mlp_append_kernel<<<(N + 127) / 128, 128, 0, s>>>(P);
+  return cudaGetLastError();
+}
+
+// Standardise the ring and take `steps` Adam steps on it.
+cudaError_t mlp_train_launch(const OuterParams& P, int steps, float lr, cudaStream_t s) {
+  mlp_stats_kernel<<<1, 1024, 0, s>>>(P);
+  cudaError_t e = cudaGetLastError();
+  const MlpDev& M = P.mlp;
+  const int cap = M.W * P.ds_N0;
+  for (int it = 0; it < steps && e == cudaSuccess; ++it)
+    e = mlp_step_launch(M.p, P.D, M.xs, M.ys, cap, &M.norm->rows, M.part, nullptr, M.loss, 1, M.m,
+                        M.v, M.step, lr, s);
+  return e;
+}
+
+cudaError_t mlp_publish_launch(const OuterParams& P, cudaStream_t s) {
+  const int n_par = mlp_nparams(P.D);
+  mlp_publish_kernel<<<(n_par + 255) / 256, 256, 0, s>>>(P.mlp, n_par);
+  return cudaGetLastError();
+}
+
+cudaError_t mlp_score_launch(const OuterParams& P, int N, cudaStream_t s) {
+  mlp_score_kernel<<<(N + kRowsCta - 1) / kRowsCta, 32 * kMlpWarps, 0, s>>>(P);
   return cudaGetLastError();
 }
 

@@ -191,22 +191,51 @@ __global__ void __launch_bounds__(kOuterBlock) propose_kernel(OuterParams P) {
   const bool act = i < N;
   const uint2 key = seed_key(P.seed);
   double a[D], b[D];
+  // random walk (Eqs. 18-19); learned proposal: theta_k = a + h L (w + z) with
+  // L L^T the population covariance and w = h/2 L^T grad log pi^(a), clipped
+  // at +-3, so that the drift is h^2/2 Sigma grad log pi^ in whitened units
+  const bool mlp = k > 1 && P.mlp.on && S.cur->mlp_used;
   if (act) {
     const uint32_t c2 = counter_c2((uint32_t)i, S.c2hi);
+    double z[D];
 #pragma unroll
     for (int g = 0; g * 4 < D; ++g) {
-      double z[4];
+      double z4[4];
       normals4<double>(make_uint4((uint32_t)g, 0u, c2,
                                   counter_c3(k == 1 ? TAG_THETA_INIT : TAG_PROPOSE, k)),
-                       key, z);
+                       key, z4);
 #pragma unroll
-      for (int r = 0; r < 4 && 4 * g + r < D; ++r) {
-        const int d = 4 * g + r;
-        if (k == 1) {
-          b[d] = P.prior_mean[d] + P.prior_sd[d] * z[r];
-        } else {
-          a[d] = S.thA[(size_t)d * N + i];
-          b[d] = a[d] + P.rw_scale * z[r];
+      for (int r = 0; r < 4 && 4 * g + r < D; ++r) z[4 * g + r] = z4[r];
+    }
+    if (k == 1) {
+#pragma unroll
+      for (int d = 0; d < D; ++d) b[d] = P.prior_mean[d] + P.prior_sd[d] * z[d];
+    } else {
+#pragma unroll
+      for (int d = 0; d < D; ++d) a[d] = S.thA[(size_t)d * N + i];
+      if (!mlp) {
+#pragma unroll
+        for (int d = 0; d < D; ++d) b[d] = a[d] + P.rw_scale * z[d];
+      } else {
+        const double* L = S.cur->Lpop;
+        const double h = P.mlp.h;
+        double g[D], u[D];
+#pragma unroll
+        for (int d = 0; d < D; ++d) g[d] = P.mlp.score[(size_t)d * N + i];
+#pragma unroll
+        for (int r = 0; r < D; ++r) {
+          double w = 0.0;
+#pragma unroll
+          for (int d = r; d < D; ++d) w += L[d * kMaxD + r] * g[d];
+          w = fmin(fmax(0.5 * h * w, -3.0), 3.0);
+          u[r] = w + z[r];
+        }
+#pragma unroll
+        for (int r = 0; r < D; ++r) {
+          double v = 0.0;
+#pragma unroll
+          for (int c = 0; c <= r; ++c) v += L[r * kMaxD + c] * u[c];
+          b[r] = a[r] + h * v;
         }
       }
     }
@@ -214,7 +243,17 @@ __global__ void __launch_bounds__(kOuterBlock) propose_kernel(OuterParams P) {
     for (int d = 0; d < D; ++d) S.thB[(size_t)d * N + i] = b[d];
     const double lp = log_prior<D>(P, b);
     S.lpB[i] = lp;
-    S.logq[i] = (k == 1) ? lp : rw_logpdf<D>(P, b, a);
+    if (k == 1) {
+      S.logq[i] = lp;
+    } else if (mlp) {
+      // N(b; a + h L w, h^2 L L^T) at b = a + h L (w + z)
+      double lq = -0.5 * D * kLog2Pi - D * log(P.mlp.h);
+#pragma unroll
+      for (int d = 0; d < D; ++d) lq += -log(S.cur->Lpop[d * kMaxD + d]) - 0.5 * z[d] * z[d];
+      S.logq[i] = lq;
+    } else {
+      S.logq[i] = rw_logpdf<D>(P, b, a);
+    }
   }
   if (k == 1 || P.lkernel != LK_GAUSS) return;
 
@@ -291,6 +330,43 @@ __device__ __forceinline__ void accumulate_recycling(double* rec, double* est_re
   for (int d = 0; d < D; ++d) est_rec[d] = rec[1 + d] / rec[0];
 }
 
+__host__ __device__ constexpr int tri(int d, int f) { return d * (d + 1) / 2 + f; }  // f <= d
+
+// Learned proposal: weighted covariance of theta_k (from second moments about
+// the prior mean) and its lower Cholesky factor; usable when every pivot is
+// positive and the population holds ESS >= 2 (D + 1).
+template <int D>
+__device__ void population_cholesky(const OuterParams& P, const smc2_iter_stats& st, const double* sqq,
+                                    double s1, IterCur* cur) {
+  double Lm[D][D];
+  bool ok = st.ess >= 2.0 * (D + 1);
+  for (int d = 0; d < D; ++d) {
+    const double md = st.est[d] - P.prior_mean[d];
+    for (int f = 0; f <= d; ++f) {
+      const double mf = st.est[f] - P.prior_mean[f];
+      Lm[d][f] = sqq[tri(d, f)] / s1 - md * mf;
+    }
+  }
+  for (int j = 0; j < D; ++j) {
+    double a = Lm[j][j];
+    for (int c = 0; c < j; ++c) a -= Lm[j][c] * Lm[j][c];
+    if (!(a > 1e-12 * fabs(Lm[j][j])) || !(a > 0.0)) {
+      ok = false;
+      a = 1.0;
+    }
+    const double ljj = sqrt(a);
+    Lm[j][j] = ljj;
+    for (int r = j + 1; r < D; ++r) {
+      double v = Lm[r][j];
+      for (int c = 0; c < j; ++c) v -= Lm[r][c] * Lm[j][c];
+      Lm[r][j] = v / ljj;
+    }
+  }
+  for (int d = 0; d < D; ++d)
+    for (int f = 0; f < D; ++f) cur->Lpop[d * kMaxD + f] = f <= d ? Lm[d][f] : 0.0;
+  cur->pop_ok = ok ? 1 : 0;
+}
+
 template <int D>
 __global__ void __launch_bounds__(kOuterBlock) weights_kernel(OuterParams P) {
   const DSDev& S = P.ds[blockIdx.y];
@@ -332,6 +408,18 @@ __global__ void __launch_bounds__(kOuterBlock) weights_kernel(OuterParams P) {
       const double sd = warp_sum(act ? e * b[d] : 0.0);
       if (lane == 0) ps[3 + d] = sd;
     }
+    if (P.mlp.on) {  // second moments about the prior mean, for the population covariance
+      double c[D];
+#pragma unroll
+      for (int d = 0; d < D; ++d) c[d] = act ? b[d] - P.prior_mean[d] : 0.0;
+#pragma unroll
+      for (int d = 0; d < D; ++d)
+#pragma unroll
+        for (int f = 0; f <= d; ++f) {
+          const double sq = warp_sum(e * c[d] * c[f]);
+          if (lane == 0) ps[3 + D + tri(d, f)] = sq;
+        }
+    }
   }
   __threadfence();
   __syncwarp();
@@ -353,6 +441,9 @@ __global__ void __launch_bounds__(kOuterBlock) weights_kernel(OuterParams P) {
     if (lane == 0) {
       raise_status(P.status, ST_NONFINITE);
       st.resampled = 0;
+      st.mlp_used = 0;
+      st.pad = 0;
+      st.mlp_loss = 0.0;
       st.ess = st.lse = st.lse2 = st.logz = NAN;
       for (int d = 0; d < kMaxD; ++d) st.est[d] = NAN;
       cur->resample = 0;
@@ -361,9 +452,14 @@ __global__ void __launch_bounds__(kOuterBlock) weights_kernel(OuterParams P) {
     }
     return;
   }
-  double s1 = 0.0, s2 = 0.0, sth[D];
+  constexpr int NQ = D * (D + 1) / 2;
+  static_assert(3 + D + NQ <= kStatStride, "statistics stride");
+  const int nq = P.mlp.on ? NQ : 0;
+  double s1 = 0.0, s2 = 0.0, sth[D], sqq[NQ];
 #pragma unroll
   for (int d = 0; d < D; ++d) sth[d] = 0.0;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) sqq[q] = 0.0;
   for (int bb = lane; bb < S.nblk; bb += 32) {
     const double* pb = S.part_st + (size_t)bb * kStatStride;
     const double mbb = __ldcg(pb);
@@ -373,11 +469,17 @@ __global__ void __launch_bounds__(kOuterBlock) weights_kernel(OuterParams P) {
     s2 += __ldcg(pb + 2) * (f * f);
 #pragma unroll
     for (int d = 0; d < D; ++d) sth[d] += __ldcg(pb + 3 + d) * f;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+      if (q < nq) sqq[q] += __ldcg(pb + 3 + D + q) * f;
   }
   s1 = warp_sum(s1);
   s2 = warp_sum(s2);
 #pragma unroll
   for (int d = 0; d < D; ++d) sth[d] = warp_sum(sth[d]);
+#pragma unroll
+  for (int q = 0; q < NQ; ++q)
+    if (q < nq) sqq[q] = warp_sum(sqq[q]);
   if (lane != 0) return;
   st.lse = m + log(s1);
   st.lse2 = 2.0 * m + log(s2);
@@ -389,6 +491,10 @@ __global__ void __launch_bounds__(kOuterBlock) weights_kernel(OuterParams P) {
   cur->lse = st.lse;
   cur->resample = st.resampled;
   cur->m_par = st.resampled ? st.lse - S.logN : m;
+  if (P.mlp.on) population_cholesky<D>(P, st, sqq, s1, cur);
+  st.mlp_used = (k > 1 && P.mlp.on) ? cur->mlp_used : 0;
+  st.pad = 0;
+  st.mlp_loss = (k > 1 && P.mlp.on) ? cur->mlp_loss : 0.0;
   accumulate_recycling(S.rec, S.est_rec, st.ess, st.est, D);
   if ((int)k <= P.K) S.hist[k - 1] = st;
   S.tickets[1] = 0;

@@ -31,6 +31,7 @@ class Config(C.Structure):
         ("npop", C.c_double), ("e0", C.c_double), ("i0", C.c_double), ("lambda_floor", C.c_double),
         ("n_sub", C.c_int), ("ppt", C.c_int), ("cta_threads", C.c_int), ("n_datasets", C.c_int),
         ("ds_N", C.POINTER(C.c_int)), ("ds_M", C.POINTER(C.c_int)), ("ds_T", C.POINTER(C.c_int)),
+        ("mlp_h", C.c_double), ("mlp_lr", C.c_double), ("mlp_steps", C.c_int), ("mlp_window", C.c_int),
     ]
 
 
@@ -38,13 +39,14 @@ class IterStats(C.Structure):
     _fields_ = [
         ("k", C.c_int), ("resampled", C.c_int), ("lk_fallback", C.c_int), ("dataset", C.c_int),
         ("ess", C.c_double), ("lse", C.c_double), ("lse2", C.c_double), ("logz", C.c_double),
-        ("est", C.c_double * MAX_D),
+        ("est", C.c_double * MAX_D), ("mlp_used", C.c_int), ("pad", C.c_int), ("mlp_loss", C.c_double),
     ]
 
     def as_dict(self, D: int) -> dict:
         return {"k": self.k, "resampled": self.resampled, "lk_fallback": self.lk_fallback,
                 "dataset": self.dataset, "ess": self.ess, "lse": self.lse, "lse2": self.lse2,
-                "logz": self.logz, "est": np.array(self.est[:D])}
+                "logz": self.logz, "est": np.array(self.est[:D]), "mlp_used": self.mlp_used,
+                "mlp_loss": self.mlp_loss}
 
 
 class SMC2Error(RuntimeError):
@@ -87,6 +89,7 @@ def _load() -> C.CDLL:
         "smc2_pf_loglik_noalloc": ([C.POINTER(Config), dp, dp, C.c_int, C.c_int, dp, vp], st),
         "smc2_mlp_loss_grad": ([C.c_int, dp, dp, dp, C.c_int, dp, dp, vp], st),
         "smc2_mlp_input_grad": ([C.c_int, dp, dp, C.c_int, dp, dp, vp], st),
+        "smc2_mlp_adam_step": ([C.c_int, dp, dp, dp, dp, dp, dp, C.c_int, C.c_float, dp, vp], st),
         "smc2_destroy": ([ctx], None),
         "smc2_status_string": ([st], C.c_char_p),
         "smc2_last_error_string": ([], C.c_char_p),
@@ -141,6 +144,8 @@ def make_config(w, **over) -> Config:
     c.ppt = get("ppt", 0)
     c.cta_threads = get("cta_threads", 0)
     c.n_datasets = 0
+    c.mlp_h, c.mlp_lr = get("mlp_h", 0.0), get("mlp_lr", 0.0)
+    c.mlp_steps, c.mlp_window = get("mlp_steps", 0), get("mlp_window", 0)
     return c
 
 
@@ -312,6 +317,17 @@ def mlp_input_grad(params, x, stream=None):
     _check(lib.smc2_mlp_input_grad(D, _ptr(params), _ptr(x), R, _ptr(s), _ptr(dx),
                                    _stream_handle(stream)), "smc2_mlp_input_grad")
     return s, dx
+
+
+def mlp_adam_step(params, m, v, step, x, y, lr: float, stream=None):
+    """One gradient + Adam step in place on CUDA float32 tensors params, m, v and
+    the CUDA int32 step counter; returns the loss before the step (CUDA tensor)."""
+    import torch
+    R, D = x.shape
+    loss = torch.empty(1, dtype=torch.float32, device=params.device)
+    _check(lib.smc2_mlp_adam_step(D, _ptr(params), _ptr(m), _ptr(v), _ptr(step), _ptr(x), _ptr(y), R,
+                                  float(lr), _ptr(loss), _stream_handle(stream)), "smc2_mlp_adam_step")
+    return loss
 
 
 def resample_systematic(q, U: int, anc, stream=None):

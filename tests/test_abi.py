@@ -53,6 +53,9 @@ def _cfg(S, **over):
     {"N": 16385}, {"M": 0}, {"M": 4097}, {"T": 0}, {"K": 0}, {"rw_scale": 0.0},
     {"rw_scale": float("nan")}, {"ess_frac": -1.0}, {"ppt": 3}, {"cta_threads": 48},
     {"cta_threads": 1024}, {"ppt": 1, "M": 4096}, {"ppt": 4, "cta_threads": 64, "M": 1024},
+    # learned proposal: needs the Gaussian L-kernel; bounded training settings
+    {"proposal": 1, "lkernel": 0}, {"proposal": 1, "mlp_steps": 257}, {"proposal": 1, "mlp_window": 17},
+    {"proposal": 1, "mlp_h": -1.0}, {"mlp_lr": 1.5}, {"mlp_h": float("nan")}, {"mlp_steps": -1},
 ])
 def test_invalid_configs_rejected_before_gpu_work(S, over):
     import numpy as np
@@ -77,6 +80,32 @@ def test_invalid_prior_and_seir_constants(S):
         assert S.lib.smc2_init(C.byref(cfg), y.ctypes.data, None, C.byref(ctx)) == S.EINVAL
     assert S.lib.smc2_init(None, y.ctypes.data, None, C.byref(ctx)) == S.EINVAL
     assert S.lib.smc2_init(C.byref(cfg), None, None, C.byref(ctx)) == S.EINVAL
+
+
+def test_learned_proposal_needs_one_dataset(S):
+    import numpy as np
+    cfg = _cfg(S, proposal=1)
+    arrs = [np.array([64, 64], dtype=np.int32), np.array([32, 32], dtype=np.int32),
+            np.array([20, 20], dtype=np.int32)]
+    cfg.n_datasets = 2
+    cfg.ds_N, cfg.ds_M, cfg.ds_T = (a.ctypes.data_as(C.POINTER(C.c_int)) for a in arrs)
+    y = np.zeros(40)
+    ctx = C.c_void_p()
+    assert S.lib.smc2_init(C.byref(cfg), y.ctypes.data, None, C.byref(ctx)) == S.EINVAL
+    assert not ctx.value
+
+
+def test_surrogate_entry_points_reject_bad_arguments(S):
+    """Rejected on the host, before any device work: no buffer is touched."""
+    a16, a20 = 4096, 4100  # never dereferenced
+    assert S.lib.smc2_mlp_loss_grad(0, a16, a16, a16, 8, a16, a16, None) == S.EINVAL
+    assert S.lib.smc2_mlp_loss_grad(4, a16, a16, a16, 0, a16, a16, None) == S.EINVAL
+    assert S.lib.smc2_mlp_loss_grad(4, a20, a16, a16, 8, a16, a16, None) == S.EINVAL
+    assert S.lib.smc2_mlp_input_grad(9, a16, a16, 8, None, a16, None) == S.EINVAL
+    assert S.lib.smc2_mlp_input_grad(4, a20, a16, 8, None, a16, None) == S.EINVAL
+    assert S.lib.smc2_mlp_adam_step(4, a16, a16, a16, None, a16, a16, 8, 1e-3, a16, None) == S.EINVAL
+    assert S.lib.smc2_mlp_adam_step(4, a20, a16, a16, a16, a16, a16, 8, 1e-3, a16, None) == S.EINVAL
+    assert S.lib.smc2_mlp_adam_step(4, a16, a16, a16, a16, a16, a16, 8, 2.0, a16, None) == S.EINVAL
 
 
 def test_null_context_calls_rejected(S):

@@ -61,3 +61,45 @@ def test_input_gradient_against_oracle(S, D, R):
     print(f"D={D} R={R} s err {es:.3g}  dx rel norm {ed:.3g}")
     assert es < 2e-3   # one bf16 step of an h2 value moves s by up to |w3| 2^-8
     assert ed < 1e-3
+
+
+def weights_bf16(p, D, H=64):
+    """W1 [D][H], W2 [H][H] and w3 [H] rounded to bfloat16; b1, b2, b3 unchanged."""
+    q = np.array(p, dtype=np.float64)
+    blocks = [(0, D * H), (D * H + H, D * H + H + H * H), (D * H + 2 * H + H * H, D * H + 3 * H + H * H)]
+    for a, b in blocks:
+        q[a:b] = [O.bf16(v) for v in q[a:b]]
+    return q
+
+
+@pytest.mark.parametrize("D,R", [(4, 300), (3, 1000)])
+def test_adam_step_against_oracle(S, D, R):
+    """Three training steps as the sampler takes them.  Each step is checked
+    stage-wise from the device's own state: the loss and the moments m, v (both
+    linear in the gradient) against the oracle's bf16-point gradient at the
+    device parameters, then the parameter update against Adam's formula
+    evaluated in FP64 from the device moments."""
+    rng = np.random.default_rng(7 * D + R)
+    x = rng.standard_normal((R, D))
+    y = rng.standard_normal(R)
+    t = lambda a: torch.tensor(a, dtype=torch.float32, device="cuda")
+    params, xs, ys = t(bf16_params(D, R)), t(x), t(y)
+    m, v = torch.zeros_like(params), torch.zeros_like(params)
+    step = torch.zeros(1, dtype=torch.int32, device="cuda")
+    lr, b1, b2, eps = 1e-2, 0.9, 0.999, 1e-8
+    for it in range(1, 4):
+        p0, m0, v0 = (a.cpu().numpy().astype(np.float64) for a in (params, m, v))
+        loss = float(S.mlp_adam_step(params, m, v, step, xs, ys, lr).item())
+        assert int(step.item()) == it
+        # the kernels use the weights W1, W2, w3 rounded to bfloat16 and the biases as they are
+        loss_o, g_o = O.mlp_loss_grad(weights_bf16(p0, D), x, y, bf16_points=True)
+        p1, m1, v1 = (a.cpu().numpy().astype(np.float64) for a in (params, m, v))
+        scale = np.max(np.abs(g_o))
+        # moments: the gradient bar of the test above (5e-3 of the largest element)
+        assert abs(loss - loss_o) <= 1e-4 * abs(loss_o)
+        assert np.max(np.abs(m1 - (b1 * m0 + (1 - b1) * g_o))) <= (1 - b1) * 5e-3 * scale
+        assert np.max(np.abs(v1 - (b2 * v0 + (1 - b2) * g_o * g_o))) <= (1 - b2) * 1e-2 * scale * scale
+        # update from the device moments: FP32 arithmetic, relative 1e-5 of a step of size lr
+        c1, c2 = 1 - b1 ** it, 1 - b2 ** it
+        expect = p0 - lr * (m1 / c1) / (np.sqrt(v1 / c2) + eps)
+        assert np.max(np.abs(p1 - expect)) <= 1e-5 * lr + 4e-7 * np.max(np.abs(p0))

@@ -135,3 +135,56 @@ def test_nonfinite_outer_weights_reported(S):
     with pytest.raises(S.SMC2Error) as e:
         ctx.run(1)
     assert e.value.status == S.ENONFINITE
+
+
+def test_batched_datasets_match_oracle(S):
+    """Datasets of different N, M and T in one context: each follows its own
+    random stream (dataset index in the counter) and must equal the oracle's
+    single-dataset run of that dataset."""
+    shapes = [(64, 128, 50), (100, 64, 30), (33, 200, 45)]
+    ws = [I.workload("lg_t50_n64", N=n, M=m, T=t, K=4, dataset=d, data_seed=10 + d)
+          for d, (n, m, t) in enumerate(shapes)]
+    y = np.concatenate([w.y for w in ws])
+    ctx = S.SMC2(S.make_config(ws[0]), y, datasets=shapes)
+    stats = ctx.run(4)
+    for d, w in enumerate(ws):
+        ref = O.SMC2(O.config_from(w), w.y).run(w.K)
+        scale = max(10.0, float(np.max(np.abs(ref.logw[np.isfinite(ref.logw)]))))
+        for k in range(w.K):
+            assert stats[k][d]["dataset"] == d
+            _compare_stats(stats[k][d], ref.stats[k], scale)
+        k, th, lp, ll, lw = ctx.get_state(d)
+        assert k == ref.k
+        assert rel_err(th, ref.theta, 1.0) < 1e-10
+        assert rel_err(ll, ref.loglik, scale) < 1e-12
+        assert rel_err(lw, ref.logw, scale) < 1e-12
+        mean, logz, ess_sum = ctx.estimate(d)
+        ref_mean, _ = ref.recycled()
+        assert rel_err(mean, ref_mean, 1.0) < 1e-9
+    ctx.close()
+
+
+def test_batched_seir_mixed_runs(S):
+    """Sixty-four SEIR-type datasets of uneven T, N and M in one mixed-precision
+    context: every dataset's statistics are finite, and dataset 0 (whose random
+    stream is that of a single-dataset context) equals a context holding it
+    alone, bit for bit, at the same launch shape."""
+    ws = I.batched_workloads(64, K=3)
+    shapes = [(w.N, w.M, w.T) for w in ws]
+    shape = dict(ppt=4, cta_threads=256)
+    ctx = S.SMC2(S.make_config(ws[0], **shape), np.concatenate([w.y for w in ws]), datasets=shapes)
+    stats = ctx.run(3)
+    for k in range(3):
+        for d in range(64):
+            s = stats[k][d]
+            assert s["dataset"] == d and s["k"] == k + 1
+            assert math.isfinite(s["lse"]) and s["ess"] >= 1.0 and np.all(np.isfinite(s["est"]))
+    w = ws[0]
+    single = S.SMC2(S.make_config(w, **shape), w.y)
+    alone = single.run(3)
+    for k in range(3):
+        for key in ("ess", "lse", "lse2", "logz", "resampled"):
+            assert alone[k][0][key] == stats[k][0][key], (k, key)
+        assert np.array_equal(alone[k][0]["est"], stats[k][0]["est"])
+    single.close()
+    ctx.close()
