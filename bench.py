@@ -35,7 +35,7 @@ ALG_OPS_PER_PARTICLE_STEP = {
 # DRAM bytes per particle-filter launch from one ncu capture of the SEIR-type
 # workload (profiles/pf_kernel_seir_t100_n1024.md), valid only for the kernel
 # source it was taken on (sha-256 prefixes of pf_impl.cuh and common.cuh).
-PF_TRAFFIC = {"bytes": 98560.0, "sources": {"pf_impl.cuh": "6ccc98f0284631fa", "common.cuh": "ae3e5d1cb62ab831"}}
+PF_TRAFFIC = {"bytes": 105728.0, "sources": {"pf_impl.cuh": "e8be6bdccedc6336", "common.cuh": "f87195a138ed91c4"}}
 
 
 def parse():
@@ -47,6 +47,8 @@ def parse():
     p.add_argument("--workload", default="seir_t100_n1024")
     p.add_argument("--no-fp64-form", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-forms", action="store_true",
+                   help="skip the accuracy comparison of the random-walk, FP64 and learned forms")
     p.add_argument("--ppt", type=int, default=0, help="pin particles per thread (0: tuner)")
     p.add_argument("--cta", type=int, default=0, help="pin threads per PF CTA (0: tuner)")
     return p.parse_args()
@@ -221,6 +223,53 @@ def time_runs(S, torch, ctx, w, steps, warmup, flush, rank_sync):
     return ms, ess_sums, pf_ms, pf_n, launches, wall
 
 
+def accuracy_forms(S, torch, I, wr, world, seeds=8):
+    """Posterior accuracy per unit time of three forms of the SMC^2 step on the
+    same data: mixed precision with the random walk, the plain FP64 GPU form,
+    and mixed precision with the learned proposal.  Accuracy is the mean
+    squared error over `seeds` runs of the recycled posterior mean against a
+    reference pooled from four random-walk runs with 8x the samples; mse x
+    time is inversely proportional to accuracy per second."""
+    import numpy as np
+
+    def runs(w, seed_list, **over):
+        ctx = S.SMC2(S.make_config(w, **over), w.y)
+        ctx.run(w.K, stats=False)
+        stream = torch.cuda.current_stream()
+        out = []
+        for sd in seed_list:
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ctx.reset(sd)
+            a.record(stream)
+            ctx.run(w.K, stats=False)
+            b.record(stream)
+            mean, _, ess = ctx.estimate()
+            out.append((mean, ess, a.elapsed_time(b)))
+        ctx.close()
+        return out
+
+    base = 10_000 * (1 + wr.seed)
+    ref = runs(wr.with_(N=8 * wr.N, ppt=0, cta_threads=0), [base + i for i in range(4)], rw_scale=0.2)
+    ref_mean = np.mean([r[0] for r in ref], axis=0)
+    forms = {"mixed_rw": wr.with_(ppt=0, cta_threads=0),
+             "fp64_rw": wr.with_(precision=I.PREC_FP64, ppt=0, cta_threads=0),
+             "mixed_learned": wr.with_(proposal=I.PROP_MLP, ppt=0, cta_threads=0)}
+    res = {}
+    for name, wf in forms.items():
+        r = runs(wf, [base + 100 + i for i in range(seeds)])
+        means = np.array([x[0] for x in r])
+        mse = ((means - ref_mean) ** 2).mean(axis=0)
+        ms = float(np.mean([x[2] for x in r]))
+        res[name] = {"ms_per_run": ms, "ess_per_s": float(np.mean([x[1] for x in r])) * world / (ms * 1e-3),
+                     "rmse": [float(v) for v in np.sqrt(mse)], "mse_x_s": float(mse.mean() * ms * 1e-3)}
+    for name in ("fp64_rw", "mixed_learned"):
+        res[name]["accuracy_per_s_vs_mixed_rw"] = res["mixed_rw"]["mse_x_s"] / res[name]["mse_x_s"]
+    res["mixed_learned"]["accuracy_per_s_vs_fp64_rw"] = res["fp64_rw"]["mse_x_s"] / res["mixed_learned"]["mse_x_s"]
+    res["mixed_learned"]["ess_per_s_vs_fp64_rw"] = res["mixed_learned"]["ess_per_s"] / res["fp64_rw"]["ess_per_s"]
+    res["reference"] = {"runs": 4, "N": 8 * wr.N, "rw_scale": 0.2, "seeds_per_form": seeds}
+    return res
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -300,6 +349,10 @@ def main():
                 "ess_per_s": statistics.mean(ess64) * world / (st64 * 1e-3), "ms_per_step": st64}
         ctx64.close()
 
+    forms = None
+    if not args.no_forms and wr.model == I.SEIR and wr.D <= 8:
+        forms = accuracy_forms(S, torch, I, wr, world)
+
     if rank != 0:
         return
     peaks = measured_peaks()
@@ -317,6 +370,7 @@ def main():
         "fp64_form": fp64,
         "speedup_vs_fp64_form": (value / fp64["value"]) if fp64 else None,
         "ess_speedup_vs_fp64_form": (ess_per_s / fp64["ess_per_s"]) if fp64 else None,
+        "forms": forms,
         "roofline": {"kernel": "pf_kernel<float,SEIR>", "bound": "alu", "achieved": achieved / 1e9,
                      "peak": peak / 1e9, "unit": "Gop/s", "frac": achieved / peak,
                      "traffic": pf_traffic_if_current() if wr.model == 1 else None,

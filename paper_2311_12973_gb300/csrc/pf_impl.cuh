@@ -6,15 +6,20 @@
 //   2. log-weight with the observation density (Eq. 2; bootstrap form of Eq. 5);
 //   3. group max of the log-weights (warp shuffles, one barrier);
 //   4. quantise q_j = floor(exp(l_j - max) 2^B), warp-local inclusive scan of q
-//      in registers + shuffles, warp totals and particle states to shared memory
-//      (second barrier);
+//      in registers + shuffles, warp totals to shared memory (second barrier);
 //   5. log-likelihood increment log((1/M) sum_j w_j) = max + log(S 2^-B) - log M
 //      from the exact integer total S (Eq. 8, with the mean-weight reset of
 //      Eq. 13 every step);
 //   6. systematic resampling (Eqs. 26-27): slot j takes the first particle whose
-//      cumulative weight exceeds floor((j + u) S / M), found by a search over
-//      the warp totals and then a binary search inside one warp's prefix;
-//      the slot's new state is gathered from shared memory.
+//      cumulative weight exceeds tau_j = floor((j + u) S / M).  Equivalently
+//      particle i fills the slots F(C_{i-1}) .. F(C_i) - 1, F(C) being the
+//      number of thresholds below C; each thread computes F at its particles'
+//      cumulative weights (a float estimate, settled by an exact 128-bit
+//      comparison near integers).  A warp's particles fill one contiguous run
+//      of slots, which the warp copies 32 slots at a time (each lane finds its
+//      slot's particle by a shuffle search over the lanes' ranges), and after
+//      a third barrier every thread reads the states of its own slots.
+//      (Staged variants keep the prefix in shared memory and search it instead.)
 // A work unit is `count` filters of one job (dataset); units are taken from an
 // atomic queue so that jobs of uneven length balance over the SMs.
 // With 8 or more particles per thread ("staged"), the log-weights and the
@@ -61,15 +66,16 @@ __host__ __device__ inline int group_threads_for(int ppt, int M) {
 }
 
 // Shared memory of one filter group (Mp = particles incl. padding, nw warps):
-//   P  u64 [Mp]      warp-local inclusive prefix of the quantised weights
-//   X  R   [Mp][ns]  particle states, one vector per particle
+//   P  u64 [Mp]      warp-local inclusive prefix of the quantised weights (staged only)
+//   X  R   [Mp][ns]  particle states, one vector per particle (per slot after resampling)
+//   Xo R   [Mp][ns]  states before resampling, by particle (register-resident variants)
 //   Z  R   [4][Mp]   the four normals of the current Philox counter of every particle
 //   L  R   [Mp]      log-weights (staged path only)
 //   wsum u64 [nw], wmax 8 B [nw], sU u32 [8] (resampling words of two groups of four steps)
 __host__ __device__ constexpr bool is_staged(int ppt) { return ppt >= 8; }
 __host__ __device__ inline size_t region_bytes(int Mp, int nw, int ns, int rsize, bool staged) {
-  size_t b = (size_t)Mp * 8 + (size_t)ns * Mp * rsize + (size_t)4 * Mp * rsize + (size_t)nw * 16 + 32;
-  if (staged) b += (size_t)Mp * rsize;
+  size_t b = (size_t)(staged ? 1 : 2) * ns * Mp * rsize + (size_t)4 * Mp * rsize + (size_t)nw * 16 + 32;
+  if (staged) b += (size_t)Mp * 8 + (size_t)Mp * rsize;
   return (b + 15) & ~(size_t)15;
 }
 
@@ -78,7 +84,7 @@ __host__ __device__ inline size_t region_bytes(int Mp, int nw, int ns, int rsize
 template <typename R, int PPT>
 struct RegCap {
   static constexpr int value =
-      sizeof(R) == 4 ? (PPT <= 2 ? 64 : (PPT == 4 ? 80 : (PPT == 8 ? 128 : 168)))
+      sizeof(R) == 4 ? (PPT <= 2 ? 64 : (PPT == 4 ? 96 : (PPT == 8 ? 128 : 168)))
                      : (PPT == 1 ? 80 : (PPT == 2 ? 96 : (PPT <= 8 ? 128 : 168)));
   static_assert(PPT == 1 || PPT == 2 || PPT == 4 || PPT == 8 || PPT == 16, "particles per thread");
 };
@@ -132,6 +138,53 @@ __device__ __forceinline__ double neg_inf<double>() {
 
 __device__ __forceinline__ uint64_t to_u64_rz(float v) { return __float2ull_rz(v); }
 __device__ __forceinline__ uint64_t to_u64_rz(double v) { return __double2ull_rz(v); }
+
+// u64 to float from its two 32-bit halves (relative error below 2^-23).
+__device__ __forceinline__ float u64_to_float(uint64_t v) {
+  return fmaf(__uint2float_rn((uint32_t)(v >> 32)), 0x1p32f, __uint2float_rn((uint32_t)v));
+}
+
+// Counting slot thresholds of systematic resampling (Eqs. 26-27) below a
+// cumulative weight C: tau_j = floor((2^33 j + 2U + 1) S / (M 2^33)) < C holds
+// exactly when (2^33 j + 2U + 1) S < C M 2^33 (both sides below 2^110).
+struct SlotCount {
+  uint64_t S, M33, U21;  // total, M 2^33, 2U + 1
+  float scale, off;      // M / S and (2U + 1) 2^-33 for the float estimate
+  float margin;          // bound on the error of the estimate
+  int M;
+};
+__device__ __forceinline__ SlotCount slot_count_setup(uint32_t U, uint64_t S, int M) {
+  SlotCount sc;
+  sc.S = S;
+  sc.M33 = (uint64_t)M << 33;
+  sc.U21 = 2ull * U + 1ull;
+  sc.scale = __fdividef((float)M, u64_to_float(S));
+  sc.off = fmaf(2.f, (float)U, 1.f) * 0x1p-33f;
+  sc.margin = fmaf((float)M, 0x1p-18f, 0x1p-16f);
+  sc.M = M;
+  return sc;
+}
+// F(C) = #{j in [0, M): tau_j < C} = ceil(C M / S - (2U+1) 2^-33) clamped to
+// [0, M].  The crossing point is estimated in float: Cf approximates C to
+// about 2^-22 relative, so the estimate is within M 2^-19 of it, inside
+// `margin`.  Away from an integer the estimate's ceiling is F; within the
+// margin of an integer n (clamped to [0, M - 1]), F is n or n + 1 and one exact
+// comparison, tau_n < C, says which.
+__device__ __forceinline__ int slots_below(const SlotCount& sc, uint64_t C, float Cf) {
+  const float est = fmaf(Cf, sc.scale, -sc.off);
+  const float nf = rintf(est);
+  int n;
+  if (fabsf(est - nf) > sc.margin) {
+    n = (int)nf + (est > nf ? 1 : 0);
+  } else {
+    n = min(max((int)nf, 0), sc.M - 1);
+    const uint64_t a = ((uint64_t)n << 33) + sc.U21;
+    const uint64_t lh = __umul64hi(a, sc.S), ll = a * sc.S;
+    const uint64_t rh = __umul64hi(C, sc.M33), rl = C * sc.M33;
+    n += (lh < rh || (lh == rh && ll < rl)) ? 1 : 0;
+  }
+  return min(max(n, 0), sc.M);
+}
 
 // exp in the working precision: the FP32 path uses the hardware exp2
 // approximation (relative error about 2^-22), the FP64 path the full-precision exp.
@@ -240,14 +293,15 @@ __device__ __forceinline__ void run_filter(const PFJob& J, const PFModel& mdl, i
   const int lane = lt & 31, warp = lt >> 5;
   const int seg = 32 * PPT;  // particles per warp
 
-  uint64_t* P = reinterpret_cast<uint64_t*>(region);   // [Mp] warp-local inclusive prefix of q
-  R* X = reinterpret_cast<R*>(P + Mp);                  // [Mp][NS] particle states
-  R* Z = X + (size_t)NS * Mp;                           // [4][Mp] cached normals
+  constexpr bool STAGED = is_staged(PPT);
+  uint64_t* P = reinterpret_cast<uint64_t*>(region);   // [Mp] warp-local inclusive prefix of q (staged)
+  R* X = reinterpret_cast<R*>(P + (STAGED ? Mp : 0));  // [Mp][NS] particle states
+  R* Xo = X + (size_t)NS * Mp;                          // [Mp][NS] states by particle (not staged)
+  R* Z = X + (size_t)NS * Mp * (STAGED ? 1 : 2);       // [4][Mp] cached normals
   uint64_t* wsum = reinterpret_cast<uint64_t*>(Z + (size_t)4 * Mp);  // [nw] warp totals
   R* wmax = reinterpret_cast<R*>(wsum + nw);            // [nw] warp maxima (8-byte slots)
   uint32_t* sU = reinterpret_cast<uint32_t*>(wsum + 2 * nw);  // [8] resampling words
   R* Lw = reinterpret_cast<R*>(reinterpret_cast<unsigned char*>(sU) + 32);  // [Mp] staged log-weights
-  constexpr bool STAGED = is_staged(PPT);
 
   auto group_sync = [&]() {
     if (nw == 1)
@@ -316,10 +370,12 @@ __device__ __forceinline__ void run_filter(const PFJob& J, const PFModel& mdl, i
         l = fp.log_pois(lam, ob);
       }
       if (isnan(l) || lt * PPT + r >= M) l = neg_inf<R>();
-      if constexpr (STAGED)
+      if constexpr (STAGED) {
         Lw[lt * PPT + r] = l;
-      else
+      } else {
         ell[r] = l;
+        StateVec<R, NS>::store(Xo, lt * PPT + r, x[r]);
+      }
       lmax = fmax(lmax, l);
     }
     // (3) group maximum
@@ -346,30 +402,37 @@ __device__ __forceinline__ void run_filter(const PFJob& J, const PFModel& mdl, i
         StateVec<R, NS>::store(X, lt * PPT + r, x[r]);
       }
     }
-    uint64_t c[STAGED ? 1 : PPT];
+    uint64_t c[STAGED ? 1 : PPT];  // thread-local inclusive prefix of q
+    float cf[STAGED ? 1 : PPT];     // the same from the unfloored values, in float
     if constexpr (!STAGED) {
+      float runf = 0.f;
 #pragma unroll
       for (int r = 0; r < PPT; ++r) {
-        const uint64_t qv = (ell[r] > neg_inf<R>()) ? to_u64_rz(fast_exp(ell[r] - m) * scaleB) : 0ull;
-        run += qv;
+        const R v = (ell[r] > neg_inf<R>()) ? fast_exp(ell[r] - m) * scaleB : (R)0;
+        run += to_u64_rz(v);
+        runf += (float)v;
         c[r] = run;
+        cf[r] = runf;
       }
     }
     const uint64_t incl = warp_incl_scan_u64(run, lane);
     const uint64_t excl = incl - run;
+    if constexpr (STAGED) {
 #pragma unroll
-    for (int r = 0; r < PPT; ++r) {
-      if constexpr (STAGED) {
-        P[lt * PPT + r] += excl;
-      } else {
-        P[lt * PPT + r] = excl + c[r];
-        StateVec<R, NS>::store(X, lt * PPT + r, x[r]);
-      }
+      for (int r = 0; r < PPT; ++r) P[lt * PPT + r] += excl;
     }
     if (lane == 31) wsum[warp] = incl;
     group_sync();
-    uint64_t S = 0;
-    for (int w = 0; w < nw; ++w) S += wsum[w];
+    // total S, and the weight `base` of the warps before this one: an inclusive
+    // scan of the warp totals across the lanes
+    uint64_t wpre = lane < nw ? wsum[lane] : 0ull;
+    for (int o = 1; o < nw; o <<= 1) {
+      const uint64_t n = __shfl_up_sync(0xffffffffu, wpre, o);
+      if (lane >= o) wpre += n;
+    }
+    const uint64_t S = __shfl_sync(0xffffffffu, wpre, nw - 1);
+    const uint64_t base_incl = __shfl_sync(0xffffffffu, wpre, warp > 0 ? warp - 1 : 0);
+    const uint64_t base = warp > 0 ? base_incl : 0ull;
     // (5) log-likelihood increment: log S from its binary exponent and mantissa
     if (lt == 0) {
       const int e = 63 - __clzll((long long)S);
@@ -382,7 +445,45 @@ __device__ __forceinline__ void run_filter(const PFJob& J, const PFModel& mdl, i
     // consecutive and their ancestors non-decreasing: the first is found by a
     // search over the warp totals and a binary search inside one warp's prefix,
     // the others by galloping forward from the previous ancestor.
-    if (t < T) {
+    if (!STAGED && t < T) {
+      const SlotCount sc = slot_count_setup(sUg[tm], S, M);
+      const uint64_t C0 = base + excl;  // cumulative weight before the thread's first particle
+      const float C0f = u64_to_float(C0);
+      int ends[PPT];
+#pragma unroll
+      for (int r = 0; r < PPT; ++r) ends[r] = slots_below(sc, C0 + c[r], C0f + cf[r]);
+      // the warp's particles fill the slots [first, last), in particle order
+      const int first = __shfl_sync(0xffffffffu, slots_below(sc, C0, C0f), 0);
+      const int last = __shfl_sync(0xffffffffu, ends[PPT - 1], 31);
+      const int pbase = warp * 32 * PPT;  // the warp's first particle
+      __syncwarp();                       // the warp's states in Xo
+      for (int j0 = first; j0 < last; j0 += 32) {
+        const int j = j0 + lane;
+        // the lane whose particles cover slot j: the lanes whose ranges end at or before j
+        int src = 0;
+#pragma unroll
+        for (int step = 16; step >= 1; step >>= 1) {
+          const int e = __shfl_sync(0xffffffffu, ends[PPT - 1], src + step - 1);
+          if (e <= j) src += step;
+        }
+        src = min(src, 31);
+        int rr = 0;
+#pragma unroll
+        for (int r = 0; r < PPT - 1; ++r) rr += __shfl_sync(0xffffffffu, ends[r], src) <= j ? 1 : 0;
+        if (j < last) {
+          const int a = pbase + src * PPT + rr;
+          R v[NS];
+          StateVec<R, NS>::load(Xo, a, v);
+          StateVec<R, NS>::store(X, j, v);
+          if (J.anc) J.anc[((size_t)i * (T - 1) + (t - 1)) * M + j] = a;
+        }
+      }
+      group_sync();
+#pragma unroll
+      for (int r = 0; r < PPT; ++r)
+        if (lt * PPT + r < M) StateVec<R, NS>::load(X, lt * PPT + r, x[r]);
+    }
+    if (STAGED && t < T) {
       const uint32_t U = sUg[tm];
       int w = 0, a = 0;
       uint64_t base = 0;
