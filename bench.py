@@ -61,6 +61,27 @@ def dist_env():
     return rank, world, local
 
 
+def replica_workload(w, rank: int, ppt: int = 0, cta: int = 0):
+    """Rank `rank`'s independent replica of the workload: same data, own seed."""
+    return w.with_(seed=w.seed + 1000 * rank, ppt=ppt, cta_threads=cta)
+
+
+def reduce_max(x: float, dist=None, device: str = "cpu") -> float:
+    """The largest value over the ranks of the default process group (x itself
+    without one): the job's step time is that of its slowest replica."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_replica_step: float, world: int, step_ms_max: float) -> float:
+    """Whole-job units per second: every replica's units over the slowest step."""
+    return units_per_replica_step * world / (step_ms_max * 1e-3)
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
 
@@ -290,19 +311,15 @@ def main():
         if dist is not None:
             dist.barrier()
 
-    def reduce_max(x: float) -> float:
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    def reduce_max_gpu(x: float) -> float:
+        return reduce_max(x, dist, "cuda")
 
     from paper_2311_12973_gb300 import build as B
     B.build()
     from paper_2311_12973_gb300 import smc2 as S
 
     # each rank runs an independent replica (its own seed): weak scaling
-    wr = w.with_(seed=w.seed + 1000 * rank, ppt=args.ppt, cta_threads=args.cta)
+    wr = replica_workload(w, rank, args.ppt, args.cta)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     ctx = S.SMC2(S.make_config(wr), wr.y)
     shape = ctx.launch_shape()
@@ -312,9 +329,9 @@ def main():
         ms, ess_sums, pf_ms, pf_n, launches, wall = time_runs(S, torch, ctx, wr, args.steps, args.warmup,
                                                               flush, rank_sync)
     clocks = clk.summary()
-    step_ms = reduce_max(sum(ms) / len(ms))
+    step_ms = reduce_max_gpu(sum(ms) / len(ms))
     units_per_step = wr.N * wr.M * wr.T * wr.K
-    value = units_per_step * world / (step_ms * 1e-3)
+    value = job_throughput(units_per_step, world, step_ms)
     ess_per_s = statistics.mean(ess_sums) * world / (step_ms * 1e-3)
 
     # end to end through the C ABI with host buffers
@@ -334,7 +351,7 @@ def main():
         b.synchronize()
         if s >= args.warmup:
             e2e_ms.append(a.elapsed_time(b))
-    e2e_step = reduce_max(sum(e2e_ms) / len(e2e_ms))
+    e2e_step = reduce_max_gpu(sum(e2e_ms) / len(e2e_ms))
     d2h = 8 * wr.D + 112 + 8 + 4
 
     # plain FP64 GPU form of the same workload
@@ -344,7 +361,7 @@ def main():
         ctx64 = S.SMC2(S.make_config(w64), w64.y)
         ms64, ess64, _, _, _, _ = time_runs(S, torch, ctx64, w64, max(2, args.steps // 3), 1, flush,
                                             rank_sync)
-        st64 = reduce_max(sum(ms64) / len(ms64))
+        st64 = reduce_max_gpu(sum(ms64) / len(ms64))
         fp64 = {"value": units_per_step * world / (st64 * 1e-3), "unit": UNIT,
                 "ess_per_s": statistics.mean(ess64) * world / (st64 * 1e-3), "ms_per_step": st64}
         ctx64.close()

@@ -207,6 +207,24 @@ smc2_status smc2_estimate(smc2_ctx* ctx, int dataset, double* mean_host,
 smc2_status smc2_get_history(smc2_ctx* ctx, int dataset, smc2_iter_stats* hist_host, int cap,
                              int* k_out);
 
+/* The proposals theta_k of the latest iteration (host, row-major [N][D]) and
+ * log q(theta_k | theta_{k-1}) (host, N; the prior's log density at k = 1),
+ * the terms of Eq. (20) that the proposal contributes.  Either pointer may
+ * be NULL.  Synchronises.  Errors: EINVAL (bad dataset). */
+smc2_status smc2_get_proposals(smc2_ctx* ctx, int dataset, double* theta_host, double* logq_host);
+
+/* The learned proposal's state that the next iteration uses
+ * (proposal = SMC2_PROP_MLP, dataset 0): params_host (FP32, the layout of
+ * smc2_mlp_loss_grad: 64 D + 4289 values), stdz_host (FP64, 2 D + 5 values:
+ * input means mu[D], input sds sd[D], tau, zmean, zsd, target variance,
+ * training loss; the score is d log pi^ / d theta_d = tau zsd (ds/dx)_d /
+ * sd_d at x_d = (theta_d - mu_d) / sd_d), L_host (FP64, row-major D x D lower
+ * Cholesky factor of the weighted population covariance) and *pop_ok (the
+ * factor is usable).  Any pointer may be NULL.  Synchronises.  Errors:
+ * EINVAL (no learned proposal in this context). */
+smc2_status smc2_get_learned_state(smc2_ctx* ctx, float* params_host, double* stdz_host, double* L_host,
+                                   int* pop_ok);
+
 /* Checkpoint / resume of a dataset's population after iteration k: theta
  * (host, row-major [N][D]), log prior, PF log-likelihood estimate and
  * unnormalised log weight (host, N each).  get synchronises; set is

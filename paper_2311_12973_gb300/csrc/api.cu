@@ -760,6 +760,52 @@ smc2_status smc2_get_state(smc2_ctx* c, int dataset, int* k_out, double* theta, 
   return st;
 }
 
+smc2_status smc2_get_proposals(smc2_ctx* c, int dataset, double* theta, double* logq) {
+  if (bad_ds(c, dataset)) return SMC2_EINVAL;
+  const DSDev& s = c->h_ds[dataset];
+  const int N = s.N, D = c->D;
+  std::vector<double> soa((size_t)D * N);
+  if (theta)
+    SMC2_TRY(cudaMemcpyAsync(soa.data(), s.thB, soa.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  if (logq) SMC2_TRY(cudaMemcpyAsync(logq, s.logq, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  const smc2_status st = sticky(c);
+  if (theta)
+    for (int i = 0; i < N; ++i)
+      for (int d = 0; d < D; ++d) theta[(size_t)i * D + d] = soa[(size_t)d * N + i];
+  return st;
+}
+
+smc2_status smc2_get_learned_state(smc2_ctx* c, float* params, double* stdz, double* L, int* pop_ok) {
+  if (!c || !c->mlp.on) return SMC2_EINVAL;
+  const int D = c->D;
+  MlpNorm nm{};
+  float loss = 0.f;
+  IterCur cur{};
+  if (params)
+    SMC2_TRY(cudaMemcpyAsync(params, c->mlp.p_use, (size_t)mlp_param_count(D) * sizeof(float),
+                             cudaMemcpyDeviceToHost, c->stream));
+  SMC2_TRY(cudaMemcpyAsync(&nm, c->mlp.norm_use, sizeof(MlpNorm), cudaMemcpyDeviceToHost, c->stream));
+  SMC2_TRY(cudaMemcpyAsync(&loss, c->mlp.loss_use, sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+  SMC2_TRY(cudaMemcpyAsync(&cur, c->h_ds[0].cur, sizeof(IterCur), cudaMemcpyDeviceToHost, c->stream));
+  const smc2_status st = sticky(c);
+  if (stdz) {
+    for (int d = 0; d < D; ++d) {
+      stdz[d] = nm.mu[d];
+      stdz[D + d] = nm.sd[d];
+    }
+    stdz[2 * D] = nm.tau;
+    stdz[2 * D + 1] = nm.zmean;
+    stdz[2 * D + 2] = nm.zsd;
+    stdz[2 * D + 3] = nm.var_y;
+    stdz[2 * D + 4] = loss;
+  }
+  if (L)
+    for (int d = 0; d < D; ++d)
+      for (int f = 0; f < D; ++f) L[d * D + f] = cur.Lpop[d * kMaxD + f];
+  if (pop_ok) *pop_ok = cur.pop_ok;
+  return st;
+}
+
 smc2_status smc2_set_state(smc2_ctx* c, int dataset, int k, const double* theta, const double* lp,
                            const double* ll, const double* lw) {
   if (bad_ds(c, dataset) || !theta || !lp || !ll || !lw || k < 0 || k > c->K) return SMC2_EINVAL;

@@ -90,6 +90,8 @@ def _load() -> C.CDLL:
         "smc2_mlp_loss_grad": ([C.c_int, dp, dp, dp, C.c_int, dp, dp, vp], st),
         "smc2_mlp_input_grad": ([C.c_int, dp, dp, C.c_int, dp, dp, vp], st),
         "smc2_mlp_adam_step": ([C.c_int, dp, dp, dp, dp, dp, dp, C.c_int, C.c_float, dp, vp], st),
+        "smc2_get_proposals": ([ctx, C.c_int, dp, dp], st),
+        "smc2_get_learned_state": ([ctx, dp, dp, dp, C.POINTER(C.c_int)], st),
         "smc2_destroy": ([ctx], None),
         "smc2_status_string": ([st], C.c_char_p),
         "smc2_last_error_string": ([], C.c_char_p),
@@ -234,6 +236,27 @@ class SMC2:
         arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (theta, logprior, loglik, logw)]
         _check(lib.smc2_set_state(self._ctx, dataset, int(k), *(a.ctypes.data for a in arrs)),
                "smc2_set_state")
+
+    def proposals(self, dataset: int = 0):
+        """theta_k of the latest iteration [N][D] and log q(theta_k | theta_{k-1}) [N]."""
+        N = self.Ns[dataset]
+        th, lq = np.zeros((N, self.D)), np.zeros(N)
+        _check(lib.smc2_get_proposals(self._ctx, dataset, th.ctypes.data, lq.ctypes.data), "smc2_get_proposals")
+        return th, lq
+
+    def learned_state(self):
+        """The learned proposal's published network and standardisation, and the
+        population Cholesky factor the next iteration proposes with."""
+        D = self.D
+        params = np.zeros(64 * D + 4289, dtype=np.float32)
+        stdz = np.zeros(2 * D + 5)
+        L = np.zeros((D, D))
+        ok = C.c_int()
+        _check(lib.smc2_get_learned_state(self._ctx, params.ctypes.data, stdz.ctypes.data, L.ctypes.data,
+                                          C.byref(ok)), "smc2_get_learned_state")
+        return {"params": params, "mu": stdz[:D].copy(), "sd": stdz[D:2 * D].copy(), "tau": stdz[2 * D],
+                "zmean": stdz[2 * D + 1], "zsd": stdz[2 * D + 2], "var_y": stdz[2 * D + 3],
+                "loss": stdz[2 * D + 4], "L": L, "pop_ok": bool(ok.value)}
 
     def reset(self, seed: int):
         _check(lib.smc2_reset(self._ctx, int(seed)), "smc2_reset")
