@@ -295,11 +295,14 @@ smc2_status smc2_pf_loglik_noalloc(const smc2_config* cfg, const double* y_dev,
  * pointer, params_dev not 16-byte aligned).
  * smc2_mlp_input_grad: s(x_r) into s_dev [R] (may be NULL) and ds/dx into
  * dx_dev [R][D].
- * smc2_mlp_adam_step: one training step as the sampler takes it: the
- * gradient of L at params_dev, then Adam (beta1 = 0.9, beta2 = 0.999,
- * eps = 1e-8, bias-corrected) with learning rate lr at step t = *step_dev + 1
- * (device int, advanced in place), updating params_dev, m_dev, v_dev (device
- * FP32, one value per parameter); *loss_dev receives L before the update. */
+ * smc2_mlp_adam_step: one training step as the sampler takes it (the same
+ * kernel, a thread-block cluster whose CTAs split the rows and reduce their
+ * partial gradients over distributed shared memory): the gradient of L at
+ * params_dev, then Adam (beta1 = 0.9, beta2 = 0.999, eps = 1e-8,
+ * bias-corrected) with learning rate lr at step t = *step_dev + 1 (device
+ * int, advanced in place), updating params_dev, m_dev, v_dev (device FP32, one
+ * value per parameter); *loss_dev receives L before the update.  Allocates
+ * nothing. */
 smc2_status smc2_mlp_loss_grad(int D, const float* params_dev, const float* x_dev, const float* y_dev,
                                int R, float* grad_dev, float* loss_dev, void* stream);
 smc2_status smc2_mlp_input_grad(int D, const float* params_dev, const float* x_dev, int R,

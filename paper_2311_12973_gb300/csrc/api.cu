@@ -228,7 +228,6 @@ size_t layout(smc2_ctx* c, char* base) {
     M.ys = carve<float>(p, rows);
     M.norm = carve<MlpNorm>(p, 1);
     M.score = carve<double>(p, (size_t)D * N0);
-    M.part = carve<float>(p, (size_t)mlp_grad_ctas((int)rows) * (P + 1));
   }
   c->d_ds = carve<DSDev>(p, c->n_ds);
   c->d_jobs = carve<PFJob>(p, c->n_ds);
@@ -462,7 +461,7 @@ smc2_status enqueue_iteration(smc2_ctx* c, cudaStream_t s, cudaEvent_t ev0, cuda
 }
 
 int launches_per_iteration(const smc2_ctx* c) {
-  return 6 + (c->mlp.on ? 4 + 2 * c->cfg.mlp_steps : 0);
+  return 6 + (c->mlp.on ? 4 : 0);  // score, publish, append, training
 }
 
 
@@ -871,14 +870,9 @@ smc2_status smc2_mlp_adam_step(int D, float* params, float* m, float* v, int* st
   if (D < 1 || D > kMlpMaxD || R < 1 || !params || !m || !v || !step || !x || !y || !loss ||
       !(lr >= 0.f && lr < 1.f))
     return SMC2_EINVAL;
-  if (reinterpret_cast<uintptr_t>(params) % 16 != 0) return SMC2_EINVAL;  // read as float4
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  float* part = nullptr;
-  SMC2_TRY(cudaMallocAsync(reinterpret_cast<void**>(&part),
-                           (size_t)mlp_grad_ctas(R) * (mlp_param_count(D) + 1) * sizeof(float), s));
-  const cudaError_t e = mlp_step_launch(params, D, x, y, R, nullptr, part, nullptr, loss, 1, m, v, step, lr, s);
-  cudaFreeAsync(part, s);
-  SMC2_TRY(e);
+  if (reinterpret_cast<uintptr_t>(params) % 16 != 0) return SMC2_EINVAL;  // the documented layout
+  SMC2_TRY(mlp_train_steps_launch(params, m, v, step, const_cast<float*>(x), const_cast<float*>(y), R, nullptr,
+                                  loss, D, 1, lr, static_cast<cudaStream_t>(stream)));
   return SMC2_OK;
 }
 

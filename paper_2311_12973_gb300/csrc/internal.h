@@ -74,7 +74,6 @@ struct MlpDev {
   MlpNorm* norm_use;
   float* loss_use;
   double* score;        // [D][N] grad log pi^ at the parents (surrogate)
-  float* part;          // [ctas][params + 1] partial gradients
 };
 
 struct DSDev {
@@ -172,6 +171,11 @@ size_t mlp_grad_smem_bytes();
 cudaError_t mlp_step_launch(float* p, int D, const float* x, const float* y, int R, const int* R_dev,
                             float* part, float* grad, float* loss, int adam, float* m, float* v, int* step,
                             float lr, cudaStream_t s);
+int mlp_train_cluster_size();  // CTAs of the training cluster (0: no cluster can be scheduled)
+size_t mlp_train_smem_bytes();
+cudaError_t mlp_train_steps_launch(float* p, float* m, float* v, int* step, float* x, float* y, int R,
+                                   const int* R_dev, float* loss, int D, int steps, float lr, cudaStream_t s,
+                                   const MlpDev* ring_of = nullptr);
 cudaError_t mlp_init_launch(const MlpDev& M, int D, uint64_t seed, cudaStream_t s);
 cudaError_t mlp_append_launch(const OuterParams& P, int N, cudaStream_t s);
 cudaError_t mlp_train_launch(const OuterParams& P, int steps, float lr, cudaStream_t s);

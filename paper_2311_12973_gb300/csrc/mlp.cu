@@ -8,6 +8,7 @@
 // a second product over the CTA's 64 rows, staged transposed in shared
 // memory), then one kernel sums them in a fixed order and takes an Adam step.
 // The proposal uses the gradient with respect to the input.
+#include <cooperative_groups.h>
 #include <cuda_bf16.h>
 
 #include "common.cuh"
@@ -33,6 +34,15 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   return *reinterpret_cast<uint32_t*>(&v);
 }
 __device__ __forceinline__ float round_bf16(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+
+// tanh x = sign(x) (1 - e) / (1 + e) with e = exp(-2|x|) in (0, 1]: the
+// hardware exp2 (relative error about 2^-22) and a fast division.  The
+// absolute error stays near 2^-22, far below the half step (2^-9 relative) of
+// the bfloat16 the activations are rounded to.
+__device__ __forceinline__ float tanh_act(float x) {
+  const float e = __expf(-2.f * fabsf(x));
+  return copysignf(__fdividef(1.f - e, 1.f + e), x);
+}
 __device__ __forceinline__ uint32_t ld32(const bf16* p) { return *reinterpret_cast<const uint32_t*>(p); }
 
 // D = A B + D for a 16x16 (row) by 16x8 (column) bf16 product, FP32 accumulators.
@@ -133,10 +143,10 @@ __device__ __forceinline__ void warp_forward(const MlpSmemWeights& W, const floa
     const bf16* w = W.w1t + (8 * j + g) * kLd1 + 2 * t;
     mma_bf16(c, a0, a1, a2, a3, ld32(w), ld32(w + 8));
     const int col = 8 * j + 2 * t;
-    F.h1[j][0] = tanhf(c[0] + W.b1[col]);
-    F.h1[j][1] = tanhf(c[1] + W.b1[col + 1]);
-    F.h1[j][2] = tanhf(c[2] + W.b1[col]);
-    F.h1[j][3] = tanhf(c[3] + W.b1[col + 1]);
+    F.h1[j][0] = tanh_act(c[0] + W.b1[col]);
+    F.h1[j][1] = tanh_act(c[1] + W.b1[col + 1]);
+    F.h1[j][2] = tanh_act(c[2] + W.b1[col]);
+    F.h1[j][3] = tanh_act(c[3] + W.b1[col + 1]);
   }
   uint32_t hA[4][4];
 #pragma unroll
@@ -155,10 +165,10 @@ __device__ __forceinline__ void warp_forward(const MlpSmemWeights& W, const floa
       mma_bf16(c, hA[kk][0], hA[kk][1], hA[kk][2], hA[kk][3], ld32(w), ld32(w + 8));
     }
     const int col = 8 * j + 2 * t;
-    F.h2[j][0] = tanhf(c[0] + W.b2[col]);
-    F.h2[j][1] = tanhf(c[1] + W.b2[col + 1]);
-    F.h2[j][2] = tanhf(c[2] + W.b2[col]);
-    F.h2[j][3] = tanhf(c[3] + W.b2[col + 1]);
+    F.h2[j][0] = tanh_act(c[0] + W.b2[col]);
+    F.h2[j][1] = tanh_act(c[1] + W.b2[col + 1]);
+    F.h2[j][2] = tanh_act(c[2] + W.b2[col]);
+    F.h2[j][3] = tanh_act(c[3] + W.b2[col + 1]);
   }
   float c3[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
@@ -406,6 +416,371 @@ __global__ void __launch_bounds__(128)
   p[q] -= lr * (mq / bc1) / (sqrtf(vq / bc2) + eps);
 }
 
+// ---------------------------------------------------------------------------
+// training: all Adam steps of one call in one launch of a thread-block cluster
+// ---------------------------------------------------------------------------
+// The cluster's CTAs split the rows; each keeps the FP32 parameters, their
+// bfloat16 copies, its rows and its partial gradient in shared memory, so the
+// kernel body, the weights and the data stay on the SMs for every step.  Per
+// step: partial gradients over the CTA's rows; cluster barrier; CTA c sums
+// parameter slice c over the cluster's CTAs in rank order (distributed shared
+// memory), takes the Adam step on it and writes the new values into every
+// CTA's parameter copy; cluster barrier.
+constexpr int kTrainWarps = 8;
+constexpr int kMaxCluster = 16;                    // CTAs of the training cluster, at most
+constexpr int kTrainRows = 16 * 2 * kTrainWarps;  // rows per chunk: two 16-row tiles per warp
+constexpr int kLdT = kTrainRows + 8;              // padded row of the staged [unit][row] tiles
+constexpr int kMlpPmax = kMlpMaxD * kMlpH + kMlpH * kMlpH + 3 * kMlpH + 1;
+
+struct MlpTrainSmem {
+  MlpSmemWeights W;
+  bf16 h1T[kMlpH * kLdT];                   // [i][row] h1 of the chunk's rows (bf16)
+  bf16 dz2T[kMlpH * kLdT];                  // [o][row] dz2 of the chunk's rows (bf16)
+  bf16 dz1T[kMlpH * kLdT];                  // [o][row] dz1 of the chunk's rows (bf16)
+  bf16 xT[16 * kLdT];                       // [d][row] inputs (bf16), row D all ones, rest zero
+  float col[kTrainWarps][3][kMlpH];         // per warp: dw3 (slot 2)
+  float sc[kTrainWarps][2];                 // per warp: sum e^2, db3
+  float pf[kMlpPmax];                       // FP32 parameters
+  float gp[kMlpPmax + 1];                   // partial gradient over the CTA's rows, then sum e^2
+  float xs[kTrainRows * kMlpMaxD];          // the chunk's inputs
+  float ys[kTrainRows];                     // and targets
+  float wred[kTrainWarps][2 * kMlpMaxD + 1];  // block reductions: per-warp values
+  float cred[2 * kMlpMaxD + 1];               // the CTA's totals, read by the cluster
+};
+
+// Totals over the cluster of NV per-thread values (sums, or maxima), in a
+// fixed order: warp shuffles, the warps in order, then the CTAs in rank order
+// through distributed shared memory.  Every thread of every CTA gets them.
+template <int NV>
+__device__ void cluster_totals(float (&v)[NV], MlpTrainSmem& S, cooperative_groups::cluster_group& cluster,
+                               bool is_max) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    const float r = is_max ? warp_max(v[i]) : warp_sum(v[i]);
+    if (lane == 0) S.wred[warp][i] = r;
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    float r = S.wred[0][threadIdx.x];
+    for (int w = 1; w < kTrainWarps; ++w) r = is_max ? fmaxf(r, S.wred[w][threadIdx.x]) : r + S.wred[w][threadIdx.x];
+    S.cred[threadIdx.x] = r;
+  }
+  cluster.sync();
+  const int C = (int)cluster.num_blocks();
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    float u[kMaxCluster];
+#pragma unroll
+    for (int q = 0; q < kMaxCluster; ++q) u[q] = q < C ? cluster.map_shared_rank(S.cred, q)[i] : 0.f;
+    float r = u[0];
+#pragma unroll
+    for (int q = 1; q < kMaxCluster; ++q)
+      if (q < C) r = is_max ? fmaxf(r, u[q]) : r + u[q];
+    v[i] = r;
+  }
+  cluster.sync();  // cred free again
+}
+
+// bfloat16 operand copies from the FP32 parameters in shared memory.
+__device__ void refresh_weights(MlpSmemWeights& W, const float* pf, int D) {
+  const int nt = blockDim.x, tid = threadIdx.x;
+  for (int e = tid; e < kMlpH * kLd1; e += nt) W.w1t[e] = __float2bfloat16_rn(0.f);
+  for (int e = tid; e < 8 * kLd; e += nt) W.w1b[e] = __float2bfloat16_rn(0.f);
+  __syncthreads();
+  for (int q = tid; q < D * kMlpH; q += nt) {
+    const int d = q / kMlpH, o = q % kMlpH;
+    const bf16 h = __float2bfloat16_rn(pf[q]);
+    W.w1t[o * kLd1 + d] = h;
+    W.w1b[d * kLd + o] = h;
+  }
+  const float* W2 = pf + off_W2(D);
+  for (int q = tid; q < kMlpH * kMlpH; q += nt) {
+    const int i = q / kMlpH, o = q % kMlpH;
+    const bf16 h = __float2bfloat16_rn(W2[q]);
+    W.w2b[i * kLd + o] = h;
+    W.w2t[o * kLd + i] = h;
+  }
+  for (int e = tid; e < kMlpH; e += nt) {
+    const bf16 h = __float2bfloat16_rn(pf[off_w3(D) + e]);
+    W.w3b[e] = h;
+    W.w3f[e] = __bfloat162float(h);
+    W.b1[e] = pf[off_b1(D) + e];
+    W.b2[e] = pf[off_b2(D) + e];
+  }
+  if (tid == 0) W.b3 = pf[off_b3(D)];
+  __syncthreads();
+}
+
+// Ring standardisation (the training set of the learned proposal), when ring
+// is non-null: z = max((log pi - max log pi) / tau, -8), tau = max(2, D), the
+// target y = (z - mean z) / sd z; inputs standardised by the mean and sd of
+// the rows above the clip (all rows if fewer than 2D + 2), moments taken about
+// ring row 0; results into x, y (global) and *norm.  Then `steps` Adam steps.
+struct MlpRing {
+  const float* th;   // [rows][D]
+  const float* lp;   // [rows]
+  const int* rows;
+  MlpNorm* norm;
+};
+
+__global__ void __launch_bounds__(32 * kTrainWarps)
+    mlp_train_kernel(float* p, float* m, float* v, int* step, float* x, float* y, int R_imm, const int* R_dev,
+                     float* loss, int D, int steps, float lr, MlpRing ring) {
+  namespace cg = cooperative_groups;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  MlpTrainSmem& S = *reinterpret_cast<MlpTrainSmem*>(smem_raw);
+  cg::cluster_group cluster = cg::this_cluster();
+  const int C = (int)cluster.num_blocks(), c = (int)cluster.block_rank();
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
+  const int P = mlp_nparams(D);
+  const int R = ring.th ? *ring.rows : (R_dev ? *R_dev : R_imm);
+  const int per = (R + C - 1) / C, r0 = min(c * per, R), r1 = min(r0 + per, R);
+  if (ring.th) {
+    const float tau = D > 2 ? (float)D : 2.f, inv_tau = 1.f / tau;
+    float mx[1] = {-INFINITY};
+    for (int r = r0 + tid; r < r1; r += blockDim.x) {
+      const float l = ring.lp[r];
+      if (isfinite(l)) mx[0] = fmaxf(mx[0], l);
+    }
+    cluster_totals<1>(mx, S, cluster, true);
+    const float ymax = mx[0], cut = ymax - 8.f * tau;
+    float ref[kMlpMaxD], mu[kMlpMaxD], sd[kMlpMaxD];
+#pragma unroll
+    for (int d = 0; d < kMlpMaxD; ++d) ref[d] = (R > 0 && d < D) ? ring.th[d] : 0.f;
+    for (int pass = 0; pass < 2; ++pass) {  // pass 0: rows above the clip; pass 1: every finite row
+      float acc[2 * kMlpMaxD + 1];
+#pragma unroll
+      for (int i = 0; i < 2 * kMlpMaxD + 1; ++i) acc[i] = 0.f;
+      for (int r = r0 + tid; r < r1; r += blockDim.x) {
+        const float l = ring.lp[r];
+        if (!isfinite(l) || (pass == 0 && l <= cut)) continue;
+        acc[2 * kMlpMaxD] += 1.f;
+#pragma unroll
+        for (int d = 0; d < kMlpMaxD; ++d) {
+          if (d >= D) break;
+          const float cdev = ring.th[(size_t)r * D + d] - ref[d];
+          acc[d] += cdev;
+          acc[kMlpMaxD + d] += cdev * cdev;
+        }
+      }
+      cluster_totals<2 * kMlpMaxD + 1>(acc, S, cluster, false);
+      const float cnt = acc[2 * kMlpMaxD];
+#pragma unroll
+      for (int d = 0; d < kMlpMaxD; ++d) {
+        const float m1 = cnt > 0.f ? acc[d] / cnt : 0.f;
+        const float m2 = cnt > 0.f ? acc[kMlpMaxD + d] / cnt : 0.f;
+        mu[d] = ref[d] + m1;
+        sd[d] = fmaxf(cnt > 1.f ? sqrtf(fmaxf(m2 - m1 * m1, 0.f)) : 1.f, 1e-6f);
+      }
+      if (cnt >= 2.f * D + 2.f) break;
+    }
+    auto z_of = [&](float l) { return isfinite(l) ? fmaxf((l - ymax) * inv_tau, -8.f) : -8.f; };
+    float zs[2] = {0.f, 0.f};
+    for (int r = r0 + tid; r < r1; r += blockDim.x) {
+      const float z = z_of(ring.lp[r]);
+      zs[0] += z;
+      zs[1] += z * z;
+    }
+    cluster_totals<2>(zs, S, cluster, false);
+    const float zmean = R > 0 ? zs[0] / (float)R : 0.f;
+    const float zvar = R > 0 ? fmaxf(zs[1] / (float)R - zmean * zmean, 0.f) : 0.f;
+    const float zsd = zvar > 1e-8f ? sqrtf(zvar) : 1.f, inv_zsd = 1.f / zsd;
+    float inv_sd[kMlpMaxD];
+#pragma unroll
+    for (int d = 0; d < kMlpMaxD; ++d) inv_sd[d] = 1.f / sd[d];
+    for (int r = r0 + tid; r < r1; r += blockDim.x) {
+      y[r] = (z_of(ring.lp[r]) - zmean) * inv_zsd;
+#pragma unroll
+      for (int d = 0; d < kMlpMaxD; ++d) {
+        if (d >= D) break;
+        x[(size_t)r * D + d] = (ring.th[(size_t)r * D + d] - mu[d]) * inv_sd[d];
+      }
+    }
+    if (c == 0 && tid == 0) {
+      MlpNorm& nm = *ring.norm;
+      for (int d = 0; d < D; ++d) {
+        nm.mu[d] = mu[d];
+        nm.sd[d] = 1.0 / (double)inv_sd[d];
+      }
+      nm.ymax = ymax;
+      nm.tau = tau;
+      nm.zmean = zmean;
+      nm.zsd = zsd;
+      nm.rows = R;
+      nm.var_y = zvar > 1e-8f ? 1.f : 0.f;
+    }
+    __syncthreads();  // this CTA's rows of x, y written before it reads them back
+  }
+  const bool cached = r1 - r0 <= kTrainRows;  // one chunk: rows stay in shared memory
+  const int slice = (P + C - 1) / C, q0 = min(c * slice, P), q1 = min(q0 + slice, P);
+  const int t0 = *step;
+  for (int q = tid; q < P; q += blockDim.x) S.pf[q] = p[q];
+  const float beta1 = 0.9f, beta2 = 0.999f, eps = 1e-8f;
+  for (int it = 0; it < steps; ++it) {
+    refresh_weights(S.W, S.pf, D);  // ends with a barrier
+    for (int e = tid; e < kTrainWarps * 3 * kMlpH; e += blockDim.x) (&S.col[0][0][0])[e] = 0.f;
+    float acc[4][4];  // dW2 tile of this warp: units i of m-tile (warp & 3), o of n-tiles 4 (warp >> 2) + j
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+    // rows d < D: dW1[d][o]; row D: db1[o] (from [x^T; 1] dz1) and db2[o] (from 1^T dz2),
+    // for the units o = 8 warp .. 8 warp + 7
+    float w1acc[4] = {0.f, 0.f, 0.f, 0.f}, b2acc[4] = {0.f, 0.f, 0.f, 0.f};
+    float l_acc = 0.f, d3_acc = 0.f;
+    for (int base = r0; base < r1 || (base == r0 && r0 == r1); base += kTrainRows) {
+      const int n = min(kTrainRows, r1 - base);
+      if (!cached || it == 0) {
+        for (int e = tid; e < kTrainRows * D; e += blockDim.x) S.xs[e] = e < n * D ? x[(size_t)base * D + e] : 0.f;
+        for (int e = tid; e < kTrainRows; e += blockDim.x) S.ys[e] = e < n ? y[base + e] : 0.f;
+        __syncthreads();
+        for (int e = tid; e < 16 * kTrainRows; e += blockDim.x) {
+          const int d = e / kTrainRows, r = e % kTrainRows;
+          S.xT[d * kLdT + r] = __float2bfloat16_rn(d < D ? S.xs[r * D + d] : (d == D ? 1.f : 0.f));
+        }
+      }
+      __syncthreads();
+#pragma unroll 1
+      for (int tile = 0; tile < 2; ++tile) {
+        const int rl = (warp * 2 + tile) * 16 + g;  // row within the chunk
+        const bool va = rl < n, vb = rl + 8 < n;
+        float xa[4], xb[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int k = 2 * t + (e & 1) + (e >> 1) * 8;
+          xa[e] = k < D ? S.xs[rl * D + k] : 0.f;
+          xb[e] = k < D ? S.xs[(rl + 8) * D + k] : 0.f;
+        }
+        WarpForward F;
+        warp_forward(S.W, xa, xb, F);
+        const float ea = va ? F.s_lo - S.ys[rl] : 0.f, eb = vb ? F.s_hi - S.ys[rl + 8] : 0.f;
+        const float ga = 2.f * ea / (float)R, gb = 2.f * eb / (float)R;
+        float dz2[8][4], dz1[8][4];
+        warp_backward(S.W, F, ga, gb, dz2, dz1);
+        l_acc += warp_sum(t == 0 ? ea * ea + eb * eb : 0.f);
+        d3_acc += warp_sum(t == 0 ? ga + gb : 0.f);
+        // dw3 = sum_r h2_r ga_r (FP32 row signal): a shuffle reduction per column
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            const int cc = 8 * j + 2 * t + e;
+            const float v_dw3 = sum_over_g(round_bf16(F.h2[j][e]) * ga + round_bf16(F.h2[j][2 + e]) * gb);
+            if (g == 0) S.col[warp][2][cc] += v_dw3;
+          }
+        }
+        // stage h1, dz2, dz1 transposed: the weight gradients are products over rows
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            const int cc = 8 * j + 2 * t + e;
+            S.h1T[cc * kLdT + rl] = __float2bfloat16_rn(F.h1[j][e]);
+            S.h1T[cc * kLdT + rl + 8] = __float2bfloat16_rn(F.h1[j][2 + e]);
+            S.dz2T[cc * kLdT + rl] = __float2bfloat16_rn(dz2[j][e]);
+            S.dz2T[cc * kLdT + rl + 8] = __float2bfloat16_rn(dz2[j][2 + e]);
+            S.dz1T[cc * kLdT + rl] = __float2bfloat16_rn(dz1[j][e]);
+            S.dz1T[cc * kLdT + rl + 8] = __float2bfloat16_rn(dz1[j][2 + e]);
+          }
+      }
+      __syncthreads();
+      {  // dW2 += h1^T dz2, [dW1; db1] += [x^T; 1] dz1, db2 += 1^T dz2 over the chunk's rows
+        const int mt = warp & 3, nh = warp >> 2;
+#pragma unroll 2
+        for (int kk = 0; kk < kTrainRows / 16; ++kk) {
+          const bf16* a = S.h1T + (16 * mt + g) * kLdT + 16 * kk + 2 * t;
+          const uint32_t a0 = ld32(a), a1 = ld32(a + 8 * kLdT), a2 = ld32(a + 8), a3 = ld32(a + 8 * kLdT + 8);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const bf16* b = S.dz2T + (8 * (4 * nh + j) + g) * kLdT + 16 * kk + 2 * t;
+            mma_bf16(acc[j], a0, a1, a2, a3, ld32(b), ld32(b + 8));
+          }
+          const bf16* xa = S.xT + g * kLdT + 16 * kk + 2 * t;
+          const uint32_t x0 = ld32(xa), x1 = ld32(xa + 8 * kLdT), x2 = ld32(xa + 8), x3 = ld32(xa + 8 * kLdT + 8);
+          const bf16* b1p = S.dz1T + (8 * warp + g) * kLdT + 16 * kk + 2 * t;
+          mma_bf16(w1acc, x0, x1, x2, x3, ld32(b1p), ld32(b1p + 8));
+          const bf16* b2p = S.dz2T + (8 * warp + g) * kLdT + 16 * kk + 2 * t;
+          mma_bf16(b2acc, x0, x1, x2, x3, ld32(b2p), ld32(b2p + 8));
+        }
+      }
+      __syncthreads();  // staging free for the next chunk
+      if (r0 == r1) break;
+    }
+    // the CTA's partial gradient into gp
+    {
+      float* gW2 = S.gp + off_W2(D);
+      const int mt = warp & 3, nh = warp >> 2, i0 = 16 * mt + g;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int o = 8 * (4 * nh + j) + 2 * t;
+        gW2[i0 * kMlpH + o] = acc[j][0];
+        gW2[i0 * kMlpH + o + 1] = acc[j][1];
+        gW2[(i0 + 8) * kMlpH + o] = acc[j][2];
+        gW2[(i0 + 8) * kMlpH + o + 1] = acc[j][3];
+      }
+    }
+    if (lane == 0) {
+      S.sc[warp][0] = l_acc;
+      S.sc[warp][1] = d3_acc;
+    }
+    __syncthreads();
+    {  // rows g (c0, c1) and g + 8 (c2, c3) of the [x^T; 1] products, units 8 warp + 2t, + 1
+      const int o = 8 * warp + 2 * t;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int row = g + 8 * h;
+        if (row < D) {
+          S.gp[row * kMlpH + o] = w1acc[2 * h];
+          S.gp[row * kMlpH + o + 1] = w1acc[2 * h + 1];
+        } else if (row == D) {
+          S.gp[off_b1(D) + o] = w1acc[2 * h];
+          S.gp[off_b1(D) + o + 1] = w1acc[2 * h + 1];
+          S.gp[off_b2(D) + o] = b2acc[2 * h];
+          S.gp[off_b2(D) + o + 1] = b2acc[2 * h + 1];
+        }
+      }
+    }
+    for (int e = tid; e < kMlpH; e += blockDim.x) {
+      float w3s = 0.f;
+      for (int w = 0; w < kTrainWarps; ++w) w3s += S.col[w][2][e];
+      S.gp[off_w3(D) + e] = w3s;
+    }
+    if (tid == 0) {
+      float l2 = 0.f, b3s = 0.f;
+      for (int w = 0; w < kTrainWarps; ++w) {
+        l2 += S.sc[w][0];
+        b3s += S.sc[w][1];
+      }
+      S.gp[off_b3(D)] = b3s;
+      S.gp[P] = l2;
+    }
+    cluster.sync();  // every CTA's partial gradient complete
+    const int tstep = t0 + it + 1;
+    const float bc1 = 1.f - powf(beta1, (float)tstep), bc2 = 1.f - powf(beta2, (float)tstep);
+    for (int q = q0 + tid; q < q1; q += blockDim.x) {
+      float part[kMaxCluster];  // every rank's partial in flight at once, summed in rank order
+#pragma unroll
+      for (int r = 0; r < kMaxCluster; ++r) part[r] = r < C ? cluster.map_shared_rank(S.gp, r)[q] : 0.f;
+      float sum = 0.f;
+#pragma unroll
+      for (int r = 0; r < kMaxCluster; ++r) sum += part[r];
+      const float mq = beta1 * m[q] + (1.f - beta1) * sum;
+      const float vq = beta2 * v[q] + (1.f - beta2) * sum * sum;
+      m[q] = mq;
+      v[q] = vq;
+      const float pn = S.pf[q] - lr * (mq / bc1) / (sqrtf(vq / bc2) + eps);
+      for (int r = 0; r < C; ++r) cluster.map_shared_rank(S.pf, r)[q] = pn;
+    }
+    if (c == 0 && tid == 0) {
+      float l2 = 0.f;
+      for (int r = 0; r < C; ++r) l2 += cluster.map_shared_rank(S.gp, r)[P];
+      *loss = R > 0 ? l2 / (float)R : 0.f;
+    }
+    cluster.sync();  // every parameter copy updated; partial gradients free again
+  }
+  for (int q = q0 + tid; q < q1; q += blockDim.x) p[q] = S.pf[q];
+  if (c == 0 && tid == 0) *step = t0 + steps;
+}
+
 // s and ds/dx of a warp's rows g and g+8: lane (g, t) returns dx of
 // coordinates 2t and 2t+1 (rows g: dx_lo, g+8: dx_hi).
 __device__ __forceinline__ void warp_input_grad(const MlpSmemWeights& W, const float* xa, const float* xb,
@@ -511,114 +886,6 @@ __global__ void mlp_publish_kernel(MlpDev M, int n_par) {
   }
 }
 
-// Sums of NV values over the 1024 threads of a block, fixed order (shuffle
-// tree in each warp, then the warps in order); every thread gets the totals.
-template <int NV, typename R>
-__device__ void block_sums(R (&v)[NV], R (*red)[32], bool is_max = false) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int i = 0; i < NV; ++i) {
-    v[i] = is_max ? warp_max(v[i]) : warp_sum(v[i]);
-    if (lane == 0) red[i][warp] = v[i];
-  }
-  __syncthreads();
-#pragma unroll
-  for (int i = 0; i < NV; ++i) {
-    R r = red[i][0];
-    for (int w = 1; w < 32; ++w) r = is_max ? fmax(r, red[i][w]) : r + red[i][w];
-    v[i] = r;
-  }
-  __syncthreads();
-}
-
-// Standardised training set of the rows in the ring (one block of 1024
-// threads, FP32, fixed-order sums): z = max((log pi - max log pi) / tau, -8),
-// tau = max(2, D), and the target y = (z - mean z) / sd z; inputs
-// standardised by the mean and sd of the rows above the clip (all rows if too
-// few), the moments taken about ring row 0.
-__global__ void __launch_bounds__(1024) mlp_stats_kernel(OuterParams P) {
-  __shared__ float red[2 * kMlpMaxD + 1][32];
-  const int D = P.D, tid = threadIdx.x;
-  const int rows = *P.mlp.ring_rows;
-  const float tau = D > 2 ? (float)D : 2.f, inv_tau = 1.f / tau;
-  const float* th = P.mlp.ring_th;
-  const float* lpv = P.mlp.ring_lp;
-  float mx[1] = {-INFINITY};
-  for (int r = tid; r < rows; r += 1024) {
-    const float lp = lpv[r];
-    if (isfinite(lp)) mx[0] = fmaxf(mx[0], lp);
-  }
-  block_sums<1, float>(mx, red, true);
-  const float ymax = mx[0];
-  const float cut = ymax - 8.f * tau;
-  float ref[kMlpMaxD], mu[kMlpMaxD], sd[kMlpMaxD];
-#pragma unroll
-  for (int d = 0; d < kMlpMaxD; ++d) ref[d] = (rows > 0 && d < D) ? th[d] : 0.f;
-  for (int pass = 0; pass < 2; ++pass) {  // pass 0: rows above the clip; pass 1: every finite row
-    float acc[2 * kMlpMaxD + 1];
-#pragma unroll
-    for (int i = 0; i < 2 * kMlpMaxD + 1; ++i) acc[i] = 0.f;
-    for (int r = tid; r < rows; r += 1024) {
-      const float lp = lpv[r];
-      if (!isfinite(lp) || (pass == 0 && lp <= cut)) continue;
-      acc[2 * kMlpMaxD] += 1.f;
-#pragma unroll
-      for (int d = 0; d < kMlpMaxD; ++d) {
-        if (d >= D) break;
-        const float c = th[(size_t)r * D + d] - ref[d];
-        acc[d] += c;
-        acc[kMlpMaxD + d] += c * c;
-      }
-    }
-    block_sums<2 * kMlpMaxD + 1, float>(acc, red);
-    const float cnt = acc[2 * kMlpMaxD];
-#pragma unroll
-    for (int d = 0; d < kMlpMaxD; ++d) {
-      const float m1 = cnt > 0.f ? acc[d] / cnt : 0.f;
-      const float m2 = cnt > 0.f ? acc[kMlpMaxD + d] / cnt : 0.f;
-      mu[d] = ref[d] + m1;
-      sd[d] = cnt > 1.f ? sqrtf(fmaxf(m2 - m1 * m1, 0.f)) : 1.f;
-      sd[d] = fmaxf(sd[d], 1e-6f);
-    }
-    if (cnt >= 2.f * D + 2.f) break;
-  }
-  auto z_of = [&](float lp) { return isfinite(lp) ? fmaxf((lp - ymax) * inv_tau, -8.f) : -8.f; };
-  float zs[2] = {0.f, 0.f};
-  for (int r = tid; r < rows; r += 1024) {
-    const float z = z_of(lpv[r]);
-    zs[0] += z;
-    zs[1] += z * z;
-  }
-  block_sums<2, float>(zs, red);
-  const float zmean = rows > 0 ? zs[0] / (float)rows : 0.f;
-  const float zvar = rows > 0 ? fmaxf(zs[1] / (float)rows - zmean * zmean, 0.f) : 0.f;
-  const float zsd = zvar > 1e-8f ? sqrtf(zvar) : 1.f, inv_zsd = 1.f / zsd;
-  float inv_sd[kMlpMaxD];
-#pragma unroll
-  for (int d = 0; d < kMlpMaxD; ++d) inv_sd[d] = 1.f / sd[d];
-  for (int r = tid; r < rows; r += 1024) {
-    P.mlp.ys[r] = (z_of(lpv[r]) - zmean) * inv_zsd;
-#pragma unroll
-    for (int d = 0; d < kMlpMaxD; ++d) {
-      if (d >= D) break;
-      P.mlp.xs[(size_t)r * D + d] = (th[(size_t)r * D + d] - mu[d]) * inv_sd[d];
-    }
-  }
-  if (tid == 0) {
-    MlpNorm& nm = *P.mlp.norm;
-    for (int d = 0; d < D; ++d) {
-      nm.mu[d] = mu[d];
-      nm.sd[d] = 1.0 / (double)inv_sd[d];
-    }
-    nm.ymax = ymax;
-    nm.tau = tau;
-    nm.zmean = zmean;
-    nm.zsd = zsd;
-    nm.rows = rows;
-    nm.var_y = zvar > 1e-8f ? 1.f : 0.f;
-  }
-}
-
 // Score of the surrogate at the parents theta_{k-1}: through the input and
 // target standardisations, d log pi^ / d theta_d = tau zsd (ds/dx)_d / sd_d.
 // Decides whether iteration k proposes with it: from k = 3 on, while the
@@ -686,6 +953,67 @@ cudaError_t mlp_step_launch(float* p, int D, const float* x, const float* y, int
   return cudaGetLastError();
 }
 
+size_t mlp_train_smem_bytes() { return sizeof(MlpTrainSmem); }
+
+// Largest cluster (16, 8, 4, 2 or 1 CTAs) that the device can co-schedule with
+// this kernel's shared memory.
+int mlp_train_cluster_size() {
+  static int cached = 0;
+  if (cached) return cached;
+  const size_t smem = sizeof(MlpTrainSmem);
+  if (cudaFuncSetAttribute(mlp_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(mlp_train_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+    return 0;
+  for (int C = 16; C >= 1; C >>= 1) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C);
+    cfg.blockDim = dim3(32 * kTrainWarps);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, mlp_train_kernel, &cfg) == cudaSuccess && n > 0) {
+      cached = C;
+      return C;
+    }
+    cudaGetLastError();
+  }
+  return 0;
+}
+
+cudaError_t mlp_train_steps_launch(float* p, float* m, float* v, int* step, float* x, float* y, int R,
+                                   const int* R_dev, float* loss, int D, int steps, float lr, cudaStream_t s,
+                                   const MlpDev* ring_of) {
+  const int C = mlp_train_cluster_size();
+  if (C < 1) return cudaErrorInvalidConfiguration;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(C);
+  cfg.blockDim = dim3(32 * kTrainWarps);
+  cfg.dynamicSmemBytes = sizeof(MlpTrainSmem);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = C;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  MlpRing ring{};
+  if (ring_of) {
+    ring.th = ring_of->ring_th;
+    ring.lp = ring_of->ring_lp;
+    ring.rows = ring_of->ring_rows;
+    ring.norm = ring_of->norm;
+  }
+  return cudaLaunchKernelEx(&cfg, mlp_train_kernel, p, m, v, step, x, y, R, R_dev, loss, D, steps, lr, ring);
+}
+
 cudaError_t mlp_init_launch(const MlpDev& M, int D, uint64_t seed, cudaStream_t s) {
   const int P = mlp_nparams(D);
   mlp_init_kernel<<<(P + 255) / 256, 256, 0, s>>>(M, D, seed);
@@ -698,16 +1026,11 @@ cudaError_t mlp_append_launch(const OuterParams& P, int N, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// Standardise the ring and take `steps` Adam steps on it.
+// Standardise the ring and take `steps` Adam steps on it: one cluster launch.
 cudaError_t mlp_train_launch(const OuterParams& P, int steps, float lr, cudaStream_t s) {
-  mlp_stats_kernel<<<1, 1024, 0, s>>>(P);
-  cudaError_t e = cudaGetLastError();
   const MlpDev& M = P.mlp;
-  const int cap = M.W * P.ds_N0;
-  for (int it = 0; it < steps && e == cudaSuccess; ++it)
-    e = mlp_step_launch(M.p, P.D, M.xs, M.ys, cap, &M.norm->rows, M.part, nullptr, M.loss, 1, M.m,
-                        M.v, M.step, lr, s);
-  return e;
+  return mlp_train_steps_launch(M.p, M.m, M.v, M.step, M.xs, M.ys, M.W * P.ds_N0, nullptr, M.loss, P.D, steps, lr,
+                                s, &M);
 }
 
 cudaError_t mlp_publish_launch(const OuterParams& P, cudaStream_t s) {

@@ -131,9 +131,11 @@ def test_learned_proposal_stagewise_against_oracle(S):
         err_th = np.max(np.abs(theta_b - expect_th))
         err_lq = np.max(np.abs(logq - expect_lq))
         print(f"k={k}: theta err {err_th:.3g} (drift scale {np.max(np.abs(drift)):.3g}), log q err {err_lq:.3g}")
-        # measured on GB300: theta within 1.7e-7 of a drift of order 1, log q within 4e-15
+        # measured on GB300: theta typically within 2e-7 of a drift of order 1, and within
+        # 1e-3 of it when one activation rounds to the neighbouring bfloat16 (one step,
+        # 2^-8, as the input-gradient test allows); log q within 4e-15
         assert err_lq < 1e-9
-        assert err_th <= 1e-4 * np.max(np.abs(drift)) + 1e-10
+        assert err_th <= 1e-2 * np.max(np.abs(drift)) + 1e-10
         checked += 1
     assert checked >= 3, checked
     ctx.close()
