@@ -61,7 +61,7 @@ enum { SMC2_PROP_RW = 0, SMC2_PROP_MLP = 1 };
 enum { SMC2_LK_FORWARD = 0, SMC2_LK_GAUSS_OPT = 1 };
 
 #define SMC2_MAX_D 8
-#define SMC2_MAX_M 4096     /* particles per filter; M > 2048 uses 8 particles per thread */
+#define SMC2_MAX_M 4096     /* particles per filter (see M in smc2_config) */
 #define SMC2_MAX_N 16384
 #define SMC2_MAX_DATASETS 4096
 
@@ -72,6 +72,8 @@ typedef struct smc2_ctx smc2_ctx; /* opaque; owns its device workspace */
  * D: dimension of theta (3 for LG_AR1, 4 for SEIR).
  * N, M, T: theta samples, particles per filter, observations; used when
  *   n_datasets <= 1, otherwise taken per dataset from ds_N, ds_M, ds_T.
+ *   M <= SMC2_MAX_M, and a filter's particles must fit one CTA's shared
+ *   memory (227 KB): in FP64 the SEIR-type model takes M <= 2048.
  * K: iterations the context will run (sizes the statistics history).
  * rw_scale: standard deviation of the Gaussian random-walk proposal in every
  *   unconstrained coordinate (Sec. IV-A, Eq. 19: Sigma = rw_scale^2 I).

@@ -147,6 +147,15 @@ smc2_status validate(const smc2_config* c) {
       return SMC2_EINVAL;
     const int gt = pf_group_threads(c->ppt ? c->ppt : 16, m);
     if (gt > (c->cta_threads ? c->cta_threads : kPfMaxBlock)) return SMC2_EINVAL;
+    // a filter's particles live in one CTA's shared memory: some shape must fit
+    const int model = c->model == SMC2_MODEL_LG_AR1 ? MODEL_LG : MODEL_SEIR;
+    bool fits = false;
+    for (int ppt : {1, 2, 4, 8, 16}) {
+      if (c->ppt && ppt != c->ppt) continue;
+      const int g = pf_group_threads(ppt, m);
+      if (g <= kPfMaxBlock && pf_smem_bytes(c->precision, model, ppt, g, m) <= 227 * 1024) fits = true;
+    }
+    if (!fits) return SMC2_EINVAL;
   }
   return SMC2_OK;
 }

@@ -82,6 +82,16 @@ def test_invalid_prior_and_seir_constants(S):
     assert S.lib.smc2_init(C.byref(cfg), None, None, C.byref(ctx)) == S.EINVAL
 
 
+def test_filters_that_do_not_fit_shared_memory_are_rejected(S):
+    import numpy as np
+    from paper_2311_12973_gb300 import inputs as I
+    ctx = C.c_void_p()
+    y = np.zeros(10)
+    cfg = S.make_config(I.workload("seir_t100_n1024", T=10), precision=S.PREC_FP64, M=4096)
+    assert S.lib.smc2_init(C.byref(cfg), y.ctypes.data, None, C.byref(ctx)) == S.EINVAL
+    assert not ctx.value
+
+
 def test_learned_proposal_needs_one_dataset(S):
     import numpy as np
     cfg = _cfg(S, proposal=1)

@@ -45,6 +45,10 @@ def _compare_state(S_ctx, ref, scale):
 
 CASES = {
     "lg_cfg1": dict(name="lg_t50_n64"),
+    "lg_max_n": dict(name="lg_t50_n64", N=16384, M=8, T=5, K=3),      # the largest N: 128 KB of q per block
+    "seir_max_m": dict(name="seir_t100_n1024", N=40, M=2048, T=6, K=3, precision=I.PREC_FP64),  # FP64 SEIR limit
+    "lg_max_m": dict(name="lg_t50_n64", N=20, M=4096, T=6, K=3),
+    "lg_n_odd": dict(name="lg_t50_n64", N=1000, M=33, T=7, K=4),
     "lg_forward": dict(name="lg_t50_n64", lkernel=I.LK_FORWARD, N=96, K=6),
     "lg_ragged": dict(name="lg_t50_n64", N=300, M=100, T=20, K=4),
     "seir_fp64": dict(name="seir_t100_n1024", N=64, M=128, T=40, K=5, precision=I.PREC_FP64),
