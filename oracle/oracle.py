@@ -62,7 +62,7 @@ class OracleStats(C.Structure):
     _fields_ = [
         ("k", C.c_int), ("resampled", C.c_int), ("lk_fallback", C.c_int), ("pad", C.c_int),
         ("lse", C.c_double), ("lse2", C.c_double), ("ess", C.c_double), ("logz", C.c_double),
-        ("est", C.c_double * MAX_D),
+        ("est", C.c_double * MAX_D), ("cov", C.c_double * (MAX_D * MAX_D)),
     ]
 
 
@@ -112,6 +112,7 @@ def _declare(L):
                                    C.POINTER(OracleStats)]
     L.oracle_smc2_step.restype = C.c_int
     L.oracle_recycle.argtypes = [C.c_int, C.c_int, C.POINTER(OracleStats), dp, dp]
+    L.oracle_recycle_cov.argtypes = [C.c_int, C.c_int, C.POINTER(OracleStats), dp]
     L.oracle_bf16.argtypes = [C.c_double]
     L.oracle_bf16.restype = C.c_double
     L.oracle_mlp_nparams.argtypes = [C.c_int, C.c_int]
@@ -299,7 +300,8 @@ def lkernel_logpdf(fit, a, b) -> float:
 
 def _stats_dict(s: OracleStats, D: int) -> dict:
     return {"k": s.k, "resampled": s.resampled, "lk_fallback": s.lk_fallback, "lse": s.lse,
-            "lse2": s.lse2, "ess": s.ess, "logz": s.logz, "est": np.array(s.est[:D])}
+            "lse2": s.lse2, "ess": s.ess, "logz": s.logz, "est": np.array(s.est[:D]),
+            "cov": np.array(s.cov[:D * D]).reshape(D, D)}
 
 
 class SMC2:
@@ -352,6 +354,13 @@ class SMC2:
         ck = np.zeros(K)
         lib().oracle_recycle(K, self.cfg.D, arr, _p(est, C.c_double), _p(ck, C.c_double))
         return est, ck
+
+    def recycled_cov(self):
+        K = len(self._raw)
+        arr = (OracleStats * K)(*self._raw)
+        cov = np.zeros((self.cfg.D, self.cfg.D))
+        lib().oracle_recycle_cov(K, self.cfg.D, arr, _p(cov, C.c_double))
+        return cov
 
 
 # --------------------------------------------------------------------------

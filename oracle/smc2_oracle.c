@@ -464,6 +464,14 @@ static int oracle_normalise(const oracle_cfg* c, const double* theta, const doub
     sum_wn2 += wn * wn;
     for (int d = 0; d < D; ++d) st->est[d] += wn * theta[i * D + d]; /* Eq. (21) */
   }
+  /* Eq. (21) with f = (theta - f~)(theta - f~)^T: the weighted covariance, second pass */
+  for (int d = 0; d < D * D; ++d) st->cov[d] = 0.0;
+  for (int i = 0; i < N; ++i) {
+    double wn = exp(logw[i] - m) / sw;
+    for (int d = 0; d < D; ++d)
+      for (int e = 0; e < D; ++e)
+        st->cov[d * D + e] += wn * (theta[i * D + d] - st->est[d]) * (theta[i * D + e] - st->est[e]);
+  }
   st->ess = 1.0 / sum_wn2; /* Eq. (25); equals l_k of Eq. (24) */
   st->logz = st->lse - log((double)N);
   return 0;
@@ -587,6 +595,22 @@ void oracle_recycle(int K, int D, const oracle_stats* st, double* est_out, doubl
     if (c_out) c_out[k] = ck;
     for (int d = 0; d < D; ++d) est_out[d] += ck * st[k].est[d];
   }
+}
+
+void oracle_recycle_cov(int K, int D, const oracle_stats* st, double* cov_out) {
+  double lsum = 0.0, mean[ORACLE_MAX_D] = {0.0};
+  for (int k = 0; k < K; ++k) lsum += st[k].ess;
+  for (int d = 0; d < D * D; ++d) cov_out[d] = 0.0;
+  for (int k = 0; k < K; ++k) {
+    const double ck = st[k].ess / lsum; /* Eqs. (23), (24) */
+    for (int d = 0; d < D; ++d) {
+      mean[d] += ck * st[k].est[d];
+      for (int e = 0; e < D; ++e)  /* the recycled second moment E[theta_d theta_e] */
+        cov_out[d * D + e] += ck * (st[k].cov[d * D + e] + st[k].est[d] * st[k].est[e]);
+    }
+  }
+  for (int d = 0; d < D; ++d)
+    for (int e = 0; e < D; ++e) cov_out[d * D + e] -= mean[d] * mean[e];
 }
 
 /* ------------------------------------------------------------------ */

@@ -67,6 +67,7 @@ typedef struct {
   int k, resampled, lk_fallback, pad;
   double lse, lse2, ess, logz;   /* LSE(log w), LSE(2 log w), ESS = l_k, log Z_k */
   double est[ORACLE_MAX_D];      /* f~_k = sum_i w~_k^i theta_k^i */
+  double cov[ORACLE_MAX_D * ORACLE_MAX_D];  /* sum_i w~_k^i (theta_k^i - f~_k)(theta_k^i - f~_k)^T, [D][D] */
 } oracle_stats;
 
 void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
@@ -109,6 +110,9 @@ void oracle_mlp_input_grad(int D, int H, const double* params, const double* x, 
 void oracle_adam_step(int n, double* params, const double* grad, double* m, double* v, int t, double lr,
                       double beta1, double beta2, double eps);
 void oracle_recycle(int K, int D, const oracle_stats* st, double* est_out, double* c_out);
+/* Recycled posterior covariance: Eq. (29) applied to f(theta) = theta theta^T,
+ * minus the recycled mean's outer product; cov_out [D][D]. */
+void oracle_recycle_cov(int K, int D, const oracle_stats* st, double* cov_out);
 
 #ifdef __cplusplus
 }

@@ -45,6 +45,8 @@ def test_k1_weights_are_the_likelihood_and_stats_are_consistent():
     assert 1.0 <= st["ess"] <= 64.0
     wn = np.exp(s.logw - lse)
     np.testing.assert_allclose(st["est"], wn @ s.theta, rtol=1e-12)
+    # Eq. (21) with f = (theta - f~)(theta - f~)^T: numpy's weighted covariance (no Bessel correction)
+    np.testing.assert_allclose(st["cov"], np.cov(s.theta.T, aweights=wn, bias=True), rtol=1e-10, atol=1e-14)
     for d in range(3):
         assert s.theta[:, d].min() <= st["est"][d] <= s.theta[:, d].max()
     for i in range(0, 64, 9):
@@ -111,6 +113,27 @@ def test_recycling_constants():
 # statistical pins against the exact posterior of the linear-Gaussian model
 # ---------------------------------------------------------------------------
 
+def test_recycled_covariance_is_the_recycled_second_moment():
+    """Eq. (29) applied to theta theta^T: with c_k from the ESS of each
+    iteration, the recycled covariance equals the c-weighted mixture of the
+    iterations' weighted populations, which numpy computes from the pooled
+    (theta, c_k w~) pairs."""
+    cfg, y = lg(N=48, M=16)
+    c = O.Config(**{**cfg.__dict__, "ess_frac": 0.0})  # never resample: each state is the weighted population
+    s = O.SMC2(c, y)
+    pooled_th, pooled_w = [], []
+    for _ in range(4):
+        st = s.step()
+        wn = np.exp(s.logw - logsumexp(s.logw))
+        pooled_th.append(s.theta.copy())
+        pooled_w.append(st["ess"] * wn)
+    th = np.concatenate(pooled_th)
+    wt = np.concatenate(pooled_w)
+    mean, _ = s.recycled()
+    np.testing.assert_allclose(mean, wt @ th / wt.sum(), rtol=1e-12)
+    np.testing.assert_allclose(s.recycled_cov(), np.cov(th.T, aweights=wt, bias=True), rtol=1e-10, atol=1e-14)
+
+
 def _quadrature(y, n, lo, hi):
     g = [np.linspace(lo[d], hi[d], n) for d in range(3)]
     P, LX, LY = np.meshgrid(*g, indexing="ij")
@@ -123,6 +146,18 @@ def _quadrature(y, n, lo, hi):
     mean = np.array([(w * X).sum() for X in (P, LX, LY)])
     sd = np.array([math.sqrt((w * (X - m) ** 2).sum()) for X, m in zip((P, LX, LY), mean)])
     return logsumexp(lj) + math.log(cell), mean, sd
+
+
+@pytest.mark.slow
+def test_recycled_posterior_variance_matches_quadrature(exact_posterior):
+    """The recycled covariance's diagonal against the exact posterior variances."""
+    y, _, _, sd = exact_posterior
+    cfg, _ = lg(N=256, M=64, lkernel=O.LK_GAUSS)
+    R = 24
+    var = np.array([np.diag(O.SMC2(O.Config(**{**cfg.__dict__, "seed": 3000 + r}), y).run(10).recycled_cov())
+                    for r in range(R)])
+    se = var.std(axis=0) / math.sqrt(R)
+    assert np.all(np.abs(var.mean(axis=0) - sd ** 2) < 4 * se + 0.05 * sd ** 2), (var.mean(axis=0), sd ** 2, se)
 
 
 @pytest.fixture(scope="module")
