@@ -140,6 +140,9 @@ typedef struct {
   int mlp_used;        /* 1: theta_k came from the learned proposal */
   int pad;
   double mlp_loss;     /* training loss of the surrogate that proposed (learned proposal) */
+  double cov[SMC2_MAX_D * SMC2_MAX_D]; /* weighted covariance of theta_k, entry (d, e) at
+                                           d * SMC2_MAX_D + e (Eq. 21 with f = (theta - est)
+                                           (theta - est)^T, before resampling) */
 } smc2_iter_stats;
 
 /* Create a context: validate cfg, allocate the device workspace, copy the
@@ -199,10 +202,13 @@ smc2_status smc2_run(smc2_ctx* ctx, int n_iter, smc2_iter_stats* stats_host);
 /* Recycled estimate after the iterations run so far (Sec. IV-C, Eq. 29 with
  * the constants of Eqs. 23-24): mean_host[D] = sum_k c_k f~_k; the latest
  * evidence estimate log Z_k; ess_sum = sum_k l_k, the ESS of the recycled
- * estimator.  Any output pointer may be NULL.  Synchronises; returns the
- * sticky device status. */
+ * estimator; cov_host (row-major D x D) = sum_k c_k (C_k + f~_k f~_k^T) -
+ * mean mean^T, the recycled posterior covariance, C_k the weighted
+ * covariance of iteration k.  Any output pointer may be NULL.  Synchronises;
+ * returns the sticky device status.  Errors: EINVAL (bad dataset), ESTATE
+ * (no iteration run yet). */
 smc2_status smc2_estimate(smc2_ctx* ctx, int dataset, double* mean_host,
-                          double* log_evidence_host, double* ess_sum_host);
+                          double* log_evidence_host, double* ess_sum_host, double* cov_host);
 
 /* Copy the statistics of iterations 1..k of a dataset to host (k entries;
  * *k_out receives k).  Synchronises. */

@@ -208,7 +208,7 @@ size_t layout(smc2_ctx* c, char* base) {
     s.lk = carve<LKParams>(p, 1);
     s.cur = carve<IterCur>(p, 1);
     s.hist = carve<smc2_iter_stats>(p, c->K);
-    s.rec = carve<double>(p, 1 + D);
+    s.rec = carve<double>(p, 1 + D + D * D);
     s.est_rec = carve<double>(p, D);
     c->d_obs[d] = carve<char>(p, obs_bytes(c, d));
     s.obs = c->d_obs[d];
@@ -360,7 +360,7 @@ smc2_status clear_run_state(smc2_ctx* c) {
     const DSDev& ds = c->h_ds[d];
     SMC2_TRY(cudaMemsetAsync(ds.tickets, 0, 4 * sizeof(unsigned), s));
     SMC2_TRY(cudaMemsetAsync(ds.hist, 0, (size_t)c->K * sizeof(smc2_iter_stats), s));
-    SMC2_TRY(cudaMemsetAsync(ds.rec, 0, (size_t)(1 + c->D) * sizeof(double), s));
+    SMC2_TRY(cudaMemsetAsync(ds.rec, 0, (size_t)(1 + c->D + c->D * c->D) * sizeof(double), s));
     SMC2_TRY(cudaMemsetAsync(ds.est_rec, 0, (size_t)c->D * sizeof(double), s));
     SMC2_TRY(cudaMemsetAsync(ds.cur, 0, sizeof(IterCur), s));
     SMC2_TRY(cudaMemsetAsync(ds.lk, 0, sizeof(LKParams), s));
@@ -724,19 +724,26 @@ smc2_status smc2_iterate(smc2_ctx* c, smc2_iter_stats* stats_host) {
 }
 
 smc2_status smc2_estimate(smc2_ctx* c, int dataset, double* mean_host, double* logz_host,
-                          double* ess_sum_host) {
+                          double* ess_sum_host, double* cov_host) {
   if (bad_ds(c, dataset)) return SMC2_EINVAL;
   if (c->k_host < 1) return SMC2_ESTATE;
   const DSDev& s = c->h_ds[dataset];
+  const int D = c->D;
   smc2_iter_stats last;
-  double rec0 = 0.0;
-  if (mean_host)
-    SMC2_TRY(cudaMemcpyAsync(mean_host, s.est_rec, c->D * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  std::vector<double> rec((size_t)1 + D + D * D);
   SMC2_TRY(cudaMemcpyAsync(&last, s.hist + (c->k_host - 1), sizeof(last), cudaMemcpyDeviceToHost, c->stream));
-  SMC2_TRY(cudaMemcpyAsync(&rec0, s.rec, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-  smc2_status st = sticky(c);
+  SMC2_TRY(cudaMemcpyAsync(rec.data(), s.rec, rec.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  const smc2_status st = sticky(c);
+  const double l = rec[0];
+  // recycled mean and covariance: the l_k-weighted first and second moments (Eq. 29)
+  for (int d = 0; d < D; ++d) {
+    const double md = rec[1 + d] / l;
+    if (mean_host) mean_host[d] = md;
+    if (cov_host)
+      for (int e = 0; e < D; ++e) cov_host[d * D + e] = rec[1 + D + d * D + e] / l - md * (rec[1 + e] / l);
+  }
   if (logz_host) *logz_host = last.logz;
-  if (ess_sum_host) *ess_sum_host = rec0;
+  if (ess_sum_host) *ess_sum_host = l;
   return st;
 }
 

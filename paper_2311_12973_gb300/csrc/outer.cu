@@ -323,30 +323,28 @@ __global__ void __launch_bounds__(32) lkfit_kernel(OuterParams P) {
 // ---------------------------------------------------------------------------
 // weights + normalisation statistics
 // ---------------------------------------------------------------------------
+// Recycling sums (Eqs. 23-24, 29): rec = [sum l_k, sum l_k f~_k [D],
+// sum l_k (C_k + f~_k f~_k^T) [D][D]], C_k the iteration's weighted covariance.
 __device__ __forceinline__ void accumulate_recycling(double* rec, double* est_rec, double ess,
-                                                     const double* est, int D) {
+                                                     const double* est, const double* cov, int D) {
   rec[0] += ess;
   for (int d = 0; d < D; ++d) rec[1 + d] += ess * est[d];
+  for (int d = 0; d < D; ++d)
+    for (int e = 0; e < D; ++e) rec[1 + D + d * D + e] += ess * (cov[d * kMaxD + e] + est[d] * est[e]);
   for (int d = 0; d < D; ++d) est_rec[d] = rec[1 + d] / rec[0];
 }
 
 __host__ __device__ constexpr int tri(int d, int f) { return d * (d + 1) / 2 + f; }  // f <= d
 
-// Learned proposal: weighted covariance of theta_k (from second moments about
-// the prior mean) and its lower Cholesky factor; usable when every pivot is
-// positive and the population holds ESS >= 2 (D + 1).
+// Learned proposal: the lower Cholesky factor of the weighted covariance of
+// theta_k; usable when every pivot is positive and the population holds
+// ESS >= 2 (D + 1).
 template <int D>
-__device__ void population_cholesky(const OuterParams& P, const smc2_iter_stats& st, const double* sqq,
-                                    double s1, IterCur* cur) {
+__device__ void population_cholesky(const smc2_iter_stats& st, IterCur* cur) {
   double Lm[D][D];
   bool ok = st.ess >= 2.0 * (D + 1);
-  for (int d = 0; d < D; ++d) {
-    const double md = st.est[d] - P.prior_mean[d];
-    for (int f = 0; f <= d; ++f) {
-      const double mf = st.est[f] - P.prior_mean[f];
-      Lm[d][f] = sqq[tri(d, f)] / s1 - md * mf;
-    }
-  }
+  for (int d = 0; d < D; ++d)
+    for (int f = 0; f <= d; ++f) Lm[d][f] = st.cov[d * kMaxD + f];
   for (int j = 0; j < D; ++j) {
     double a = Lm[j][j];
     for (int c = 0; c < j; ++c) a -= Lm[j][c] * Lm[j][c];
@@ -408,10 +406,11 @@ __global__ void __launch_bounds__(kOuterBlock) weights_kernel(OuterParams P) {
       const double sd = warp_sum(act ? e * b[d] : 0.0);
       if (lane == 0) ps[3 + d] = sd;
     }
-    if (P.mlp.on) {  // second moments about the prior mean, for the population covariance
+    {  // second moments about the dataset's first proposal (close to the population, so
+       // the covariance loses little to cancellation)
       double c[D];
 #pragma unroll
-      for (int d = 0; d < D; ++d) c[d] = act ? b[d] - P.prior_mean[d] : 0.0;
+      for (int d = 0; d < D; ++d) c[d] = act ? b[d] - S.thB[(size_t)d * N] : 0.0;
 #pragma unroll
       for (int d = 0; d < D; ++d)
 #pragma unroll
@@ -446,6 +445,7 @@ __global__ void __launch_bounds__(kOuterBlock) weights_kernel(OuterParams P) {
       st.mlp_loss = 0.0;
       st.ess = st.lse = st.lse2 = st.logz = NAN;
       for (int d = 0; d < kMaxD; ++d) st.est[d] = NAN;
+      for (int q = 0; q < kMaxD * kMaxD; ++q) st.cov[q] = NAN;
       cur->resample = 0;
       if ((int)k <= P.K) S.hist[k - 1] = st;
       S.tickets[1] = 0;
@@ -454,7 +454,7 @@ __global__ void __launch_bounds__(kOuterBlock) weights_kernel(OuterParams P) {
   }
   constexpr int NQ = D * (D + 1) / 2;
   static_assert(3 + D + NQ <= kStatStride, "statistics stride");
-  const int nq = P.mlp.on ? NQ : 0;
+  const int nq = NQ;
   double s1 = 0.0, s2 = 0.0, sth[D], sqq[NQ];
 #pragma unroll
   for (int d = 0; d < D; ++d) sth[d] = 0.0;
@@ -491,11 +491,24 @@ __global__ void __launch_bounds__(kOuterBlock) weights_kernel(OuterParams P) {
   cur->lse = st.lse;
   cur->resample = st.resampled;
   cur->m_par = st.resampled ? st.lse - S.logN : m;
-  if (P.mlp.on) population_cholesky<D>(P, st, sqq, s1, cur);
+  // weighted covariance of theta_k (Eq. 21 with f = (theta - f~)(theta - f~)^T)
+  for (int q = 0; q < kMaxD * kMaxD; ++q) st.cov[q] = 0.0;
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    const double md = st.est[d] - S.thB[(size_t)d * N];
+#pragma unroll
+    for (int f = 0; f <= d; ++f) {
+      const double mf = st.est[f] - S.thB[(size_t)f * N];
+      const double v = sqq[tri(d, f)] / s1 - md * mf;
+      st.cov[d * kMaxD + f] = v;
+      st.cov[f * kMaxD + d] = v;
+    }
+  }
+  if (P.mlp.on) population_cholesky<D>(st, cur);
   st.mlp_used = (k > 1 && P.mlp.on) ? cur->mlp_used : 0;
   st.pad = 0;
   st.mlp_loss = (k > 1 && P.mlp.on) ? cur->mlp_loss : 0.0;
-  accumulate_recycling(S.rec, S.est_rec, st.ess, st.est, D);
+  accumulate_recycling(S.rec, S.est_rec, st.ess, st.est, st.cov, D);
   if ((int)k <= P.K) S.hist[k - 1] = st;
   S.tickets[1] = 0;
 }
@@ -656,11 +669,11 @@ __global__ void parent_reference_kernel(OuterParams P, int dataset) {
 // same accumulation as the weights kernel.
 __global__ void rebuild_recycling_kernel(OuterParams P, int dataset, int k) {
   const DSDev& S = P.ds[dataset];
-  for (int a = 0; a <= P.D; ++a) S.rec[a] = 0.0;
+  for (int a = 0; a <= P.D + P.D * P.D; ++a) S.rec[a] = 0.0;
   for (int d = 0; d < P.D; ++d) S.est_rec[d] = 0.0;
   for (int e = 0; e < k; ++e) {
-    const smc2_iter_stats st = S.hist[e];
-    if (isfinite(st.ess)) accumulate_recycling(S.rec, S.est_rec, st.ess, st.est, P.D);
+    const smc2_iter_stats& st = S.hist[e];
+    if (isfinite(st.ess)) accumulate_recycling(S.rec, S.est_rec, st.ess, st.est, st.cov, P.D);
   }
 }
 

@@ -40,13 +40,15 @@ class IterStats(C.Structure):
         ("k", C.c_int), ("resampled", C.c_int), ("lk_fallback", C.c_int), ("dataset", C.c_int),
         ("ess", C.c_double), ("lse", C.c_double), ("lse2", C.c_double), ("logz", C.c_double),
         ("est", C.c_double * MAX_D), ("mlp_used", C.c_int), ("pad", C.c_int), ("mlp_loss", C.c_double),
+        ("cov", C.c_double * (MAX_D * MAX_D)),
     ]
 
     def as_dict(self, D: int) -> dict:
         return {"k": self.k, "resampled": self.resampled, "lk_fallback": self.lk_fallback,
                 "dataset": self.dataset, "ess": self.ess, "lse": self.lse, "lse2": self.lse2,
                 "logz": self.logz, "est": np.array(self.est[:D]), "mlp_used": self.mlp_used,
-                "mlp_loss": self.mlp_loss}
+                "mlp_loss": self.mlp_loss,
+                "cov": np.array(self.cov[:]).reshape(MAX_D, MAX_D)[:D, :D].copy()}
 
 
 class SMC2Error(RuntimeError):
@@ -74,7 +76,7 @@ def _load() -> C.CDLL:
         "smc2_pf_trace": ([ctx, dp, C.c_int, C.c_int, C.c_int, dp, dp, i32p], st),
         "smc2_iterate": ([ctx, C.POINTER(IterStats)], st),
         "smc2_run": ([ctx, C.c_int, C.POINTER(IterStats)], st),
-        "smc2_estimate": ([ctx, C.c_int, dp, dp, dp], st),
+        "smc2_estimate": ([ctx, C.c_int, dp, dp, dp, dp], st),
         "smc2_get_history": ([ctx, C.c_int, C.POINTER(IterStats), C.c_int, C.POINTER(C.c_int)], st),
         "smc2_get_state": ([ctx, C.c_int, C.POINTER(C.c_int), dp, dp, dp, dp], st),
         "smc2_set_state": ([ctx, C.c_int, C.c_int, dp, dp, dp, dp], st),
@@ -203,9 +205,15 @@ class SMC2:
     def estimate(self, dataset: int = 0):
         mean = np.zeros(self.D)
         logz, ess = C.c_double(), C.c_double()
-        _check(lib.smc2_estimate(self._ctx, dataset, mean.ctypes.data, C.byref(logz), C.byref(ess)),
+        _check(lib.smc2_estimate(self._ctx, dataset, mean.ctypes.data, C.byref(logz), C.byref(ess), None),
                "smc2_estimate")
         return mean, logz.value, ess.value
+
+    def estimate_cov(self, dataset: int = 0):
+        """Recycled posterior covariance [D][D] (Eq. 29 applied to theta theta^T)."""
+        cov = np.zeros((self.D, self.D))
+        _check(lib.smc2_estimate(self._ctx, dataset, None, None, None, cov.ctypes.data), "smc2_estimate")
+        return cov
 
     def history(self, dataset: int = 0, cap: int | None = None):
         cap = cap or self.cfg.K

@@ -81,6 +81,8 @@ def _compare_stats(g, o, scale):
         assert rel_err(g[key], o[key], scale) < 1e-12, (key, g[key], o[key])
     assert rel_err(g["ess"], o["ess"]) < 1e-9
     assert rel_err(g["est"], o["est"], 1.0) < 1e-9
+    # covariance: one pass about the first proposal on the device, two passes in the oracle
+    assert rel_err(g["cov"], o["cov"], max(float(np.max(np.abs(o["cov"]))), 1e-300)) < 1e-8, (g["cov"], o["cov"])
 
 
 def test_full_size_iterations_fp64_match_oracle(S):

@@ -32,6 +32,8 @@ def _compare_stats(g, o, scale):
         assert rel_err(g[key], o[key], scale) < 1e-12, (key, g[key], o[key])
     assert rel_err(g["ess"], o["ess"]) < 1e-9, (g["ess"], o["ess"])
     assert rel_err(g["est"], o["est"], 1.0) < 1e-9, (g["est"], o["est"])
+    # covariance: one pass about the first proposal on the device, two passes in the oracle
+    assert rel_err(g["cov"], o["cov"], max(float(np.max(np.abs(o["cov"]))), 1e-300)) < 1e-8, (g["cov"], o["cov"])
 
 
 def _compare_state(S_ctx, ref, scale):
@@ -70,6 +72,8 @@ def test_fp64_run_matches_oracle(S, case):
     mean, logz, ess_sum = ctx.estimate()
     ref_mean, _ = ref.recycled()
     assert rel_err(mean, ref_mean, 1.0) < 1e-9
+    ref_cov = ref.recycled_cov()
+    assert rel_err(ctx.estimate_cov(), ref_cov, max(float(np.max(np.abs(ref_cov))), 1e-300)) < 1e-8
     assert rel_err(logz, ref.stats[-1]["logz"], scale) < 1e-12
     assert rel_err(ess_sum, sum(s["ess"] for s in ref.stats)) < 1e-9
     ctx.close()
