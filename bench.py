@@ -376,6 +376,7 @@ def main():
         return
     peaks = measured_peaks()
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    fma32, fma64 = S.fma_rates()
     pf_avg_ms = pf_ms / max(pf_n, 1)
     ops = ALG_OPS_PER_PARTICLE_STEP[wr.model] * wr.N * wr.M * wr.T
     achieved = ops / (pf_avg_ms * 1e-3)
@@ -398,7 +399,12 @@ def main():
                      "pf_share_of_step": pf_ms / max(sum(ms), 1e-9),
                      "launch_shape": shape,
                      "peak_basis": f"{props.multi_processor_count} SMs x 128 lanes x {sm_mhz:.0f} MHz "
-                                   "(max SM clock of MEASURED_PEAKS.json)"},
+                                   "(max SM clock of MEASURED_PEAKS.json)",
+                     "measured_fma_tflops": {"fp32": fma32 / 1e12, "fp64": fma64 / 1e12}},
+        # the whole step against the time its particle filter work needs at the issue peak
+        "ess_roofline": {"bound": "alu", "t_roof_ms": 1e3 * units_per_step * ALG_OPS_PER_PARTICLE_STEP[wr.model] / peak,
+                         "ms_per_step": step_ms,
+                         "frac": 1e3 * units_per_step * ALG_OPS_PER_PARTICLE_STEP[wr.model] / peak / step_ms},
         "e2e": {"value": units_per_step * world / (e2e_step * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": 8 * wr.T, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_step},
         "gpu_launches": launches,

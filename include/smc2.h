@@ -285,6 +285,14 @@ smc2_status smc2_pf_loglik_noalloc(const smc2_config* cfg, const double* y_dev,
                                    const double* theta_dev, int n, int iteration,
                                    double* loglik_dev, void* stream);
 
+/* Diagnostic (the paper has no counterpart): the device's FP32 and FP64
+ * fused multiply-add throughput in FLOP/s (host outputs, either may be NULL),
+ * from kernels of independent FMA chains that fill every SM, timed with CUDA
+ * events on `stream`.  These are the arithmetic rates the roofline of the
+ * particle filter (FP32) and of the outer FP64 kernels is stated against.
+ * Synchronises `stream`; allocates nothing.  Errors: ECUDA. */
+smc2_status smc2_fma_rates(double* fp32_flops, double* fp64_flops, void* stream);
+
 /* Surrogate network of the learned proposal (not in the paper; it proposes
  * theta_k in place of the random walk of Sec. IV-A, and the L-kernel weights
  * of Eq. (20) keep the estimator exact): s(x) = w3.h2 + b3, h2 = tanh(W2^T h1

@@ -135,3 +135,65 @@ extern "C" smc2_status smc2_pf_loglik_noalloc(const smc2_config* cfg, const doub
   if (e != cudaSuccess) return fail(SMC2_ECUDA, cudaGetErrorString(e));
   return SMC2_OK;
 }
+
+// ---------------------------------------------------------------------------
+// FMA throughput (diagnostic)
+// ---------------------------------------------------------------------------
+namespace smc2 {
+namespace {
+
+__device__ double g_fma_sink;  // keeps the chains live
+
+constexpr int kFmaChains = 8;
+
+template <typename R>
+__global__ void __launch_bounds__(256) fma_rate_kernel(int iters, R b, R c) {
+  R a[kFmaChains];
+#pragma unroll
+  for (int q = 0; q < kFmaChains; ++q) a[q] = (R)(threadIdx.x + q) * (R)1e-3;
+  for (int it = 0; it < iters; ++it)
+#pragma unroll
+    for (int q = 0; q < kFmaChains; ++q) a[q] = fma(a[q], b, c);
+  R s = 0;
+#pragma unroll
+  for (int q = 0; q < kFmaChains; ++q) s += a[q];
+  if (s == (R)-12345.0) g_fma_sink = (double)s;  // never true for these inputs
+}
+
+template <typename R>
+smc2_status fma_rate(int iters, double* flops, cudaStream_t s) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return SMC2_ECUDA;
+  const int grid = sms * 8, block = 256;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return SMC2_ECUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return SMC2_ECUDA;
+  }
+  float ms = 0.f;
+  fma_rate_kernel<R><<<grid, block, 0, s>>>(iters / 8, (R)0.9999, (R)1e-7);  // warm-up
+  cudaEventRecord(e0, s);
+  fma_rate_kernel<R><<<grid, block, 0, s>>>(iters, (R)0.9999, (R)1e-7);
+  cudaEventRecord(e1, s);
+  const bool ok = cudaGetLastError() == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+                  cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms > 0.f;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (!ok) return SMC2_ECUDA;
+  *flops = 2.0 * kFmaChains * (double)iters * grid * block / (ms * 1e-3);
+  return SMC2_OK;
+}
+
+}  // namespace
+}  // namespace smc2
+
+extern "C" smc2_status smc2_fma_rates(double* fp32_flops, double* fp64_flops, void* stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  smc2_status st = SMC2_OK;
+  if (fp32_flops) st = fma_rate<float>(1 << 16, fp32_flops, s);
+  if (st == SMC2_OK && fp64_flops) st = fma_rate<double>(1 << 11, fp64_flops, s);
+  return st;
+}

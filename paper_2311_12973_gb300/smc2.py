@@ -93,6 +93,7 @@ def _load() -> C.CDLL:
         "smc2_mlp_input_grad": ([C.c_int, dp, dp, C.c_int, dp, dp, vp], st),
         "smc2_mlp_adam_step": ([C.c_int, dp, dp, dp, dp, dp, dp, C.c_int, C.c_float, dp, vp], st),
         "smc2_get_proposals": ([ctx, C.c_int, dp, dp], st),
+        "smc2_fma_rates": ([dp, dp, vp], st),
         "smc2_get_learned_state": ([ctx, dp, dp, dp, C.POINTER(C.c_int)], st),
         "smc2_destroy": ([ctx], None),
         "smc2_status_string": ([st], C.c_char_p),
@@ -359,6 +360,13 @@ def mlp_adam_step(params, m, v, step, x, y, lr: float, stream=None):
     _check(lib.smc2_mlp_adam_step(D, _ptr(params), _ptr(m), _ptr(v), _ptr(step), _ptr(x), _ptr(y), R,
                                   float(lr), _ptr(loss), _stream_handle(stream)), "smc2_mlp_adam_step")
     return loss
+
+
+def fma_rates(stream=None):
+    """Measured FP32 and FP64 FMA throughput of the device, FLOP/s."""
+    f32, f64 = C.c_double(), C.c_double()
+    _check(lib.smc2_fma_rates(C.byref(f32), C.byref(f64), _stream_handle(stream)), "smc2_fma_rates")
+    return f32.value, f64.value
 
 
 def resample_systematic(q, U: int, anc, stream=None):
