@@ -394,31 +394,32 @@ __global__ void __launch_bounds__(kOuterBlock) weights_kernel(OuterParams P) {
   const double mb = warp_max(lw);
   const double e = (act && lw > -HUGE_VAL) ? exp(lw - mb) : 0.0;
   double* ps = S.part_st + (size_t)blockIdx.x * kStatStride;
+  constexpr int NV = 2 + D + D * (D + 1) / 2;  // sums of e, e^2, e theta_d, e c_d c_f
+  __shared__ double terms[NV][kOuterBlock + 1];
+  __shared__ double totals[NV];
   {
-    const double s1 = warp_sum(e), s2 = warp_sum(e * e);
-    if (lane == 0) {
-      ps[0] = mb;
-      ps[1] = s1;
-      ps[2] = s2;
+    // the block's sums of e, e^2, e theta_d and e c_d c_f (second moments about the
+    // dataset's first proposal, close to the population, so the covariance loses
+    // little to cancellation): every lane writes its terms to a padded row, then
+    // lane q adds column q over the lanes in order
+    double c[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) c[d] = act ? b[d] - S.thB[(size_t)d * N] : 0.0;
+    terms[0][lane] = e;
+    terms[1][lane] = e * e;
+#pragma unroll
+    for (int d = 0; d < D; ++d) terms[2 + d][lane] = act ? e * b[d] : 0.0;
+#pragma unroll
+    for (int d = 0; d < D; ++d)
+#pragma unroll
+      for (int f = 0; f <= d; ++f) terms[2 + D + tri(d, f)][lane] = e * c[d] * c[f];
+    __syncwarp();
+    if (lane < NV) {
+      double sum = 0.0;
+      for (int l = 0; l < kOuterBlock; ++l) sum += terms[lane][l];
+      ps[1 + lane] = sum;
     }
-#pragma unroll
-    for (int d = 0; d < D; ++d) {
-      const double sd = warp_sum(act ? e * b[d] : 0.0);
-      if (lane == 0) ps[3 + d] = sd;
-    }
-    {  // second moments about the dataset's first proposal (close to the population, so
-       // the covariance loses little to cancellation)
-      double c[D];
-#pragma unroll
-      for (int d = 0; d < D; ++d) c[d] = act ? b[d] - S.thB[(size_t)d * N] : 0.0;
-#pragma unroll
-      for (int d = 0; d < D; ++d)
-#pragma unroll
-        for (int f = 0; f <= d; ++f) {
-          const double sq = warp_sum(e * c[d] * c[f]);
-          if (lane == 0) ps[3 + D + tri(d, f)] = sq;
-        }
-    }
+    if (lane == 0) ps[0] = mb;
   }
   __threadfence();
   __syncwarp();
@@ -454,38 +455,42 @@ __global__ void __launch_bounds__(kOuterBlock) weights_kernel(OuterParams P) {
   }
   constexpr int NQ = D * (D + 1) / 2;
   static_assert(3 + D + NQ <= kStatStride, "statistics stride");
-  const int nq = NQ;
-  double s1 = 0.0, s2 = 0.0, sth[D], sqq[NQ];
+  // every lane rescales its blocks' sums to the common maximum; then lane q adds
+  // statistic q over the lanes in order (a transpose through shared memory)
+  double v[NV];
 #pragma unroll
-  for (int d = 0; d < D; ++d) sth[d] = 0.0;
-#pragma unroll
-  for (int q = 0; q < NQ; ++q) sqq[q] = 0.0;
+  for (int q = 0; q < NV; ++q) v[q] = 0.0;
   for (int bb = lane; bb < S.nblk; bb += 32) {
     const double* pb = S.part_st + (size_t)bb * kStatStride;
     const double mbb = __ldcg(pb);
     if (!(mbb > -HUGE_VAL)) continue;
     const double f = exp(mbb - m);
-    s1 += __ldcg(pb + 1) * f;
-    s2 += __ldcg(pb + 2) * (f * f);
+    v[1] += __ldcg(pb + 2) * (f * f);
 #pragma unroll
-    for (int d = 0; d < D; ++d) sth[d] += __ldcg(pb + 3 + d) * f;
-#pragma unroll
-    for (int q = 0; q < NQ; ++q)
-      if (q < nq) sqq[q] += __ldcg(pb + 3 + D + q) * f;
+    for (int q = 0; q < NV; ++q)
+      if (q != 1) v[q] += __ldcg(pb + 1 + q) * f;
   }
-  s1 = warp_sum(s1);
-  s2 = warp_sum(s2);
 #pragma unroll
-  for (int d = 0; d < D; ++d) sth[d] = warp_sum(sth[d]);
+  for (int q = 0; q < NV; ++q) terms[q][lane] = v[q];
+  __syncwarp();
+  if (lane < NV) {
+    double sum = 0.0;
+    for (int l = 0; l < kOuterBlock; ++l) sum += terms[lane][l];
+    totals[lane] = sum;
+  }
+  __syncwarp();
+  const double s1 = totals[0], s2 = totals[1], inv_s1 = 1.0 / s1;
+  double sth[D], sqq[NQ];
 #pragma unroll
-  for (int q = 0; q < NQ; ++q)
-    if (q < nq) sqq[q] = warp_sum(sqq[q]);
+  for (int d = 0; d < D; ++d) sth[d] = totals[2 + d];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) sqq[q] = totals[2 + D + q];
   if (lane != 0) return;
   st.lse = m + log(s1);
   st.lse2 = 2.0 * m + log(s2);
   st.ess = (s1 * s1) / s2;
   st.logz = st.lse - S.logN;
-  for (int d = 0; d < kMaxD; ++d) st.est[d] = d < D ? sth[d] / s1 : 0.0;
+  for (int d = 0; d < kMaxD; ++d) st.est[d] = d < D ? sth[d] * inv_s1 : 0.0;
   st.resampled = st.ess < P.ess_frac * (double)N;
   cur->m = m;
   cur->lse = st.lse;
@@ -499,7 +504,7 @@ __global__ void __launch_bounds__(kOuterBlock) weights_kernel(OuterParams P) {
 #pragma unroll
     for (int f = 0; f <= d; ++f) {
       const double mf = st.est[f] - S.thB[(size_t)f * N];
-      const double v = sqq[tri(d, f)] / s1 - md * mf;
+      const double v = sqq[tri(d, f)] * inv_s1 - md * mf;
       st.cov[d * kMaxD + f] = v;
       st.cov[f * kMaxD + d] = v;
     }
