@@ -30,6 +30,8 @@ LK_FORWARD, LK_GAUSS = 0, 1
 MAX_D = 8
 TAG_THETA_INIT, TAG_PROPOSE, TAG_OUTER_RES = 1, 2, 3
 TAG_PF_INIT, TAG_PF_PROP, TAG_PF_RES = 4, 5, 6
+TAG_PF_MULTI = 8
+PF_SYSTEMATIC, PF_MULTINOMIAL = 0, 1
 
 
 def build(force: bool = False) -> str:
@@ -55,6 +57,7 @@ class OracleCfg(C.Structure):
         ("prior_mean", C.c_double * MAX_D), ("prior_sd", C.c_double * MAX_D),
         ("npop", C.c_double), ("e0", C.c_double), ("i0", C.c_double),
         ("lambda_floor", C.c_double), ("n_sub", C.c_int),
+        ("pf_scheme", C.c_int), ("pf_ess_frac", C.c_double),
     ]
 
 
@@ -112,6 +115,11 @@ def _declare(L):
                                    C.POINTER(OracleStats)]
     L.oracle_smc2_step.restype = C.c_int
     L.oracle_recycle.argtypes = [C.c_int, C.c_int, C.POINTER(OracleStats), dp, dp]
+    L.oracle_multinomial_from_q.argtypes = [C.POINTER(C.c_uint64), C.c_int, C.POINTER(C.c_uint32),
+                                            C.POINTER(C.c_int32)]
+    L.oracle_multinomial_from_q.restype = C.c_int
+    L.oracle_ess_from_q.argtypes = [C.POINTER(C.c_uint64), C.c_int]
+    L.oracle_ess_from_q.restype = C.c_double
     L.oracle_recycle_cov.argtypes = [C.c_int, C.c_int, C.POINTER(OracleStats), dp]
     L.oracle_bf16.argtypes = [C.c_double]
     L.oracle_bf16.restype = C.c_double
@@ -150,6 +158,8 @@ class Config:
     i0: float = 0.0
     lambda_floor: float = 1e-3
     n_sub: int = 2
+    pf_scheme: int = 0          # 0 systematic, 1 multinomial
+    pf_ess_frac: float = 0.0    # <= 0: resample every step; else when ESS < pf_ess_frac * M
 
     def ctype(self) -> OracleCfg:
         c = OracleCfg()
@@ -161,6 +171,7 @@ class Config:
             c.prior_sd[d] = self.prior_sd[d]
         c.npop, c.e0, c.i0 = self.npop, self.e0, self.i0
         c.lambda_floor, c.n_sub = self.lambda_floor, self.n_sub
+        c.pf_scheme, c.pf_ess_frac = self.pf_scheme, self.pf_ess_frac
         return c
 
 
@@ -208,6 +219,22 @@ def quantise(logw):
     q = np.zeros(len(logw), dtype=np.uint64)
     B = lib().oracle_quantise(_p(logw, C.c_double), len(logw), _p(q, C.c_uint64))
     return q, B
+
+
+def multinomial_from_q(q, U):
+    """Multinomial slots on integer weights: a_j = min{i : C_i > floor((2 U_j + 1) S / 2^33)}."""
+    qq = np.ascontiguousarray(q, dtype=np.uint64)
+    UU = np.ascontiguousarray(U, dtype=np.uint32)
+    anc = np.zeros(len(qq), dtype=np.int32)
+    rc = lib().oracle_multinomial_from_q(_p(qq, C.c_uint64), len(qq), _p(UU, C.c_uint32), _p(anc, C.c_int32))
+    if rc != 0:
+        raise ValueError("all weights zero")
+    return anc
+
+
+def ess_from_q(q) -> float:
+    qq = np.ascontiguousarray(q, dtype=np.uint64)
+    return lib().oracle_ess_from_q(_p(qq, C.c_uint64), len(qq))
 
 
 def systematic_from_q(q, U):

@@ -243,6 +243,45 @@ double oracle_log_obs(const oracle_cfg* c, const double* theta, const double* x,
  * (with q = f the factor is g(y_t | x_t)).  Resampling is systematic after
  * every step t < T.  delta_out (T entries) receives
  * log p^(y_{1:t}) - log p^(y_{1:t-1}); anc_out ((T-1) x M) the ancestors. */
+int oracle_multinomial_from_q(const uint64_t* q, int n, const uint32_t* U, int32_t* anc) {
+  uint64_t* C = (uint64_t*)malloc(sizeof(uint64_t) * n);
+  uint64_t S = 0;
+  for (int i = 0; i < n; ++i) {
+    S += q[i];
+    C[i] = S;
+  }
+  if (S == 0) {
+    free(C);
+    return -1;
+  }
+  for (int j = 0; j < n; ++j) {
+    const unsigned __int128 num = (unsigned __int128)(2ull * U[j] + 1ull) * S;
+    const uint64_t tau = (uint64_t)(num >> 33); /* floor(u_j S), u_j < 1 so tau < S */
+    int lo = 0, hi = n - 1;                     /* smallest i with C_i > tau */
+    while (lo < hi) {
+      const int mid = (lo + hi) / 2;
+      if (C[mid] > tau)
+        hi = mid;
+      else
+        lo = mid + 1;
+    }
+    anc[j] = lo;
+  }
+  free(C);
+  return 0;
+}
+
+double oracle_ess_from_q(const uint64_t* q, int n) {
+  uint64_t S = 0;
+  unsigned __int128 Q2 = 0;
+  for (int i = 0; i < n; ++i) {
+    S += q[i];
+    Q2 += (unsigned __int128)q[i] * q[i];
+  }
+  const double q2 = (double)(uint64_t)(Q2 >> 64) * 0x1p64 + (double)(uint64_t)Q2;
+  return (double)S * (double)S / q2;
+}
+
 double oracle_pf_loglik(const oracle_cfg* c, const double* theta, const double* y, uint32_t k,
                         uint32_t i, double* delta_out, int32_t* anc_out) {
   const int M = c->M, T = c->T, SD = 5;
@@ -257,8 +296,9 @@ double oracle_pf_loglik(const oracle_cfg* c, const double* theta, const double* 
     oracle_initial_state(c, theta, k, c2, j, x + SD * j);
     lw[j] = 0.0;
   }
-  double L = 0.0; /* log of the common weight: w_0 = 1 */
-  double loglik = 0.0;
+  double L = 0.0;    /* log of the common weight: w_0 = 1 */
+  double loglik = 0.0; /* log p^(y_{1:t}) */
+  uint32_t* Um = (uint32_t*)malloc(sizeof(uint32_t) * M);
   for (int t = 1; t <= T; ++t) {
     for (int j = 0; j < M; ++j) {
       double z[4];
@@ -282,22 +322,34 @@ double oracle_pf_loglik(const oracle_cfg* c, const double* theta, const double* 
     for (int j = 0; j < M; ++j) sum += exp(lw[j] - m);
     /* Eq. (8): log of (1/M) sum_j exp(L + lw_j). */
     double logp = L + m + log(sum) - log((double)M);
-    if (delta_out) delta_out[t - 1] = logp - L;
+    if (delta_out) delta_out[t - 1] = logp - loglik;
     loglik = logp;
     if (t < T) {
-      uint32_t U = oracle_word0(c->seed, 0, (uint32_t)t, c2, ORACLE_TAG_PF_RES | (k << 4));
       oracle_quantise(lw, M, q);
-      oracle_systematic_from_q(q, M, U, ncop, anc);
-      for (int j = 0; j < M; ++j) memcpy(xn + SD * j, x + SD * anc[j], sizeof(double) * SD);
-      double* tmp = x; x = xn; xn = tmp;
+      /* the schedule: every step, or when the ESS (Eq. 12) is below pf_ess_frac M */
+      const int resample = !(c->pf_ess_frac > 0.0) || oracle_ess_from_q(q, M) < c->pf_ess_frac * (double)M;
+      if (resample) {
+        if (c->pf_scheme == ORACLE_PF_MULTINOMIAL) {
+          for (int j = 0; j < M; ++j)
+            Um[j] = oracle_word0(c->seed, (uint32_t)j, (uint32_t)t, c2, ORACLE_TAG_PF_MULTI | (k << 4));
+          oracle_multinomial_from_q(q, M, Um, anc);
+        } else {
+          uint32_t U = oracle_word0(c->seed, 0, (uint32_t)t, c2, ORACLE_TAG_PF_RES | (k << 4));
+          oracle_systematic_from_q(q, M, U, ncop, anc);
+        }
+        for (int j = 0; j < M; ++j) memcpy(xn + SD * j, x + SD * anc[j], sizeof(double) * SD);
+        double* tmp = x; x = xn; xn = tmp;
+        /* Eq. (13): every particle now carries the mean weight. */
+        L = logp;
+        for (int j = 0; j < M; ++j) lw[j] = 0.0;
+      } else {
+        for (int j = 0; j < M; ++j) anc[j] = j; /* no resampling: each particle keeps its weight */
+      }
       if (anc_out) memcpy(anc_out + (size_t)(t - 1) * M, anc, sizeof(int32_t) * M);
-      /* Eq. (13): every particle now carries the mean weight. */
-      L = logp;
-      for (int j = 0; j < M; ++j) lw[j] = 0.0;
     }
   }
 done:
-  free(x); free(xn); free(lw); free(q); free(ncop); free(anc);
+  free(x); free(xn); free(lw); free(q); free(ncop); free(anc); free(Um);
   return loglik;
 }
 

@@ -45,8 +45,10 @@ enum { ORACLE_LG = 0, ORACLE_SEIR = 1 };
 enum { ORACLE_LK_FORWARD = 0, ORACLE_LK_GAUSS = 1 };
 enum {
   ORACLE_TAG_THETA_INIT = 1, ORACLE_TAG_PROPOSE = 2, ORACLE_TAG_OUTER_RES = 3,
-  ORACLE_TAG_PF_INIT = 4, ORACLE_TAG_PF_PROP = 5, ORACLE_TAG_PF_RES = 6
+  ORACLE_TAG_PF_INIT = 4, ORACLE_TAG_PF_PROP = 5, ORACLE_TAG_PF_RES = 6,
+  ORACLE_TAG_PF_MULTI = 8
 };
+enum { ORACLE_PF_SYSTEMATIC = 0, ORACLE_PF_MULTINOMIAL = 1 };
 #define ORACLE_MAX_D 8
 
 typedef struct {
@@ -61,6 +63,11 @@ typedef struct {
   /* SEIR constants: population, E0, I0, Euler substeps per day, incidence floor */
   double npop, e0, i0, lambda_floor;
   int n_sub;
+  /* PF resampling (Sec. II): scheme, and the schedule -- every step t < T when
+   * pf_ess_frac <= 0, otherwise when the ESS of the PF weights (Eq. 12) is
+   * below pf_ess_frac * M (the paper's choice is multinomial below M/2). */
+  int pf_scheme;
+  double pf_ess_frac;
 } oracle_cfg;
 
 typedef struct {
@@ -79,6 +86,15 @@ double oracle_kalman_loglik(double phi, double sx, double sy, const double* y, i
 int oracle_fixed_point_bits(int n);
 int oracle_quantise(const double* logw, int n, uint64_t* q);
 int oracle_systematic_from_q(const uint64_t* q, int n, uint32_t U, int32_t* ncopies, int32_t* anc);
+/* Multinomial resampling on the same integer weights: slot j draws its own
+ * u_j = (2 U_j + 1) / 2^33 and takes a_j = min{i : C_i > floor(u_j S)},
+ * C the inclusive prefix of q.  Returns 0, or -1 when S = 0. */
+int oracle_multinomial_from_q(const uint64_t* q, int n, const uint32_t* U, int32_t* anc);
+/* ESS of the integer weights, S^2 / sum q^2 (Eq. 12), formed as
+ * (double)S * (double)S / ((double)hi * 2^64 + (double)lo) from the exact
+ * 128-bit sum of squares hi:lo: every operation correctly rounded, so any
+ * machine forms the same value. */
+double oracle_ess_from_q(const uint64_t* q, int n);
 
 double oracle_log_obs(const oracle_cfg* c, const double* theta, const double* x, double y);
 double oracle_pf_loglik(const oracle_cfg* c, const double* theta, const double* y, uint32_t k,

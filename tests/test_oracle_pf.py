@@ -79,3 +79,84 @@ def test_zero_likelihood_filter():
     cfg, y = lg_cfg(M=8, T=5)
     ll = O.pf_loglik(cfg, np.array([0.5, 0.0, np.nan]), y, k=1, i=0)
     assert ll == -np.inf
+
+
+# ---------------------------------------------------------------------------
+# the paper's own PF resampling: multinomial, when the ESS (Eq. 12) drops below M/2
+# ---------------------------------------------------------------------------
+
+def test_multinomial_slots_follow_their_definition():
+    """Slot j takes the first i with C_i > floor((2 U_j + 1) S / 2^33): checked in
+    Python integers, including zero weights and a dominant weight."""
+    rng = np.random.default_rng(11)
+    for n in (1, 7, 64, 300):
+        q = rng.integers(0, 2 ** 40, size=n, dtype=np.uint64)
+        q[rng.random(n) < 0.3] = 0
+        q[0] = max(int(q[0]), 1)
+        U = rng.integers(0, 2 ** 32, size=n, dtype=np.uint64).astype(np.uint32)
+        anc = O.multinomial_from_q(q, U)
+        S = sum(int(v) for v in q)
+        C = np.cumsum([int(v) for v in q], dtype=object)
+        for j in range(n):
+            tau = ((2 * int(U[j]) + 1) * S) >> 33
+            assert anc[j] == next(i for i in range(n) if C[i] > tau)
+            assert q[anc[j]] > 0                      # a zero weight is never drawn
+
+
+def test_multinomial_draws_in_proportion_to_the_weights():
+    rng = np.random.default_rng(12)
+    q = np.array([1, 0, 5, 2, 8, 0, 3, 1], dtype=np.uint64) << np.uint64(40)
+    draws = 20000
+    U = rng.integers(0, 2 ** 32, size=draws, dtype=np.uint64).astype(np.uint32)
+    counts = np.zeros(len(q))
+    for c0 in range(0, draws, len(q)):
+        a = O.multinomial_from_q(q, U[c0:c0 + len(q)])
+        np.add.at(counts, a, 1)
+    p = q.astype(float) / q.astype(float).sum()
+    se = np.sqrt(draws * p * (1 - p))
+    assert np.all(np.abs(counts - draws * p) < 4 * se + 1e-9)
+
+
+def test_ess_of_integer_weights():
+    from fractions import Fraction
+    rng = np.random.default_rng(13)
+    for n in (1, 5, 512):
+        q = rng.integers(1, 2 ** 52, size=n, dtype=np.uint64)
+        S = sum(int(v) for v in q)
+        exact = Fraction(S * S, sum(int(v) ** 2 for v in q))
+        assert O.ess_from_q(q) == pytest.approx(float(exact), rel=4e-16)
+    assert O.ess_from_q(np.full(64, 2 ** 45, dtype=np.uint64)) == 64.0   # equal weights
+    one = np.zeros(64, dtype=np.uint64)
+    one[5] = 2 ** 52
+    assert O.ess_from_q(one) == 1.0                                      # one survivor
+
+
+@pytest.mark.parametrize("scheme,frac", [(O.PF_SYSTEMATIC, 0.5), (O.PF_MULTINOMIAL, 0.5), (O.PF_MULTINOMIAL, 0.0)])
+def test_adaptive_and_multinomial_pf_unbiased_for_kalman_likelihood(scheme, frac):
+    cfg, y = lg_cfg(M=64, T=20)
+    cfg = O.Config(**{**cfg.__dict__, "pf_scheme": scheme, "pf_ess_frac": frac})
+    theta = np.array([0.8, math.log(0.5), math.log(1.0)])
+    kf = O.kalman_loglik(0.8, 0.5, 1.0, y)
+    R = 400
+    r = np.array([math.exp(O.pf_loglik(cfg, theta, y, k=1 + s // 64, i=s % 64) - kf) for s in range(R)])
+    assert abs(r.mean() - 1.0) < 4 * r.std() / math.sqrt(R)
+
+
+def test_adaptive_schedule_keeps_weights_between_resampling_events():
+    """With the ESS trigger a step either resamples (ancestors of systematic
+    resampling, non-decreasing) or keeps every particle (identity), and the
+    increments still add up to the estimate.  With uninformative observations
+    (a huge sigma_y) the weights stay flat and no step resamples."""
+    cfg, y = lg_cfg(M=32, T=15)
+    cfg = O.Config(**{**cfg.__dict__, "pf_ess_frac": 0.5})
+    theta = np.array([0.5, -0.5, -0.5])
+    ll, delta, anc = O.pf_loglik(cfg, theta, y, k=1, i=3, trace=True)
+    assert ll == pytest.approx(delta.sum(), rel=1e-13)
+    ident = np.arange(32)
+    kept = [np.array_equal(a, ident) for a in anc]
+    assert any(kept) and not all(kept)
+    for a in anc:
+        assert np.all(np.diff(a) >= 0)
+    flat = np.array([0.5, -0.5, 8.0])
+    _, _, anc_flat = O.pf_loglik(cfg, flat, y, k=1, i=3, trace=True)
+    assert all(np.array_equal(a, ident) for a in anc_flat)
