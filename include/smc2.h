@@ -59,6 +59,7 @@ enum { SMC2_MODEL_LG_AR1 = 0, SMC2_MODEL_SEIR = 1 };
 enum { SMC2_PREC_FP64 = 0, SMC2_PREC_MIXED = 1 };   /* MIXED: FP32 particles, FP64 outer */
 enum { SMC2_PROP_RW = 0, SMC2_PROP_MLP = 1 };
 enum { SMC2_LK_FORWARD = 0, SMC2_LK_GAUSS_OPT = 1 };
+enum { SMC2_PF_SYSTEMATIC = 0, SMC2_PF_MULTINOMIAL = 1 };
 
 #define SMC2_MAX_D 8
 #define SMC2_MAX_M 4096     /* particles per filter (see M in smc2_config) */
@@ -99,6 +100,13 @@ typedef struct smc2_ctx smc2_ctx; /* opaque; owns its device workspace */
  *   is the exact Gaussian density, so Eq. (20) with the Gaussian L-kernel
  *   keeps the weights valid.  Requires lkernel = SMC2_LK_GAUSS_OPT and one
  *   dataset.
+ * pf_scheme, pf_ess_frac: particle-filter resampling (Sec. II).  The default
+ *   (0, 0) resamples systematically after every step t < T.  pf_scheme =
+ *   SMC2_PF_MULTINOMIAL draws every slot on its own; pf_ess_frac in (0, 1]
+ *   resamples only when the ESS of the filter's weights (Eq. 12) is below
+ *   pf_ess_frac * M, carrying the weights in between (Eq. 5) and resetting them
+ *   to their mean on resampling (Eq. 13) -- the paper's filter is multinomial
+ *   with pf_ess_frac = 1/2.  Either option needs ppt <= 4 (M <= 2048).
  * mlp_h, mlp_lr, mlp_steps, mlp_window: step h of the learned proposal, Adam
  *   learning rate, Adam steps per iteration, iterations of training pairs
  *   kept (0 selects 1.0, 5e-3, 16, 4; steps <= 256, window <= 16).
@@ -124,6 +132,9 @@ typedef struct {
   const int* ds_T;
   double mlp_h, mlp_lr;
   int mlp_steps, mlp_window;
+  double pf_ess_frac;
+  int pf_scheme;
+  int pf_reserved;  /* set to 0 */
 } smc2_config;
 
 /* Statistics of one iteration k of one dataset (Sec. IV-A, IV-B):

@@ -236,13 +236,9 @@ double oracle_log_obs(const oracle_cfg* c, const double* theta, const double* x,
 /* Bootstrap particle filter: Sec. II                                   */
 /* ------------------------------------------------------------------ */
 
-/* Returns log p^(y_{1:T} | theta), Eq. (8), for filter i of iteration k.
- * The unnormalised weight of particle j is carried as exp(L + lw_j): L is
- * the log of the common weight given to every particle at the last reset
- * (Eq. 13), lw_j the log of the product of the Eq. (5) factors since then
- * (with q = f the factor is g(y_t | x_t)).  Resampling is systematic after
- * every step t < T.  delta_out (T entries) receives
- * log p^(y_{1:t}) - log p^(y_{1:t-1}); anc_out ((T-1) x M) the ancestors. */
+/* Multinomial resampling on integer weights q (Sec. II): slot j takes the
+ * first index i whose cumulative weight C_i exceeds floor(u_j S), with
+ * u_j = (2 U_j + 1) / 2^33 from its own word U_j.  Returns -1 when S = 0. */
 int oracle_multinomial_from_q(const uint64_t* q, int n, const uint32_t* U, int32_t* anc) {
   uint64_t* C = (uint64_t*)malloc(sizeof(uint64_t) * n);
   uint64_t S = 0;
@@ -282,6 +278,16 @@ double oracle_ess_from_q(const uint64_t* q, int n) {
   return (double)S * (double)S / q2;
 }
 
+/* Returns log p^(y_{1:T} | theta), Eq. (8), for filter i of iteration k.
+ * The unnormalised weight of particle j is carried as exp(L + lw_j): L is
+ * the log of the common weight given to every particle at the last reset
+ * (Eq. 13), lw_j the log of the product of the Eq. (5) factors since then
+ * (with q = f the factor is g(y_t | x_t)).  After step t < T the filter
+ * resamples -- systematically, or multinomially with pf_scheme = 1 -- at
+ * every step, or with pf_ess_frac > 0 only when the ESS of Eq. (12) is
+ * below pf_ess_frac M.  delta_out (T entries) receives
+ * log p^(y_{1:t}) - log p^(y_{1:t-1}); anc_out ((T-1) x M) the ancestors
+ * (the identity on steps that keep every particle). */
 double oracle_pf_loglik(const oracle_cfg* c, const double* theta, const double* y, uint32_t k,
                         uint32_t i, double* delta_out, int32_t* anc_out) {
   const int M = c->M, T = c->T, SD = 5;

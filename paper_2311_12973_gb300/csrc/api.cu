@@ -67,6 +67,7 @@ struct smc2_ctx {
   unsigned* d_grid_ticket = nullptr;
   int ppt = 4, pf_block = 256, pf_grid = 1;
   bool pf_named = false;
+  bool pf_general = false;  // the paper's PF variants: multinomial slots, ESS-triggered resampling
   size_t pf_smem = 0;
   int k_host = 0;
   std::map<GraphKey, TimedGraph> graphs;
@@ -134,6 +135,11 @@ smc2_status validate(const smc2_config* c) {
   }
   if (c->ppt != 0 && c->ppt != 1 && c->ppt != 2 && c->ppt != 4 && c->ppt != 8 && c->ppt != 16)
     return SMC2_EINVAL;
+  if ((c->pf_scheme != SMC2_PF_SYSTEMATIC && c->pf_scheme != SMC2_PF_MULTINOMIAL) ||
+      !(c->pf_ess_frac >= 0.0 && c->pf_ess_frac <= 1.0) || c->pf_reserved != 0)
+    return SMC2_EINVAL;
+  const bool general = c->pf_scheme != SMC2_PF_SYSTEMATIC || c->pf_ess_frac > 0.0;
+  if (general && c->ppt > 4) return SMC2_EINVAL;  // the variants run in the register-resident shapes
   if (c->cta_threads != 0 && (c->cta_threads < 32 || c->cta_threads > kPfMaxBlock || c->cta_threads % 32))
     return SMC2_EINVAL;
   const int nd = c->n_datasets <= 1 ? 1 : c->n_datasets;
@@ -151,9 +157,9 @@ smc2_status validate(const smc2_config* c) {
     const int model = c->model == SMC2_MODEL_LG_AR1 ? MODEL_LG : MODEL_SEIR;
     bool fits = false;
     for (int ppt : {1, 2, 4, 8, 16}) {
-      if (c->ppt && ppt != c->ppt) continue;
+      if ((c->ppt && ppt != c->ppt) || (general && ppt > 4)) continue;
       const int g = pf_group_threads(ppt, m);
-      if (g <= kPfMaxBlock && pf_smem_bytes(c->precision, model, ppt, g, m) <= 227 * 1024) fits = true;
+      if (g <= kPfMaxBlock && pf_smem_bytes(c->precision, model, ppt, general, g, m) <= 227 * 1024) fits = true;
     }
     if (!fits) return SMC2_EINVAL;
   }
@@ -278,14 +284,14 @@ smc2_status apply_shape(smc2_ctx* c, int ppt, int block, bool named, bool upload
   c->pf_block = block;
   c->pf_named = named;
   size_t smem = 0;
-  for (int m : c->M) smem = std::max(smem, pf_smem_bytes(c->precision, c->model, ppt, block, m));
+  for (int m : c->M) smem = std::max(smem, pf_smem_bytes(c->precision, c->model, ppt, c->pf_general, block, m));
   if (smem > 227 * 1024) return SMC2_EINVAL;
   c->pf_smem = smem;
-  SMC2_TRY(pf_configure(c->precision, c->model, ppt, named, smem));
+  SMC2_TRY(pf_configure(c->precision, c->model, ppt, named, c->pf_general, smem));
   std::vector<int4> wus;
   build_work_units(c, wus);
   c->n_wus = (int)wus.size();
-  const int occ = pf_occupancy(c->precision, c->model, ppt, named, block, smem);
+  const int occ = pf_occupancy(c->precision, c->model, ppt, named, c->pf_general, block, smem);
   if (occ < 1) return SMC2_EINVAL;
   c->pf_grid = std::min(c->n_wus, occ * c->sms);
   c->pl.n_wu = c->n_wus;
@@ -305,6 +311,7 @@ smc2_status choose_launch_shape(smc2_ctx* c) {
   std::vector<Shape> cand;
   for (int ppt : {1, 2, 4, 8, 16}) {
     if (c->cfg.ppt && ppt != c->cfg.ppt) continue;
+    if (c->pf_general && ppt > 4) continue;  // the variants run in the register-resident shapes
     for (int block = 32; block <= kPfMaxBlock; block += 32) {
       if (c->cfg.cta_threads && block != c->cfg.cta_threads) continue;
       if (!c->cfg.cta_threads && (block & (block - 1))) continue;  // powers of two when tuning
@@ -333,7 +340,7 @@ smc2_status choose_launch_shape(smc2_ctx* c) {
       L.t_cap = rep == 0 ? 4 : 32;
       ok = cudaMemsetAsync(c->d_wu_counter, 0, sizeof(int), s) == cudaSuccess &&
            cudaEventRecord(e0, s) == cudaSuccess &&
-           pf_launch(c->precision, c->model, c->ppt, c->pf_named, c->pf_grid, c->pf_block, c->pf_smem,
+           pf_launch(c->precision, c->model, c->ppt, c->pf_named, c->pf_general, c->pf_grid, c->pf_block, c->pf_smem,
                      L, s) == cudaSuccess &&
            cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
            cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
@@ -424,6 +431,8 @@ void fill_params(smc2_ctx* c) {
   L.mdl.i0 = c->cfg.i0;
   L.mdl.lambda_floor = c->cfg.lambda_floor;
   L.mdl.n_sub = c->cfg.n_sub;
+  L.mdl.pf_scheme = c->cfg.pf_scheme;
+  L.mdl.pf_ess_frac = c->cfg.pf_ess_frac;
 }
 
 // One iteration of every dataset, enqueued on s; the L-kernel fit runs on the
@@ -449,7 +458,7 @@ smc2_status enqueue_iteration(smc2_ctx* c, cudaStream_t s, cudaEvent_t ev0, cuda
   SMC2_TRY(cudaEventRecord(c->ev_join, c->side_stream));
   SMC2_TRY(cudaMemsetAsync(c->d_wu_counter, 0, sizeof(int), s));
   if (ev0) SMC2_TRY(cudaEventRecordWithFlags(ev0, s, cudaEventRecordExternal));
-  SMC2_TRY(pf_launch(c->precision, c->model, c->ppt, c->pf_named, c->pf_grid, c->pf_block, c->pf_smem,
+  SMC2_TRY(pf_launch(c->precision, c->model, c->ppt, c->pf_named, c->pf_general, c->pf_grid, c->pf_block, c->pf_smem,
                      c->pl, s));
   if (ev1) SMC2_TRY(cudaEventRecordWithFlags(ev1, s, cudaEventRecordExternal));
   SMC2_TRY(cudaStreamWaitEvent(s, c->ev_join, 0));
@@ -553,6 +562,7 @@ smc2_status smc2_init(const smc2_config* cfg, const double* y, void* stream, smc
   smc2_ctx* c = new (std::nothrow) smc2_ctx();
   if (!c) return SMC2_ENOMEM;
   c->cfg = *cfg;
+  c->pf_general = cfg->pf_scheme != SMC2_PF_SYSTEMATIC || cfg->pf_ess_frac > 0.0;
   if (c->cfg.mlp_h == 0.0) c->cfg.mlp_h = kMlpStep;
   if (c->cfg.mlp_lr == 0.0) c->cfg.mlp_lr = kMlpLr;
   if (c->cfg.mlp_steps == 0) c->cfg.mlp_steps = kMlpSteps;
@@ -672,9 +682,9 @@ static smc2_status pf_standalone(smc2_ctx* c, const double* theta, int n, int it
   L.k_done = nullptr;
   L.k_imm = iteration;
   const int occ =
-      std::max(1, pf_occupancy(c->precision, c->model, c->ppt, c->pf_named, c->pf_block, c->pf_smem));
+      std::max(1, pf_occupancy(c->precision, c->model, c->ppt, c->pf_named, c->pf_general, c->pf_block, c->pf_smem));
   const int grid = std::min(L.n_wu, occ * c->sms);
-  SMC2_TRY(pf_launch(c->precision, c->model, c->ppt, c->pf_named, grid, c->pf_block, c->pf_smem, L,
+  SMC2_TRY(pf_launch(c->precision, c->model, c->ppt, c->pf_named, c->pf_general, grid, c->pf_block, c->pf_smem, L,
                      c->stream));
   c->kernel_launches++;
   return SMC2_OK;

@@ -19,6 +19,7 @@ enum : uint32_t {
   TAG_PF_PROP = 5,     // c0 = particle, c1 = (t-1) >> 2; normal (t-1) & 3
   TAG_PF_RES = 6,      // c0 = 0, c1 = t; word 0
   TAG_MLP_INIT = 7,    // c0 = parameter index; word 0 (surrogate network initial weights)
+  TAG_PF_MULTI = 8,    // c0 = slot, c1 = t; word 0 (multinomial PF resampling)
 };
 
 // Device status bits (sticky; mapped to smc2_status codes on the host).

@@ -125,7 +125,8 @@ struct PFJob {
 struct PFModel {
   double npop, e0, i0, lambda_floor;
   int n_sub;
-  int pad;
+  int pf_scheme;       // PF resampling: 0 systematic, 1 multinomial
+  double pf_ess_frac;  // <= 0: every step; else when the ESS is below pf_ess_frac * M
 };
 
 struct PFLaunch {
@@ -145,12 +146,12 @@ struct PFLaunch {
 };
 
 // Launch-shape helpers (pf.cu).
-size_t pf_smem_bytes(int precision, int model, int ppt, int block, int M);
+size_t pf_smem_bytes(int precision, int model, int ppt, bool general, int block, int M);
 int pf_group_threads(int ppt, int M);
-cudaError_t pf_launch(int precision, int model, int ppt, bool named, int grid, int block, size_t smem,
-                      const PFLaunch& L, cudaStream_t s);
-cudaError_t pf_configure(int precision, int model, int ppt, bool named, size_t smem);
-int pf_occupancy(int precision, int model, int ppt, bool named, int block, size_t smem);
+cudaError_t pf_launch(int precision, int model, int ppt, bool named, bool general, int grid, int block,
+                      size_t smem, const PFLaunch& L, cudaStream_t s);
+cudaError_t pf_configure(int precision, int model, int ppt, bool named, bool general, size_t smem);
+int pf_occupancy(int precision, int model, int ppt, bool named, bool general, int block, size_t smem);
 
 // Outer kernels (outer.cu).
 cudaError_t outer_obs_terms(int precision, int model, const double* y, int T, void* obs,

@@ -77,6 +77,11 @@ extern "C" smc2_status smc2_pf_loglik_noalloc(const smc2_config* cfg, const doub
     return fail(SMC2_EINVAL, "invalid SEIR constants");
   const int ppt = cfg->ppt ? cfg->ppt : 2;
   if (ppt != 1 && ppt != 2 && ppt != 4 && ppt != 8 && ppt != 16) return fail(SMC2_EINVAL, "ppt");
+  if ((cfg->pf_scheme != SMC2_PF_SYSTEMATIC && cfg->pf_scheme != SMC2_PF_MULTINOMIAL) ||
+      !(cfg->pf_ess_frac >= 0.0 && cfg->pf_ess_frac <= 1.0))
+    return fail(SMC2_EINVAL, "pf_scheme / pf_ess_frac");
+  const bool general = cfg->pf_scheme != SMC2_PF_SYSTEMATIC || cfg->pf_ess_frac > 0.0;
+  if (general && ppt > 4) return fail(SMC2_EINVAL, "the PF variants need ppt <= 4");
   const int gt = pf_group_threads(ppt, cfg->M);
   if (gt > kPfMaxBlock) return fail(SMC2_EINVAL, "M too large for this ppt");
 
@@ -90,11 +95,11 @@ extern "C" smc2_status smc2_pf_loglik_noalloc(const smc2_config* cfg, const doub
 
   // one filter group per CTA (or several one-warp groups): no named barriers
   const int block = gt > 32 ? gt : 256;
-  const size_t smem = pf_smem_bytes(cfg->precision, model, ppt, block, cfg->M);
+  const size_t smem = pf_smem_bytes(cfg->precision, model, ppt, general, block, cfg->M);
   if (smem > 227 * 1024) return fail(SMC2_EINVAL, "shared memory of the launch shape");
-  cudaError_t e = pf_configure(cfg->precision, model, ppt, false, smem);
+  cudaError_t e = pf_configure(cfg->precision, model, ppt, false, general, smem);
   if (e != cudaSuccess) return fail(SMC2_ECUDA, cudaGetErrorString(e));
-  const int occ = pf_occupancy(cfg->precision, model, ppt, false, block, smem);
+  const int occ = pf_occupancy(cfg->precision, model, ppt, false, general, block, smem);
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || occ < 1)
@@ -129,9 +134,11 @@ extern "C" smc2_status smc2_pf_loglik_noalloc(const smc2_config* cfg, const doub
   L.mdl.i0 = cfg->i0;
   L.mdl.lambda_floor = cfg->lambda_floor;
   L.mdl.n_sub = cfg->n_sub;
+  L.mdl.pf_scheme = cfg->pf_scheme;
+  L.mdl.pf_ess_frac = cfg->pf_ess_frac;
   L.t_cap = 0;
   const int grid = L.n_wu < occ * sms ? L.n_wu : occ * sms;
-  e = pf_launch(cfg->precision, model, ppt, false, grid, block, smem, L, s);
+  e = pf_launch(cfg->precision, model, ppt, false, general, grid, block, smem, L, s);
   if (e != cudaSuccess) return fail(SMC2_ECUDA, cudaGetErrorString(e));
   return SMC2_OK;
 }

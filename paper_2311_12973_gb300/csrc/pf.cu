@@ -9,35 +9,38 @@ namespace smc2 {
 
 int pf_group_threads(int ppt, int M) { return group_threads_for(ppt, M); }
 
-size_t pf_smem_bytes(int precision, int model, int ppt, int block, int M) {
+size_t pf_smem_bytes(int precision, int model, int ppt, bool general, int block, int M) {
   const int gt = group_threads_for(ppt, M);
   const int fpc = block / gt;
   const int ns = model == MODEL_LG ? 1 : 4;
   const int rs = precision == SMC2_PREC_FP64 ? 8 : 4;
-  return (size_t)fpc * region_bytes(gt * ppt, gt >> 5, ns, rs, is_staged(ppt));
+  return (size_t)fpc * region_bytes(gt * ppt, gt >> 5, ns, rs, is_staged(ppt), general);
 }
 
-static const void* select_kernel(int precision, int model, int ppt, bool named) {
+static const void* select_kernel(int precision, int model, int ppt, bool named, bool general) {
+  if (general)
+    return precision == SMC2_PREC_FP64 ? pf_select_general_f64(model, ppt, named)
+                                       : pf_select_general_f32(model, ppt, named);
   return precision == SMC2_PREC_FP64 ? pf_select_f64(model, ppt, named)
                                      : pf_select_f32(model, ppt, named);
 }
 
-cudaError_t pf_configure(int precision, int model, int ppt, bool named, size_t smem) {
-  const void* f = select_kernel(precision, model, ppt, named);
+cudaError_t pf_configure(int precision, int model, int ppt, bool named, bool general, size_t smem) {
+  const void* f = select_kernel(precision, model, ppt, named, general);
   if (!f) return cudaErrorInvalidValue;
   return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-int pf_occupancy(int precision, int model, int ppt, bool named, int block, size_t smem) {
-  const void* f = select_kernel(precision, model, ppt, named);
+int pf_occupancy(int precision, int model, int ppt, bool named, bool general, int block, size_t smem) {
+  const void* f = select_kernel(precision, model, ppt, named, general);
   int n = 0;
   if (!f || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, block, smem) != cudaSuccess) return 0;
   return n;
 }
 
-cudaError_t pf_launch(int precision, int model, int ppt, bool named, int grid, int block, size_t smem,
-                      const PFLaunch& L, cudaStream_t s) {
-  const void* f = select_kernel(precision, model, ppt, named);
+cudaError_t pf_launch(int precision, int model, int ppt, bool named, bool general, int grid, int block,
+                      size_t smem, const PFLaunch& L, cudaStream_t s) {
+  const void* f = select_kernel(precision, model, ppt, named, general);
   if (!f) return cudaErrorInvalidValue;
   void* args[] = {const_cast<PFLaunch*>(&L)};
   return cudaLaunchKernel(f, dim3(grid), dim3(block), args, smem, s);

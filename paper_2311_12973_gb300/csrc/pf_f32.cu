@@ -3,6 +3,6 @@
 
 namespace smc2 {
 const void* pf_select_f32(int model, int ppt, bool named) {
-  return pf_select_precision<float>(model, ppt, named);
+  return pf_select_precision<float, false>(model, ppt, named);
 }
 }  // namespace smc2

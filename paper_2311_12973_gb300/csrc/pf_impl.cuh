@@ -66,16 +66,21 @@ __host__ __device__ inline int group_threads_for(int ppt, int M) {
 }
 
 // Shared memory of one filter group (Mp = particles incl. padding, nw warps):
-//   P  u64 [Mp]      warp-local inclusive prefix of the quantised weights (staged only)
+//   P  u64 [Mp]      inclusive prefix of the quantised weights (staged: warp-local; variants:
+//                    global, for multinomial slots; absent otherwise)
 //   X  R   [Mp][ns]  particle states, one vector per particle (per slot after resampling)
 //   Xo R   [Mp][ns]  states before resampling, by particle (register-resident variants)
 //   Z  R   [4][Mp]   the four normals of the current Philox counter of every particle
 //   L  R   [Mp]      log-weights (staged path only)
-//   wsum u64 [nw], wmax 8 B [nw], sU u32 [8] (resampling words of two groups of four steps)
+//   wsum u64 [nw], wmax 8 B [nw], wq2 u128 [nw] (variants: sums of q^2 for the ESS),
+//   sU u32 [8] (resampling words of two groups of four steps)
 __host__ __device__ constexpr bool is_staged(int ppt) { return ppt >= 8; }
-__host__ __device__ inline size_t region_bytes(int Mp, int nw, int ns, int rsize, bool staged) {
+__host__ __device__ inline size_t region_bytes(int Mp, int nw, int ns, int rsize, bool staged,
+                                               bool general) {
   size_t b = (size_t)(staged ? 1 : 2) * ns * Mp * rsize + (size_t)4 * Mp * rsize + (size_t)nw * 16 + 32;
-  if (staged) b += (size_t)Mp * 8 + (size_t)Mp * rsize;
+  if (staged || general) b += (size_t)Mp * 8;
+  if (general) b += (size_t)nw * 16;
+  if (staged) b += (size_t)Mp * rsize;
   return (b + 15) & ~(size_t)15;
 }
 
@@ -280,7 +285,7 @@ struct FilterParams<R, MODEL_SEIR> {
 // barriers 1..15 (ptxas then reserves all 16 barriers of the CTA, which limits
 // residency to four CTAs per SM).  Otherwise a wide group is the whole CTA and
 // uses __syncthreads, and a one-warp group uses __syncwarp.
-template <typename R, int MODEL, int PPT, bool NAMED>
+template <typename R, int MODEL, int PPT, bool NAMED, bool GENERAL>
 __device__ __forceinline__ void run_filter(const PFJob& J, const PFModel& mdl, int i, int g, int lt,
                                            int gt, unsigned char* region, uint2 key, uint32_t k,
                                            int t_cap) {
@@ -294,13 +299,15 @@ __device__ __forceinline__ void run_filter(const PFJob& J, const PFModel& mdl, i
   const int seg = 32 * PPT;  // particles per warp
 
   constexpr bool STAGED = is_staged(PPT);
-  uint64_t* P = reinterpret_cast<uint64_t*>(region);   // [Mp] warp-local inclusive prefix of q (staged)
-  R* X = reinterpret_cast<R*>(P + (STAGED ? Mp : 0));  // [Mp][NS] particle states
+  constexpr bool GEN = GENERAL && !STAGED;
+  uint64_t* P = reinterpret_cast<uint64_t*>(region);   // [Mp] inclusive prefix of q (staged, variants)
+  R* X = reinterpret_cast<R*>(P + (STAGED || GEN ? Mp : 0));  // [Mp][NS] particle states
   R* Xo = X + (size_t)NS * Mp;                          // [Mp][NS] states by particle (not staged)
   R* Z = X + (size_t)NS * Mp * (STAGED ? 1 : 2);       // [4][Mp] cached normals
   uint64_t* wsum = reinterpret_cast<uint64_t*>(Z + (size_t)4 * Mp);  // [nw] warp totals
   R* wmax = reinterpret_cast<R*>(wsum + nw);            // [nw] warp maxima (8-byte slots)
-  uint32_t* sU = reinterpret_cast<uint32_t*>(wsum + 2 * nw);  // [8] resampling words
+  unsigned __int128* wq2 = reinterpret_cast<unsigned __int128*>(wsum + 2 * nw);  // [nw] sums of q^2 (variants)
+  uint32_t* sU = reinterpret_cast<uint32_t*>(wsum + (GEN ? 4 : 2) * nw);  // [8] resampling words
   R* Lw = reinterpret_cast<R*>(reinterpret_cast<unsigned char*>(sU) + 32);  // [Mp] staged log-weights
 
   auto group_sync = [&]() {
@@ -321,6 +328,7 @@ __device__ __forceinline__ void run_filter(const PFJob& J, const PFModel& mdl, i
   const uint32_t c2 = counter_c2((uint32_t)i, J.c2hi);
   const uint32_t c3prop = counter_c3(TAG_PF_PROP, k);
   const uint32_t c3res = counter_c3(TAG_PF_RES, k);
+  const uint32_t c3multi = counter_c3(TAG_PF_MULTI, k);
   const int B = fixed_point_bits(M);
   const int log2M = ((M & (M - 1)) == 0) ? (__ffs(M) - 1) : -1;
   const R scaleB = (R)ldexp(1.0, B);
@@ -339,7 +347,18 @@ __device__ __forceinline__ void run_filter(const PFJob& J, const PFModel& mdl, i
     fp.init(x[r], z0, th);
   }
 
-  double loglik = 0.0;
+  // Weights (Eq. 5): exp(Lc + lwc_j), Lc the common log weight set by the last
+  // resampling (Eq. 13), lwc_j the particle's log factor since (register-resident
+  // variants; with resampling every step lwc stays zero).
+  // (GENERAL instantiations only: the ESS schedule and multinomial slots; the default
+  // instantiations resample systematically every step and keep no factors)
+  const bool adaptive = GEN && mdl.pf_ess_frac > 0.0;
+  const bool multinomial = GEN && mdl.pf_scheme == 1;
+  R lwc[GEN ? PPT : 1];
+#pragma unroll
+  for (int r = 0; r < (GEN ? PPT : 1); ++r) lwc[r] = (R)0;
+  double Lc = 0.0;
+  double loglik = 0.0;  // log p^(y_{1:t}) (Eq. 8)
   for (int t = 1; t <= T; ++t) {
     const int tm = (t - 1) & 3;
     if (tm == 0) {  // one Philox call per particle every four steps; normals kept in shared memory
@@ -373,6 +392,7 @@ __device__ __forceinline__ void run_filter(const PFJob& J, const PFModel& mdl, i
       if constexpr (STAGED) {
         Lw[lt * PPT + r] = l;
       } else {
+        if constexpr (GEN) l = lwc[GEN ? r : 0] + l;  // Eq. (5) in logs: the factor since the last resampling
         ell[r] = l;
         StateVec<R, NS>::store(Xo, lt * PPT + r, x[r]);
       }
@@ -422,6 +442,25 @@ __device__ __forceinline__ void run_filter(const PFJob& J, const PFModel& mdl, i
       for (int r = 0; r < PPT; ++r) P[lt * PPT + r] += excl;
     }
     if (lane == 31) wsum[warp] = incl;
+    if (adaptive) {  // the warp's sum of q^2, exact in 128 bits
+      unsigned __int128 q2 = 0;
+      if constexpr (!STAGED) {
+        uint64_t prev = 0;
+#pragma unroll
+        for (int r = 0; r < PPT; ++r) {
+          const uint64_t qv = c[r] - prev;
+          prev = c[r];
+          q2 += (unsigned __int128)qv * qv;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const uint64_t lo = __shfl_xor_sync(0xffffffffu, (uint64_t)q2, o);
+        const uint64_t hi = __shfl_xor_sync(0xffffffffu, (uint64_t)(q2 >> 64), o);
+        q2 += ((unsigned __int128)hi << 64) | lo;
+      }
+      if (lane == 0) wq2[warp] = q2;
+    }
     group_sync();
     // total S, and the weight `base` of the warps before this one: an inclusive
     // scan of the warp totals across the lanes
@@ -434,12 +473,75 @@ __device__ __forceinline__ void run_filter(const PFJob& J, const PFModel& mdl, i
     const uint64_t base_incl = __shfl_sync(0xffffffffu, wpre, warp > 0 ? warp - 1 : 0);
     const uint64_t base = warp > 0 ? base_incl : 0ull;
     // (5) log-likelihood increment: log S from its binary exponent and mantissa
+    // log p^(y_{1:t}) = Lc + log((1/M) sum_j exp(lwc_j + l_j)) from the exact integer total
+    // (thread 0 of the group carries Lc and the estimate)
     if (lt == 0) {
       const int e = 63 - __clzll((long long)S);
       const R mant = (R)(e >= 52 ? (S >> (e - 52)) : (S << (52 - e))) * (R)0x1p-52;
-      const double delta = (double)m + ((double)e * kLn2 + (double)log(mant)) + log_norm;
-      loglik += delta;
+      const double lmean = (double)m + ((double)e * kLn2 + (double)log(mant)) + log_norm;
+      double delta = lmean;
+      if constexpr (GEN) {
+        const double logp_prev = loglik;
+        loglik = Lc + lmean;
+        delta = loglik - logp_prev;
+      } else {
+        loglik += lmean;
+      }
       if (J.delta) J.delta[(size_t)i * T + (t - 1)] = delta;
+    }
+    // the schedule: every step, or when the ESS of the integer weights (Eq. 12) is below
+    // pf_ess_frac M, formed with the same correctly rounded operations as the oracle (by
+    // lane 0 of every warp, from the same totals, so the whole group decides alike)
+    bool resample = t < T;
+    if (adaptive && resample) {
+      int below = 0;
+      if (lane == 0) {
+        unsigned __int128 Q2 = 0;
+        for (int w = 0; w < nw; ++w) Q2 += wq2[w];
+        const double q2 = (double)(uint64_t)(Q2 >> 64) * 0x1p64 + (double)(uint64_t)Q2;
+        const double ess = __ddiv_rn((double)S * (double)S, q2);
+        below = ess < mdl.pf_ess_frac * (double)M;
+      }
+      resample = __shfl_sync(0xffffffffu, below, 0) != 0;
+    }
+    if constexpr (GEN) {
+      if (resample) Lc = loglik;  // Eq. (13): every particle will carry the mean weight (thread 0)
+      if (t < T && !resample) {  // every particle keeps its state and its factor
+#pragma unroll
+        for (int r = 0; r < (GEN ? PPT : 1); ++r) {
+          lwc[r] = ell[STAGED ? 0 : r];
+          const int j = lt * PPT + r;
+          if (J.anc && j < M) J.anc[((size_t)i * (T - 1) + (t - 1)) * M + j] = j;
+        }
+        continue;
+      }
+#pragma unroll
+      for (int r = 0; r < (GEN ? PPT : 1); ++r) lwc[r] = (R)0;
+    }
+    if (GEN && resample && multinomial) {
+      // slot j draws u_j = (2 U_j + 1) / 2^33 and takes the first particle with C_i > floor(u_j S)
+#pragma unroll
+      for (int r = 0; r < PPT; ++r) P[lt * PPT + r] = base + excl + c[r];
+      group_sync();
+#pragma unroll
+      for (int r = 0; r < PPT; ++r) {
+        const int j = lt * PPT + r;
+        if (j >= M) continue;
+        const uint32_t Uj = philox4x32_10(make_uint4((uint32_t)j, (uint32_t)t, c2, c3multi), key).x;
+        const uint64_t tau = (uint64_t)(((unsigned __int128)(2ull * Uj + 1ull) * S) >> 33);
+        int lo = 0, hi = M - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (P[mid] > tau)
+            hi = mid;
+          else
+            lo = mid + 1;
+        }
+        StateVec<R, NS>::load(Xo, lo, x[r]);
+        if (J.anc) J.anc[((size_t)i * (T - 1) + (t - 1)) * M + j] = lo;
+      }
+      group_sync();  // P and Xo free for the next step
+      continue;
     }
     // (6) systematic resampling and ancestor gather.  The thread's slots are
     // consecutive and their ancestors non-decreasing: the first is found by a
@@ -534,7 +636,7 @@ __device__ __forceinline__ void run_filter(const PFJob& J, const PFModel& mdl, i
   if (lt == 0) J.loglik[i] = loglik;
 }
 
-template <typename R, int MODEL, int PPT, bool NAMED>
+template <typename R, int MODEL, int PPT, bool NAMED, bool GENERAL>
 __global__ void __maxnreg__((RegCap<R, PPT>::value)) pf_kernel(PFLaunch L) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_wu;
@@ -566,39 +668,47 @@ __global__ void __maxnreg__((RegCap<R, PPT>::value)) pf_kernel(PFLaunch L) {
     const PFJob J = L.jobs ? L.jobs[job] : L.job0;
     const int gt = group_threads_for(PPT, J.M);
     const int g = threadIdx.x / gt, lt = threadIdx.x - g * gt;
-    const size_t rb = region_bytes(gt * PPT, gt >> 5, NS, (int)sizeof(R), is_staged(PPT));
+    const size_t rb = region_bytes(gt * PPT, gt >> 5, NS, (int)sizeof(R), is_staged(PPT), GENERAL);
     if (g < count && (g + 1) * gt <= (int)blockDim.x)
-      run_filter<R, MODEL, PPT, NAMED>(J, L.mdl, first + g, g, lt, gt, smem + g * rb, key, k, L.t_cap);
+      run_filter<R, MODEL, PPT, NAMED, GENERAL>(J, L.mdl, first + g, g, lt, gt, smem + g * rb, key, k,
+                                                L.t_cap);
     if (!L.wu_counter) __syncthreads();
   }
 }
 
 
-template <typename R, int MODEL, int PPT, bool NAMED>
+template <typename R, int MODEL, int PPT, bool NAMED, bool GENERAL>
 const void* pf_kernel_ptr() {
-  return reinterpret_cast<const void*>(&pf_kernel<R, MODEL, PPT, NAMED>);
+  return reinterpret_cast<const void*>(&pf_kernel<R, MODEL, PPT, NAMED, GENERAL>);
 }
 
-template <typename R, int MODEL, bool NAMED>
+// The GENERAL instantiations exist for the register-resident shapes only.
+template <typename R, int MODEL, bool NAMED, bool GENERAL>
 const void* pf_select_ppt(int ppt) {
   switch (ppt) {
-    case 1: return pf_kernel_ptr<R, MODEL, 1, NAMED>();
-    case 2: return pf_kernel_ptr<R, MODEL, 2, NAMED>();
-    case 4: return pf_kernel_ptr<R, MODEL, 4, NAMED>();
-    case 8: return pf_kernel_ptr<R, MODEL, 8, NAMED>();
-    case 16: return pf_kernel_ptr<R, MODEL, 16, NAMED>();
+    case 1: return pf_kernel_ptr<R, MODEL, 1, NAMED, GENERAL>();
+    case 2: return pf_kernel_ptr<R, MODEL, 2, NAMED, GENERAL>();
+    case 4: return pf_kernel_ptr<R, MODEL, 4, NAMED, GENERAL>();
+    case 8:
+      if constexpr (GENERAL) return nullptr;  // the variants run in the register-resident shapes only
+      else return pf_kernel_ptr<R, MODEL, 8, NAMED, false>();
+    case 16:
+      if constexpr (GENERAL) return nullptr;
+      else return pf_kernel_ptr<R, MODEL, 16, NAMED, false>();
     default: return nullptr;
   }
 }
 
-template <typename R>
+template <typename R, bool GENERAL>
 const void* pf_select_precision(int model, int ppt, bool named) {
   if (model == MODEL_LG)
-    return named ? pf_select_ppt<R, MODEL_LG, true>(ppt) : pf_select_ppt<R, MODEL_LG, false>(ppt);
-  return named ? pf_select_ppt<R, MODEL_SEIR, true>(ppt) : pf_select_ppt<R, MODEL_SEIR, false>(ppt);
+    return named ? pf_select_ppt<R, MODEL_LG, true, GENERAL>(ppt) : pf_select_ppt<R, MODEL_LG, false, GENERAL>(ppt);
+  return named ? pf_select_ppt<R, MODEL_SEIR, true, GENERAL>(ppt) : pf_select_ppt<R, MODEL_SEIR, false, GENERAL>(ppt);
 }
 
 const void* pf_select_f32(int model, int ppt, bool named);
 const void* pf_select_f64(int model, int ppt, bool named);
+const void* pf_select_general_f32(int model, int ppt, bool named);
+const void* pf_select_general_f64(int model, int ppt, bool named);
 
 }  // namespace smc2

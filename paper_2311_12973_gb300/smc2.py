@@ -19,6 +19,7 @@ OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ECHOL, ETIMEOUT, EBOUNDS, ESTATE = range(
 MODEL_LG_AR1, MODEL_SEIR = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
 PROP_RW, PROP_MLP = 0, 1
+PF_SYSTEMATIC, PF_MULTINOMIAL = 0, 1
 LK_FORWARD, LK_GAUSS_OPT = 0, 1
 
 
@@ -32,6 +33,7 @@ class Config(C.Structure):
         ("n_sub", C.c_int), ("ppt", C.c_int), ("cta_threads", C.c_int), ("n_datasets", C.c_int),
         ("ds_N", C.POINTER(C.c_int)), ("ds_M", C.POINTER(C.c_int)), ("ds_T", C.POINTER(C.c_int)),
         ("mlp_h", C.c_double), ("mlp_lr", C.c_double), ("mlp_steps", C.c_int), ("mlp_window", C.c_int),
+        ("pf_ess_frac", C.c_double), ("pf_scheme", C.c_int), ("pf_reserved", C.c_int),
     ]
 
 
@@ -151,6 +153,7 @@ def make_config(w, **over) -> Config:
     c.n_datasets = 0
     c.mlp_h, c.mlp_lr = get("mlp_h", 0.0), get("mlp_lr", 0.0)
     c.mlp_steps, c.mlp_window = get("mlp_steps", 0), get("mlp_window", 0)
+    c.pf_ess_frac, c.pf_scheme = get("pf_ess_frac", 0.0), get("pf_scheme", PF_SYSTEMATIC)
     return c
 
 

@@ -56,6 +56,10 @@ def _cfg(S, **over):
     # learned proposal: needs the Gaussian L-kernel; bounded training settings
     {"proposal": 1, "lkernel": 0}, {"proposal": 1, "mlp_steps": 257}, {"proposal": 1, "mlp_window": 17},
     {"proposal": 1, "mlp_h": -1.0}, {"mlp_lr": 1.5}, {"mlp_h": float("nan")}, {"mlp_steps": -1},
+    # particle-filter variants: known scheme, ESS fraction in [0, 1], register-resident shapes only
+    {"pf_scheme": 2}, {"pf_scheme": -1}, {"pf_ess_frac": 1.5}, {"pf_ess_frac": -0.1},
+    {"pf_ess_frac": float("nan")}, {"pf_reserved": 1}, {"pf_scheme": 1, "ppt": 8},
+    {"pf_ess_frac": 0.5, "ppt": 16}, {"pf_scheme": 1, "M": 4096},
 ])
 def test_invalid_configs_rejected_before_gpu_work(S, over):
     import numpy as np
