@@ -25,12 +25,13 @@ _SRC = os.path.join(_HERE, "smc2_oracle.c")
 _LIB_DIR = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_LIB_DIR, "liboracle.so")
 
-LG, SEIR = 0, 1
+LG, SEIR, SIR = 0, 1, 2
+PRIOR_GAUSS, PRIOR_UNIFORM = 0, 1
 LK_FORWARD, LK_GAUSS = 0, 1
 MAX_D = 8
 TAG_THETA_INIT, TAG_PROPOSE, TAG_OUTER_RES = 1, 2, 3
 TAG_PF_INIT, TAG_PF_PROP, TAG_PF_RES = 4, 5, 6
-TAG_PF_MULTI = 8
+TAG_PF_MULTI, TAG_PF_BINOM = 8, 9
 PF_SYSTEMATIC, PF_MULTINOMIAL = 0, 1
 
 
@@ -58,6 +59,7 @@ class OracleCfg(C.Structure):
         ("npop", C.c_double), ("e0", C.c_double), ("i0", C.c_double),
         ("lambda_floor", C.c_double), ("n_sub", C.c_int),
         ("pf_scheme", C.c_int), ("pf_ess_frac", C.c_double),
+        ("prior_kind", C.c_int), ("prior_lo", C.c_double * MAX_D), ("prior_hi", C.c_double * MAX_D),
     ]
 
 
@@ -121,6 +123,8 @@ def _declare(L):
     L.oracle_ess_from_q.argtypes = [C.POINTER(C.c_uint64), C.c_int]
     L.oracle_ess_from_q.restype = C.c_double
     L.oracle_recycle_cov.argtypes = [C.c_int, C.c_int, C.POINTER(OracleStats), dp]
+    L.oracle_binomial.argtypes = [C.c_double, C.c_double, C.c_uint64] + [C.c_uint32] * 4 + [ip]
+    L.oracle_binomial.restype = C.c_double
     L.oracle_bf16.argtypes = [C.c_double]
     L.oracle_bf16.restype = C.c_double
     L.oracle_mlp_nparams.argtypes = [C.c_int, C.c_int]
@@ -160,6 +164,9 @@ class Config:
     n_sub: int = 2
     pf_scheme: int = 0          # 0 systematic, 1 multinomial
     pf_ess_frac: float = 0.0    # <= 0: resample every step; else when ESS < pf_ess_frac * M
+    prior_kind: int = PRIOR_GAUSS
+    prior_lo: list = field(default_factory=list)   # uniform prior support (PRIOR_UNIFORM)
+    prior_hi: list = field(default_factory=list)
 
     def ctype(self) -> OracleCfg:
         c = OracleCfg()
@@ -172,6 +179,11 @@ class Config:
         c.npop, c.e0, c.i0 = self.npop, self.e0, self.i0
         c.lambda_floor, c.n_sub = self.lambda_floor, self.n_sub
         c.pf_scheme, c.pf_ess_frac = self.pf_scheme, self.pf_ess_frac
+        c.prior_kind = self.prior_kind
+        if self.prior_kind == PRIOR_UNIFORM:
+            for d in range(self.D):
+                c.prior_lo[d] = self.prior_lo[d]
+                c.prior_hi[d] = self.prior_hi[d]
         return c
 
 
@@ -230,6 +242,14 @@ def multinomial_from_q(q, U):
     if rc != 0:
         raise ValueError("all weights zero")
     return anc
+
+
+def binomial(n, p, seed, c0, c1, c2, c3, words: bool = False):
+    """Bin(n, p) from the PF_BINOM word stream (counters c0 + 8192 m, c1, c2, c3)."""
+    used = np.zeros(1, dtype=np.int32)
+    k = lib().oracle_binomial(float(n), float(p), int(seed), int(c0), int(c1), int(c2), int(c3),
+                              _p(used, C.c_int32))
+    return (k, int(used[0])) if words else k
 
 
 def ess_from_q(q) -> float:

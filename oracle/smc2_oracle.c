@@ -174,13 +174,118 @@ int oracle_systematic_from_q(const uint64_t* q, int n, uint32_t U, int32_t* ncop
 }
 
 /* ------------------------------------------------------------------ */
+/* Binomial variates (the SIR flows of Sec. V-A)                        */
+/* ------------------------------------------------------------------ */
+
+/* The words of one draw, read in order from Philox calls m = 0, 1, ... */
+typedef struct {
+  uint32_t key[2], ctr[4], w[4];
+  int used, calls, words;
+} binom_words;
+
+/* Next uniform (2w + 1) 2^-33 in (0, 1); 0 when the 64 calls are spent. */
+static double binom_next_u(binom_words* b) {
+  if (b->used == 4) {
+    if (b->calls == 64) return 0.0;
+    uint32_t ctr[4] = {b->ctr[0] + 8192u * (uint32_t)b->calls, b->ctr[1], b->ctr[2], b->ctr[3]};
+    oracle_philox4x32_10(ctr, b->key, b->w);
+    b->calls++;
+    b->used = 0;
+  }
+  b->words++;
+  return (2.0 * (double)b->w[b->used++] + 1.0) * 0x1p-33;
+}
+
+/* log k! through the gamma function. */
+static double log_factorial(double k) { return lgamma(k + 1.0); }
+
+/* Bin(n, p) for 0 < p <= 1/2; returns -1 when the words run out. */
+static double binom_half(double n, double p, binom_words* b) {
+  const double q = 1.0 - p;
+  if (n * p < 10.0) {
+    /* inversion: P(0) = q^n, P(k) = P(k-1) ((n + 1) s / k - s) with s = p / q */
+    const double s = p / q, a = (n + 1.0) * s, r0 = exp(n * log1p(-p));
+    for (;;) {
+      double u = binom_next_u(b);
+      if (u == 0.0) return -1.0;
+      double r = r0, k = 0.0;
+      while (u > r) {
+        u -= r;
+        k += 1.0;
+        if (k > n) break; /* rounding left u above the total mass: draw again */
+        r *= a / k - s;
+      }
+      if (k <= n) return k;
+    }
+  }
+  /* BTRS: a transformed-rejection proposal k = floor((2a/us + b) u + c) with a
+   * squeeze accepting most draws outright; otherwise the exact test of the
+   * log-pmf ratio to the mode m against log(v alpha / (a/us^2 + b)). */
+  const double spq = sqrt(n * p * q);
+  const double bb = 1.15 + 2.53 * spq;
+  const double aa = -0.0873 + 0.0248 * bb + 0.01 * p;
+  const double c = n * p + 0.5;
+  const double vr = 0.92 - 4.2 / bb;
+  for (;;) {
+    const double u1 = binom_next_u(b);
+    const double v1 = binom_next_u(b);
+    if (u1 == 0.0 || v1 == 0.0) return -1.0;
+    const double u = u1 - 0.5;
+    const double us = 0.5 - fabs(u);
+    const double k = floor((2.0 * aa / us + bb) * u + c);
+    if (k < 0.0 || k > n) continue;
+    if (us >= 0.07 && v1 <= vr) return k;
+    const double alpha = (2.83 + 5.1 / bb) * spq;
+    const double lpq = log(p / q);
+    const double m = floor((n + 1.0) * p);
+    const double h = log_factorial(m) + log_factorial(n - m);
+    const double v = log(v1 * alpha / (aa / (us * us) + bb));
+    if (v <= h - log_factorial(k) - log_factorial(n - k) + (k - m) * lpq) return k;
+  }
+}
+
+double oracle_binomial(double n, double p, uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2,
+                       uint32_t c3, int* words) {
+  binom_words b;
+  b.key[0] = (uint32_t)seed;
+  b.key[1] = (uint32_t)(seed >> 32);
+  b.ctr[0] = c0;
+  b.ctr[1] = c1;
+  b.ctr[2] = c2;
+  b.ctr[3] = c3;
+  b.used = 4;
+  b.calls = 0;
+  b.words = 0;
+  double k;
+  if (!(p > 0.0) || n <= 0.0) {
+    k = 0.0;
+  } else if (!(p < 1.0)) {
+    k = n;
+  } else if (p > 0.5) {
+    const double r = binom_half(n, 1.0 - p, &b);
+    k = r < 0.0 ? floor((n + 1.0) * p) : n - r;
+  } else {
+    const double r = binom_half(n, p, &b);
+    k = r < 0.0 ? floor((n + 1.0) * p) : r;
+  }
+  if (words) *words = b.words;
+  return k;
+}
+
+/* ------------------------------------------------------------------ */
 /* State-space models: Sec. II, Eqs. (1)-(2)                            */
 /* ------------------------------------------------------------------ */
 
 /* Linear-Gaussian AR(1): theta = (phi, log sx, log sy).
  * SEIR-type: theta = (log beta0, log sigma_rw, log kappa, log gamma); the
  * state is (S, E, I, log beta_t, lambda_t) with R = Npop - S - E - I and
- * lambda_t the day's incidence (the E -> I flow), observed as Poisson. */
+ * lambda_t the day's incidence (the E -> I flow), observed as Poisson.
+ * SIR (Sec. V-A): theta = (beta, gamma); the state is (S, I), integers, with
+ * R = Npop - S - I, I_0 = i0, and each day the binomial flows
+ *   n(S->I) ~ Bin(S, 1 - exp(-beta I / Npop)),  n(I->R) ~ Bin(I, 1 - exp(-gamma)),
+ * observed as y_t ~ Poisson(I_t).  The printed S->I probability also carries
+ * S_{t-1} in the exponent; the oracle takes the per-susceptible hazard
+ * beta I / Npop of the chain-binomial SIR model the section cites. */
 
 static void oracle_initial_state(const oracle_cfg* c, const double* theta, uint32_t k, uint32_t c2,
                                  int j, double* x) {
@@ -188,6 +293,9 @@ static void oracle_initial_state(const oracle_cfg* c, const double* theta, uint3
     double z[4];
     oracle_normals4(c->seed, (uint32_t)j, 0, c2, ORACLE_TAG_PF_INIT | (k << 4), z);
     x[0] = z[0];
+  } else if (c->model == ORACLE_SIR) {
+    x[0] = c->npop - c->i0;
+    x[1] = c->i0;
   } else {
     x[0] = c->npop - c->e0 - c->i0;
     x[1] = c->e0;
@@ -220,8 +328,27 @@ static void oracle_propagate(const oracle_cfg* c, const double* theta, double z,
   }
 }
 
+/* One day of the SIR model for particle j at step t: both flows from the
+ * previous day's (S, I); probabilities 1 - exp(-h) formed as -expm1(-h). */
+static void oracle_propagate_sir(const oracle_cfg* c, const double* theta, uint32_t k, uint32_t c2,
+                                 int j, int t, double* x) {
+  const double S = x[0], I = x[1];
+  const double p_si = -expm1(-(theta[0] * I / c->npop));
+  const double p_ir = -expm1(-theta[1]);
+  const uint32_t c3 = ORACLE_TAG_PF_BINOM | (k << 4);
+  const double n_si = oracle_binomial(S, p_si, c->seed, (uint32_t)j, (uint32_t)t, c2, c3, NULL);
+  const double n_ir = oracle_binomial(I, p_ir, c->seed, (uint32_t)j + 4096u, (uint32_t)t, c2, c3, NULL);
+  x[0] = S - n_si;
+  x[1] = I + n_si - n_ir;
+}
+
 /* log g(y_t | x_t, theta), Eq. (2). */
 double oracle_log_obs(const oracle_cfg* c, const double* theta, const double* x, double y) {
+  if (c->model == ORACLE_SIR) { /* Poisson(y; I), a point mass at 0 when I = 0 */
+    const double I = x[1];
+    if (I > 0.0) return (y > 0.0 ? y * log(I) : 0.0) - I - lgamma(y + 1.0);
+    return y > 0.0 ? -INFINITY : 0.0;
+  }
   if (c->model == ORACLE_LG) {
     double sy = exp(theta[2]);
     double r = (y - x[0]) / sy;
@@ -307,10 +434,14 @@ double oracle_pf_loglik(const oracle_cfg* c, const double* theta, const double* 
   uint32_t* Um = (uint32_t*)malloc(sizeof(uint32_t) * M);
   for (int t = 1; t <= T; ++t) {
     for (int j = 0; j < M; ++j) {
-      double z[4];
-      oracle_normals4(c->seed, (uint32_t)j, (uint32_t)((t - 1) >> 2), c2,
-                      ORACLE_TAG_PF_PROP | (k << 4), z);
-      oracle_propagate(c, theta, z[(t - 1) & 3], x + SD * j);
+      if (c->model == ORACLE_SIR) {
+        oracle_propagate_sir(c, theta, k, c2, j, t, x + SD * j);
+      } else {
+        double z[4];
+        oracle_normals4(c->seed, (uint32_t)j, (uint32_t)((t - 1) >> 2), c2,
+                        ORACLE_TAG_PF_PROP | (k << 4), z);
+        oracle_propagate(c, theta, z[(t - 1) & 3], x + SD * j);
+      }
       double ell = oracle_log_obs(c, theta, x + SD * j, y[t - 1]);
       if (isnan(ell)) ell = -INFINITY;
       lw[j] = lw[j] + ell; /* Eq. (5) in logs */
@@ -363,9 +494,17 @@ done:
 /* SMC^2 outer sampler: Sec. IV                                         */
 /* ------------------------------------------------------------------ */
 
-/* log p(theta): independent Gaussians in the unconstrained coordinates. */
+/* log p(theta): independent Gaussians in the unconstrained coordinates, or
+ * independent uniforms on [lo, hi] (-inf outside). */
 double oracle_log_prior(const oracle_cfg* c, const double* theta) {
   double lp = 0.0;
+  if (c->prior_kind == ORACLE_PRIOR_UNIFORM) {
+    for (int d = 0; d < c->D; ++d) {
+      if (!(theta[d] >= c->prior_lo[d] && theta[d] <= c->prior_hi[d])) return -INFINITY;
+      lp -= log(c->prior_hi[d] - c->prior_lo[d]);
+    }
+    return lp;
+  }
   for (int d = 0; d < c->D; ++d) {
     double r = (theta[d] - c->prior_mean[d]) / c->prior_sd[d];
     lp += -0.5 * LOG_2PI - log(c->prior_sd[d]) - 0.5 * r * r;
@@ -555,9 +694,21 @@ int oracle_smc2_step(const oracle_cfg* c, const double* y, int k, double* theta,
     /* Eq. (16): theta_1^i ~ q_1 = prior; Eq. (17): w_1 = pi / q_1. */
     for (int i = 0; i < N; ++i) {
       for (int g = 0; g * 4 < D; ++g) {
+        const uint32_t c3 = ORACLE_TAG_THETA_INIT | ((uint32_t)k << 4);
+        if (c->prior_kind == ORACLE_PRIOR_UNIFORM) { /* theta_d = lo + (hi - lo) u, u = (2w + 1) 2^-33 */
+          const uint32_t ctr[4] = {(uint32_t)g, 0u, (uint32_t)i | ds, c3};
+          const uint32_t key[2] = {(uint32_t)c->seed, (uint32_t)(c->seed >> 32)};
+          uint32_t w[4];
+          oracle_philox4x32_10(ctr, key, w);
+          for (int r = 0; r < 4 && 4 * g + r < D; ++r) {
+            int d = 4 * g + r;
+            double u = (2.0 * (double)w[r] + 1.0) * 0x1p-33;
+            th_new[i * D + d] = c->prior_lo[d] + (c->prior_hi[d] - c->prior_lo[d]) * u;
+          }
+          continue;
+        }
         double z[4];
-        oracle_normals4(c->seed, (uint32_t)g, 0, (uint32_t)i | ds,
-                        ORACLE_TAG_THETA_INIT | ((uint32_t)k << 4), z);
+        oracle_normals4(c->seed, (uint32_t)g, 0, (uint32_t)i | ds, c3, z);
         for (int r = 0; r < 4 && 4 * g + r < D; ++r) {
           int d = 4 * g + r;
           th_new[i * D + d] = c->prior_mean[d] + c->prior_sd[d] * z[r];

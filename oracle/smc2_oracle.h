@@ -24,6 +24,13 @@
  *     4 PF_INIT      c0 = particle j, c1 = 0; normal 0 is the initial draw
  *     5 PF_PROP      c0 = particle j, c1 = (t-1) >> 2; step t uses normal (t-1) & 3
  *     6 PF_RES       c0 = 0, c1 = t; word 0 is U for the resampling after step t
+ *     8 PF_MULTI     c0 = slot j, c1 = t; word 0 is U_j for multinomial resampling
+ *     9 PF_BINOM     c0 = j + 4096 b + 8192 m, c1 = t: call m of the word stream
+ *                    of particle j's binomial draw b at step t (b = 0 the S -> I
+ *                    flow, 1 the I -> R flow of the SIR model); the draw reads
+ *                    the words of calls m = 0, 1, ... in order (x, y, z, w).
+ *  A word w read by the binomial sampler becomes u = (2w + 1) 2^-33 (exact in
+ *  double); a uniform prior draw uses the same form of the THETA_INIT words.
  *
  *  Systematic resampling in integers.  For log-weights l_0..l_{n-1} with
  *  maximum m, q_i = floor(exp(l_i - m) * 2^B) with B = min(52, 63 - ceil(log2 n)),
@@ -41,18 +48,19 @@
 extern "C" {
 #endif
 
-enum { ORACLE_LG = 0, ORACLE_SEIR = 1 };
+enum { ORACLE_LG = 0, ORACLE_SEIR = 1, ORACLE_SIR = 2 };
+enum { ORACLE_PRIOR_GAUSS = 0, ORACLE_PRIOR_UNIFORM = 1 };
 enum { ORACLE_LK_FORWARD = 0, ORACLE_LK_GAUSS = 1 };
 enum {
   ORACLE_TAG_THETA_INIT = 1, ORACLE_TAG_PROPOSE = 2, ORACLE_TAG_OUTER_RES = 3,
   ORACLE_TAG_PF_INIT = 4, ORACLE_TAG_PF_PROP = 5, ORACLE_TAG_PF_RES = 6,
-  ORACLE_TAG_PF_MULTI = 8
+  ORACLE_TAG_PF_MULTI = 8, ORACLE_TAG_PF_BINOM = 9
 };
 enum { ORACLE_PF_SYSTEMATIC = 0, ORACLE_PF_MULTINOMIAL = 1 };
 #define ORACLE_MAX_D 8
 
 typedef struct {
-  int model;             /* ORACLE_LG or ORACLE_SEIR */
+  int model;             /* ORACLE_LG, ORACLE_SEIR or ORACLE_SIR */
   int D, N, M, T;        /* dim theta, theta samples, PF particles, time steps */
   int lkernel;           /* ORACLE_LK_FORWARD or ORACLE_LK_GAUSS */
   int dataset;           /* dataset index (random-stream key only) */
@@ -60,7 +68,8 @@ typedef struct {
   double ess_frac;       /* outer resampling when ESS < ess_frac * N */
   uint64_t seed;
   double prior_mean[ORACLE_MAX_D], prior_sd[ORACLE_MAX_D];
-  /* SEIR constants: population, E0, I0, Euler substeps per day, incidence floor */
+  /* SEIR constants: population, E0, I0, Euler substeps per day, incidence floor;
+   * the SIR model uses npop and i0 */
   double npop, e0, i0, lambda_floor;
   int n_sub;
   /* PF resampling (Sec. II): scheme, and the schedule -- every step t < T when
@@ -68,6 +77,10 @@ typedef struct {
    * below pf_ess_frac * M (the paper's choice is multinomial below M/2). */
   int pf_scheme;
   double pf_ess_frac;
+  /* Prior: independent Gaussians N(prior_mean, prior_sd^2), or with
+   * ORACLE_PRIOR_UNIFORM independent uniforms on [prior_lo, prior_hi]. */
+  int prior_kind;
+  double prior_lo[ORACLE_MAX_D], prior_hi[ORACLE_MAX_D];
 } oracle_cfg;
 
 typedef struct {
@@ -95,6 +108,18 @@ int oracle_multinomial_from_q(const uint64_t* q, int n, const uint32_t* U, int32
  * 128-bit sum of squares hi:lo: every operation correctly rounded, so any
  * machine forms the same value. */
 double oracle_ess_from_q(const uint64_t* q, int n);
+
+/* Binomial(n, p) variate from the PF_BINOM word stream with counters
+ * (c0 + 8192 m, c1, c2, c3), m = 0, 1, ...  n a non-negative integer.
+ * p <= 0 (or NaN) gives 0, p >= 1 gives n; p > 1/2 draws n - Bin(n, 1 - p).
+ * n p < 10: inversion, a sequential search from 0 on the pmf recurrence
+ * (a redraw if rounding carries the search past n).  Otherwise Hormann's
+ * transformed rejection with squeeze (W. Hormann, "The generation of binomial
+ * random variates", J. Statist. Comput. Simul. 46, 1993, algorithm BTRS).
+ * After 64 calls (256 words; probability below 1e-40 for any n, p) the draw
+ * returns floor((n + 1) p).  *words (if not NULL) receives the words read. */
+double oracle_binomial(double n, double p, uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2,
+                       uint32_t c3, int* words);
 
 double oracle_log_obs(const oracle_cfg* c, const double* theta, const double* x, double y);
 double oracle_pf_loglik(const oracle_cfg* c, const double* theta, const double* y, uint32_t k,

@@ -14,6 +14,10 @@ Workloads (sizes follow the benchmark configurations of the method):
 * ``seir_t100_n1024_mlp``  as ``seir_t100_n1024`` with the learned proposal
 * ``seir_batched_64``  64 SEIR-type datasets, T ~ U{50..400}, N in {256,1024,4096},
   M in {128,512,1024}, K=10
+* ``sir_t30_n1024``    the paper's binomial SIR experiment (Sec. V-A): population 1e4,
+  3 infected, T=30, theta = (beta, gamma) ~ U[0,1]^2, random walk Sigma = 0.1 I,
+  N=1024 (256 and 512 by override), M=500, K=10, the paper's particle filter
+  (multinomial resampling when the ESS falls below M/2), FP32 particles
 """
 from __future__ import annotations
 
@@ -22,14 +26,17 @@ from dataclasses import dataclass, field, replace
 
 import numpy as np
 
-LG, SEIR = 0, 1
+LG, SEIR, SIR = 0, 1, 2
 PREC_FP64, PREC_MIXED = 0, 1
+PRIOR_GAUSS, PRIOR_UNIFORM = 0, 1
+PF_SYSTEMATIC, PF_MULTINOMIAL = 0, 1
 PROP_RW, PROP_MLP = 0, 1
 LK_FORWARD, LK_GAUSS = 0, 1
 
 LG_TRUTH = (0.8, 0.5, 1.0)                # phi, sigma_x, sigma_y
 SEIR_TRUTH = (0.6, 0.05, 0.25, 0.2)       # beta0, sigma_rw, kappa, gamma
 SEIR_PRIOR_MEDIAN = (0.5, 0.1, 0.2, 0.2)  # log-normal prior medians, log-sd 0.5
+SIR_TRUTH = (0.85, 0.20)                  # beta, gamma (Sec. V-A)
 
 
 @dataclass
@@ -56,6 +63,11 @@ class Workload:
     i0: float = 0.0
     lambda_floor: float = 1e-3
     n_sub: int = 2
+    prior_kind: int = PRIOR_GAUSS
+    prior_lo: list = field(default_factory=list)
+    prior_hi: list = field(default_factory=list)
+    pf_scheme: int = PF_SYSTEMATIC
+    pf_ess_frac: float = 0.0
     ppt: int = 0            # particle-filter launch shape (0: the library's tuner)
     cta_threads: int = 0
     y: np.ndarray | None = None
@@ -124,7 +136,24 @@ def seir_constant_beta_incidence(T: int, beta0: float, kappa: float, gamma: floa
     return lam
 
 
+def simulate_sir(T: int, beta: float, gamma: float, npop: float, i0: float, seed: int) -> np.ndarray:
+    """Daily Poisson counts of the infected from the binomial SIR model: each day
+    Bin(S, 1 - exp(-beta I / npop)) susceptibles are infected and Bin(I, 1 - exp(-gamma))
+    infected recover, both from the previous day's compartments; y_t ~ Poisson(I_t)."""
+    rng = np.random.default_rng(seed)
+    S, I = int(npop - i0), int(i0)
+    y = np.empty(T)
+    for t in range(T):
+        n_si = rng.binomial(S, -math.expm1(-beta * I / npop))
+        n_ir = rng.binomial(I, -math.expm1(-gamma))
+        S, I = S - n_si, I + n_si - n_ir
+        y[t] = rng.poisson(I)
+    return y.astype(np.float64)
+
+
 def simulate(w: Workload) -> np.ndarray:
+    if w.model == SIR:
+        return simulate_sir(w.T, *SIR_TRUTH, w.npop, w.i0, seed=w.data_seed)
     if w.model == LG:
         return simulate_lg(w.T, *LG_TRUTH, seed=w.data_seed)
     return simulate_seir(w.T, *SEIR_TRUTH, w.npop, w.e0, w.i0, w.n_sub, w.lambda_floor,
@@ -149,7 +178,19 @@ def _seir(**kw) -> Workload:
     return w
 
 
+def _sir(**kw) -> Workload:
+    w = Workload(name="sir", model=SIR, D=2, N=1024, M=500, T=30, K=10, precision=PREC_MIXED,
+                 rw_scale=math.sqrt(0.1), prior_kind=PRIOR_UNIFORM, prior_lo=[0.0, 0.0],
+                 prior_hi=[1.0, 1.0], prior_mean=[0.5, 0.5], prior_sd=[1.0, 1.0],
+                 npop=1e4, i0=3.0, pf_scheme=PF_MULTINOMIAL, pf_ess_frac=0.5, seed=4, data_seed=4)
+    w = replace(w, **kw)
+    w.y = simulate(w)
+    return w
+
+
 def workload(name: str, **kw) -> Workload:
+    if name == "sir_t30_n1024":
+        return _sir(name=name, **kw)
     if name == "lg_t50_n64":
         return _lg(name=name, **kw)
     if name == "seir_t100_n1024":
@@ -177,6 +218,9 @@ def batched_workloads(n: int = 64, K: int = 10, seed: int = 100) -> list[Workloa
 def theta_near_prior(w: Workload, n: int, seed: int, spread: float = 1.0) -> np.ndarray:
     """n parameter vectors drawn around the prior (row-major [n][D])."""
     rng = np.random.default_rng(seed)
+    if w.prior_kind == PRIOR_UNIFORM:  # uniform on the support shrunk about its centre
+        lo, hi = np.asarray(w.prior_lo, dtype=np.float64), np.asarray(w.prior_hi, dtype=np.float64)
+        return 0.5 * (lo + hi) + (rng.random((n, w.D)) - 0.5) * (hi - lo) * min(spread, 1.0)
     mu = np.asarray(w.prior_mean, dtype=np.float64)
     sd = np.asarray(w.prior_sd, dtype=np.float64) * spread
     return mu + sd * rng.standard_normal((n, w.D))
