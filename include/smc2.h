@@ -55,7 +55,8 @@ typedef enum {
   SMC2_ESTATE = 8      /* call not valid in the context's current state */
 } smc2_status;
 
-enum { SMC2_MODEL_LG_AR1 = 0, SMC2_MODEL_SEIR = 1 };
+enum { SMC2_MODEL_LG_AR1 = 0, SMC2_MODEL_SEIR = 1, SMC2_MODEL_SIR = 2 };
+enum { SMC2_PRIOR_GAUSS = 0, SMC2_PRIOR_UNIFORM = 1 };
 enum { SMC2_PREC_FP64 = 0, SMC2_PREC_MIXED = 1 };   /* MIXED: FP32 particles, FP64 outer */
 enum { SMC2_PROP_RW = 0, SMC2_PROP_MLP = 1 };
 enum { SMC2_LK_FORWARD = 0, SMC2_LK_GAUSS_OPT = 1 };
@@ -70,7 +71,7 @@ typedef struct smc2_ctx smc2_ctx; /* opaque; owns its device workspace */
 
 /* Sampler configuration (host memory, read during smc2_init only).
  * model, precision, proposal, lkernel: the enums above.
- * D: dimension of theta (3 for LG_AR1, 4 for SEIR).
+ * D: dimension of theta (3 for LG_AR1, 4 for SEIR, 2 for SIR).
  * N, M, T: theta samples, particles per filter, observations; used when
  *   n_datasets <= 1, otherwise taken per dataset from ds_N, ds_M, ds_T.
  *   M <= SMC2_MAX_M, and a filter's particles must fit one CTA's shared
@@ -82,8 +83,17 @@ typedef struct smc2_ctx smc2_ctx; /* opaque; owns its device workspace */
  * seed: key of the random stream.
  * prior_mean, prior_sd: independent Gaussian prior (= q_1 of Eq. 16) in the
  *   unconstrained coordinates, first D entries used.
+ * prior_kind, prior_lo, prior_hi: SMC2_PRIOR_UNIFORM replaces the Gaussian
+ *   prior by independent uniforms on [prior_lo, prior_hi] (the SIR experiment
+ *   of Sec. V-A draws theta_1 from U[0, 1]); its log-density is -inf outside,
+ *   so proposals there get zero weight.
  * npop, e0, i0, n_sub, lambda_floor: SEIR constants (population, initial
  *   exposed and infectious, Euler substeps per day, floor of the Poisson mean).
+ *   The SIR model (Sec. V-A, theta = (beta, gamma) in natural units, state
+ *   (S, I) with S_0 = npop - i0, I_0 = i0) uses npop (an integer <= 2^24) and
+ *   i0; each day n(S->I) ~ Bin(S, 1 - exp(-beta I / npop)) and
+ *   n(I->R) ~ Bin(I, 1 - exp(-gamma)), y_t ~ Poisson(I_t).  It runs with
+ *   ppt <= 4 (M <= 2048) and the random-walk proposal.
  * ppt: particles per thread of the particle-filter kernel (0 = pick by the
  *   built-in tuner; otherwise 1, 2, 4, 8 or 16).
  * proposal = SMC2_PROP_MLP (learned proposal; not in the paper): once the
@@ -134,7 +144,8 @@ typedef struct {
   int mlp_steps, mlp_window;
   double pf_ess_frac;
   int pf_scheme;
-  int pf_reserved;  /* set to 0 */
+  int prior_kind;
+  double prior_lo[SMC2_MAX_D], prior_hi[SMC2_MAX_D];
 } smc2_config;
 
 /* Statistics of one iteration k of one dataset (Sec. IV-A, IV-B):

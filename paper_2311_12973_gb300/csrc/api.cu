@@ -112,7 +112,8 @@ bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
 
 smc2_status validate(const smc2_config* c) {
   if (!c) return SMC2_EINVAL;
-  if (c->model != SMC2_MODEL_LG_AR1 && c->model != SMC2_MODEL_SEIR) return SMC2_EINVAL;
+  if (c->model != SMC2_MODEL_LG_AR1 && c->model != SMC2_MODEL_SEIR && c->model != SMC2_MODEL_SIR)
+    return SMC2_EINVAL;
   if (c->precision != SMC2_PREC_FP64 && c->precision != SMC2_PREC_MIXED) return SMC2_EINVAL;
   if (c->proposal != SMC2_PROP_RW && c->proposal != SMC2_PROP_MLP) return SMC2_EINVAL;
   if (c->proposal == SMC2_PROP_MLP &&
@@ -122,11 +123,25 @@ smc2_status validate(const smc2_config* c) {
       c->mlp_steps < 0 || c->mlp_steps > 256 || c->mlp_window < 0 || c->mlp_window > 16)
     return SMC2_EINVAL;
   if (c->lkernel != SMC2_LK_FORWARD && c->lkernel != SMC2_LK_GAUSS_OPT) return SMC2_EINVAL;
-  if (c->D != (c->model == SMC2_MODEL_LG_AR1 ? 3 : 4)) return SMC2_EINVAL;
+  if (c->D != (c->model == SMC2_MODEL_LG_AR1 ? 3 : c->model == SMC2_MODEL_SIR ? 2 : 4)) return SMC2_EINVAL;
   if (c->K < 1 || c->K > (1 << 27)) return SMC2_EINVAL;
   if (!finite_pos(c->rw_scale) || !std::isfinite(c->ess_frac) || c->ess_frac < 0.0) return SMC2_EINVAL;
-  for (int d = 0; d < c->D; ++d)
-    if (!std::isfinite(c->prior_mean[d]) || !finite_pos(c->prior_sd[d])) return SMC2_EINVAL;
+  if (c->prior_kind != SMC2_PRIOR_GAUSS && c->prior_kind != SMC2_PRIOR_UNIFORM) return SMC2_EINVAL;
+  for (int d = 0; d < c->D; ++d) {
+    if (c->prior_kind == SMC2_PRIOR_UNIFORM) {
+      if (!std::isfinite(c->prior_lo[d]) || !std::isfinite(c->prior_hi[d]) ||
+          !finite_pos(c->prior_hi[d] - c->prior_lo[d]))
+        return SMC2_EINVAL;
+    } else if (!std::isfinite(c->prior_mean[d]) || !finite_pos(c->prior_sd[d])) {
+      return SMC2_EINVAL;
+    }
+  }
+  if (c->model == SMC2_MODEL_SIR) {  // integer compartments, exact in float
+    if (!finite_pos(c->npop) || c->npop > 16777216.0 || c->npop != std::floor(c->npop) ||
+        !(c->i0 >= 0.0 && c->i0 <= c->npop) || c->i0 != std::floor(c->i0) || c->ppt > 4 ||
+        c->proposal != SMC2_PROP_RW)
+      return SMC2_EINVAL;
+  }
   if (c->model == SMC2_MODEL_SEIR) {
     if (!finite_pos(c->npop) || !std::isfinite(c->e0) || !std::isfinite(c->i0) || c->e0 < 0 ||
         c->i0 < 0 || c->e0 + c->i0 > c->npop || c->n_sub < 1 || c->n_sub > 64 ||
@@ -136,7 +151,7 @@ smc2_status validate(const smc2_config* c) {
   if (c->ppt != 0 && c->ppt != 1 && c->ppt != 2 && c->ppt != 4 && c->ppt != 8 && c->ppt != 16)
     return SMC2_EINVAL;
   if ((c->pf_scheme != SMC2_PF_SYSTEMATIC && c->pf_scheme != SMC2_PF_MULTINOMIAL) ||
-      !(c->pf_ess_frac >= 0.0 && c->pf_ess_frac <= 1.0) || c->pf_reserved != 0)
+      !(c->pf_ess_frac >= 0.0 && c->pf_ess_frac <= 1.0))
     return SMC2_EINVAL;
   const bool general = c->pf_scheme != SMC2_PF_SYSTEMATIC || c->pf_ess_frac > 0.0;
   if (general && c->ppt > 4) return SMC2_EINVAL;  // the variants run in the register-resident shapes
@@ -154,10 +169,10 @@ smc2_status validate(const smc2_config* c) {
     const int gt = pf_group_threads(c->ppt ? c->ppt : 16, m);
     if (gt > (c->cta_threads ? c->cta_threads : kPfMaxBlock)) return SMC2_EINVAL;
     // a filter's particles live in one CTA's shared memory: some shape must fit
-    const int model = c->model == SMC2_MODEL_LG_AR1 ? MODEL_LG : MODEL_SEIR;
+    const int model = c->model;  // the internal model ids equal the ABI's
     bool fits = false;
     for (int ppt : {1, 2, 4, 8, 16}) {
-      if ((c->ppt && ppt != c->ppt) || (general && ppt > 4)) continue;
+      if ((c->ppt && ppt != c->ppt) || ((general || model == MODEL_SIR) && ppt > 4)) continue;
       const int g = pf_group_threads(ppt, m);
       if (g <= kPfMaxBlock && pf_smem_bytes(c->precision, model, ppt, general, g, m) <= 227 * 1024) fits = true;
     }
@@ -311,7 +326,7 @@ smc2_status choose_launch_shape(smc2_ctx* c) {
   std::vector<Shape> cand;
   for (int ppt : {1, 2, 4, 8, 16}) {
     if (c->cfg.ppt && ppt != c->cfg.ppt) continue;
-    if (c->pf_general && ppt > 4) continue;  // the variants run in the register-resident shapes
+    if ((c->pf_general || c->model == MODEL_SIR) && ppt > 4) continue;  // register-resident shapes only
     for (int block = 32; block <= kPfMaxBlock; block += 32) {
       if (c->cfg.cta_threads && block != c->cfg.cta_threads) continue;
       if (!c->cfg.cta_threads && (block & (block - 1))) continue;  // powers of two when tuning
@@ -406,7 +421,12 @@ void fill_params(smc2_ctx* c) {
     P.prior_sd[d] = c->cfg.prior_sd[d];
     P.inv_prior_sd[d] = d < c->D ? 1.0 / c->cfg.prior_sd[d] : 0.0;
     P.log_prior_sd[d] = d < c->D ? std::log(c->cfg.prior_sd[d]) : 0.0;
+    P.prior_lo[d] = c->cfg.prior_lo[d];
+    P.prior_hi[d] = c->cfg.prior_hi[d];
+    P.log_prior_width[d] =
+        (d < c->D && c->cfg.prior_kind == SMC2_PRIOR_UNIFORM) ? std::log(c->cfg.prior_hi[d] - c->cfg.prior_lo[d]) : 0.0;
   }
+  P.prior_kind = c->cfg.prior_kind;
   P.inv_rw = 1.0 / c->cfg.rw_scale;
   P.log_rw = std::log(c->cfg.rw_scale);
   P.seed = c->cfg.seed;
@@ -571,7 +591,7 @@ smc2_status smc2_init(const smc2_config* cfg, const double* y, void* stream, smc
   c->D = cfg->D;
   c->K = cfg->K;
   c->precision = cfg->precision;
-  c->model = cfg->model == SMC2_MODEL_LG_AR1 ? MODEL_LG : MODEL_SEIR;
+  c->model = cfg->model;  // the internal model ids equal the ABI's
   for (int d = 0; d < c->n_ds; ++d) {
     c->N.push_back(cfg->n_datasets > 1 ? cfg->ds_N[d] : cfg->N);
     c->M.push_back(cfg->n_datasets > 1 ? cfg->ds_M[d] : cfg->M);

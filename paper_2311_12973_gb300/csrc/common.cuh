@@ -20,12 +20,13 @@ enum : uint32_t {
   TAG_PF_RES = 6,      // c0 = 0, c1 = t; word 0
   TAG_MLP_INIT = 7,    // c0 = parameter index; word 0 (surrogate network initial weights)
   TAG_PF_MULTI = 8,    // c0 = slot, c1 = t; word 0 (multinomial PF resampling)
+  TAG_PF_BINOM = 9,    // c0 = particle + 4096 flow + 8192 call, c1 = t (SIR binomial flows)
 };
 
 // Device status bits (sticky; mapped to smc2_status codes on the host).
 enum : int { ST_NONFINITE = 1, ST_TIMEOUT = 2, ST_BOUNDS = 4 };
 
-enum : int { MODEL_LG = 0, MODEL_SEIR = 1 };
+enum : int { MODEL_LG = 0, MODEL_SEIR = 1, MODEL_SIR = 2 };
 enum : int { LK_FORWARD = 0, LK_GAUSS = 1 };
 
 constexpr int kMaxD = 8;

@@ -101,6 +101,8 @@ struct OuterParams {
   double rw_scale, ess_frac;
   double prior_mean[8], prior_sd[8];
   double inv_prior_sd[8], log_prior_sd[8];   // configuration constants
+  double prior_lo[8], prior_hi[8], log_prior_width[8];  // uniform prior (prior_kind 1)
+  int prior_kind;
   double inv_rw, log_rw;
   uint64_t seed;
   int* k_done;         // completed iterations; the running iteration is k_done + 1

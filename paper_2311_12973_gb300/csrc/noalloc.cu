@@ -63,7 +63,7 @@ extern "C" smc2_status smc2_pf_loglik_noalloc(const smc2_config* cfg, const doub
                                               const double* theta_dev, int n, int iteration,
                                               double* loglik_dev, void* stream) {
   if (!cfg || !y_dev || !theta_dev || !loglik_dev) return fail(SMC2_EINVAL, "null pointer argument");
-  if (cfg->model != SMC2_MODEL_LG_AR1 && cfg->model != SMC2_MODEL_SEIR)
+  if (cfg->model != SMC2_MODEL_LG_AR1 && cfg->model != SMC2_MODEL_SEIR && cfg->model != SMC2_MODEL_SIR)
     return fail(SMC2_EINVAL, "unknown model");
   if (cfg->precision != SMC2_PREC_FP64 && cfg->precision != SMC2_PREC_MIXED)
     return fail(SMC2_EINVAL, "unknown precision");
@@ -75,6 +75,10 @@ extern "C" smc2_status smc2_pf_loglik_noalloc(const smc2_config* cfg, const doub
   if (cfg->model == SMC2_MODEL_SEIR &&
       (!(cfg->npop > 0) || cfg->n_sub < 1 || !(cfg->lambda_floor > 0)))
     return fail(SMC2_EINVAL, "invalid SEIR constants");
+  if (cfg->model == SMC2_MODEL_SIR &&
+      (!(cfg->npop > 0) || cfg->npop > 16777216.0 || cfg->npop != floor(cfg->npop) ||
+       !(cfg->i0 >= 0 && cfg->i0 <= cfg->npop) || cfg->i0 != floor(cfg->i0)))
+    return fail(SMC2_EINVAL, "invalid SIR constants");
   const int ppt = cfg->ppt ? cfg->ppt : 2;
   if (ppt != 1 && ppt != 2 && ppt != 4 && ppt != 8 && ppt != 16) return fail(SMC2_EINVAL, "ppt");
   if ((cfg->pf_scheme != SMC2_PF_SYSTEMATIC && cfg->pf_scheme != SMC2_PF_MULTINOMIAL) ||
@@ -82,6 +86,7 @@ extern "C" smc2_status smc2_pf_loglik_noalloc(const smc2_config* cfg, const doub
     return fail(SMC2_EINVAL, "pf_scheme / pf_ess_frac");
   const bool general = cfg->pf_scheme != SMC2_PF_SYSTEMATIC || cfg->pf_ess_frac > 0.0;
   if (general && ppt > 4) return fail(SMC2_EINVAL, "the PF variants need ppt <= 4");
+  if (cfg->model == SMC2_MODEL_SIR && ppt > 4) return fail(SMC2_EINVAL, "the SIR model needs ppt <= 4");
   const int gt = pf_group_threads(ppt, cfg->M);
   if (gt > kPfMaxBlock) return fail(SMC2_EINVAL, "M too large for this ppt");
 
@@ -90,7 +95,7 @@ extern "C" smc2_status smc2_pf_loglik_noalloc(const smc2_config* cfg, const doub
   if (st != SMC2_OK) return st;
   int* counter = static_cast<int*>(scratch);
   void* obs = static_cast<unsigned char*>(scratch) + kNoallocCounterBytes;
-  const int model = cfg->model == SMC2_MODEL_LG_AR1 ? MODEL_LG : MODEL_SEIR;
+  const int model = cfg->model;  // the internal model ids equal the ABI's
   cudaStream_t s = static_cast<cudaStream_t>(stream);
 
   // one filter group per CTA (or several one-warp groups): no named barriers

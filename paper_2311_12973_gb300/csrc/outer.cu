@@ -29,6 +29,14 @@ static_assert(kOuterBlock == 32, "the per-sample outer kernels are one warp per 
 template <int D>
 __device__ __forceinline__ double log_prior(const OuterParams& P, const double* th) {
   double lp = 0.0;
+  if (P.prior_kind == 1) {  // independent uniforms on [lo, hi]
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      if (!(th[d] >= P.prior_lo[d] && th[d] <= P.prior_hi[d])) return -HUGE_VAL;
+      lp -= P.log_prior_width[d];
+    }
+    return lp;
+  }
 #pragma unroll
   for (int d = 0; d < D; ++d) {
     const double r = (th[d] - P.prior_mean[d]) * P.inv_prior_sd[d];
@@ -207,7 +215,20 @@ __global__ void __launch_bounds__(kOuterBlock) propose_kernel(OuterParams P) {
 #pragma unroll
       for (int r = 0; r < 4 && 4 * g + r < D; ++r) z[4 * g + r] = z4[r];
     }
-    if (k == 1) {
+    if (k == 1 && P.prior_kind == 1) {
+      // uniform prior: theta_d = lo + (hi - lo) u from the THETA_INIT words, u = (2w + 1) 2^-33
+#pragma unroll
+      for (int g = 0; g * 4 < D; ++g) {
+        const uint4 w = philox4x32_10(make_uint4((uint32_t)g, 0u, c2, counter_c3(TAG_THETA_INIT, k)), key);
+        const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int r = 0; r < 4 && 4 * g + r < D; ++r) {
+          const double u = ((double)ws[r] * 2.0 + 1.0) * 0x1p-33;
+          const int d = 4 * g + r;
+          b[d] = __dadd_rn(P.prior_lo[d], __dmul_rn(__dsub_rn(P.prior_hi[d], P.prior_lo[d]), u));
+        }
+      }
+    } else if (k == 1) {
 #pragma unroll
       for (int d = 0; d < D; ++d) b[d] = P.prior_mean[d] + P.prior_sd[d] * z[d];
     } else {
@@ -651,7 +672,7 @@ __global__ void obs_terms_kernel(int model, const double* y, int T, R* obs) {
   if (t >= T) return;
   const double v = y[t];
   double inv = 0.0, c = 0.0;
-  if (model == MODEL_SEIR && v > 0.0) {
+  if (model != MODEL_LG && v > 0.0) {  // Poisson terms (SEIR-type and SIR)
     inv = 1.0 / v;
     c = -lgamma(v + 1.0) + v * log(v) - v;
   }
@@ -697,7 +718,9 @@ cudaError_t outer_obs_terms(int precision, int model, const double* y, int T, vo
 
 cudaError_t outer_propose(const OuterParams& P, int max_nblk, cudaStream_t s) {
   const dim3 grid(max_nblk, P.n_ds);
-  if (P.D == 3)
+  if (P.D == 2)
+    propose_kernel<2><<<grid, kOuterBlock, 0, s>>>(P);
+  else if (P.D == 3)
     propose_kernel<3><<<grid, kOuterBlock, 0, s>>>(P);
   else if (P.D == 4)
     propose_kernel<4><<<grid, kOuterBlock, 0, s>>>(P);
@@ -707,7 +730,9 @@ cudaError_t outer_propose(const OuterParams& P, int max_nblk, cudaStream_t s) {
 }
 cudaError_t outer_lkfit(const OuterParams& P, cudaStream_t s) {
   const dim3 grid(1, P.n_ds);
-  if (P.D == 3)
+  if (P.D == 2)
+    lkfit_kernel<2><<<grid, 32, 0, s>>>(P);
+  else if (P.D == 3)
     lkfit_kernel<3><<<grid, 32, 0, s>>>(P);
   else if (P.D == 4)
     lkfit_kernel<4><<<grid, 32, 0, s>>>(P);
@@ -717,7 +742,9 @@ cudaError_t outer_lkfit(const OuterParams& P, cudaStream_t s) {
 }
 cudaError_t outer_weights(const OuterParams& P, int max_nblk, cudaStream_t s) {
   const dim3 grid(max_nblk, P.n_ds);
-  if (P.D == 3)
+  if (P.D == 2)
+    weights_kernel<2><<<grid, kOuterBlock, 0, s>>>(P);
+  else if (P.D == 3)
     weights_kernel<3><<<grid, kOuterBlock, 0, s>>>(P);
   else if (P.D == 4)
     weights_kernel<4><<<grid, kOuterBlock, 0, s>>>(P);

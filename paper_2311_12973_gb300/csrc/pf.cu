@@ -12,12 +12,15 @@ int pf_group_threads(int ppt, int M) { return group_threads_for(ppt, M); }
 size_t pf_smem_bytes(int precision, int model, int ppt, bool general, int block, int M) {
   const int gt = group_threads_for(ppt, M);
   const int fpc = block / gt;
-  const int ns = model == MODEL_LG ? 1 : 4;
+  const int ns = model == MODEL_LG ? 1 : model == MODEL_SIR ? 2 : 4;
   const int rs = precision == SMC2_PREC_FP64 ? 8 : 4;
   return (size_t)fpc * region_bytes(gt * ppt, gt >> 5, ns, rs, is_staged(ppt), general);
 }
 
 static const void* select_kernel(int precision, int model, int ppt, bool named, bool general) {
+  if (model == MODEL_SIR)
+    return precision == SMC2_PREC_FP64 ? pf_select_sir_f64(ppt, named, general)
+                                       : pf_select_sir_f32(ppt, named, general);
   if (general)
     return precision == SMC2_PREC_FP64 ? pf_select_general_f64(model, ppt, named)
                                        : pf_select_general_f32(model, ppt, named);

@@ -30,6 +30,7 @@
 #include <cfloat>
 #include <cmath>
 
+#include "binomial.cuh"
 #include "common.cuh"
 #include "internal.h"
 
@@ -58,6 +59,10 @@ struct ModelDims<MODEL_LG> {
 template <>
 struct ModelDims<MODEL_SEIR> {
   static constexpr int D = 4, NS = 4;
+};
+template <>
+struct ModelDims<MODEL_SIR> {
+  static constexpr int D = 2, NS = 2;
 };
 
 __host__ __device__ inline int group_threads_for(int ppt, int M) {
@@ -100,6 +105,28 @@ template <typename R>
 struct StateVec<R, 1> {
   __device__ __forceinline__ static void store(R* X, int j, const R* x) { X[j] = x[0]; }
   __device__ __forceinline__ static void load(const R* X, int j, R* x) { x[0] = X[j]; }
+};
+template <>
+struct StateVec<float, 2> {
+  __device__ __forceinline__ static void store(float* X, int j, const float* x) {
+    reinterpret_cast<float2*>(X)[j] = make_float2(x[0], x[1]);
+  }
+  __device__ __forceinline__ static void load(const float* X, int j, float* x) {
+    const float2 v = reinterpret_cast<const float2*>(X)[j];
+    x[0] = v.x;
+    x[1] = v.y;
+  }
+};
+template <>
+struct StateVec<double, 2> {
+  __device__ __forceinline__ static void store(double* X, int j, const double* x) {
+    reinterpret_cast<double2*>(X)[j] = make_double2(x[0], x[1]);
+  }
+  __device__ __forceinline__ static void load(const double* X, int j, double* x) {
+    const double2 v = reinterpret_cast<const double2*>(X)[j];
+    x[0] = v.x;
+    x[1] = v.y;
+  }
 };
 template <>
 struct StateVec<float, 4> {
@@ -281,6 +308,51 @@ struct FilterParams<R, MODEL_SEIR> {
   }
 };
 
+// Binomial SIR model (Sec. V-A): theta = (beta, gamma), state (S, I) integers
+// held in the working precision (exact below 2^24).  Each day, from the previous
+// day's compartments, n(S->I) ~ Bin(S, 1 - exp(-beta I / Npop)) and
+// n(I->R) ~ Bin(I, 1 - exp(-gamma)); y_t ~ Poisson(I_t).  (The printed S->I
+// probability also carries S_{t-1} in the exponent; this is the per-susceptible
+// hazard of the chain-binomial model the section cites.)  Both flows are drawn
+// in double from particle j's word streams (j and j + 4096) of step t.
+template <typename R>
+struct FilterParams<R, MODEL_SIR> {
+  R beta, npop, S0, I0;
+  double p_ir;
+  __device__ void load(const double* th, const PFModel& m) {
+    beta = (R)th[0];
+    npop = (R)m.npop;
+    p_ir = -expm1(-th[1]);
+    S0 = (R)(m.npop - m.i0);
+    I0 = (R)m.i0;
+  }
+  __device__ __forceinline__ void init(R* x, R, const double*) const {
+    x[0] = S0;
+    x[1] = I0;
+  }
+  __device__ __forceinline__ void day(R* x, uint32_t j, uint32_t t, uint32_t c2, uint32_t c3,
+                                      uint2 key) const {
+    const R S = x[0], I = x[1];
+    const R h = beta * I / npop;
+    const double p_si = (double)(-expm1(-h));
+    const double n_si = binomial_draw((double)S, p_si, make_uint4(j, t, c2, c3), key);
+    const double n_ir = binomial_draw((double)I, p_ir, make_uint4(j + 4096u, t, c2, c3), key);
+    x[0] = (R)((double)S - n_si);
+    x[1] = (R)(((double)I + n_si) - n_ir);
+  }
+  // Poisson(y; I) as for the SEIR-type model, with a point mass at 0 when I = 0
+  template <typename R4>
+  __device__ __forceinline__ R log_obs(const R* x, const R4& ob) const {
+    const R I = x[1];
+    if (!(I > (R)0)) return ob.x > (R)0 ? neg_inf<R>() : (R)0;
+    if (ob.x > (R)0) {
+      const R d = (I - ob.x) * ob.y;
+      return ob.x * (log1p(d) - d) + ob.z;
+    }
+    return -I;
+  }
+};
+
 // NAMED: groups wider than a warp that share a CTA synchronise on named
 // barriers 1..15 (ptxas then reserves all 16 barriers of the CTA, which limits
 // residency to four CTAs per SM).  Otherwise a wide group is the whole CTA and
@@ -329,6 +401,7 @@ __device__ __forceinline__ void run_filter(const PFJob& J, const PFModel& mdl, i
   const uint32_t c3prop = counter_c3(TAG_PF_PROP, k);
   const uint32_t c3res = counter_c3(TAG_PF_RES, k);
   const uint32_t c3multi = counter_c3(TAG_PF_MULTI, k);
+  const uint32_t c3binom = counter_c3(TAG_PF_BINOM, k);
   const int B = fixed_point_bits(M);
   const int log2M = ((M & (M - 1)) == 0) ? (__ffs(M) - 1) : -1;
   const R scaleB = (R)ldexp(1.0, B);
@@ -361,7 +434,7 @@ __device__ __forceinline__ void run_filter(const PFJob& J, const PFModel& mdl, i
   double loglik = 0.0;  // log p^(y_{1:t}) (Eq. 8)
   for (int t = 1; t <= T; ++t) {
     const int tm = (t - 1) & 3;
-    if (tm == 0) {  // one Philox call per particle every four steps; normals kept in shared memory
+    if (MODEL != MODEL_SIR && tm == 0) {  // one Philox call per particle every four steps; normals kept in shared memory
 #pragma unroll
       for (int r = 0; r < PPT; ++r) {
         R z4[4];
@@ -380,11 +453,15 @@ __device__ __forceinline__ void run_filter(const PFJob& J, const PFModel& mdl, i
     R lmax = neg_inf<R>();
 #pragma unroll
     for (int r = 0; r < PPT; ++r) {
-      fp.propagate(x[r], Z[tm * Mp + lt * PPT + r]);
       R l;
-      if constexpr (MODEL == MODEL_LG) {
+      if constexpr (MODEL == MODEL_SIR) {
+        fp.day(x[r], (uint32_t)(lt * PPT + r), (uint32_t)t, c2, c3binom, key);
+        l = fp.log_obs(x[r], ob);
+      } else if constexpr (MODEL == MODEL_LG) {
+        fp.propagate(x[r], Z[tm * Mp + lt * PPT + r]);
         l = fp.log_obs(x[r], ob);
       } else {
+        fp.propagate(x[r], Z[tm * Mp + lt * PPT + r]);
         const R lam = fp.day(x[r]);
         l = fp.log_pois(lam, ob);
       }
@@ -689,11 +766,11 @@ const void* pf_select_ppt(int ppt) {
     case 1: return pf_kernel_ptr<R, MODEL, 1, NAMED, GENERAL>();
     case 2: return pf_kernel_ptr<R, MODEL, 2, NAMED, GENERAL>();
     case 4: return pf_kernel_ptr<R, MODEL, 4, NAMED, GENERAL>();
-    case 8:
-      if constexpr (GENERAL) return nullptr;  // the variants run in the register-resident shapes only
+    case 8:  // the variants and the SIR model run in the register-resident shapes only
+      if constexpr (GENERAL || MODEL == MODEL_SIR) return nullptr;
       else return pf_kernel_ptr<R, MODEL, 8, NAMED, false>();
     case 16:
-      if constexpr (GENERAL) return nullptr;
+      if constexpr (GENERAL || MODEL == MODEL_SIR) return nullptr;
       else return pf_kernel_ptr<R, MODEL, 16, NAMED, false>();
     default: return nullptr;
   }
@@ -706,9 +783,17 @@ const void* pf_select_precision(int model, int ppt, bool named) {
   return named ? pf_select_ppt<R, MODEL_SEIR, true, GENERAL>(ppt) : pf_select_ppt<R, MODEL_SEIR, false, GENERAL>(ppt);
 }
 
+template <typename R, bool GENERAL>
+const void* pf_select_sir(int ppt, bool named) {
+  return named ? pf_select_ppt<R, MODEL_SIR, true, GENERAL>(ppt) : pf_select_ppt<R, MODEL_SIR, false, GENERAL>(ppt);
+}
+
 const void* pf_select_f32(int model, int ppt, bool named);
 const void* pf_select_f64(int model, int ppt, bool named);
 const void* pf_select_general_f32(int model, int ppt, bool named);
 const void* pf_select_general_f64(int model, int ppt, bool named);
+// the SIR model's instantiations (pf_sir_f32.cu, pf_sir_f64.cu)
+const void* pf_select_sir_f32(int ppt, bool named, bool general);
+const void* pf_select_sir_f64(int ppt, bool named, bool general);
 
 }  // namespace smc2

@@ -20,6 +20,7 @@ MODEL_LG_AR1, MODEL_SEIR = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
 PROP_RW, PROP_MLP = 0, 1
 PF_SYSTEMATIC, PF_MULTINOMIAL = 0, 1
+PRIOR_GAUSS, PRIOR_UNIFORM = 0, 1
 LK_FORWARD, LK_GAUSS_OPT = 0, 1
 
 
@@ -33,7 +34,8 @@ class Config(C.Structure):
         ("n_sub", C.c_int), ("ppt", C.c_int), ("cta_threads", C.c_int), ("n_datasets", C.c_int),
         ("ds_N", C.POINTER(C.c_int)), ("ds_M", C.POINTER(C.c_int)), ("ds_T", C.POINTER(C.c_int)),
         ("mlp_h", C.c_double), ("mlp_lr", C.c_double), ("mlp_steps", C.c_int), ("mlp_window", C.c_int),
-        ("pf_ess_frac", C.c_double), ("pf_scheme", C.c_int), ("pf_reserved", C.c_int),
+        ("pf_ess_frac", C.c_double), ("pf_scheme", C.c_int), ("prior_kind", C.c_int),
+        ("prior_lo", C.c_double * MAX_D), ("prior_hi", C.c_double * MAX_D),
     ]
 
 
@@ -154,6 +156,11 @@ def make_config(w, **over) -> Config:
     c.mlp_h, c.mlp_lr = get("mlp_h", 0.0), get("mlp_lr", 0.0)
     c.mlp_steps, c.mlp_window = get("mlp_steps", 0), get("mlp_window", 0)
     c.pf_ess_frac, c.pf_scheme = get("pf_ess_frac", 0.0), get("pf_scheme", PF_SYSTEMATIC)
+    c.prior_kind = get("prior_kind", PRIOR_GAUSS)
+    if c.prior_kind == PRIOR_UNIFORM:
+        for d in range(c.D):
+            c.prior_lo[d] = get("prior_lo")[d]
+            c.prior_hi[d] = get("prior_hi")[d]
     return c
 
 

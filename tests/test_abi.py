@@ -58,8 +58,13 @@ def _cfg(S, **over):
     {"proposal": 1, "mlp_h": -1.0}, {"mlp_lr": 1.5}, {"mlp_h": float("nan")}, {"mlp_steps": -1},
     # particle-filter variants: known scheme, ESS fraction in [0, 1], register-resident shapes only
     {"pf_scheme": 2}, {"pf_scheme": -1}, {"pf_ess_frac": 1.5}, {"pf_ess_frac": -0.1},
-    {"pf_ess_frac": float("nan")}, {"pf_reserved": 1}, {"pf_scheme": 1, "ppt": 8},
+    {"pf_ess_frac": float("nan")}, {"pf_scheme": 1, "ppt": 8},
     {"pf_ess_frac": 0.5, "ppt": 16}, {"pf_scheme": 1, "M": 4096},
+    # priors and the SIR model: D = 2, integer population and infected, ppt <= 4, random walk
+    {"prior_kind": 2}, {"model": 2}, {"model": 2, "D": 2, "npop": 10.5, "i0": 3.0},
+    {"model": 2, "D": 2, "npop": 1e4, "i0": 2e4}, {"model": 2, "D": 2, "npop": 1e4, "i0": 2.5},
+    {"model": 2, "D": 2, "npop": 1e8, "i0": 3.0}, {"model": 2, "D": 2, "npop": 1e4, "i0": 3.0, "ppt": 8},
+    {"model": 2, "D": 2, "npop": 1e4, "i0": 3.0, "proposal": 1},
 ])
 def test_invalid_configs_rejected_before_gpu_work(S, over):
     import numpy as np
@@ -68,6 +73,18 @@ def test_invalid_configs_rejected_before_gpu_work(S, over):
     ctx = C.c_void_p()
     assert S.lib.smc2_init(C.byref(cfg), y.ctypes.data, None, C.byref(ctx)) == S.EINVAL
     assert not ctx.value
+
+
+def test_uniform_prior_needs_an_interval(S):
+    import numpy as np
+    from paper_2311_12973_gb300 import inputs as I
+    y = np.zeros(64)
+    ctx = C.c_void_p()
+    for lo, hi in [(0.5, 0.5), (1.0, 0.0), (float("nan"), 1.0), (0.0, float("inf"))]:
+        cfg = S.make_config(I.workload("sir_t30_n1024"))
+        cfg.prior_lo[1], cfg.prior_hi[1] = lo, hi
+        assert S.lib.smc2_init(C.byref(cfg), y.ctypes.data, None, C.byref(ctx)) == S.EINVAL
+        assert not ctx.value
 
 
 def test_invalid_prior_and_seir_constants(S):
