@@ -17,10 +17,10 @@
 // w giving u = (2w + 1) 2^-33 (exact in double).  After 64 calls (probability
 // far below 1e-40 for any n, p) the draw returns floor((n + 1) p).
 //
-// The arithmetic is in double in both precisions (the log-pmf differences of
-// the exact test cancel to a few units in float at n ~ 1e4), with explicitly
-// rounded operations, so that the decisions follow the same roundings on any
-// IEEE machine; only exp, log1p, log and lgamma round on their own.
+// The FP64 form below does every step in double with explicitly rounded
+// operations, so that its decisions follow the same roundings on any IEEE
+// machine (only exp, log1p, log and lgamma round on their own); the FP32 form
+// further down serves the mixed-precision filter.
 #pragma once
 
 #include "common.cuh"
@@ -109,6 +109,128 @@ __device__ __forceinline__ double binomial_draw(double n, double p, uint4 ctr, u
   }
   const double r = binomial_half(n, p, b);
   return r < 0.0 ? floor(__dmul_rn(__dadd_rn(n, 1.0), p)) : r;
+}
+
+// ---------------------------------------------------------------------------
+// FP32 form (mixed precision).  The same two methods in float, with float
+// uniforms u = ((w >> 9) + 0.5) 2^-23 (exact) from the same word stream.  A
+// warp pays for a branch any of its lanes takes, and a double instruction
+// occupies the narrow FP64 unit for the whole warp, so the rare exact test is
+// in float too, in a form without cancellation: with m the mode, r = p / q and
+// Stirling's log j! = (j + 1/2) log(j + 1) - (j + 1) + log(2 pi)/2 + fc(j),
+//   log f(k)/f(m) = (m + 1/2) log1p((m - k)/(k + 1))
+//                 + (n - m + 1/2) log1p((k - m)/(n - k + 1))
+//                 + (k - m) log1p(((n + 2) p - (k + 1)) / ((k + 1) q))
+//                 + fc(m) + fc(n - m) - fc(k) - fc(n - k),
+// every log of a ratio near 1 at the k the test sees; only (n + 2) p - (k + 1)
+// is formed in double.  Its error is below 5e-5 for n <= 1e4 (1.3e-3 at
+// n = 2^24), against the exact log-pmf ratio.  BTRS's proposal adds the large
+// offset c = n p + 1/2 as floor(c) + floor(t + frac(c)), so the float rounding
+// of the sum is that of the small part.  This is the FP64 sampler up to float
+// roundings, not bit for bit.
+// ---------------------------------------------------------------------------
+
+// fc(j) = log j! - [(j + 1/2) log(j + 1) - (j + 1) + log(2 pi)/2]: the series
+// 1/(12 x) - 1/(360 x^3) + 1/(1260 x^5), x = j + 1, for j >= 10 (error below
+// 1/(1680 x^7)); from the exact factorial below 10.
+__device__ __forceinline__ float stirling_fc(float j) {
+  const float x = j + 1.f;
+  if (j < 10.f) {
+    float f = 1.f;
+    for (int i = 2; i <= (int)j; ++i) f *= (float)i;  // exact: 9! < 2^24
+    return logf(f) - ((j + 0.5f) * logf(x) - x + 0.918938533f);
+  }
+  const float r = __fdividef(1.f, x), r2 = r * r;
+  return r * (1.f / 12.f - r2 * (1.f / 360.f - r2 * (1.f / 1260.f)));
+}
+
+struct BinomWordsF {
+  uint4 ctr;
+  uint2 key;
+  uint4 cur;
+  int left, calls;
+
+  __device__ __forceinline__ BinomWordsF(uint4 c, uint2 k) : ctr(c), key(k), cur(), left(0), calls(0) {}
+
+  __device__ __forceinline__ float next() {
+    if (left == 0) {
+      if (calls == 64) return 0.f;
+      cur = philox4x32_10(make_uint4(ctr.x + 8192u * (uint32_t)calls, ctr.y, ctr.z, ctr.w), key);
+      ++calls;
+      left = 4;
+    }
+    const uint32_t w = cur.x;
+    cur.x = cur.y;
+    cur.y = cur.z;
+    cur.z = cur.w;
+    --left;
+    return ((float)(w >> 9) + 0.5f) * 0x1p-23f;
+  }
+};
+
+static __device__ __noinline__ float binomial_half_f32(float n, float p, BinomWordsF& b) {
+  const float q = 1.f - p;
+  if (n * p < 10.f) {
+    const float s = p / q;
+    const float a = (n + 1.f) * s;
+    const float r0 = expf(n * log1pf(-p));
+    for (;;) {
+      float u = b.next();
+      if (u == 0.f) return -1.f;
+      float r = r0, k = 0.f;
+      while (u > r) {
+        u -= r;
+        k += 1.f;
+        if (k > n) break;
+        r *= __fdividef(a, k) - s;
+      }
+      if (k <= n) return k;
+    }
+  }
+  const float spq = sqrtf(n * p * q);
+  const float bb = 1.15f + 2.53f * spq;
+  const float aa = -0.0873f + 0.0248f * bb + 0.01f * p;
+  const float c = n * p + 0.5f;
+  const float ci = floorf(c), cf = c - ci;
+  const float vr = 0.92f - __fdividef(4.2f, bb);
+  bool have_m = false;
+  float m = 0.f, fcm = 0.f, alpha = 0.f;
+  for (;;) {
+    const float u1 = b.next();
+    const float v1 = b.next();
+    if (u1 == 0.f || v1 == 0.f) return -1.f;
+    const float u = u1 - 0.5f;
+    const float us = 0.5f - fabsf(u);
+    const float k = ci + floorf((__fdividef(2.f * aa, us) + bb) * u + cf);
+    if (k < 0.f || k > n) continue;
+    if (us >= 0.07f && v1 <= vr) return k;
+    if (!have_m) {
+      m = floorf((float)(((double)n + 1.0) * (double)p));
+      fcm = stirling_fc(m) + stirling_fc(n - m);
+      alpha = (2.83f + __fdividef(5.1f, bb)) * spq;
+      have_m = true;
+    }
+    const float d = (float)(((double)n + 2.0) * (double)p - ((double)k + 1.0));
+    const float lr = (m + 0.5f) * log1pf(__fdividef(m - k, k + 1.f)) +
+                     (n - m + 0.5f) * log1pf(__fdividef(k - m, n - k + 1.f)) +
+                     (k - m) * log1pf(__fdividef(d, (k + 1.f) * q)) + fcm - stirling_fc(k) -
+                     stirling_fc(n - k);
+    const float v = logf(__fdividef(v1 * alpha, __fdividef(aa, us * us) + bb));
+    if (v <= lr) return k;
+  }
+}
+
+// Bin(n, p) in the FP32 form, for an integer n >= 0 below 2^24.
+__device__ __forceinline__ float binomial_draw(float n, float p, uint4 ctr, uint2 key) {
+  if (!(p > 0.f) || n <= 0.f) return 0.f;
+  if (!(p < 1.f)) return n;
+  BinomWordsF b(ctr, key);
+  if (p > 0.5f) {
+    const float r = binomial_half_f32(n, 1.f - p, b);
+    return r < 0.f ? floorf((n + 1.f) * p) : n - r;
+  }
+  const float r = binomial_half_f32(n, p, b);
+  return r < 0.f ? floorf((n + 1.f) * p) : r;
 }
 
 }  // namespace smc2

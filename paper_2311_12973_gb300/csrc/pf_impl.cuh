@@ -314,15 +314,15 @@ struct FilterParams<R, MODEL_SEIR> {
 // n(I->R) ~ Bin(I, 1 - exp(-gamma)); y_t ~ Poisson(I_t).  (The printed S->I
 // probability also carries S_{t-1} in the exponent; this is the per-susceptible
 // hazard of the chain-binomial model the section cites.)  Both flows are drawn
-// in double from particle j's word streams (j and j + 4096) of step t.
+// from particle j's word streams (j and j + 4096) of step t, by the binomial
+// sampler of the working precision.
 template <typename R>
 struct FilterParams<R, MODEL_SIR> {
-  R beta, npop, S0, I0;
-  double p_ir;
+  R beta, npop, S0, I0, p_ir;
   __device__ void load(const double* th, const PFModel& m) {
     beta = (R)th[0];
     npop = (R)m.npop;
-    p_ir = -expm1(-th[1]);
+    p_ir = (R)(-expm1(-th[1]));
     S0 = (R)(m.npop - m.i0);
     I0 = (R)m.i0;
   }
@@ -334,11 +334,11 @@ struct FilterParams<R, MODEL_SIR> {
                                       uint2 key) const {
     const R S = x[0], I = x[1];
     const R h = beta * I / npop;
-    const double p_si = (double)(-expm1(-h));
-    const double n_si = binomial_draw((double)S, p_si, make_uint4(j, t, c2, c3), key);
-    const double n_ir = binomial_draw((double)I, p_ir, make_uint4(j + 4096u, t, c2, c3), key);
-    x[0] = (R)((double)S - n_si);
-    x[1] = (R)(((double)I + n_si) - n_ir);
+    const R p_si = -expm1(-h);
+    const R n_si = binomial_draw(S, p_si, make_uint4(j, t, c2, c3), key);
+    const R n_ir = binomial_draw(I, p_ir, make_uint4(j + 4096u, t, c2, c3), key);
+    x[0] = S - n_si;
+    x[1] = (I + n_si) - n_ir;  // integers: exact in either precision
   }
   // Poisson(y; I) as for the SEIR-type model, with a point mass at 0 when I = 0
   template <typename R4>

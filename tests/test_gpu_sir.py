@@ -4,9 +4,10 @@ FP64: the binomial flows are decided by the same correctly rounded operations
 on both sides (only exp, log1p, log and lgamma round on their own, a flip
 needing a uniform within an ulp of a boundary), so ancestors agree bit for bit
 and increments to 1e-12 of T times the magnitude of the Poisson terms.  FP32
-particles (the binomial draws stay in double) give independent estimates of the
-same likelihood after their first differing draw: no offset, and unbiased for
-the exact likelihood of a small population."""
+particles draw the flows with the float form of the sampler, so they give
+independent estimates of the same likelihood: no offset against the oracle,
+unbiased for the exact likelihood of a small population, and for the exact
+one-day likelihood in every regime of the sampler."""
 import math
 
 import numpy as np
@@ -17,7 +18,7 @@ from oracle import oracle as O
 from paper_2311_12973_gb300 import inputs as I
 
 from gpu_util import rel_err, soa
-from test_oracle_sir import sir_exact_loglik
+from test_oracle_sir import ONE_DAY, one_day_likelihood, sir_exact_loglik
 
 pytestmark = pytest.mark.gpu
 
@@ -90,6 +91,25 @@ def test_unbiased_for_exact_likelihood(S, precision, pf):
     ctx.close()
     r = np.exp(ll - exact)
     assert abs(r.mean() - 1.0) < 4 * r.std() / math.sqrt(len(r)), (r.mean(), r.std())
+
+
+@pytest.mark.parametrize("precision", [I.PREC_FP64, I.PREC_MIXED])
+@pytest.mark.parametrize("npop,i0,beta,gamma", ONE_DAY)
+def test_one_day_filter_unbiased(S, precision, npop, i0, beta, gamma):
+    # one day from (npop - i0, i0): E[p^] is the exact convolution of the two binomial
+    # laws against Poisson(y_1; I_1); 4096 filters of 1024 particles see the sampler's
+    # distribution (rejection, inversion and mirror regimes) to a few 1e-3
+    S0, I0 = npop - i0, i0
+    mean = I0 + S0 * -math.expm1(-beta * I0 / npop) - I0 * -math.expm1(-gamma)
+    for z in (-2.0, 0.0, 1.5):
+        y = np.array([max(0.0, round(mean + z * math.sqrt(mean + 1.0) * 1.3))])
+        w = I.workload("sir_t30_n1024", N=4096, M=1024, T=1, npop=npop, i0=i0, precision=precision)
+        exact = one_day_likelihood(npop, i0, beta, gamma, y[0])
+        ctx = S.SMC2(S.make_config(w), y)
+        ll = ctx.pf_loglik(soa(np.tile([beta, gamma], (w.N, 1))), iteration=1).cpu().numpy()
+        ctx.close()
+        r = np.exp(ll - math.log(exact))
+        assert abs(r.mean() - 1.0) < 4 * r.std() / math.sqrt(len(r)), (z, r.mean(), r.std())
 
 
 def test_mixed_precision_no_offset(S):

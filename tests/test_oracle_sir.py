@@ -121,6 +121,37 @@ def sir_exact_loglik(beta, gamma, npop, i0, y):
     return ll
 
 
+def one_day_likelihood(npop, i0, beta, gamma, y):
+    """p(y_1 | theta) after one day from (npop - i0, i0): the S->I and I->R flows
+    are independent binomials, so I_1 = i0 + a - b has the convolution of their
+    pmfs, and p(y_1) = sum over I_1 of Poisson(y_1; I_1) P(I_1)."""
+    S0, I0 = int(npop - i0), int(i0)
+    pa = stats.binom.pmf(np.arange(S0 + 1), S0, -math.expm1(-beta * I0 / npop))
+    pb = stats.binom.pmf(np.arange(I0 + 1), I0, -math.expm1(-gamma))
+    dist = np.convolve(pa, pb[::-1])  # index a + (I0 - b) = I_1
+    return float(np.sum(dist * stats.poisson.pmf(y, np.arange(len(dist)))))
+
+
+# (npop, i0, beta, gamma): both flows by rejection; S->I by rejection and I->R
+# by inversion; the I->R flow with p > 1/2 (the mirror)
+ONE_DAY = [(1e4, 2000.0, 0.9, 0.2), (1e4, 20.0, 0.9, 0.2), (1e4, 2000.0, 0.9, 1.5)]
+
+
+@pytest.mark.parametrize("npop,i0,beta,gamma", ONE_DAY)
+def test_one_day_filter_unbiased(npop, i0, beta, gamma):
+    # E[p^] = p(y_1 | theta) for y_1 in the bulk and the tails of the one-day law
+    w = I.workload("sir_t30_n1024", N=1, M=256, T=1, npop=npop, i0=i0, precision=I.PREC_FP64)
+    cfg = O.config_from(w)
+    S0, I0 = npop - i0, i0
+    mean = I0 + S0 * -math.expm1(-beta * I0 / npop) - I0 * -math.expm1(-gamma)
+    for z in (-2.0, 0.0, 1.5):
+        y = np.array([max(0.0, round(mean + z * math.sqrt(mean + 1.0) * 1.3))])
+        exact = one_day_likelihood(npop, i0, beta, gamma, y[0])
+        r = np.array([math.exp(O.pf_loglik(cfg, np.array([beta, gamma]), y, k=1, i=s) - math.log(exact))
+                      for s in range(200)])
+        assert abs(r.mean() - 1.0) < 4 * r.std() / math.sqrt(len(r)), (z, r.mean(), r.std())
+
+
 def small_sir(T=10, beta=0.9, gamma=0.3, npop=30.0, i0=3.0, seed=5, **over):
     y = I.simulate_sir(T, beta, gamma, npop, i0, seed=seed)
     w = I.workload("sir_t30_n1024", N=1, M=64, T=T, npop=npop, i0=i0, precision=I.PREC_FP64)
