@@ -122,9 +122,10 @@ __device__ __forceinline__ double binomial_draw(double n, double p, uint4 ctr, u
 //                 + (n - m + 1/2) log1p((k - m)/(n - k + 1))
 //                 + (k - m) log1p(((n + 2) p - (k + 1)) / ((k + 1) q))
 //                 + fc(m) + fc(n - m) - fc(k) - fc(n - k),
-// every log of a ratio near 1 at the k the test sees; only (n + 2) p - (k + 1)
-// is formed in double.  Its error is below 5e-5 for n <= 1e4 (1.3e-3 at
-// n = 2^24), against the exact log-pmf ratio.  BTRS's proposal adds the large
+// every log of a ratio near 1 at the k the test sees; (n + 2) p - (k + 1)
+// takes the product's exact rounding error from an FMA, so the difference of
+// two nearby values keeps its accuracy.  The error is below 5e-5 for n <= 1e4
+// (1.3e-3 at n = 2^24), against the exact log-pmf ratio.  BTRS's proposal adds the large
 // offset c = n p + 1/2 as floor(c) + floor(t + frac(c)), so the float rounding
 // of the sum is that of the small part.  This is the FP64 sampler up to float
 // roundings, not bit for bit.
@@ -194,7 +195,7 @@ static __device__ __noinline__ float binomial_half_f32(float n, float p, BinomWo
   const float ci = floorf(c), cf = c - ci;
   const float vr = 0.92f - __fdividef(4.2f, bb);
   bool have_m = false;
-  float m = 0.f, fcm = 0.f, alpha = 0.f;
+  float m = 0.f, fcm = 0.f, alpha = 0.f, np2 = 0.f, np2_err = 0.f;
   for (;;) {
     const float u1 = b.next();
     const float v1 = b.next();
@@ -205,12 +206,15 @@ static __device__ __noinline__ float binomial_half_f32(float n, float p, BinomWo
     if (k < 0.f || k > n) continue;
     if (us >= 0.07f && v1 <= vr) return k;
     if (!have_m) {
-      m = floorf((float)(((double)n + 1.0) * (double)p));
+      m = floorf(fmaf(n, p, p));  // floor((n + 1) p), one rounding
       fcm = stirling_fc(m) + stirling_fc(n - m);
       alpha = (2.83f + __fdividef(5.1f, bb)) * spq;
+      const float n2 = n + 2.f;
+      np2 = n2 * p;
+      np2_err = fmaf(n2, p, -np2);  // (n + 2) p = np2 + np2_err exactly
       have_m = true;
     }
-    const float d = (float)(((double)n + 2.0) * (double)p - ((double)k + 1.0));
+    const float d = ((np2 - (k + 1.f)) + np2_err);
     const float lr = (m + 0.5f) * log1pf(__fdividef(m - k, k + 1.f)) +
                      (n - m + 0.5f) * log1pf(__fdividef(k - m, n - k + 1.f)) +
                      (k - m) * log1pf(__fdividef(d, (k + 1.f) * q)) + fcm - stirling_fc(k) -

@@ -426,6 +426,7 @@ __device__ __forceinline__ void run_filter(const PFJob& J, const PFModel& mdl, i
   // (GENERAL instantiations only: the ESS schedule and multinomial slots; the default
   // instantiations resample systematically every step and keep no factors)
   const bool adaptive = GEN && mdl.pf_ess_frac > 0.0;
+  const float ess_thr = (float)(mdl.pf_ess_frac * (double)M);  // mixed precision's ESS threshold
   const bool multinomial = GEN && mdl.pf_scheme == 1;
   R lwc[GEN ? PPT : 1];
 #pragma unroll
@@ -575,9 +576,15 @@ __device__ __forceinline__ void run_filter(const PFJob& J, const PFModel& mdl, i
       if (lane == 0) {
         unsigned __int128 Q2 = 0;
         for (int w = 0; w < nw; ++w) Q2 += wq2[w];
-        const double q2 = (double)(uint64_t)(Q2 >> 64) * 0x1p64 + (double)(uint64_t)Q2;
-        const double ess = __ddiv_rn((double)S * (double)S, q2);
-        below = ess < mdl.pf_ess_frac * (double)M;
+        if constexpr (sizeof(R) == 8) {  // the oracle's operations, bit for bit
+          const double q2 = (double)(uint64_t)(Q2 >> 64) * 0x1p64 + (double)(uint64_t)Q2;
+          const double ess = __ddiv_rn((double)S * (double)S, q2);
+          below = ess < mdl.pf_ess_frac * (double)M;
+        } else {  // mixed precision: the same test in float, S^2 < threshold sum q^2
+          const float q2 = fmaf(__ull2float_rn((uint64_t)(Q2 >> 64)), 0x1p64f, __ull2float_rn((uint64_t)Q2));
+          const float Sf = u64_to_float(S);
+          below = Sf * Sf < ess_thr * q2;
+        }
       }
       resample = __shfl_sync(0xffffffffu, below, 0) != 0;
     }
