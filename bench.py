@@ -29,11 +29,17 @@ UNIT = "particle-steps/s"
 # Algorithmic lane operations per particle-step of the particle-filter kernel,
 # counted from the kernel source by category: Philox share 20.5, Box-Muller
 # share 10.5, propagation 32 (LG 1), log-weight 15 (LG 5), checks and max 4,
-# quantisation 5, prefix sum and store 6, resampling 15.
+# quantisation 5, prefix sum and store 6, resampling 15.  Binomial SIR: two
+# Philox calls 164 (82 each, one per flow), the two binomial draws 80 (about
+# 40 each: BTRS setup 15, 1.2 proposals of 13 and 2.4 word conversions of 3;
+# inversion's setup and short search cost about the same), the hazard and
+# flows 12, log-weight 15, weights and resampling 30.
 ALG_OPS_PER_PARTICLE_STEP = {
     0: 67.0,    # linear-Gaussian AR(1)
     1: 108.0,   # SEIR-type
+    2: 301.0,   # binomial SIR (Sec. V-A)
 }
+MODEL_NAMES = {0: "LG-AR(1)", 1: "SEIR-type", 2: "binomial SIR"}
 # DRAM bytes per particle-filter launch from one ncu capture of the SEIR-type
 # workload (profiles/pf_kernel_seir_t100_n1024.md), valid only for the kernel
 # source it was taken on (sha-256 prefixes of pf_impl.cuh and common.cuh).
@@ -210,10 +216,16 @@ def run_reference(args, w, rank, world):
 
 
 def workload_config(w, precision: str) -> dict:
-    return {"workload": w.name, "model": "SEIR-type" if w.model == 1 else "LG-AR(1)", "N": w.N,
-            "M": w.M, "T": w.T, "K": w.K, "precision": precision, "proposal": "random walk",
-            "lkernel": "approx. optimal Gaussian",
-            "l2": "flushed between timed steps (256 MiB write outside the step events)"}
+    c = {"workload": w.name, "model": MODEL_NAMES[w.model], "N": w.N,
+         "M": w.M, "T": w.T, "K": w.K, "precision": precision, "proposal": "random walk",
+         "lkernel": "approx. optimal Gaussian",
+         "l2": "flushed between timed steps (256 MiB write outside the step events)"}
+    if w.pf_scheme or w.pf_ess_frac:
+        c["pf_resampling"] = (("multinomial" if w.pf_scheme else "systematic") +
+                              (f" when ESS < {w.pf_ess_frac:g} M" if w.pf_ess_frac else " every step"))
+    if w.prior_kind:
+        c["prior"] = f"uniform on {list(zip(w.prior_lo, w.prior_hi))}"
+    return c
 
 
 def time_runs(S, torch, ctx, w, steps, warmup, flush, rank_sync):
@@ -391,7 +403,7 @@ def main():
         "speedup_vs_fp64_form": (value / fp64["value"]) if fp64 else None,
         "ess_speedup_vs_fp64_form": (ess_per_s / fp64["ess_per_s"]) if fp64 else None,
         "forms": forms,
-        "roofline": {"kernel": "pf_kernel<float,SEIR>", "bound": "alu", "achieved": achieved / 1e9,
+        "roofline": {"kernel": f"pf_kernel<float,{MODEL_NAMES[wr.model]}>", "bound": "alu", "achieved": achieved / 1e9,
                      "peak": peak / 1e9, "unit": "Gop/s", "frac": achieved / peak,
                      "traffic": pf_traffic_if_current() if wr.model == 1 else None,
                      "ops_per_particle_step": ALG_OPS_PER_PARTICLE_STEP[wr.model],
