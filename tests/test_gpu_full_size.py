@@ -74,6 +74,34 @@ def test_full_size_pf_fp64_sampled_and_mixed(S, name):
     assert abs(d.mean()) < 4 * se
 
 
+def test_full_size_sir_fp64_sampled_and_mixed(S):
+    """The paper's SIR experiment at full size (N = 1024, M = 500, T = 30, the
+    paper's filter): sampled filters of the FP64 launch bit-exact against the
+    oracle; the mixed launch, whose FP32 sampler reads its words differently,
+    without offset against the FP64 one over all 1024 filters."""
+    w = I.workload("sir_t30_n1024")
+    u = np.random.default_rng(12).random((w.N, 2))
+    theta = np.column_stack([0.85 + 0.1 * (u[:, 0] - 0.5), 0.20 + 0.05 * (u[:, 1] - 0.5)])
+    ll64, shape64 = _full_pf(S, w, theta, I.PREC_FP64)
+    ll32, shape32 = _full_pf(S, w, theta, I.PREC_MIXED)
+    cfg = O.config_from(w)
+    idx = np.sort(np.random.default_rng(4).choice(w.N, size=8, replace=False))
+    for i in idx:
+        r_ll, r_delta, r_anc = O.pf_loglik(cfg, theta[i], w.y, 1, i, trace=True)
+        if np.isfinite(r_ll):
+            assert abs(ll64[i] - r_ll) / max(abs(r_ll), 10.0) < 1e-12, (i, ll64[i], r_ll)
+        else:
+            assert ll64[i] == r_ll
+    fin = np.isfinite(ll64) & np.isfinite(ll32)
+    assert fin.mean() > 0.9
+    d = ll32[fin] - ll64[fin]
+    se = d.std(ddof=1) / math.sqrt(len(d))
+    print(f"sir: shapes fp64 {shape64} mixed {shape32}; mixed - fp64 mean {d.mean():.3g} +- {se:.3g}")
+    # E[p^] is the same in both forms; log p^ of independent filters differs in mean by
+    # at most the difference of their log-variance biases, small against the spread here
+    assert abs(d.mean()) < 4 * se + 0.1 * d.std()
+
+
 def _compare_stats(g, o, scale):
     assert g["k"] == o["k"] and g["resampled"] == o["resampled"], (g, o)
     assert g["lk_fallback"] == o["lk_fallback"]
