@@ -57,6 +57,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-forms", action="store_true",
                    help="skip the accuracy comparison of the random-walk, FP64 and learned forms")
+    p.add_argument("--pf", default="workload", choices=["workload", "systematic", "paper"],
+                   help="particle-filter resampling: the workload's own, systematic after every step, "
+                        "or the paper's (multinomial when the ESS falls below M/2)")
     p.add_argument("--ppt", type=int, default=0, help="pin particles per thread (0: tuner)")
     p.add_argument("--cta", type=int, default=0, help="pin threads per PF CTA (0: tuner)")
     return p.parse_args()
@@ -310,6 +313,10 @@ def main():
     rank, world, local = dist_env()
     from paper_2311_12973_gb300 import inputs as I
     w = I.workload(args.workload)
+    if args.pf == "systematic":
+        w = w.with_(pf_scheme=I.PF_SYSTEMATIC, pf_ess_frac=0.0)
+    elif args.pf == "paper":
+        w = w.with_(pf_scheme=I.PF_MULTINOMIAL, pf_ess_frac=0.5)
     if args.impl == "reference":
         run_reference(args, w, rank, world)
         return
