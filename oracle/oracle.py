@@ -245,7 +245,7 @@ def multinomial_from_q(q, U):
 
 
 def binomial(n, p, seed, c0, c1, c2, c3, words: bool = False):
-    """Bin(n, p) from the PF_BINOM word stream (counters c0 + 8192 m, c1, c2, c3)."""
+    """Bin(n, p) from a fresh word stream (counters c0 + 4096 m, c1, c2, c3)."""
     used = np.zeros(1, dtype=np.int32)
     k = lib().oracle_binomial(float(n), float(p), int(seed), int(c0), int(c1), int(c2), int(c3),
                               _p(used, C.c_int32))

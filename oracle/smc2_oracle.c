@@ -72,12 +72,16 @@ void oracle_normals4(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint3
   }
 }
 
-static uint32_t oracle_word0(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3) {
+static uint32_t oracle_word(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, int idx) {
   uint32_t ctr[4] = {c0, c1, c2, c3};
   uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
   uint32_t w[4];
   oracle_philox4x32_10(ctr, key, w);
-  return w[0];
+  return w[idx];
+}
+
+static uint32_t oracle_word0(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3) {
+  return oracle_word(seed, c0, c1, c2, c3, 0);
 }
 
 /* ------------------------------------------------------------------ */
@@ -183,11 +187,24 @@ typedef struct {
   int used, calls, words;
 } binom_words;
 
+static void binom_words_init(binom_words* b, uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2,
+                             uint32_t c3) {
+  b->key[0] = (uint32_t)seed;
+  b->key[1] = (uint32_t)(seed >> 32);
+  b->ctr[0] = c0;
+  b->ctr[1] = c1;
+  b->ctr[2] = c2;
+  b->ctr[3] = c3;
+  b->used = 4;
+  b->calls = 0;
+  b->words = 0;
+}
+
 /* Next uniform (2w + 1) 2^-33 in (0, 1); 0 when the 64 calls are spent. */
 static double binom_next_u(binom_words* b) {
   if (b->used == 4) {
     if (b->calls == 64) return 0.0;
-    uint32_t ctr[4] = {b->ctr[0] + 8192u * (uint32_t)b->calls, b->ctr[1], b->ctr[2], b->ctr[3]};
+    uint32_t ctr[4] = {b->ctr[0] + 4096u * (uint32_t)b->calls, b->ctr[1], b->ctr[2], b->ctr[3]};
     oracle_philox4x32_10(ctr, b->key, b->w);
     b->calls++;
     b->used = 0;
@@ -244,30 +261,23 @@ static double binom_half(double n, double p, binom_words* b) {
   }
 }
 
+/* Bin(n, p) reading the stream b from where it stands. */
+static double binomial_from(double n, double p, binom_words* b) {
+  if (!(p > 0.0) || n <= 0.0) return 0.0;
+  if (!(p < 1.0)) return n;
+  if (p > 0.5) {
+    const double r = binom_half(n, 1.0 - p, b);
+    return r < 0.0 ? floor((n + 1.0) * p) : n - r;
+  }
+  const double r = binom_half(n, p, b);
+  return r < 0.0 ? floor((n + 1.0) * p) : r;
+}
+
 double oracle_binomial(double n, double p, uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2,
                        uint32_t c3, int* words) {
   binom_words b;
-  b.key[0] = (uint32_t)seed;
-  b.key[1] = (uint32_t)(seed >> 32);
-  b.ctr[0] = c0;
-  b.ctr[1] = c1;
-  b.ctr[2] = c2;
-  b.ctr[3] = c3;
-  b.used = 4;
-  b.calls = 0;
-  b.words = 0;
-  double k;
-  if (!(p > 0.0) || n <= 0.0) {
-    k = 0.0;
-  } else if (!(p < 1.0)) {
-    k = n;
-  } else if (p > 0.5) {
-    const double r = binom_half(n, 1.0 - p, &b);
-    k = r < 0.0 ? floor((n + 1.0) * p) : n - r;
-  } else {
-    const double r = binom_half(n, p, &b);
-    k = r < 0.0 ? floor((n + 1.0) * p) : r;
-  }
+  binom_words_init(&b, seed, c0, c1, c2, c3);
+  const double k = binomial_from(n, p, &b);
   if (words) *words = b.words;
   return k;
 }
@@ -329,15 +339,18 @@ static void oracle_propagate(const oracle_cfg* c, const double* theta, double z,
 }
 
 /* One day of the SIR model for particle j at step t: both flows from the
- * previous day's (S, I); probabilities 1 - exp(-h) formed as -expm1(-h). */
+ * previous day's (S, I); probabilities 1 - exp(-h) formed as -expm1(-h).  The
+ * two draws read one word stream, the I->R draw from where the S->I draw
+ * stopped. */
 static void oracle_propagate_sir(const oracle_cfg* c, const double* theta, uint32_t k, uint32_t c2,
                                  int j, int t, double* x) {
   const double S = x[0], I = x[1];
   const double p_si = -expm1(-(theta[0] * I / c->npop));
   const double p_ir = -expm1(-theta[1]);
-  const uint32_t c3 = ORACLE_TAG_PF_BINOM | (k << 4);
-  const double n_si = oracle_binomial(S, p_si, c->seed, (uint32_t)j, (uint32_t)t, c2, c3, NULL);
-  const double n_ir = oracle_binomial(I, p_ir, c->seed, (uint32_t)j + 4096u, (uint32_t)t, c2, c3, NULL);
+  binom_words b;
+  binom_words_init(&b, c->seed, (uint32_t)j, (uint32_t)t, c2, ORACLE_TAG_PF_BINOM | (k << 4));
+  const double n_si = binomial_from(S, p_si, &b);
+  const double n_ir = binomial_from(I, p_ir, &b);
   x[0] = S - n_si;
   x[1] = I + n_si - n_ir;
 }
@@ -468,7 +481,7 @@ double oracle_pf_loglik(const oracle_cfg* c, const double* theta, const double* 
       if (resample) {
         if (c->pf_scheme == ORACLE_PF_MULTINOMIAL) {
           for (int j = 0; j < M; ++j)
-            Um[j] = oracle_word0(c->seed, (uint32_t)j, (uint32_t)t, c2, ORACLE_TAG_PF_MULTI | (k << 4));
+            Um[j] = oracle_word(c->seed, (uint32_t)j >> 2, (uint32_t)t, c2, ORACLE_TAG_PF_MULTI | (k << 4), j & 3);
           oracle_multinomial_from_q(q, M, Um, anc);
         } else {
           uint32_t U = oracle_word0(c->seed, 0, (uint32_t)t, c2, ORACLE_TAG_PF_RES | (k << 4));

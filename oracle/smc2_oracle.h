@@ -24,11 +24,12 @@
  *     4 PF_INIT      c0 = particle j, c1 = 0; normal 0 is the initial draw
  *     5 PF_PROP      c0 = particle j, c1 = (t-1) >> 2; step t uses normal (t-1) & 3
  *     6 PF_RES       c0 = 0, c1 = t; word 0 is U for the resampling after step t
- *     8 PF_MULTI     c0 = slot j, c1 = t; word 0 is U_j for multinomial resampling
- *     9 PF_BINOM     c0 = j + 4096 b + 8192 m, c1 = t: call m of the word stream
- *                    of particle j's binomial draw b at step t (b = 0 the S -> I
- *                    flow, 1 the I -> R flow of the SIR model); the draw reads
- *                    the words of calls m = 0, 1, ... in order (x, y, z, w).
+ *     8 PF_MULTI     c0 = slot j >> 2, c1 = t; word j & 3 is U_j for multinomial
+ *                    resampling after step t (one call serves four slots)
+ *     9 PF_BINOM     c0 = j + 4096 m, c1 = t: call m of particle j's word stream
+ *                    at step t; the SIR model's S -> I draw reads the words of
+ *                    calls m = 0, 1, ... in order (x, y, z, w), and its I -> R
+ *                    draw continues from where the first stopped.
  *  A word w read by the binomial sampler becomes u = (2w + 1) 2^-33 (exact in
  *  double); a uniform prior draw uses the same form of the THETA_INIT words.
  *
@@ -109,8 +110,8 @@ int oracle_multinomial_from_q(const uint64_t* q, int n, const uint32_t* U, int32
  * machine forms the same value. */
 double oracle_ess_from_q(const uint64_t* q, int n);
 
-/* Binomial(n, p) variate from the PF_BINOM word stream with counters
- * (c0 + 8192 m, c1, c2, c3), m = 0, 1, ...  n a non-negative integer.
+/* Binomial(n, p) variate from a fresh PF_BINOM-layout word stream with
+ * counters (c0 + 4096 m, c1, c2, c3), m = 0, 1, ...  n a non-negative integer.
  * p <= 0 (or NaN) gives 0, p >= 1 gives n; p > 1/2 draws n - Bin(n, 1 - p).
  * n p < 10: inversion, a sequential search from 0 on the pmf recurrence
  * (a redraw if rounding carries the search past n).  Otherwise Hormann's

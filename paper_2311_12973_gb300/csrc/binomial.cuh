@@ -12,10 +12,11 @@
 //    (-1/2, 1/2), us = 1/2 - |u|; the squeeze us >= 0.07, v <= v_r accepts most
 //    proposals outright, the rest pass the exact test of log(v alpha / (a/us^2 + b))
 //    against the log-pmf ratio to the mode m.
-// Uniforms come from the draw's own Philox word stream: call m = 0, 1, ... of
-// counter (c0 + 8192 m, c1, c2, c3), words read in order x, y, z, w, each word
-// w giving u = (2w + 1) 2^-33 (exact in double).  After 64 calls (probability
-// far below 1e-40 for any n, p) the draw returns floor((n + 1) p).
+// Uniforms come from a Philox word stream: call m = 0, 1, ... of counter
+// (c0 + 4096 m, c1, c2, c3), words read in order x, y, z, w, each word w giving
+// u = (2w + 1) 2^-33 (exact in double).  Consecutive draws may share a stream,
+// each reading from where the last stopped.  After 64 calls (probability far
+// below 1e-40) a draw returns floor((n + 1) p).
 //
 // The FP64 form below does every step in double with explicitly rounded
 // operations, so that its decisions follow the same roundings on any IEEE
@@ -39,7 +40,7 @@ struct BinomWords {
   __device__ __forceinline__ double next() {
     if (left == 0) {
       if (calls == 64) return 0.0;
-      cur = philox4x32_10(make_uint4(ctr.x + 8192u * (uint32_t)calls, ctr.y, ctr.z, ctr.w), key);
+      cur = philox4x32_10(make_uint4(ctr.x + 4096u * (uint32_t)calls, ctr.y, ctr.z, ctr.w), key);
       ++calls;
       left = 4;
     }
@@ -98,11 +99,10 @@ static __device__ __noinline__ double binomial_half(double n, double p, BinomWor
   }
 }
 
-// Bin(n, p) for an integer n >= 0 from the word stream of counter ctr.
-__device__ __forceinline__ double binomial_draw(double n, double p, uint4 ctr, uint2 key) {
+// Bin(n, p) for an integer n >= 0, reading the stream b from where it stands.
+__device__ __forceinline__ double binomial_draw(double n, double p, BinomWords& b) {
   if (!(p > 0.0) || n <= 0.0) return 0.0;
   if (!(p < 1.0)) return n;
-  BinomWords b(ctr, key);
   if (p > 0.5) {
     const double r = binomial_half(n, __dsub_rn(1.0, p), b);
     return r < 0.0 ? floor(__dmul_rn(__dadd_rn(n, 1.0), p)) : __dsub_rn(n, r);
@@ -156,7 +156,7 @@ struct BinomWordsF {
   __device__ __forceinline__ float next() {
     if (left == 0) {
       if (calls == 64) return 0.f;
-      cur = philox4x32_10(make_uint4(ctr.x + 8192u * (uint32_t)calls, ctr.y, ctr.z, ctr.w), key);
+      cur = philox4x32_10(make_uint4(ctr.x + 4096u * (uint32_t)calls, ctr.y, ctr.z, ctr.w), key);
       ++calls;
       left = 4;
     }
@@ -224,11 +224,11 @@ static __device__ __noinline__ float binomial_half_f32(float n, float p, BinomWo
   }
 }
 
-// Bin(n, p) in the FP32 form, for an integer n >= 0 below 2^24.
-__device__ __forceinline__ float binomial_draw(float n, float p, uint4 ctr, uint2 key) {
+// Bin(n, p) in the FP32 form, for an integer n >= 0 below 2^24, reading the
+// stream b from where it stands.
+__device__ __forceinline__ float binomial_draw(float n, float p, BinomWordsF& b) {
   if (!(p > 0.f) || n <= 0.f) return 0.f;
   if (!(p < 1.f)) return n;
-  BinomWordsF b(ctr, key);
   if (p > 0.5f) {
     const float r = binomial_half_f32(n, 1.f - p, b);
     return r < 0.f ? floorf((n + 1.f) * p) : n - r;

@@ -19,8 +19,8 @@ enum : uint32_t {
   TAG_PF_PROP = 5,     // c0 = particle, c1 = (t-1) >> 2; normal (t-1) & 3
   TAG_PF_RES = 6,      // c0 = 0, c1 = t; word 0
   TAG_MLP_INIT = 7,    // c0 = parameter index; word 0 (surrogate network initial weights)
-  TAG_PF_MULTI = 8,    // c0 = slot, c1 = t; word 0 (multinomial PF resampling)
-  TAG_PF_BINOM = 9,    // c0 = particle + 4096 flow + 8192 call, c1 = t (SIR binomial flows)
+  TAG_PF_MULTI = 8,    // c0 = slot >> 2, c1 = t; word slot & 3 (multinomial PF resampling)
+  TAG_PF_BINOM = 9,    // c0 = particle + 4096 call, c1 = t (the SIR flows' shared word stream)
 };
 
 // Device status bits (sticky; mapped to smc2_status codes on the host).

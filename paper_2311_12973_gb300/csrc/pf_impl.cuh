@@ -29,6 +29,7 @@
 #pragma once
 #include <cfloat>
 #include <cmath>
+#include <type_traits>
 
 #include "binomial.cuh"
 #include "common.cuh"
@@ -314,8 +315,8 @@ struct FilterParams<R, MODEL_SEIR> {
 // n(I->R) ~ Bin(I, 1 - exp(-gamma)); y_t ~ Poisson(I_t).  (The printed S->I
 // probability also carries S_{t-1} in the exponent; this is the per-susceptible
 // hazard of the chain-binomial model the section cites.)  Both flows are drawn
-// from particle j's word streams (j and j + 4096) of step t, by the binomial
-// sampler of the working precision.
+// by the binomial sampler of the working precision from particle j's one word
+// stream of step t, the I->R draw reading from where the S->I draw stopped.
 template <typename R>
 struct FilterParams<R, MODEL_SIR> {
   R beta, npop, S0, I0, p_ir;
@@ -335,8 +336,9 @@ struct FilterParams<R, MODEL_SIR> {
     const R S = x[0], I = x[1];
     const R h = beta * I / npop;
     const R p_si = -expm1(-h);
-    const R n_si = binomial_draw(S, p_si, make_uint4(j, t, c2, c3), key);
-    const R n_ir = binomial_draw(I, p_ir, make_uint4(j + 4096u, t, c2, c3), key);
+    typename std::conditional<sizeof(R) == 8, BinomWords, BinomWordsF>::type b(make_uint4(j, t, c2, c3), key);
+    const R n_si = binomial_draw(S, p_si, b);
+    const R n_ir = binomial_draw(I, p_ir, b);
     x[0] = S - n_si;
     x[1] = (I + n_si) - n_ir;  // integers: exact in either precision
   }
@@ -603,15 +605,19 @@ __device__ __forceinline__ void run_filter(const PFJob& J, const PFModel& mdl, i
       for (int r = 0; r < (GEN ? PPT : 1); ++r) lwc[r] = (R)0;
     }
     if (GEN && resample && multinomial) {
-      // slot j draws u_j = (2 U_j + 1) / 2^33 and takes the first particle with C_i > floor(u_j S)
+      // slot j draws u_j = (2 U_j + 1) / 2^33 (word j & 3 of call j >> 2) and takes the
+      // first particle with C_i > floor(u_j S)
 #pragma unroll
       for (int r = 0; r < PPT; ++r) P[lt * PPT + r] = base + excl + c[r];
       group_sync();
+      uint4 wj = make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
       for (int r = 0; r < PPT; ++r) {
         const int j = lt * PPT + r;
+        if (r == 0 || (j & 3) == 0)  // a thread's consecutive slots share their calls
+          wj = philox4x32_10(make_uint4((uint32_t)j >> 2, (uint32_t)t, c2, c3multi), key);
         if (j >= M) continue;
-        const uint32_t Uj = philox4x32_10(make_uint4((uint32_t)j, (uint32_t)t, c2, c3multi), key).x;
+        const uint32_t Uj = (j & 2) ? ((j & 1) ? wj.w : wj.z) : ((j & 1) ? wj.y : wj.x);
         const uint64_t tau = (uint64_t)(((unsigned __int128)(2ull * Uj + 1ull) * S) >> 33);
         int lo = 0, hi = M - 1;
         while (lo < hi) {
