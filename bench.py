@@ -29,15 +29,18 @@ UNIT = "particle-steps/s"
 # Algorithmic lane operations per particle-step of the particle-filter kernel,
 # counted from the kernel source by category: Philox share 20.5, Box-Muller
 # share 10.5, propagation 32 (LG 1), log-weight 15 (LG 5), checks and max 4,
-# quantisation 5, prefix sum and store 6, resampling 15.  Binomial SIR: two
-# Philox calls 164 (82 each, one per flow), the two binomial draws 80 (about
-# 40 each: BTRS setup 15, 1.2 proposals of 13 and 2.4 word conversions of 3;
-# inversion's setup and short search cost about the same), the hazard and
-# flows 12, log-weight 15, weights and resampling 30.
+# quantisation 5, prefix sum and store 6, resampling 15.  Binomial SIR with
+# the paper's filter: 1.28 Philox calls of 82 for the two flows' shared word
+# stream (105), the two binomial draws 80 (about 40 each: BTRS setup 15, 1.2
+# proposals of 13 and 2.4 word conversions of 3; inversion's setup and short
+# search cost about the same), the hazard and flows 12, log-weight 15, checks,
+# max, quantisation and prefix sum 15, the ESS's sum of q^2 5, and multinomial
+# slots on the 86 % of steps that resample (a quarter Philox call, a 9-step
+# binary search, the state read: 51.5) 44.
 ALG_OPS_PER_PARTICLE_STEP = {
     0: 67.0,    # linear-Gaussian AR(1)
     1: 108.0,   # SEIR-type
-    2: 301.0,   # binomial SIR (Sec. V-A)
+    2: 276.0,   # binomial SIR (Sec. V-A), the paper's filter
 }
 MODEL_NAMES = {0: "LG-AR(1)", 1: "SEIR-type", 2: "binomial SIR"}
 # DRAM bytes per particle-filter launch from one ncu capture of the SEIR-type
