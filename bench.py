@@ -46,7 +46,7 @@ MODEL_NAMES = {0: "LG-AR(1)", 1: "SEIR-type", 2: "binomial SIR"}
 # DRAM bytes per particle-filter launch from one ncu capture of the SEIR-type
 # workload (profiles/pf_kernel_seir_t100_n1024.md), valid only for the kernel
 # source it was taken on (sha-256 prefixes of pf_impl.cuh and common.cuh).
-PF_TRAFFIC = {"bytes": 108544.0, "sources": {"pf_impl.cuh": "304aba5f4b8533a2", "common.cuh": "1b077c79d670fbf8"}}
+PF_TRAFFIC = {"bytes": 106496.0, "sources": {"pf_impl.cuh": "47574a10041971f0", "common.cuh": "4a6a88e11701ac7a"}}
 
 
 def parse():
