@@ -311,6 +311,33 @@ def accuracy_forms(S, torch, I, wr, world, seeds=8):
     return res
 
 
+def sir_paper_table(S, torch, I, wr, runs=10):
+    """The paper's SIR results table (Sec. V) on this GPU: `runs` Monte Carlo
+    runs of the workload with their own seeds; the mean of the recycled
+    estimates of (beta, gamma), their mean squared error against the
+    simulation truth, and the device time of one run."""
+    import numpy as np
+    ctx = S.SMC2(S.make_config(wr), wr.y)
+    ctx.run(wr.K, stats=False)
+    stream = torch.cuda.current_stream()
+    est, ms = [], []
+    for r in range(runs):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ctx.reset(wr.seed + 7919 * (r + 1))
+        a.record(stream)
+        ctx.run(wr.K, stats=False)
+        b.record(stream)
+        mean, _, _ = ctx.estimate()
+        est.append(mean[:2])
+        ms.append(a.elapsed_time(b))
+    ctx.close()
+    est = np.array(est)
+    truth = np.array(I.SIR_TRUTH)
+    return {"runs": runs, "E_beta": float(est[:, 0].mean()), "E_gamma": float(est[:, 1].mean()),
+            "mse": float(((est - truth) ** 2).mean()), "ms_per_run": float(np.mean(ms)),
+            "truth": list(I.SIR_TRUTH), "K_x_N": wr.K * wr.N, "M": wr.M}
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -393,6 +420,9 @@ def main():
     forms = None
     if not args.no_forms and wr.model == I.SEIR and wr.D <= 8:
         forms = accuracy_forms(S, torch, I, wr, world)
+    paper_table = None
+    if not args.no_forms and wr.model == I.SIR:
+        paper_table = sir_paper_table(S, torch, I, wr)
 
     if rank != 0:
         return
@@ -413,6 +443,7 @@ def main():
         "speedup_vs_fp64_form": (value / fp64["value"]) if fp64 else None,
         "ess_speedup_vs_fp64_form": (ess_per_s / fp64["ess_per_s"]) if fp64 else None,
         "forms": forms,
+        "paper_table": paper_table,
         "roofline": {"kernel": f"pf_kernel<float,{MODEL_NAMES[wr.model]}>", "bound": "alu", "achieved": achieved / 1e9,
                      "peak": peak / 1e9, "unit": "Gop/s", "frac": achieved / peak,
                      "traffic": pf_traffic_if_current() if wr.model == 1 else None,
