@@ -93,7 +93,7 @@ typedef struct smc2_ctx smc2_ctx; /* opaque; owns its device workspace */
  *   (S, I) with S_0 = npop - i0, I_0 = i0) uses npop (an integer <= 2^24) and
  *   i0; each day n(S->I) ~ Bin(S, 1 - exp(-beta I / npop)) and
  *   n(I->R) ~ Bin(I, 1 - exp(-gamma)), y_t ~ Poisson(I_t).  It runs with
- *   ppt <= 4 (M <= 2048) and the random-walk proposal.
+ *   ppt <= 4 (M <= 2048).
  * ppt: particles per thread of the particle-filter kernel (0 = pick by the
  *   built-in tuner; otherwise 1, 2, 4, 8 or 16).
  * proposal = SMC2_PROP_MLP (learned proposal; not in the paper): once the

@@ -138,8 +138,7 @@ smc2_status validate(const smc2_config* c) {
   }
   if (c->model == SMC2_MODEL_SIR) {  // integer compartments, exact in float
     if (!finite_pos(c->npop) || c->npop > 16777216.0 || c->npop != std::floor(c->npop) ||
-        !(c->i0 >= 0.0 && c->i0 <= c->npop) || c->i0 != std::floor(c->i0) || c->ppt > 4 ||
-        c->proposal != SMC2_PROP_RW)
+        !(c->i0 >= 0.0 && c->i0 <= c->npop) || c->i0 != std::floor(c->i0) || c->ppt > 4)
       return SMC2_EINVAL;
   }
   if (c->model == SMC2_MODEL_SEIR) {

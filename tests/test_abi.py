@@ -60,11 +60,10 @@ def _cfg(S, **over):
     {"pf_scheme": 2}, {"pf_scheme": -1}, {"pf_ess_frac": 1.5}, {"pf_ess_frac": -0.1},
     {"pf_ess_frac": float("nan")}, {"pf_scheme": 1, "ppt": 8},
     {"pf_ess_frac": 0.5, "ppt": 16}, {"pf_scheme": 1, "M": 4096},
-    # priors and the SIR model: D = 2, integer population and infected, ppt <= 4, random walk
+    # priors and the SIR model: D = 2, integer population and infected, ppt <= 4
     {"prior_kind": 2}, {"model": 2}, {"model": 2, "D": 2, "npop": 10.5, "i0": 3.0},
     {"model": 2, "D": 2, "npop": 1e4, "i0": 2e4}, {"model": 2, "D": 2, "npop": 1e4, "i0": 2.5},
     {"model": 2, "D": 2, "npop": 1e8, "i0": 3.0}, {"model": 2, "D": 2, "npop": 1e4, "i0": 3.0, "ppt": 8},
-    {"model": 2, "D": 2, "npop": 1e4, "i0": 3.0, "proposal": 1},
 ])
 def test_invalid_configs_rejected_before_gpu_work(S, over):
     import numpy as np

@@ -172,3 +172,27 @@ def test_paper_workload_recovers_truth(S):
     sd = np.sqrt(np.diag(cov))
     assert np.all(np.abs(mean - np.array(I.SIR_TRUTH)) < 0.05 + 4 * sd), (mean, sd)
     assert all(1.0 <= s[0]["ess"] <= w.N for s in stats)
+
+
+def test_learned_proposal_on_the_papers_experiment(S):
+    # At the paper's size the random walk (Sigma = 0.1 I) keeps the ESS near 1, so the
+    # learned proposal's guard (ESS >= 2 (D + 1) in the previous population) never
+    # passes and the run is the random walk's, bit for bit.  With N = 8192 the guard
+    # passes in some iterations and the network's proposals raise the ESS.
+    def run(w, proposal):
+        ctx = S.SMC2(S.make_config(w, proposal=proposal), w.y)
+        st = [s[0] for s in ctx.run(w.K)]
+        mean, logz, ess = ctx.estimate()
+        ctx.close()
+        return st, mean, ess
+    w = I.workload("sir_t30_n1024", seed=201)
+    st_rw, m_rw, e_rw = run(w, I.PROP_RW)
+    st_ml, m_ml, e_ml = run(w, I.PROP_MLP)
+    assert all(s["mlp_used"] == 0 for s in st_ml)
+    assert np.array_equal(m_rw, m_ml) and e_rw == e_ml
+    wb = I.workload("sir_t30_n1024", N=8192, K=20, seed=101)
+    st_rw, m_rw, e_rw = run(wb, I.PROP_RW)
+    st_ml, m_ml, e_ml = run(wb, I.PROP_MLP)
+    used = sum(s["mlp_used"] for s in st_ml)
+    print(f"N=8192 K=20: random walk ESS sum {e_rw:.0f}; learned ESS sum {e_ml:.0f} ({used} iterations by the network)")
+    assert used >= 1 and e_ml > 2 * e_rw
