@@ -196,3 +196,27 @@ def test_learned_proposal_on_the_papers_experiment(S):
     used = sum(s["mlp_used"] for s in st_ml)
     print(f"N=8192 K=20: random walk ESS sum {e_rw:.0f}; learned ESS sum {e_ml:.0f} ({used} iterations by the network)")
     assert used >= 1 and e_ml > 2 * e_rw
+
+
+def test_mixed_smc2_posterior_mean_matches_quadrature(S):
+    # mixed precision end to end (the FP32 sampler, the float ESS trigger) against the
+    # posterior mean by quadrature of the exact likelihood of a 30-person population
+    T = 10
+    y = I.simulate_sir(T, 0.9, 0.3, 30.0, 3.0, seed=5)
+    G = 24
+    g = (np.arange(G) + 0.5) / G
+    L = np.array([[sir_exact_loglik(b, c, 30.0, 3.0, y) for c in g] for b in g])
+    W = np.exp(L - L.max())
+    W /= W.sum()
+    quad = np.array([(W.sum(axis=1) * g).sum(), (W.sum(axis=0) * g).sum()])
+    w = I.workload("sir_t30_n1024", N=256, M=64, T=T, K=10, npop=30.0, i0=3.0)
+    ctx = S.SMC2(S.make_config(w), y)
+    est = []
+    for s in range(24):
+        ctx.reset(300 + s)
+        ctx.run(w.K, stats=False)
+        est.append(ctx.estimate()[0][:2])
+    ctx.close()
+    est = np.array(est)
+    se = est.std(axis=0, ddof=1) / math.sqrt(len(est))
+    assert np.all(np.abs(est.mean(axis=0) - quad) < 4 * se + 2e-3), (est.mean(axis=0), quad, se)
