@@ -66,3 +66,16 @@ def test_reference_arm_under_torchrun_prints_one_line():
     line = json.loads(lines[0])
     assert line["impl"] == "reference" and line["value"] > 0 and line["n_gpus"] == 2
     assert line["cpu_baseline"]["kind"] == "oracle"
+
+
+@pytest.mark.parametrize("pf", ["workload", "systematic"])
+def test_reference_arm_on_the_papers_sir_experiment(pf):
+    """The reference arm on the SIR workload, with its own filter and with the default one."""
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+           "--warmup", "0", "--workload", "sir_t30_n1024", "--pf", pf]
+    r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads([l for l in r.stdout.splitlines() if l.startswith("{")][-1])
+    assert line["impl"] == "reference" and line["value"] > 0 and line["config"]["model"] == "binomial SIR"
+    assert line["config"]["prior"].startswith("uniform")
+    assert ("pf_resampling" in line["config"]) == (pf == "workload")
