@@ -32,8 +32,11 @@ def _compare_stats(g, o, scale):
         assert rel_err(g[key], o[key], scale) < 1e-12, (key, g[key], o[key])
     assert rel_err(g["ess"], o["ess"]) < 1e-9, (g["ess"], o["ess"])
     assert rel_err(g["est"], o["est"], 1.0) < 1e-9, (g["est"], o["est"])
-    # covariance: one pass about the first proposal on the device, two passes in the oracle
-    assert rel_err(g["cov"], o["cov"], max(float(np.max(np.abs(o["cov"]))), 1e-300)) < 1e-8, (g["cov"], o["cov"])
+    # covariance: one pass about the first proposal on the device, two passes in the oracle;
+    # the one-pass form's rounding floor is about 1e-16 of the squared scale of theta, which
+    # dominates when the population collapses onto one point (ESS near 1)
+    floor = 1e-15 * max(1.0, float(np.max(np.abs(o["est"]))) ** 2)
+    assert np.max(np.abs(g["cov"] - o["cov"])) <= 1e-8 * float(np.max(np.abs(o["cov"]))) + floor, (g["cov"], o["cov"])
 
 
 def _compare_state(S_ctx, ref, scale):
@@ -145,27 +148,39 @@ def test_nonfinite_outer_weights_reported(S):
     assert e.value.status == S.ENONFINITE
 
 
-def test_batched_datasets_match_oracle(S):
+BATCHED = {
+    "lg": ("lg_t50_n64", [(64, 128, 50), (100, 64, 30), (33, 200, 45)], {}),
+    "lg_paper_pf": ("lg_t50_n64", [(64, 128, 50), (100, 64, 30), (33, 200, 45)],
+                    dict(pf_scheme=I.PF_MULTINOMIAL, pf_ess_frac=0.5)),
+    "sir": ("sir_t30_n1024", [(64, 100, 30), (96, 64, 20), (40, 150, 25)], dict(precision=I.PREC_FP64)),
+}
+
+
+@pytest.mark.parametrize("case", list(BATCHED))
+def test_batched_datasets_match_oracle(S, case):
     """Datasets of different N, M and T in one context: each follows its own
     random stream (dataset index in the counter) and must equal the oracle's
-    single-dataset run of that dataset."""
-    shapes = [(64, 128, 50), (100, 64, 30), (33, 200, 45)]
-    ws = [I.workload("lg_t50_n64", N=n, M=m, T=t, K=4, dataset=d, data_seed=10 + d)
+    single-dataset run of that dataset; with the paper's particle filter, and
+    for the SIR model with its uniform prior."""
+    name, shapes, over = BATCHED[case]
+    ws = [I.workload(name, N=n, M=m, T=t, K=4, dataset=d, data_seed=10 + d, **over)
           for d, (n, m, t) in enumerate(shapes)]
     y = np.concatenate([w.y for w in ws])
     ctx = S.SMC2(S.make_config(ws[0]), y, datasets=shapes)
     stats = ctx.run(4)
     for d, w in enumerate(ws):
         ref = O.SMC2(O.config_from(w), w.y).run(w.K)
-        scale = max(10.0, float(np.max(np.abs(ref.logw[np.isfinite(ref.logw)]))))
+        fin = np.isfinite(ref.logw)
+        scale = max(10.0, float(np.max(np.abs(ref.logw[fin]))))
         for k in range(w.K):
             assert stats[k][d]["dataset"] == d
             _compare_stats(stats[k][d], ref.stats[k], scale)
         k, th, lp, ll, lw = ctx.get_state(d)
         assert k == ref.k
         assert rel_err(th, ref.theta, 1.0) < 1e-10
-        assert rel_err(ll, ref.loglik, scale) < 1e-12
-        assert rel_err(lw, ref.logw, scale) < 1e-12
+        assert np.array_equal(np.isfinite(lw), fin)  # zero-weight samples (outside a uniform prior) alike
+        assert rel_err(ll[fin], ref.loglik[fin], scale) < 1e-12
+        assert rel_err(lw[fin], ref.logw[fin], scale) < 1e-12
         mean, logz, ess_sum = ctx.estimate(d)
         ref_mean, _ = ref.recycled()
         assert rel_err(mean, ref_mean, 1.0) < 1e-9
