@@ -116,8 +116,8 @@ __device__ __forceinline__ double binomial_draw(double n, double p, BinomWords& 
 // uniforms u = ((w >> 9) + 0.5) 2^-23 (exact) from the same word stream.  A
 // warp pays for a branch any of its lanes takes, and a double instruction
 // occupies the narrow FP64 unit for the whole warp, so the rare exact test is
-// in float too, in a form without cancellation: with m the mode, r = p / q and
-// Stirling's log j! = (j + 1/2) log(j + 1) - (j + 1) + log(2 pi)/2 + fc(j),
+// in float too, in a form without cancellation: with m the mode and Stirling's
+// log j! = (j + 1/2) log(j + 1) - (j + 1) + log(2 pi)/2 + fc(j),
 //   log f(k)/f(m) = (m + 1/2) log1p((m - k)/(k + 1))
 //                 + (n - m + 1/2) log1p((k - m)/(n - k + 1))
 //                 + (k - m) log1p(((n + 2) p - (k + 1)) / ((k + 1) q))
