@@ -42,6 +42,24 @@ ALG_OPS_PER_PARTICLE_STEP = {
     1: 108.0,   # SEIR-type
     2: 276.0,   # binomial SIR (Sec. V-A), the paper's filter
 }
+# The same counts for the other particle filter: the every-step systematic
+# resampling (15) replaced by the paper's ESS test (5) and multinomial slots
+# (51.5) on the fraction of steps that resample, measured on the oracle (SEIR
+# 58 % at theta near the prior; SIR 86 %), or the other way round.
+ALG_OPS_OTHER_PF = {
+    (1, "paper"): 108.0 - 15.0 + 5.0 + 0.584 * 51.5,     # 128
+    (2, "systematic"): 276.0 - 5.0 - 0.86 * 51.5 + 15.0,  # 242
+}
+
+
+def alg_ops(w) -> float:
+    """Algorithmic lane operations per particle-step of the filter w runs."""
+    paper = bool(w.pf_scheme) or w.pf_ess_frac > 0
+    default_paper = w.model == 2
+    if paper == default_paper:
+        return ALG_OPS_PER_PARTICLE_STEP[w.model]
+    return ALG_OPS_OTHER_PF.get((w.model, "paper" if paper else "systematic"),
+                                ALG_OPS_PER_PARTICLE_STEP[w.model])
 MODEL_NAMES = {0: "LG-AR(1)", 1: "SEIR-type", 2: "binomial SIR"}
 # DRAM bytes per particle-filter launch from one ncu capture of the SEIR-type
 # workload (profiles/pf_kernel_seir_t100_n1024.md), valid only for the kernel
@@ -430,7 +448,8 @@ def main():
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     fma32, fma64 = S.fma_rates()
     pf_avg_ms = pf_ms / max(pf_n, 1)
-    ops = ALG_OPS_PER_PARTICLE_STEP[wr.model] * wr.N * wr.M * wr.T
+    ops_pps = alg_ops(wr)
+    ops = ops_pps * wr.N * wr.M * wr.T
     achieved = ops / (pf_avg_ms * 1e-3)
     peak = alu_peak_ops(props.multi_processor_count, sm_mhz)
     line = {
@@ -447,7 +466,7 @@ def main():
         "roofline": {"kernel": f"pf_kernel<float,{MODEL_NAMES[wr.model]}>", "bound": "alu", "achieved": achieved / 1e9,
                      "peak": peak / 1e9, "unit": "Gop/s", "frac": achieved / peak,
                      "traffic": pf_traffic_if_current() if wr.model == 1 else None,
-                     "ops_per_particle_step": ALG_OPS_PER_PARTICLE_STEP[wr.model],
+                     "ops_per_particle_step": ops_pps,
                      "pf_ms_per_launch": pf_avg_ms, "pf_launches": pf_n,
                      "pf_share_of_step": pf_ms / max(sum(ms), 1e-9),
                      "launch_shape": shape,
@@ -455,9 +474,9 @@ def main():
                                    "(max SM clock of MEASURED_PEAKS.json)",
                      "measured_fma_tflops": {"fp32": fma32 / 1e12, "fp64": fma64 / 1e12}},
         # the whole step against the time its particle filter work needs at the issue peak
-        "ess_roofline": {"bound": "alu", "t_roof_ms": 1e3 * units_per_step * ALG_OPS_PER_PARTICLE_STEP[wr.model] / peak,
+        "ess_roofline": {"bound": "alu", "t_roof_ms": 1e3 * units_per_step * ops_pps / peak,
                          "ms_per_step": step_ms,
-                         "frac": 1e3 * units_per_step * ALG_OPS_PER_PARTICLE_STEP[wr.model] / peak / step_ms},
+                         "frac": 1e3 * units_per_step * ops_pps / peak / step_ms},
         "e2e": {"value": units_per_step * world / (e2e_step * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": 8 * wr.T, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_step},
         "gpu_launches": launches,
