@@ -61,9 +61,9 @@ def alg_ops(w) -> float:
     return ALG_OPS_OTHER_PF.get((w.model, "paper" if paper else "systematic"),
                                 ALG_OPS_PER_PARTICLE_STEP[w.model])
 MODEL_NAMES = {0: "LG-AR(1)", 1: "SEIR-type", 2: "binomial SIR"}
-# DRAM bytes per particle-filter launch from one ncu capture of the SEIR-type
-# workload (profiles/pf_kernel_seir_t100_n1024.md), valid only for the kernel
-# source it was taken on (sha-256 prefixes of pf_impl.cuh and common.cuh).
+# DRAM bytes per particle-filter launch (dram__bytes_read.sum + dram__bytes_write.sum)
+# from one ncu capture of the SEIR-type workload N=1024, M=512, T=100, valid only for
+# the kernel source it was taken on (sha-256 prefixes of pf_impl.cuh and common.cuh).
 PF_TRAFFIC = {"bytes": 106496.0, "sources": {"pf_impl.cuh": "47574a10041971f0", "common.cuh": "4a6a88e11701ac7a"}}
 
 

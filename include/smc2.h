@@ -21,10 +21,13 @@
  *    smc2_init (NULL = the legacy default stream) and is asynchronous unless
  *    the call says it synchronises.  Caller buffers must stay valid until the
  *    work that uses them has completed on that stream.
- *  - Device-side errors (a non-finite outer weight set, an exhausted bounded
- *    wait, an index out of range) are recorded in a device status word and
- *    reported by the next synchronising call; the first error is sticky until
- *    smc2_destroy or smc2_reset.
+ *  - Device-side errors (an outer weight set that is zero or NaN throughout)
+ *    are recorded in a device status word and reported by the next
+ *    synchronising call; the first error is sticky until smc2_destroy or
+ *    smc2_reset.  The kernels hold no spin-waits (their only waits are
+ *    hardware barriers) and compute every index they use from exact integer
+ *    arithmetic on validated sizes, so no device status exists for an expired
+ *    wait or an index out of range.
  *  - Parameters theta are in unconstrained coordinates:
  *      SMC2_MODEL_LG_AR1: (phi, log sigma_x, log sigma_y), D = 3;
  *      SMC2_MODEL_SEIR:   (log beta0, log sigma_rw, log kappa, log gamma), D = 4.
@@ -50,8 +53,8 @@ typedef enum {
   SMC2_ECUDA = 3,      /* a CUDA runtime call failed */
   SMC2_ENONFINITE = 4, /* every outer importance weight is zero or NaN */
   SMC2_ECHOL = 5,      /* reserved: L-kernel factorisation failures fall back, see smc2_iter_stats */
-  SMC2_ETIMEOUT = 6,   /* a bounded device-side wait gave up */
-  SMC2_EBOUNDS = 7,    /* a device-side index check failed */
+  SMC2_ETIMEOUT = 6,   /* reserved, never returned: no kernel of this library spin-waits */
+  SMC2_EBOUNDS = 7,    /* reserved, never returned: device indices are exact by construction */
   SMC2_ESTATE = 8      /* call not valid in the context's current state */
 } smc2_status;
 
@@ -301,7 +304,10 @@ smc2_status smc2_philox_normals(uint64_t seed, const uint32_t* ctr_dev, int n, i
  * array's device address (cudaGetSymbolAddress) and should come before any
  * stream capture.  Every call reuses the same array and clears the counter
  * it needs, so calls that overlap on the GPU (other streams, other threads)
- * race on it.  Asynchronous on `stream`.  Errors: EINVAL, ECUDA. */
+ * race on it.  Asynchronous on `stream`.  The filter kernel records no
+ * device status: a filter whose weights all vanish returns -inf in
+ * loglik_dev, and a non-finite theta gives a non-finite entry there, which the
+ * caller reads.  Errors: EINVAL, ECUDA. */
 #define SMC2_NOALLOC_MAX_T 32000
 smc2_status smc2_pf_loglik_noalloc(const smc2_config* cfg, const double* y_dev,
                                    const double* theta_dev, int n, int iteration,

@@ -103,8 +103,6 @@ smc2_status record_cuda(cudaError_t e, const char* what) {
 
 smc2_status status_from_bits(int bits) {
   if (bits & ST_NONFINITE) return SMC2_ENONFINITE;
-  if (bits & ST_TIMEOUT) return SMC2_ETIMEOUT;
-  if (bits & ST_BOUNDS) return SMC2_EBOUNDS;
   return SMC2_OK;
 }
 
@@ -567,8 +565,8 @@ const char* smc2_status_string(smc2_status s) {
     case SMC2_ECUDA: return "CUDA runtime error";
     case SMC2_ENONFINITE: return "every importance weight is zero or not finite";
     case SMC2_ECHOL: return "covariance factorisation failed";
-    case SMC2_ETIMEOUT: return "bounded device wait expired";
-    case SMC2_EBOUNDS: return "device index out of range";
+    case SMC2_ETIMEOUT: return "reserved (never returned)";
+    case SMC2_EBOUNDS: return "reserved (never returned)";
     case SMC2_ESTATE: return "call not valid in the current state";
   }
   return "unknown status";

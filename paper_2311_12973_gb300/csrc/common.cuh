@@ -24,7 +24,7 @@ enum : uint32_t {
 };
 
 // Device status bits (sticky; mapped to smc2_status codes on the host).
-enum : int { ST_NONFINITE = 1, ST_TIMEOUT = 2, ST_BOUNDS = 4 };
+enum : int { ST_NONFINITE = 1 };
 
 enum : int { MODEL_LG = 0, MODEL_SEIR = 1, MODEL_SIR = 2 };
 enum : int { LK_FORWARD = 0, LK_GAUSS = 1 };

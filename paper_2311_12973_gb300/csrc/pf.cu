@@ -1,4 +1,6 @@
 // pf.cu -- host side of the particle-filter kernel: shapes, attributes, launches.
+#include <mutex>
+
 #include "pf_impl.cuh"
 
 namespace smc2 {
@@ -28,9 +30,19 @@ static const void* select_kernel(int precision, int model, int ppt, bool named, 
                                      : pf_select_f32(model, ppt, named);
 }
 
+// The dynamic shared-memory limit is an attribute of the kernel, shared by
+// every context and by the allocation-free entry point that launch the same
+// instantiation: it is only ever raised, so that one caller's smaller shape
+// never refuses another's larger launch.
 cudaError_t pf_configure(int precision, int model, int ppt, bool named, bool general, size_t smem) {
   const void* f = select_kernel(precision, model, ppt, named, general);
   if (!f) return cudaErrorInvalidValue;
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lock(mu);
+  cudaFuncAttributes a{};
+  const cudaError_t e = cudaFuncGetAttributes(&a, f);
+  if (e != cudaSuccess) return e;
+  if ((size_t)a.maxDynamicSharedSizeBytes >= smem) return cudaSuccess;
   return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 

@@ -333,8 +333,25 @@ def pf_loglik_noalloc(cfg: Config, y_dev, theta_soa, iteration: int, out=None, s
     """smc2_pf_loglik_noalloc: no context and no device allocation by the library.
     y_dev: CUDA float64 [T]; theta_soa: CUDA float64 [D][n]; returns CUDA float64 [n]."""
     import torch
+
+    def device_f64(t, what):
+        if not (hasattr(t, "is_cuda") and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+            raise SMC2Error(EINVAL, f"smc2_pf_loglik_noalloc: {what} must be a contiguous CUDA float64 tensor")
+
+    # the C entry point reads T doubles of y and D rows of theta through raw pointers
+    device_f64(y_dev, "y_dev")
+    device_f64(theta_soa, "theta_soa")
+    if y_dev.numel() < cfg.T:
+        raise SMC2Error(EINVAL, f"smc2_pf_loglik_noalloc: y_dev holds {y_dev.numel()} < T = {cfg.T} values")
+    if theta_soa.dim() != 2 or theta_soa.shape[0] != cfg.D:
+        raise SMC2Error(EINVAL, f"smc2_pf_loglik_noalloc: theta_soa must be [D = {cfg.D}][n]")
     n = theta_soa.shape[1]
-    out = out if out is not None else torch.empty(n, dtype=torch.float64, device=theta_soa.device)
+    if out is None:
+        out = torch.empty(n, dtype=torch.float64, device=theta_soa.device)
+    else:
+        device_f64(out, "out")
+        if out.numel() < n:
+            raise SMC2Error(EINVAL, "smc2_pf_loglik_noalloc: out holds fewer than n values")
     _check(lib.smc2_pf_loglik_noalloc(C.byref(cfg), _ptr(y_dev), _ptr(theta_soa), n, int(iteration),
                                       _ptr(out), _stream_handle(stream)), "smc2_pf_loglik_noalloc")
     return out
