@@ -248,15 +248,30 @@ smc2_status smc2_get_proposals(smc2_ctx* ctx, int dataset, double* theta_host, d
 
 /* The learned proposal's state that the next iteration uses
  * (proposal = SMC2_PROP_MLP, dataset 0): params_host (FP32, the layout of
- * smc2_mlp_loss_grad: 64 D + 4289 values), stdz_host (FP64, 2 D + 5 values:
+ * smc2_mlp_loss_grad: 64 D + 4289 values), stdz_host (FP64, 2 D + 6 values:
  * input means mu[D], input sds sd[D], tau, zmean, zsd, target variance,
- * training loss; the score is d log pi^ / d theta_d = tau zsd (ds/dx)_d /
+ * training loss, ymax; the score is d log pi^ / d theta_d = tau zsd (ds/dx)_d /
  * sd_d at x_d = (theta_d - mu_d) / sd_d), L_host (FP64, row-major D x D lower
  * Cholesky factor of the weighted population covariance) and *pop_ok (the
  * factor is usable).  Any pointer may be NULL.  Synchronises.  Errors:
  * EINVAL (no learned proposal in this context). */
 smc2_status smc2_get_learned_state(smc2_ctx* ctx, float* params_host, double* stdz_host, double* L_host,
                                    int* pop_ok);
+
+/* The learned proposal's training state after the latest training call (not
+ * yet published; the call after iteration k trains on the ring holding the
+ * pairs of iterations k - W + 1 .. k, and its result proposes at k + 2):
+ * params_host, m_host, v_host (FP32, 64 D + 4289 values each: parameters and
+ * Adam moments), *step_host (Adam steps taken), stdz_host (FP64, 2 D + 6
+ * values in the layout of smc2_get_learned_state, from that call's
+ * standardisation and its loss), ring_th_host (FP32, row-major
+ * [mlp_window N][D]) and ring_lp_host (FP32, mlp_window N values: log prior
+ * + PF log-likelihood) with *ring_rows_host rows filled (iteration k's pairs
+ * in rows ((k - 1) mod W) N .. + N - 1).  Any pointer may be NULL.
+ * Synchronises.  Errors: EINVAL (no learned proposal in this context). */
+smc2_status smc2_get_learned_training(smc2_ctx* ctx, float* params_host, float* m_host, float* v_host,
+                                      int* step_host, double* stdz_host, float* ring_th_host,
+                                      float* ring_lp_host, int* ring_rows_host);
 
 /* Checkpoint / resume of a dataset's population after iteration k: theta
  * (host, row-major [N][D]), log prior, PF log-likelihood estimate and
@@ -346,7 +361,22 @@ smc2_status smc2_fma_rates(double* fp32_flops, double* fp64_flops, void* stream)
  * bias-corrected) with learning rate lr at step t = *step_dev + 1 (device
  * int, advanced in place), updating params_dev, m_dev, v_dev (device FP32, one
  * value per parameter); *loss_dev receives L before the update.  Allocates
- * nothing. */
+ * nothing.
+ * smc2_mlp_train_ring: the sampler's training call on caller buffers (the
+ * same kernel).  From R rows of (theta, log pi^) -- ring_th_dev [R][D] and
+ * ring_lp_dev [R], device FP32 -- it forms the training set: tau = max(2, D),
+ * z = max((log pi^ - ymax) / tau, -8) with ymax the largest finite log pi^
+ * (-8 for a non-finite one), target y = (z - mean z) / sd z over all rows
+ * (sd 1 and target variance 0 when var z <= 1e-8), inputs x = (theta - mu) /
+ * sd with the mean and standard deviation of the rows above the clip (of
+ * every finite row when fewer than 2 D + 2 are; sd at least 1e-6), written
+ * to x_dev [R][D] and y_dev [R]; then `steps` Adam steps as
+ * smc2_mlp_adam_step takes them, continuing params, m, v and *step_dev.
+ * stdz_dev (device FP64, 2 D + 6 values in the layout of
+ * smc2_get_learned_state) receives the standardisation and the loss of the
+ * last step before its update (0 when steps = 0).  Allocates a few hundred
+ * bytes on `stream` (stream-ordered).  Errors: EINVAL (D outside 1..8, R < 1,
+ * steps outside 0..256, a NULL pointer, params_dev not 16-byte aligned). */
 smc2_status smc2_mlp_loss_grad(int D, const float* params_dev, const float* x_dev, const float* y_dev,
                                int R, float* grad_dev, float* loss_dev, void* stream);
 smc2_status smc2_mlp_input_grad(int D, const float* params_dev, const float* x_dev, int R,
@@ -354,6 +384,9 @@ smc2_status smc2_mlp_input_grad(int D, const float* params_dev, const float* x_d
 smc2_status smc2_mlp_adam_step(int D, float* params_dev, float* m_dev, float* v_dev, int* step_dev,
                                const float* x_dev, const float* y_dev, int R, float lr, float* loss_dev,
                                void* stream);
+smc2_status smc2_mlp_train_ring(int D, float* params_dev, float* m_dev, float* v_dev, int* step_dev,
+                                const float* ring_th_dev, const float* ring_lp_dev, int R, int steps, float lr,
+                                float* x_dev, float* y_dev, double* stdz_dev, void* stream);
 
 /* Wait for the context stream and return the sticky device status. */
 smc2_status smc2_sync(smc2_ctx* ctx);

@@ -71,6 +71,32 @@ class OracleStats(C.Structure):
     ]
 
 
+class MlpNorm(C.Structure):
+    _fields_ = [
+        ("mu", C.c_double * MAX_D), ("sd", C.c_double * MAX_D), ("ymax", C.c_double), ("tau", C.c_double),
+        ("zmean", C.c_double), ("zsd", C.c_double), ("var_y", C.c_double), ("rows", C.c_int),
+        ("rows_moments", C.c_int),
+    ]
+
+    def as_dict(self, D: int) -> dict:
+        return {"mu": np.array(self.mu[:D]), "sd": np.array(self.sd[:D]), "ymax": self.ymax, "tau": self.tau,
+                "zmean": self.zmean, "zsd": self.zsd, "var_y": self.var_y, "rows": self.rows,
+                "rows_moments": self.rows_moments}
+
+    @classmethod
+    def from_dict(cls, d: dict) -> "MlpNorm":
+        n = cls()
+        D = len(d["mu"])
+        for i in range(D):
+            n.mu[i] = float(d["mu"][i])
+            n.sd[i] = float(d["sd"][i])
+        for k in ("ymax", "tau", "zmean", "zsd", "var_y"):
+            setattr(n, k, float(d.get(k, 0.0)))
+        n.rows = int(d.get("rows", 0))
+        n.rows_moments = int(d.get("rows_moments", 0))
+        return n
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -135,6 +161,18 @@ def _declare(L):
     L.oracle_mlp_input_grad.argtypes = [C.c_int, C.c_int, dp, dp, C.c_int, C.c_int, dp, dp]
     L.oracle_adam_step.argtypes = [C.c_int, dp, dp, dp, dp, C.c_int, C.c_double, C.c_double,
                                    C.c_double, C.c_double]
+    L.oracle_mlp_weights_bf16.argtypes = [C.c_int, C.c_int, dp, dp]
+    L.oracle_mlp_standardise.argtypes = [C.c_int, C.c_int, dp, dp, dp, dp, C.POINTER(MlpNorm)]
+    L.oracle_mlp_standardise.restype = C.c_int
+    L.oracle_mlp_train.argtypes = [C.c_int, C.c_int, C.c_int, dp, dp, C.c_int, C.c_double, C.c_int,
+                                   dp, dp, dp, C.POINTER(C.c_int), C.POINTER(MlpNorm), dp, dp]
+    L.oracle_mlp_train.restype = C.c_double
+    L.oracle_mlp_score.argtypes = [C.c_int, C.c_int, dp, C.POINTER(MlpNorm), dp, C.c_int, C.c_int, dp]
+    L.oracle_population_factor.argtypes = [C.c_int, dp, C.c_double, dp]
+    L.oracle_population_factor.restype = C.c_int
+    L.oracle_learned_decision.argtypes = [C.c_int, C.c_double, C.c_double, C.c_int]
+    L.oracle_learned_decision.restype = C.c_int
+    L.oracle_langevin_propose.argtypes = [C.c_int, C.c_double, dp, dp, dp, dp, dp, dp]
 
 
 # --------------------------------------------------------------------------
@@ -458,3 +496,87 @@ def adam_step(params, grad, m, v, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
     """In place on params, m, v (float64 numpy arrays)."""
     lib().oracle_adam_step(len(params), _p(params, C.c_double), _p(np.ascontiguousarray(grad), C.c_double),
                            _p(m, C.c_double), _p(v, C.c_double), int(t), lr, beta1, beta2, eps)
+
+
+# --------------------------------------------------------------------------
+# the learned proposal's sampler-side steps (choices L2-L4)
+# --------------------------------------------------------------------------
+
+def mlp_weights_bf16(params, D: int, H: int = 64) -> np.ndarray:
+    """W1, W2, w3 rounded to bfloat16 as the kernels use them; biases unchanged."""
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    out = np.zeros_like(p)
+    lib().oracle_mlp_weights_bf16(D, H, _p(p, C.c_double), _p(out, C.c_double))
+    return out
+
+
+def mlp_standardise(theta, lp):
+    """Training set of the surrogate from rows (theta [R][D], log pi^ [R]): (x, y, norm dict)."""
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    l = np.ascontiguousarray(lp, dtype=np.float64)
+    R, D = th.shape
+    x = np.zeros((R, D))
+    y = np.zeros(R)
+    nm = MlpNorm()
+    lib().oracle_mlp_standardise(D, R, _p(th, C.c_double), _p(l, C.c_double), _p(x, C.c_double),
+                                 _p(y, C.c_double), C.byref(nm))
+    return x, y, nm.as_dict(D)
+
+
+def mlp_train(params, m, v, t: int, theta, lp, steps: int, lr: float, H: int = 64, bf16_points: bool = True):
+    """One training call: standardise the rows, then `steps` Adam steps from the
+    state (params, m, v, step counter t).  Returns (params, m, v, t, loss of the
+    last step before its update, norm dict, x, y); the inputs are not modified."""
+    p = np.array(params, dtype=np.float64)
+    mm = np.array(m, dtype=np.float64)
+    vv = np.array(v, dtype=np.float64)
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    l = np.ascontiguousarray(lp, dtype=np.float64)
+    R, D = th.shape
+    tt = C.c_int(int(t))
+    nm = MlpNorm()
+    x = np.zeros((R, D))
+    y = np.zeros(R)
+    loss = lib().oracle_mlp_train(D, H, R, _p(th, C.c_double), _p(l, C.c_double), int(steps), float(lr),
+                                  int(bf16_points), _p(p, C.c_double), _p(mm, C.c_double), _p(vv, C.c_double),
+                                  C.byref(tt), C.byref(nm), _p(x, C.c_double), _p(y, C.c_double))
+    return p, mm, vv, tt.value, loss, nm.as_dict(D), x, y
+
+
+def mlp_score(params, norm: dict, theta, H: int = 64, bf16_points: bool = True) -> np.ndarray:
+    """d log pi^ / d theta of the surrogate at rows theta [R][D]."""
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    R, D = th.shape
+    nm = MlpNorm.from_dict(norm)
+    out = np.zeros((R, D))
+    lib().oracle_mlp_score(D, H, _p(p, C.c_double), C.byref(nm), _p(th, C.c_double), R, int(bf16_points),
+                           _p(out, C.c_double))
+    return out
+
+
+def population_factor(cov, ess: float):
+    """(L, usable) for the population covariance [D][D] and its ESS."""
+    c = np.ascontiguousarray(cov, dtype=np.float64)
+    D = c.shape[0]
+    L = np.zeros((D, D))
+    ok = lib().oracle_population_factor(D, _p(c, C.c_double), float(ess), _p(L, C.c_double))
+    return L, bool(ok)
+
+
+def learned_decision(k: int, loss: float, var_y: float, pop_ok: bool) -> bool:
+    return bool(lib().oracle_learned_decision(int(k), float(loss), float(var_y), int(bool(pop_ok))))
+
+
+def langevin_propose(h: float, L, theta_prev, score, z):
+    """theta_k = theta_{k-1} + h L (w + z), w = clip(h/2 L^T g, +-3); returns (theta_k, log q)."""
+    LL = np.ascontiguousarray(L, dtype=np.float64)
+    a = np.ascontiguousarray(theta_prev, dtype=np.float64)
+    g = np.ascontiguousarray(score, dtype=np.float64)
+    zz = np.ascontiguousarray(z, dtype=np.float64)
+    D = len(a)
+    out = np.zeros(D)
+    lq = np.zeros(1)
+    lib().oracle_langevin_propose(D, float(h), _p(LL, C.c_double), _p(a, C.c_double), _p(g, C.c_double),
+                                  _p(zz, C.c_double), _p(out, C.c_double), _p(lq, C.c_double))
+    return out, float(lq[0])

@@ -965,3 +965,205 @@ void oracle_adam_step(int n, double* params, const double* grad, double* m, doub
     params[q] -= lr * mh / (sqrt(vh) + eps);
   }
 }
+
+/* ------------------------------------------------------------------ */
+/* The learned proposal inside the sampler (not in the paper)           */
+/* ------------------------------------------------------------------ */
+
+/* The weights W1, W2 and w3 rounded to bfloat16 as the tensor-core kernels
+ * use them; the biases b1, b2 and b3 unchanged. */
+void oracle_mlp_weights_bf16(int D, int H, const double* params, double* out) {
+  const int P = oracle_mlp_nparams(D, H);
+  const int b1 = D * H, W2 = b1 + H, b2 = W2 + H * H, w3 = b2 + H, b3 = w3 + H;
+  for (int q = 0; q < P; ++q) {
+    const int weight = q < b1 || (q >= W2 && q < b2) || (q >= w3 && q < b3);
+    out[q] = weight ? oracle_bf16(params[q]) : params[q];
+  }
+}
+
+/* Training set of the surrogate (choice L2).  Rows r < R hold theta_r (R x D)
+ * and the log target estimate lp_r = log p(theta_r) + log p^(y | theta_r).
+ *   tau = max(2, D), ymax = the largest finite lp,
+ *   z_r = max((lp_r - ymax) / tau, -8) (-8 for a non-finite lp_r),
+ *   y_r = (z_r - mean z) / sd z over all R rows (population moments; when the
+ *         variance of z is at most 1e-8 the sd is taken as 1 and var_y = 0,
+ *         otherwise var_y = 1, the variance of the targets),
+ *   x_r = (theta_r - mu) / sd, mu and sd the mean and population standard
+ *         deviation of theta over the rows whose z lies above the clip -- or
+ *         over every row with a finite lp when fewer than 2 D + 2 rows do;
+ *         sd = 1 for fewer than two such rows, and at least 1e-6.  With no
+ *         such row, mu = 0 and sd = 1.
+ * Returns the number of rows the input moments were taken over. */
+int oracle_mlp_standardise(int D, int R, const double* th, const double* lp, double* x, double* y,
+                           oracle_mlp_norm* nm) {
+  memset(nm, 0, sizeof(*nm));
+  const double tau = D > 2 ? (double)D : 2.0;
+  double ymax = -INFINITY;
+  for (int r = 0; r < R; ++r)
+    if (isfinite(lp[r]) && lp[r] > ymax) ymax = lp[r];
+  double* z = (double*)malloc(sizeof(double) * (R > 0 ? R : 1));
+  int above = 0;
+  for (int r = 0; r < R; ++r) {
+    if (isfinite(lp[r])) {
+      const double v = (lp[r] - ymax) / tau;
+      z[r] = v > -8.0 ? v : -8.0;
+      if (v > -8.0) ++above;
+    } else {
+      z[r] = -8.0;
+    }
+  }
+  /* input moments: the rows above the clip, else every row with a finite lp */
+  const int use_all = above < 2 * D + 2;
+  int cnt = 0;
+  double mean[ORACLE_MAX_D] = {0.0}, var[ORACLE_MAX_D] = {0.0};
+  for (int r = 0; r < R; ++r) {
+    if (!isfinite(lp[r]) || (!use_all && !(z[r] > -8.0))) continue;
+    ++cnt;
+    for (int d = 0; d < D; ++d) mean[d] += th[(size_t)r * D + d];
+  }
+  for (int d = 0; d < D; ++d) mean[d] = cnt > 0 ? mean[d] / cnt : 0.0;
+  for (int r = 0; r < R; ++r) {
+    if (!isfinite(lp[r]) || (!use_all && !(z[r] > -8.0))) continue;
+    for (int d = 0; d < D; ++d) {
+      const double e = th[(size_t)r * D + d] - mean[d];
+      var[d] += e * e;
+    }
+  }
+  for (int d = 0; d < D; ++d) {
+    double sd = cnt > 1 ? sqrt(var[d] / cnt) : 1.0;
+    nm->mu[d] = mean[d];
+    nm->sd[d] = sd > 1e-6 ? sd : 1e-6;
+  }
+  /* targets */
+  double zm = 0.0, zv = 0.0;
+  for (int r = 0; r < R; ++r) zm += z[r];
+  zm = R > 0 ? zm / R : 0.0;
+  for (int r = 0; r < R; ++r) zv += (z[r] - zm) * (z[r] - zm);
+  zv = R > 0 ? zv / R : 0.0;
+  nm->tau = tau;
+  nm->ymax = ymax;
+  nm->zmean = zm;
+  nm->zsd = zv > 1e-8 ? sqrt(zv) : 1.0;
+  nm->var_y = zv > 1e-8 ? 1.0 : 0.0;
+  nm->rows = R;
+  nm->rows_moments = cnt;
+  for (int r = 0; r < R; ++r) {
+    if (y) y[r] = (z[r] - zm) / nm->zsd;
+    if (x)
+      for (int d = 0; d < D; ++d) x[(size_t)r * D + d] = (th[(size_t)r * D + d] - nm->mu[d]) / nm->sd[d];
+  }
+  free(z);
+  return cnt;
+}
+
+/* One training call of the surrogate (choices L1, L2): the training set of
+ * oracle_mlp_standardise from the R rows (th, lp), then `steps` full-batch
+ * Adam steps (beta = (0.9, 0.999), eps = 1e-8, learning rate lr) on the mean
+ * squared error, continuing the step counter *t and the moments m, v.  With
+ * bf16 != 0 every gradient is taken as the kernels take it: at the weights
+ * rounded to bfloat16 (oracle_mlp_weights_bf16) with the bfloat16 rounding
+ * points of oracle_mlp_loss_grad; the update applies to the unrounded
+ * params.  nm, x, y (R x D and R values; either may be NULL) receive the
+ * training set.  Returns the loss of the last step, before its update. */
+double oracle_mlp_train(int D, int H, int R, const double* th, const double* lp, int steps, double lr,
+                        int bf16, double* params, double* m, double* v, int* t, oracle_mlp_norm* nm,
+                        double* x_out, double* y_out) {
+  const int P = oracle_mlp_nparams(D, H);
+  double* x = (double*)malloc(sizeof(double) * (size_t)(R > 0 ? R : 1) * D);
+  double* y = (double*)malloc(sizeof(double) * (R > 0 ? R : 1));
+  double* pw = (double*)malloc(sizeof(double) * P);
+  double* g = (double*)malloc(sizeof(double) * P);
+  oracle_mlp_norm local;
+  oracle_mlp_standardise(D, R, th, lp, x, y, nm ? nm : &local);
+  double loss = 0.0;
+  for (int it = 0; it < steps; ++it) {
+    if (bf16)
+      oracle_mlp_weights_bf16(D, H, params, pw);
+    else
+      memcpy(pw, params, sizeof(double) * P);
+    loss = R > 0 ? oracle_mlp_loss_grad(D, H, pw, x, y, R, bf16, g) : 0.0;
+    if (R == 0)
+      for (int q = 0; q < P; ++q) g[q] = 0.0;
+    *t += 1;
+    oracle_adam_step(P, params, g, m, v, *t, lr, 0.9, 0.999, 1e-8);
+  }
+  if (x_out) memcpy(x_out, x, sizeof(double) * (size_t)R * D);
+  if (y_out) memcpy(y_out, y, sizeof(double) * R);
+  free(x); free(y); free(pw); free(g);
+  return loss;
+}
+
+/* Gradient of the surrogate's log target at theta (choice L3): with
+ * x = (theta - mu) / sd, the fitted log target is ymax + tau (zmean + zsd s(x)),
+ * so d log pi^ / d theta_d = tau zsd (ds/dx)_d / sd_d.  R rows of theta
+ * (R x D) into score (R x D).  bf16 as in oracle_mlp_train. */
+void oracle_mlp_score(int D, int H, const double* params, const oracle_mlp_norm* nm, const double* theta,
+                      int R, int bf16, double* score) {
+  const int P = oracle_mlp_nparams(D, H);
+  double* pw = (double*)malloc(sizeof(double) * P);
+  double* x = (double*)malloc(sizeof(double) * (size_t)(R > 0 ? R : 1) * D);
+  if (bf16)
+    oracle_mlp_weights_bf16(D, H, params, pw);
+  else
+    memcpy(pw, params, sizeof(double) * P);
+  for (int r = 0; r < R; ++r)
+    for (int d = 0; d < D; ++d) x[(size_t)r * D + d] = (theta[(size_t)r * D + d] - nm->mu[d]) / nm->sd[d];
+  oracle_mlp_input_grad(D, H, pw, x, R, bf16, NULL, score);
+  for (int r = 0; r < R; ++r)
+    for (int d = 0; d < D; ++d) score[(size_t)r * D + d] *= nm->tau * nm->zsd / nm->sd[d];
+  free(pw); free(x);
+}
+
+/* Lower Cholesky factor L of the population covariance (row-major D x D)
+ * that the learned proposal scales its steps by (choice L4).  Returns 1 when
+ * it is usable -- the population's ESS is at least 2 (D + 1) and every pivot
+ * exceeds 1e-12 of its diagonal entry -- and 0 otherwise. */
+int oracle_population_factor(int D, const double* cov, double ess, double* L) {
+  const double zero[ORACLE_MAX_D] = {0.0};
+  const int chol_ok = oracle_cholesky(D, cov, zero, L) == 0;
+  return chol_ok && ess >= 2.0 * (D + 1);
+}
+
+/* Whether iteration k proposes with the network (choice L4): from k = 3 on,
+ * while the published network's training loss is finite and below half the
+ * variance of its targets, and the previous population's factor is usable;
+ * otherwise the random walk of Eq. (19). */
+int oracle_learned_decision(int k, double loss, double var_y, int pop_ok) {
+  return k >= 3 && isfinite(loss) && var_y > 0.0 && loss < 0.5 * var_y && pop_ok;
+}
+
+/* The learned proposal (choice L3): a Langevin step preconditioned by the
+ * population covariance Sigma = L L^T with the surrogate's score g:
+ *   w = clip(h/2 L^T g, -3, 3) coordinatewise (the drift in whitened units),
+ *   theta_k = theta_{k-1} + h L (w + z),  z ~ N(0, I),
+ * so theta_k ~ N(theta_{k-1} + h L w, h^2 L L^T); *logq receives that
+ * Gaussian density at theta_k, evaluated from its definition. */
+void oracle_langevin_propose(int D, double h, const double* L, const double* theta_prev, const double* g,
+                             const double* z, double* theta_out, double* logq) {
+  double w[ORACLE_MAX_D], mean[ORACLE_MAX_D], u[ORACLE_MAX_D];
+  for (int r = 0; r < D; ++r) { /* (L^T g)_r = sum_d L_dr g_d */
+    double s = 0.0;
+    for (int d = 0; d < D; ++d) s += L[d * D + r] * g[d];
+    s *= 0.5 * h;
+    w[r] = s < -3.0 ? -3.0 : (s > 3.0 ? 3.0 : s);
+  }
+  for (int d = 0; d < D; ++d) {
+    double lw = 0.0, lz = 0.0;
+    for (int c = 0; c <= d; ++c) {
+      lw += L[d * D + c] * w[c];
+      lz += L[d * D + c] * (w[c] + z[c]);
+    }
+    mean[d] = theta_prev[d] + h * lw;
+    theta_out[d] = theta_prev[d] + h * lz;
+  }
+  /* log N(theta_k; mean, h^2 L L^T): solve L u = (theta_k - mean) / h */
+  double logdet = 0.0, ss = 0.0;
+  for (int d = 0; d < D; ++d) {
+    double r = (theta_out[d] - mean[d]) / h;
+    for (int c = 0; c < d; ++c) r -= L[d * D + c] * u[c];
+    u[d] = r / L[d * D + d];
+    ss += u[d] * u[d];
+    logdet += log(h * L[d * D + d]);
+  }
+  *logq = -0.5 * D * LOG_2PI - logdet - 0.5 * ss;
+}

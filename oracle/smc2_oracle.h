@@ -151,6 +151,32 @@ void oracle_mlp_input_grad(int D, int H, const double* params, const double* x, 
                            double* s_out, double* dx);
 void oracle_adam_step(int n, double* params, const double* grad, double* m, double* v, int t, double lr,
                       double beta1, double beta2, double eps);
+/* The learned proposal's sampler-side steps (not in the paper; the builder's
+ * choices L2-L4 of the learned proposal, written from their statement).  The
+ * network proposing at iteration k was trained by the call after iteration
+ * k - 2, which continued the parameters and Adam state of the call before it
+ * on the (theta, log pi^) pairs of the last W iterations. */
+typedef struct {
+  double mu[ORACLE_MAX_D], sd[ORACLE_MAX_D]; /* input standardisation */
+  double ymax, tau;                          /* z = max((log pi^ - ymax) / tau, -8) */
+  double zmean, zsd;                         /* target y = (z - zmean) / zsd */
+  double var_y;                              /* variance of the targets: 1, or 0 for constant z */
+  int rows;                                  /* rows of the training set */
+  int rows_moments;                          /* rows the input moments were taken over */
+} oracle_mlp_norm;
+void oracle_mlp_weights_bf16(int D, int H, const double* params, double* out);
+int oracle_mlp_standardise(int D, int R, const double* th, const double* lp, double* x, double* y,
+                           oracle_mlp_norm* nm);
+double oracle_mlp_train(int D, int H, int R, const double* th, const double* lp, int steps, double lr,
+                        int bf16, double* params, double* m, double* v, int* t, oracle_mlp_norm* nm,
+                        double* x_out, double* y_out);
+void oracle_mlp_score(int D, int H, const double* params, const oracle_mlp_norm* nm, const double* theta,
+                      int R, int bf16, double* score);
+int oracle_population_factor(int D, const double* cov, double ess, double* L);
+int oracle_learned_decision(int k, double loss, double var_y, int pop_ok);
+void oracle_langevin_propose(int D, double h, const double* L, const double* theta_prev, const double* g,
+                             const double* z, double* theta_out, double* logq);
+
 void oracle_recycle(int K, int D, const oracle_stats* st, double* est_out, double* c_out);
 /* Recycled posterior covariance: Eq. (29) applied to f(theta) = theta theta^T,
  * minus the recycled mean's outer product; cov_out [D][D]. */

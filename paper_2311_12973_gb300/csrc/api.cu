@@ -840,11 +840,48 @@ smc2_status smc2_get_learned_state(smc2_ctx* c, float* params, double* stdz, dou
     stdz[2 * D + 2] = nm.zsd;
     stdz[2 * D + 3] = nm.var_y;
     stdz[2 * D + 4] = loss;
+    stdz[2 * D + 5] = nm.ymax;
   }
   if (L)
     for (int d = 0; d < D; ++d)
       for (int f = 0; f < D; ++f) L[d * D + f] = cur.Lpop[d * kMaxD + f];
   if (pop_ok) *pop_ok = cur.pop_ok;
+  return st;
+}
+
+smc2_status smc2_get_learned_training(smc2_ctx* c, float* params, float* m, float* v, int* step, double* stdz,
+                                      float* ring_th, float* ring_lp, int* ring_rows) {
+  if (!c || !c->mlp.on) return SMC2_EINVAL;
+  const int D = c->D;
+  const size_t P = (size_t)mlp_param_count(D), rows = (size_t)c->mlp.W * c->N[0];
+  cudaStream_t s = c->stream;
+  MlpNorm nm{};
+  float loss = 0.f;
+  int hs = 0, hr = 0;
+  if (params) SMC2_TRY(cudaMemcpyAsync(params, c->mlp.p, P * sizeof(float), cudaMemcpyDeviceToHost, s));
+  if (m) SMC2_TRY(cudaMemcpyAsync(m, c->mlp.m, P * sizeof(float), cudaMemcpyDeviceToHost, s));
+  if (v) SMC2_TRY(cudaMemcpyAsync(v, c->mlp.v, P * sizeof(float), cudaMemcpyDeviceToHost, s));
+  if (ring_th) SMC2_TRY(cudaMemcpyAsync(ring_th, c->mlp.ring_th, rows * D * sizeof(float), cudaMemcpyDeviceToHost, s));
+  if (ring_lp) SMC2_TRY(cudaMemcpyAsync(ring_lp, c->mlp.ring_lp, rows * sizeof(float), cudaMemcpyDeviceToHost, s));
+  SMC2_TRY(cudaMemcpyAsync(&hs, c->mlp.step, sizeof(int), cudaMemcpyDeviceToHost, s));
+  SMC2_TRY(cudaMemcpyAsync(&hr, c->mlp.ring_rows, sizeof(int), cudaMemcpyDeviceToHost, s));
+  SMC2_TRY(cudaMemcpyAsync(&nm, c->mlp.norm, sizeof(MlpNorm), cudaMemcpyDeviceToHost, s));
+  SMC2_TRY(cudaMemcpyAsync(&loss, c->mlp.loss, sizeof(float), cudaMemcpyDeviceToHost, s));
+  const smc2_status st = sticky(c);
+  if (step) *step = hs;
+  if (ring_rows) *ring_rows = hr;
+  if (stdz) {
+    for (int d = 0; d < D; ++d) {
+      stdz[d] = nm.mu[d];
+      stdz[D + d] = nm.sd[d];
+    }
+    stdz[2 * D] = nm.tau;
+    stdz[2 * D + 1] = nm.zmean;
+    stdz[2 * D + 2] = nm.zsd;
+    stdz[2 * D + 3] = nm.var_y;
+    stdz[2 * D + 4] = loss;
+    stdz[2 * D + 5] = nm.ymax;
+  }
   return st;
 }
 
@@ -916,6 +953,33 @@ smc2_status smc2_mlp_adam_step(int D, float* params, float* m, float* v, int* st
   if (reinterpret_cast<uintptr_t>(params) % 16 != 0) return SMC2_EINVAL;  // the documented layout
   SMC2_TRY(mlp_train_steps_launch(params, m, v, step, const_cast<float*>(x), const_cast<float*>(y), R, nullptr,
                                   loss, D, 1, lr, static_cast<cudaStream_t>(stream)));
+  return SMC2_OK;
+}
+
+smc2_status smc2_mlp_train_ring(int D, float* params, float* m, float* v, int* step, const float* ring_th,
+                                const float* ring_lp, int R, int steps, float lr, float* x, float* y,
+                                double* stdz, void* stream) {
+  if (D < 1 || D > kMlpMaxD || R < 1 || steps < 0 || steps > 256 || !params || !m || !v || !step || !ring_th ||
+      !ring_lp || !x || !y || !stdz || !(lr >= 0.f && lr < 1.f))
+    return SMC2_EINVAL;
+  if (reinterpret_cast<uintptr_t>(params) % 16 != 0) return SMC2_EINVAL;  // the documented layout
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  struct Scratch {
+    MlpNorm nm;
+    float loss;
+    int rows;
+  };
+  Scratch* w = nullptr;
+  SMC2_TRY(cudaMallocAsync(reinterpret_cast<void**>(&w), sizeof(Scratch), s));
+  cudaError_t e = cudaMemsetAsync(w, 0, sizeof(Scratch), s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&w->rows, &R, sizeof(int), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = mlp_train_ring_launch(params, m, v, step, ring_th, ring_lp, &w->rows, R, &w->nm, x, y, &w->loss, D, steps,
+                              lr, s);
+  if (e == cudaSuccess) e = mlp_norm_export_launch(&w->nm, &w->loss, D, stdz, s);
+  const cudaError_t ef = cudaFreeAsync(w, s);
+  SMC2_TRY(e);
+  SMC2_TRY(ef);
   return SMC2_OK;
 }
 

@@ -179,6 +179,10 @@ size_t mlp_train_smem_bytes();
 cudaError_t mlp_train_steps_launch(float* p, float* m, float* v, int* step, float* x, float* y, int R,
                                    const int* R_dev, float* loss, int D, int steps, float lr, cudaStream_t s,
                                    const MlpDev* ring_of = nullptr);
+cudaError_t mlp_train_ring_launch(float* p, float* m, float* v, int* step, const float* th, const float* lp,
+                                  const int* rows_dev, int R, MlpNorm* norm, float* x, float* y, float* loss,
+                                  int D, int steps, float lr, cudaStream_t s);
+cudaError_t mlp_norm_export_launch(const MlpNorm* nm, const float* loss, int D, double* out, cudaStream_t s);
 cudaError_t mlp_init_launch(const MlpDev& M, int D, uint64_t seed, cudaStream_t s);
 cudaError_t mlp_append_launch(const OuterParams& P, int N, cudaStream_t s);
 cudaError_t mlp_train_launch(const OuterParams& P, int steps, float lr, cudaStream_t s);

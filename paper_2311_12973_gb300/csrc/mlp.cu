@@ -616,6 +616,7 @@ __global__ void __launch_bounds__(32 * kTrainWarps)
   const int slice = (P + C - 1) / C, q0 = min(c * slice, P), q1 = min(q0 + slice, P);
   const int t0 = *step;
   for (int q = tid; q < P; q += blockDim.x) S.pf[q] = p[q];
+  __syncthreads();  // every parameter loaded before any thread reads another's (also with no step)
   const float beta1 = 0.9f, beta2 = 0.999f, eps = 1e-8f;
   for (int it = 0; it < steps; ++it) {
     refresh_weights(S.W, S.pf, D);  // ends with a barrier
@@ -1012,6 +1013,43 @@ cudaError_t mlp_train_steps_launch(float* p, float* m, float* v, int* step, floa
     ring.norm = ring_of->norm;
   }
   return cudaLaunchKernelEx(&cfg, mlp_train_kernel, p, m, v, step, x, y, R, R_dev, loss, D, steps, lr, ring);
+}
+
+// The training call on caller buffers: the ring (th, lp) of *rows_dev rows is
+// standardised into x, y and *norm, then `steps` Adam steps continue (p, m, v,
+// *step); the same kernel and cluster shape as the sampler's own call.
+cudaError_t mlp_train_ring_launch(float* p, float* m, float* v, int* step, const float* th, const float* lp,
+                                  const int* rows_dev, int R, MlpNorm* norm, float* x, float* y, float* loss,
+                                  int D, int steps, float lr, cudaStream_t s) {
+  MlpDev M{};
+  M.ring_th = const_cast<float*>(th);
+  M.ring_lp = const_cast<float*>(lp);
+  M.ring_rows = const_cast<int*>(rows_dev);
+  M.norm = norm;
+  return mlp_train_steps_launch(p, m, v, step, x, y, R, nullptr, loss, D, steps, lr, s, &M);
+}
+
+// The standardisation and training loss as FP64 values: mu[D], sd[D], tau, zmean,
+// zsd, var_y, loss, ymax.
+__global__ void mlp_norm_export_kernel(const MlpNorm* nm, const float* loss, int D, double* out) {
+  const int e = threadIdx.x;
+  if (e < D) {
+    out[e] = nm->mu[e];
+    out[D + e] = nm->sd[e];
+  }
+  if (e == 0) {
+    out[2 * D] = nm->tau;
+    out[2 * D + 1] = nm->zmean;
+    out[2 * D + 2] = nm->zsd;
+    out[2 * D + 3] = nm->var_y;
+    out[2 * D + 4] = *loss;
+    out[2 * D + 5] = nm->ymax;
+  }
+}
+
+cudaError_t mlp_norm_export_launch(const MlpNorm* nm, const float* loss, int D, double* out, cudaStream_t s) {
+  mlp_norm_export_kernel<<<1, 32, 0, s>>>(nm, loss, D, out);
+  return cudaGetLastError();
 }
 
 cudaError_t mlp_init_launch(const MlpDev& M, int D, uint64_t seed, cudaStream_t s) {

@@ -99,6 +99,9 @@ def _load() -> C.CDLL:
         "smc2_get_proposals": ([ctx, C.c_int, dp, dp], st),
         "smc2_fma_rates": ([dp, dp, vp], st),
         "smc2_get_learned_state": ([ctx, dp, dp, dp, C.POINTER(C.c_int)], st),
+        "smc2_get_learned_training": ([ctx, dp, dp, dp, C.POINTER(C.c_int), dp, dp, dp, C.POINTER(C.c_int)], st),
+        "smc2_mlp_train_ring": ([C.c_int, dp, dp, dp, dp, dp, dp, C.c_int, C.c_int, C.c_float, dp, dp, dp, vp],
+                                st),
         "smc2_destroy": ([ctx], None),
         "smc2_status_string": ([st], C.c_char_p),
         "smc2_last_error_string": ([], C.c_char_p),
@@ -268,14 +271,31 @@ class SMC2:
         population Cholesky factor the next iteration proposes with."""
         D = self.D
         params = np.zeros(64 * D + 4289, dtype=np.float32)
-        stdz = np.zeros(2 * D + 5)
+        stdz = np.zeros(2 * D + 6)
         L = np.zeros((D, D))
         ok = C.c_int()
         _check(lib.smc2_get_learned_state(self._ctx, params.ctypes.data, stdz.ctypes.data, L.ctypes.data,
                                           C.byref(ok)), "smc2_get_learned_state")
-        return {"params": params, "mu": stdz[:D].copy(), "sd": stdz[D:2 * D].copy(), "tau": stdz[2 * D],
-                "zmean": stdz[2 * D + 1], "zsd": stdz[2 * D + 2], "var_y": stdz[2 * D + 3],
-                "loss": stdz[2 * D + 4], "L": L, "pop_ok": bool(ok.value)}
+        return {"params": params, **_stdz_dict(stdz, D), "L": L, "pop_ok": bool(ok.value)}
+
+    def learned_training(self):
+        """The learned proposal's training state after the latest training call
+        (not yet published): parameters, Adam moments and step, the call's
+        standardisation and loss, and the ring of training pairs."""
+        D = self.D
+        P = 64 * D + 4289
+        rows = 16 * self.Ns[0]   # room for the largest ring (mlp_window <= 16 iterations of N rows)
+        params, m, v = (np.zeros(P, dtype=np.float32) for _ in range(3))
+        stdz = np.zeros(2 * D + 6)
+        th = np.zeros((rows, D), dtype=np.float32)
+        lp = np.zeros(rows, dtype=np.float32)
+        step, filled = C.c_int(), C.c_int()
+        _check(lib.smc2_get_learned_training(self._ctx, params.ctypes.data, m.ctypes.data, v.ctypes.data,
+                                             C.byref(step), stdz.ctypes.data, th.ctypes.data, lp.ctypes.data,
+                                             C.byref(filled)), "smc2_get_learned_training")
+        return {"params": params, "m": m, "v": v, "step": step.value, **_stdz_dict(stdz, D),
+                "ring_th": th[:filled.value].copy(), "ring_lp": lp[:filled.value].copy(),
+                "ring_rows": filled.value}
 
     def reset(self, seed: int):
         _check(lib.smc2_reset(self._ctx, int(seed)), "smc2_reset")
@@ -327,6 +347,26 @@ class SMC2:
         _check(lib.smc2_get_timing(self._ctx, C.byref(ms), C.byref(n), C.byref(kl), int(reset)),
                "smc2_get_timing")
         return ms.value, n.value, kl.value
+
+
+def _stdz_dict(stdz, D: int) -> dict:
+    """The 2 D + 6 standardisation values of the learned proposal, by name."""
+    return {"mu": stdz[:D].copy(), "sd": stdz[D:2 * D].copy(), "tau": stdz[2 * D], "zmean": stdz[2 * D + 1],
+            "zsd": stdz[2 * D + 2], "var_y": stdz[2 * D + 3], "loss": stdz[2 * D + 4], "ymax": stdz[2 * D + 5]}
+
+
+def mlp_train_ring(params, m, v, step, ring_th, ring_lp, steps: int, lr: float, stream=None):
+    """The sampler's training call on CUDA float32 tensors (in place on params,
+    m, v and the int32 step counter); returns (x, y, stdz dict) of the training set."""
+    import torch
+    R, D = ring_th.shape
+    x = torch.empty((R, D), dtype=torch.float32, device=params.device)
+    y = torch.empty(R, dtype=torch.float32, device=params.device)
+    stdz = torch.empty(2 * D + 6, dtype=torch.float64, device=params.device)
+    _check(lib.smc2_mlp_train_ring(D, _ptr(params), _ptr(m), _ptr(v), _ptr(step), _ptr(ring_th), _ptr(ring_lp),
+                                   R, int(steps), float(lr), _ptr(x), _ptr(y), _ptr(stdz),
+                                   _stream_handle(stream)), "smc2_mlp_train_ring")
+    return x, y, _stdz_dict(stdz.cpu().numpy(), D)
 
 
 def pf_loglik_noalloc(cfg: Config, y_dev, theta_soa, iteration: int, out=None, stream=None):

@@ -80,23 +80,15 @@ def test_learned_proposal_gain_over_random_walk(S):
     assert np.all(np.abs(means_l.mean(axis=0) - ref) < 4 * se + 0.005), (means_l.mean(axis=0), ref, se)
 
 
-def _weights_bf16(p, D, H=64):
-    """W1, W2, w3 rounded to bfloat16 as the kernels use them; biases unchanged."""
-    from oracle import oracle as O
-    q = np.array(p, dtype=np.float64)
-    for a, b in ((0, D * H), (D * H + H, D * H + H + H * H), (D * H + 2 * H + H * H, D * H + 3 * H + H * H)):
-        q[a:b] = [O.bf16(v) for v in q[a:b]]
-    return q
-
-
 def test_learned_proposal_stagewise_against_oracle(S):
-    """Each learned proposal recomputed by the oracle from the state the device
-    published before the iteration: the parents theta_{k-1}, the network and its
-    standardisation, the population Cholesky factor L, and the Philox normals z
-    of the proposal stream.  theta_k = theta_{k-1} + h L (w + z) with
-    w = clip(h/2 L^T grad log pi^, +-3); log q = N(theta_k; theta_{k-1} + h L w,
-    h^2 L L^T) exactly.  The score passes through the bf16 network, so theta_k
-    agrees to the network's input-gradient bar; log q depends only on z and L."""
+    """Each iteration's proposal step recomputed by the oracle from the state the
+    device published before it: the decision to use the network and the
+    population factor L (choice L4) from the previous iteration's weighted
+    covariance and ESS; the score of the published network at the parents
+    theta_{k-1} and the preconditioned Langevin proposal with its exact density
+    (choice L3), with the proposal stream's Philox normals z.  The score passes
+    through the bfloat16 network, so theta_k agrees to the network's
+    input-gradient bar; log q depends only on z and L."""
     from oracle import oracle as O
     h = 1.0
     w = I.workload("seir_t100_n1024_mlp", N=256, M=128, T=40, K=14, precision=I.PREC_FP64)
@@ -106,28 +98,28 @@ def test_learned_proposal_stagewise_against_oracle(S):
     for _ in range(w.K):
         ls = ctx.learned_state()
         k_prev, theta_a, _, _, _ = ctx.get_state()
+        hist = ctx.history()
         st = ctx.run(1)[0][0]
-        if not st["mlp_used"]:
-            continue
-        assert ls["pop_ok"] and ls["loss"] < 0.5 * ls["var_y"]
         k = st["k"]
         assert k == k_prev + 1
+        if k >= 2:
+            prev = hist[k - 2]
+            L_o, ok_o = O.population_factor(prev["cov"], prev["ess"])
+            assert ok_o == ls["pop_ok"], (k, ok_o, ls["pop_ok"])
+            if ok_o:
+                assert np.allclose(ls["L"], L_o, rtol=1e-12, atol=1e-12 * np.max(np.abs(L_o)))
+            assert bool(st["mlp_used"]) == O.learned_decision(k, ls["loss"], ls["var_y"], ok_o), (k, st, ls["loss"])
+        if not st["mlp_used"]:
+            continue
         theta_b, logq = ctx.proposals()
-        pw = _weights_bf16(ls["params"], D)
-        x = ((theta_a - ls["mu"]) / ls["sd"]).astype(np.float32).astype(np.float64)
-        _, dx = O.mlp_input_grad(pw, x, bf16_points=True)
-        g = ls["tau"] * ls["zsd"] * dx / ls["sd"]
-        L = ls["L"]
+        g = O.mlp_score(ls["params"].astype(np.float64), ls, theta_a)
         expect_th = np.empty((N, D))
         expect_lq = np.empty(N)
         drift = np.empty((N, D))
         for i in range(N):
             z = np.concatenate([O.normals4(w.seed, gi, 0, i, O.TAG_PROPOSE | (k << 4)) for gi in range(0, D, 4)])[:D]
-            wv = np.clip(0.5 * h * (L.T @ g[i]), -3.0, 3.0)
-            drift[i] = h * (L @ wv)
-            expect_th[i] = theta_a[i] + h * (L @ (wv + z))
-            expect_lq[i] = -0.5 * D * math.log(2 * math.pi) - D * math.log(h) - np.sum(np.log(np.diag(L))) \
-                - 0.5 * z @ z
+            expect_th[i], expect_lq[i] = O.langevin_propose(h, ls["L"], theta_a[i], g[i], z)
+            drift[i] = O.langevin_propose(h, ls["L"], theta_a[i], g[i], np.zeros(D))[0] - theta_a[i]
         err_th = np.max(np.abs(theta_b - expect_th))
         err_lq = np.max(np.abs(logq - expect_lq))
         print(f"k={k}: theta err {err_th:.3g} (drift scale {np.max(np.abs(drift)):.3g}), log q err {err_lq:.3g}")

@@ -86,7 +86,8 @@ def test_adam_step_against_oracle(S, D, R):
     params, xs, ys = t(bf16_params(D, R)), t(x), t(y)
     m, v = torch.zeros_like(params), torch.zeros_like(params)
     step = torch.zeros(1, dtype=torch.int32, device="cuda")
-    lr, b1, b2, eps = 1e-2, 0.9, 0.999, 1e-8
+    lr = 1e-2
+    b1, b2, eps = (float(np.float32(c)) for c in (0.9, 0.999, 1e-8))  # as the FP32 kernel holds them
     for it in range(1, 4):
         p0, m0, v0 = (a.cpu().numpy().astype(np.float64) for a in (params, m, v))
         loss = float(S.mlp_adam_step(params, m, v, step, xs, ys, lr).item())
@@ -97,9 +98,14 @@ def test_adam_step_against_oracle(S, D, R):
         scale = np.max(np.abs(g_o))
         # moments: the gradient bar of the test above (5e-3 of the largest element)
         assert abs(loss - loss_o) <= 1e-4 * abs(loss_o)
-        assert np.max(np.abs(m1 - (b1 * m0 + (1 - b1) * g_o))) <= (1 - b1) * 5e-3 * scale
-        assert np.max(np.abs(v1 - (b2 * v0 + (1 - b2) * g_o * g_o))) <= (1 - b2) * 1e-2 * scale * scale
-        # update from the device moments: FP32 arithmetic, relative 1e-5 of a step of size lr
-        c1, c2 = 1 - b1 ** it, 1 - b2 ** it
-        expect = p0 - lr * (m1 / c1) / (np.sqrt(v1 / c2) + eps)
-        assert np.max(np.abs(p1 - expect)) <= 1e-5 * lr + 4e-7 * np.max(np.abs(p0))
+        m_g, v_g = m0.copy(), v0.copy()   # the oracle's moments after its step on g_o
+        O.adam_step(p0.copy(), g_o, m_g, v_g, it, lr, b1, b2, eps)
+        assert np.max(np.abs(m1 - m_g)) <= (1 - b1) * 5e-3 * scale
+        assert np.max(np.abs(v1 - v_g)) <= (1 - b2) * 1e-2 * scale * scale
+        # the update: the oracle's Adam on the gradient the device used (read from its first
+        # moment), from the device's moments: FP32 arithmetic, relative 1e-5 of a step of size lr
+        g_dev = (m1 - b1 * m0) / (1 - b1)
+        p_o, m_o, v_o = p0.copy(), m0.copy(), v0.copy()
+        O.adam_step(p_o, g_dev, m_o, v_o, it, lr, b1, b2, eps)
+        assert np.max(np.abs(v1 - v_o)) <= 1e-5 * np.max(v_o) + 1e-30
+        assert np.max(np.abs(p1 - p_o)) <= 1e-5 * lr + 4e-7 * np.max(np.abs(p0))
