@@ -64,6 +64,7 @@ enum { SMC2_PREC_FP64 = 0, SMC2_PREC_MIXED = 1 };   /* MIXED: FP32 particles, FP
 enum { SMC2_PROP_RW = 0, SMC2_PROP_MLP = 1 };
 enum { SMC2_LK_FORWARD = 0, SMC2_LK_GAUSS_OPT = 1 };
 enum { SMC2_PF_SYSTEMATIC = 0, SMC2_PF_MULTINOMIAL = 1 };
+enum { SMC2_PF_ANY = 0, SMC2_PF_GROUPS = 1, SMC2_PF_ONE_GROUP = 2 };
 
 #define SMC2_MAX_D 8
 #define SMC2_MAX_M 4096     /* particles per filter (see M in smc2_config) */
@@ -127,6 +128,12 @@ typedef struct smc2_ctx smc2_ctx; /* opaque; owns its device workspace */
  *   otherwise a multiple of 32 up to 512 that holds whole filter groups).
  *   The tuner times every valid (ppt, cta_threads) pair on the context's own
  *   work list, prior draws of theta and min(T, 32) steps, during smc2_init.
+ * pf_family: the particle-filter kernel the tuner may pick: 0 either,
+ *   SMC2_PF_GROUPS pf_kernel only (filter groups of any width, several per
+ *   CTA), SMC2_PF_ONE_GROUP the FP32 filter with one filter per CTA and 4, 8 or
+ *   16 particles per thread (mixed precision, LG or SEIR model, the default
+ *   filter, every dataset's group of the same width).  Both compute the same
+ *   filter; they differ in speed only.
  * n_datasets: number of independent datasets run together (<= 1: one).
  * ds_N, ds_M, ds_T: host arrays of n_datasets sizes (NULL when n_datasets <= 1). */
 typedef struct {
@@ -149,6 +156,7 @@ typedef struct {
   int pf_scheme;
   int prior_kind;
   double prior_lo[SMC2_MAX_D], prior_hi[SMC2_MAX_D];
+  int pf_family;
 } smc2_config;
 
 /* Statistics of one iteration k of one dataset (Sec. IV-A, IV-B):
@@ -205,6 +213,22 @@ smc2_status smc2_pf_loglik(smc2_ctx* ctx, const double* theta_dev, int n, int it
  * (either may be NULL).  Diagnostic path for checking the filter. */
 smc2_status smc2_pf_trace(smc2_ctx* ctx, const double* theta_dev, int n, int iteration,
                           int dataset, double* loglik_dev, double* delta_dev, int32_t* anc_dev);
+
+/* As smc2_pf_trace, and also the per-step quantities of the FP32 filter that a
+ * stage-wise check needs (mixed precision, LG or SEIR model, the default
+ * filter; the context's ppt must be 4, 8 or 16): after the propagation of
+ * step t (0-based t < T), by particle j, at index (i T + t) M + j:
+ * x_dev[.. * 5 + e] the state (LG: x in e = 0; SEIR: S, E, I, log beta and the
+ * day's incidence lambda in e = 0..4), logw_dev the log-weight log g(y_t | x_t)
+ * (Eq. 2; -inf for a NaN), q_dev the quantised weight floor(exp(logw - max)
+ * 2^B) the resampling after step t used (Eqs. 26-27).  All outputs device
+ * memory; delta_dev and anc_dev as in smc2_pf_trace (may be NULL).  It runs
+ * the traced instantiation of the one-group-per-CTA FP32 filter, whose
+ * arithmetic equals the untraced one's.  Errors: EINVAL (another precision,
+ * model or filter, a ppt outside 4, 8, 16, a NULL trace pointer). */
+smc2_status smc2_pf_trace_states(smc2_ctx* ctx, const double* theta_dev, int n, int iteration, int dataset,
+                                 double* loglik_dev, double* delta_dev, int32_t* anc_dev, float* x_dev,
+                                 float* logw_dev, uint64_t* q_dev);
 
 /* One SMC^2 iteration of every dataset (Sec. IV):
  *  k = 1: draw theta ~ q_1 = prior (Eq. 16), weight w = pi / q_1 (Eq. 17);
@@ -401,8 +425,9 @@ smc2_status smc2_get_timing(smc2_ctx* ctx, double* pf_ms, int64_t* pf_launches,
                             int64_t* kernel_launches, int reset);
 
 /* The particle-filter launch shape in use: particles per thread, threads per
- * CTA, CTAs per launch (host outputs, any may be NULL). */
-smc2_status smc2_get_launch_shape(smc2_ctx* ctx, int* ppt, int* cta_threads, int* grid);
+ * CTA, CTAs per launch, and *one_group = 1 when the filter kernel is the FP32
+ * one with one filter per CTA (host outputs, any may be NULL). */
+smc2_status smc2_get_launch_shape(smc2_ctx* ctx, int* ppt, int* cta_threads, int* grid, int* one_group);
 
 /* Release the context and its device workspace (synchronises its stream). */
 void smc2_destroy(smc2_ctx* ctx);

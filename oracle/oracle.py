@@ -132,6 +132,11 @@ def _declare(L):
     L.oracle_log_obs.argtypes = [C.POINTER(OracleCfg), dp, dp, C.c_double]
     L.oracle_log_obs.restype = C.c_double
     L.oracle_pf_loglik.argtypes = [C.POINTER(OracleCfg), dp, dp, C.c_uint32, C.c_uint32, dp, ip]
+    L.oracle_pf_initial.argtypes = [C.POINTER(OracleCfg), dp, C.c_uint32, C.c_uint32, dp]
+    L.oracle_pf_propagate.argtypes = [C.POINTER(OracleCfg), dp, C.c_uint32, C.c_uint32, C.c_int, C.c_double, dp, dp]
+    L.oracle_pf_resample_word.argtypes = [C.POINTER(OracleCfg), C.c_uint32, C.c_uint32, C.c_int]
+    L.oracle_pf_resample_word.restype = C.c_uint32
+    L.oracle_pf_log_weights.argtypes = [C.POINTER(OracleCfg), dp, dp, C.c_double, dp]
     L.oracle_pf_loglik.restype = C.c_double
     L.oracle_log_prior.argtypes = [C.POINTER(OracleCfg), dp]
     L.oracle_log_prior.restype = C.c_double
@@ -325,6 +330,40 @@ def pf_loglik(cfg: Config, theta, y, k: int, i: int, trace: bool = False):
     ll = lib().oracle_pf_loglik(C.byref(c), _p(th, C.c_double), _p(yy, C.c_double), int(k), int(i),
                                 _p(delta, C.c_double), _p(anc, C.c_int32))
     return (ll, delta, anc) if trace else ll
+
+
+def pf_initial(cfg: Config, theta, k: int, i: int) -> np.ndarray:
+    """Initial particle states of filter i at iteration k, [M][5]."""
+    c = cfg.ctype()
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    x = np.zeros((cfg.M, 5))
+    lib().oracle_pf_initial(C.byref(c), _p(th, C.c_double), int(k), int(i), _p(x, C.c_double))
+    return x
+
+
+def pf_propagate(cfg: Config, theta, k: int, i: int, t: int, y_t: float, x):
+    """One step t of the filter from states x [M][5] (copied): (propagated states, log-weights)."""
+    c = cfg.ctype()
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    xx = np.array(x, dtype=np.float64, order="C")
+    ell = np.zeros(cfg.M)
+    lib().oracle_pf_propagate(C.byref(c), _p(th, C.c_double), int(k), int(i), int(t), float(y_t),
+                              _p(xx, C.c_double), _p(ell, C.c_double))
+    return xx, ell
+
+
+def pf_log_weights(cfg: Config, theta, x, y_t: float) -> np.ndarray:
+    """log g(y_t | x_j) for the M states x [M][5]."""
+    c = cfg.ctype()
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    xx = np.ascontiguousarray(x, dtype=np.float64)
+    ell = np.zeros(cfg.M)
+    lib().oracle_pf_log_weights(C.byref(c), _p(th, C.c_double), _p(xx, C.c_double), float(y_t), _p(ell, C.c_double))
+    return ell
+
+
+def pf_resample_word(cfg: Config, k: int, i: int, t: int) -> int:
+    return int(lib().oracle_pf_resample_word(C.byref(cfg.ctype()), int(k), int(i), int(t)))
 
 
 def pf_loglik_many(cfg: Config, thetas, y, k: int, i0: int = 0, threads: int = 1) -> np.ndarray:

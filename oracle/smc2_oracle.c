@@ -418,6 +418,47 @@ double oracle_ess_from_q(const uint64_t* q, int n) {
   return (double)S * (double)S / q2;
 }
 
+/* The body of the filter's step loop, exposed for stage-wise checks: the
+ * initial states of filter i at iteration k (M x 5, the layout below), and one
+ * step t: every particle j propagated by Eq. (1) with the step's normal of slot
+ * j (or its binomial flows), then ell[j] = log g(y_t | x_j) (Eq. 2; -inf for a
+ * NaN).  oracle_pf_loglik runs the same two functions in its loop. */
+void oracle_pf_initial(const oracle_cfg* c, const double* theta, uint32_t k, uint32_t i, double* x) {
+  const uint32_t c2 = i | ((uint32_t)c->dataset << 20);
+  for (int j = 0; j < c->M; ++j) oracle_initial_state(c, theta, k, c2, j, x + 5 * j);
+}
+
+void oracle_pf_propagate(const oracle_cfg* c, const double* theta, uint32_t k, uint32_t i, int t, double y,
+                         double* x, double* ell) {
+  const uint32_t c2 = i | ((uint32_t)c->dataset << 20);
+  for (int j = 0; j < c->M; ++j) {
+    double* xj = x + 5 * j;
+    if (c->model == ORACLE_SIR) {
+      oracle_propagate_sir(c, theta, k, c2, j, t, xj);
+    } else {
+      double z[4];
+      oracle_normals4(c->seed, (uint32_t)j, (uint32_t)((t - 1) >> 2), c2, ORACLE_TAG_PF_PROP | (k << 4), z);
+      oracle_propagate(c, theta, z[(t - 1) & 3], xj);
+    }
+    const double l = oracle_log_obs(c, theta, xj, y);
+    ell[j] = isnan(l) ? -INFINITY : l;
+  }
+}
+
+/* ell[j] = log g(y | x_j) (Eq. 2; -inf for a NaN) for the M states x (M x 5). */
+void oracle_pf_log_weights(const oracle_cfg* c, const double* theta, const double* x, double y, double* ell) {
+  for (int j = 0; j < c->M; ++j) {
+    const double l = oracle_log_obs(c, theta, x + 5 * j, y);
+    ell[j] = isnan(l) ? -INFINITY : l;
+  }
+}
+
+/* The word U of the systematic resampling after step t of filter i at iteration k. */
+uint32_t oracle_pf_resample_word(const oracle_cfg* c, uint32_t k, uint32_t i, int t) {
+  const uint32_t c2 = i | ((uint32_t)c->dataset << 20);
+  return oracle_word0(c->seed, 0, (uint32_t)t, c2, ORACLE_TAG_PF_RES | (k << 4));
+}
+
 /* Returns log p^(y_{1:T} | theta), Eq. (8), for filter i of iteration k.
  * The unnormalised weight of particle j is carried as exp(L + lw_j): L is
  * the log of the common weight given to every particle at the last reset
@@ -438,27 +479,15 @@ double oracle_pf_loglik(const oracle_cfg* c, const double* theta, const double* 
   uint64_t* q = (uint64_t*)malloc(sizeof(uint64_t) * M);
   int32_t* ncop = (int32_t*)malloc(sizeof(int32_t) * M);
   int32_t* anc = (int32_t*)malloc(sizeof(int32_t) * M);
-  for (int j = 0; j < M; ++j) {
-    oracle_initial_state(c, theta, k, c2, j, x + SD * j);
-    lw[j] = 0.0;
-  }
+  oracle_pf_initial(c, theta, k, i, x);
+  for (int j = 0; j < M; ++j) lw[j] = 0.0;
   double L = 0.0;    /* log of the common weight: w_0 = 1 */
   double loglik = 0.0; /* log p^(y_{1:t}) */
   uint32_t* Um = (uint32_t*)malloc(sizeof(uint32_t) * M);
+  double* ell = (double*)malloc(sizeof(double) * M);
   for (int t = 1; t <= T; ++t) {
-    for (int j = 0; j < M; ++j) {
-      if (c->model == ORACLE_SIR) {
-        oracle_propagate_sir(c, theta, k, c2, j, t, x + SD * j);
-      } else {
-        double z[4];
-        oracle_normals4(c->seed, (uint32_t)j, (uint32_t)((t - 1) >> 2), c2,
-                        ORACLE_TAG_PF_PROP | (k << 4), z);
-        oracle_propagate(c, theta, z[(t - 1) & 3], x + SD * j);
-      }
-      double ell = oracle_log_obs(c, theta, x + SD * j, y[t - 1]);
-      if (isnan(ell)) ell = -INFINITY;
-      lw[j] = lw[j] + ell; /* Eq. (5) in logs */
-    }
+    oracle_pf_propagate(c, theta, k, i, t, y[t - 1], x, ell);
+    for (int j = 0; j < M; ++j) lw[j] = lw[j] + ell[j]; /* Eq. (5) in logs */
     double m = -INFINITY;
     for (int j = 0; j < M; ++j)
       if (lw[j] > m) m = lw[j];
@@ -484,8 +513,7 @@ double oracle_pf_loglik(const oracle_cfg* c, const double* theta, const double* 
             Um[j] = oracle_word(c->seed, (uint32_t)j >> 2, (uint32_t)t, c2, ORACLE_TAG_PF_MULTI | (k << 4), j & 3);
           oracle_multinomial_from_q(q, M, Um, anc);
         } else {
-          uint32_t U = oracle_word0(c->seed, 0, (uint32_t)t, c2, ORACLE_TAG_PF_RES | (k << 4));
-          oracle_systematic_from_q(q, M, U, ncop, anc);
+          oracle_systematic_from_q(q, M, oracle_pf_resample_word(c, k, i, t), ncop, anc);
         }
         for (int j = 0; j < M; ++j) memcpy(xn + SD * j, x + SD * anc[j], sizeof(double) * SD);
         double* tmp = x; x = xn; xn = tmp;
@@ -499,7 +527,7 @@ double oracle_pf_loglik(const oracle_cfg* c, const double* theta, const double* 
     }
   }
 done:
-  free(x); free(xn); free(lw); free(q); free(ncop); free(anc); free(Um);
+  free(x); free(xn); free(lw); free(q); free(ncop); free(anc); free(Um); free(ell);
   return loglik;
 }
 

@@ -123,6 +123,14 @@ double oracle_binomial(double n, double p, uint64_t seed, uint32_t c0, uint32_t 
                        uint32_t c3, int* words);
 
 double oracle_log_obs(const oracle_cfg* c, const double* theta, const double* x, double y);
+/* The filter's step loop body (Sec. II), for stage-wise checks: initial states
+ * (M x 5), one step's propagation (Eq. 1) and log-weights (Eq. 2) in place on
+ * x, and the word U of the resampling after step t. */
+void oracle_pf_initial(const oracle_cfg* c, const double* theta, uint32_t k, uint32_t i, double* x);
+void oracle_pf_propagate(const oracle_cfg* c, const double* theta, uint32_t k, uint32_t i, int t, double y,
+                         double* x, double* ell);
+uint32_t oracle_pf_resample_word(const oracle_cfg* c, uint32_t k, uint32_t i, int t);
+void oracle_pf_log_weights(const oracle_cfg* c, const double* theta, const double* x, double y, double* ell);
 double oracle_pf_loglik(const oracle_cfg* c, const double* theta, const double* y, uint32_t k,
                         uint32_t i, double* delta_out, int32_t* anc_out);
 

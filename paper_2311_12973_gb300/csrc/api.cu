@@ -68,6 +68,7 @@ struct smc2_ctx {
   int ppt = 4, pf_block = 256, pf_grid = 1;
   bool pf_named = false;
   bool pf_general = false;  // the paper's PF variants: multinomial slots, ESS-triggered resampling
+  bool pf_fast = false;     // the one-group-per-CTA FP32 filter (pf_fast.cuh) runs
   size_t pf_smem = 0;
   int k_host = 0;
   std::map<GraphKey, TimedGraph> graphs;
@@ -147,6 +148,7 @@ smc2_status validate(const smc2_config* c) {
   }
   if (c->ppt != 0 && c->ppt != 1 && c->ppt != 2 && c->ppt != 4 && c->ppt != 8 && c->ppt != 16)
     return SMC2_EINVAL;
+  if (c->pf_family < SMC2_PF_ANY || c->pf_family > SMC2_PF_ONE_GROUP) return SMC2_EINVAL;
   if ((c->pf_scheme != SMC2_PF_SYSTEMATIC && c->pf_scheme != SMC2_PF_MULTINOMIAL) ||
       !(c->pf_ess_frac >= 0.0 && c->pf_ess_frac <= 1.0))
     return SMC2_EINVAL;
@@ -291,19 +293,48 @@ void build_work_units(smc2_ctx* c, std::vector<int4>& wus) {
   });
 }
 
-smc2_status apply_shape(smc2_ctx* c, int ppt, int block, bool named, bool upload) {
+// The particle-filter launch of the context's shape, either kernel family.
+cudaError_t ctx_pf_launch(const smc2_ctx* c, int grid, const PFLaunch& L, cudaStream_t s, bool trace = false) {
+  if (c->pf_fast) return pf_fast_launch(c->model, c->ppt, trace, grid, c->pf_block, c->pf_smem, L, s);
+  return pf_launch(c->precision, c->model, c->ppt, c->pf_named, c->pf_general, grid, c->pf_block, c->pf_smem, L, s);
+}
+
+int ctx_pf_occupancy(const smc2_ctx* c, bool trace = false) {
+  if (c->pf_fast) return pf_fast_occupancy(c->model, c->ppt, trace, c->pf_block, c->pf_smem);
+  return pf_occupancy(c->precision, c->model, c->ppt, c->pf_named, c->pf_general, c->pf_block, c->pf_smem);
+}
+
+// The one-group-per-CTA filter at ppt: every dataset's group has the CTA's width
+// (block threads), so no thread of a CTA idles on a narrower filter.
+bool fast_shape_valid(const smc2_ctx* c, int ppt, int* block) {
+  if (!pf_fast_eligible(c->precision, c->model, c->pf_general, ppt)) return false;
+  const int gt = pf_group_threads(ppt, c->M[0]);
+  for (int m : c->M)
+    if (pf_group_threads(ppt, m) != gt || pf_fast_smem_bytes(c->model, ppt, m) > 227 * 1024) return false;
+  if (gt > kPfMaxBlock || (c->cfg.cta_threads && gt != c->cfg.cta_threads)) return false;
+  *block = gt;
+  return true;
+}
+
+smc2_status apply_shape(smc2_ctx* c, int ppt, int block, bool named, bool upload, bool fast = false) {
   c->ppt = ppt;
   c->pf_block = block;
   c->pf_named = named;
+  c->pf_fast = fast;
   size_t smem = 0;
-  for (int m : c->M) smem = std::max(smem, pf_smem_bytes(c->precision, c->model, ppt, c->pf_general, block, m));
+  for (int m : c->M)
+    smem = std::max(smem, fast ? pf_fast_smem_bytes(c->model, ppt, m)
+                               : pf_smem_bytes(c->precision, c->model, ppt, c->pf_general, block, m));
   if (smem > 227 * 1024) return SMC2_EINVAL;
   c->pf_smem = smem;
-  SMC2_TRY(pf_configure(c->precision, c->model, ppt, named, c->pf_general, smem));
+  if (fast)
+    SMC2_TRY(pf_fast_configure(c->model, ppt, false, smem));
+  else
+    SMC2_TRY(pf_configure(c->precision, c->model, ppt, named, c->pf_general, smem));
   std::vector<int4> wus;
   build_work_units(c, wus);
   c->n_wus = (int)wus.size();
-  const int occ = pf_occupancy(c->precision, c->model, ppt, named, c->pf_general, block, smem);
+  const int occ = ctx_pf_occupancy(c);
   if (occ < 1) return SMC2_EINVAL;
   c->pf_grid = std::min(c->n_wus, occ * c->sms);
   c->pl.n_wu = c->n_wus;
@@ -318,23 +349,29 @@ smc2_status apply_shape(smc2_ctx* c, int ppt, int block, bool named, bool upload
 smc2_status choose_launch_shape(smc2_ctx* c) {
   struct Shape {
     int ppt, block;
-    bool named;
+    bool named, fast;
   };
   std::vector<Shape> cand;
+  for (int ppt : {2, 4, 8}) {  // the one-group-per-CTA FP32 filter
+    int block = 0;
+    if (c->cfg.pf_family != SMC2_PF_GROUPS && (!c->cfg.ppt || ppt == c->cfg.ppt) && fast_shape_valid(c, ppt, &block))
+      cand.push_back({ppt, block, false, true});
+  }
   for (int ppt : {1, 2, 4, 8, 16}) {
     if (c->cfg.ppt && ppt != c->cfg.ppt) continue;
     if ((c->pf_general || c->model == MODEL_SIR) && ppt > 4) continue;  // register-resident shapes only
+    if (c->cfg.pf_family == SMC2_PF_ONE_GROUP) break;
     for (int block = 32; block <= kPfMaxBlock; block += 32) {
       if (c->cfg.cta_threads && block != c->cfg.cta_threads) continue;
       if (!c->cfg.cta_threads && (block & (block - 1))) continue;  // powers of two when tuning
       if (shape_valid(c, ppt, block, false))
-        cand.push_back({ppt, block, false});
+        cand.push_back({ppt, block, false, false});
       else if (shape_valid(c, ppt, block, true))
-        cand.push_back({ppt, block, true});
+        cand.push_back({ppt, block, true, false});
     }
   }
   if (cand.empty()) return SMC2_EINVAL;
-  if (cand.size() == 1) return apply_shape(c, cand[0].ppt, cand[0].block, cand[0].named, true);
+  if (cand.size() == 1) return apply_shape(c, cand[0].ppt, cand[0].block, cand[0].named, true, cand[0].fast);
   cudaStream_t s = c->stream;
   SMC2_TRY(outer_propose(c->op, c->max_nblk, s));  // k = 1: prior draws into the proposal buffers
   cudaEvent_t e0, e1;
@@ -343,7 +380,7 @@ smc2_status choose_launch_shape(smc2_ctx* c) {
   float best = 1e30f;
   Shape pick = cand[0];
   for (const auto& cb : cand) {
-    if (apply_shape(c, cb.ppt, cb.block, cb.named, true) != SMC2_OK) continue;
+    if (apply_shape(c, cb.ppt, cb.block, cb.named, true, cb.fast) != SMC2_OK) continue;
     PFLaunch L = c->pl;
     float ms = 0.f;
     bool ok = true;
@@ -352,8 +389,7 @@ smc2_status choose_launch_shape(smc2_ctx* c) {
       L.t_cap = rep == 0 ? 4 : 32;
       ok = cudaMemsetAsync(c->d_wu_counter, 0, sizeof(int), s) == cudaSuccess &&
            cudaEventRecord(e0, s) == cudaSuccess &&
-           pf_launch(c->precision, c->model, c->ppt, c->pf_named, c->pf_general, c->pf_grid, c->pf_block, c->pf_smem,
-                     L, s) == cudaSuccess &&
+           ctx_pf_launch(c, c->pf_grid, L, s) == cudaSuccess &&
            cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
            cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
       c->kernel_launches++;
@@ -367,7 +403,7 @@ smc2_status choose_launch_shape(smc2_ctx* c) {
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  return apply_shape(c, pick.ppt, pick.block, pick.named, true);
+  return apply_shape(c, pick.ppt, pick.block, pick.named, true, pick.fast);
 }
 
 smc2_status clear_run_state(smc2_ctx* c) {
@@ -475,8 +511,7 @@ smc2_status enqueue_iteration(smc2_ctx* c, cudaStream_t s, cudaEvent_t ev0, cuda
   SMC2_TRY(cudaEventRecord(c->ev_join, c->side_stream));
   SMC2_TRY(cudaMemsetAsync(c->d_wu_counter, 0, sizeof(int), s));
   if (ev0) SMC2_TRY(cudaEventRecordWithFlags(ev0, s, cudaEventRecordExternal));
-  SMC2_TRY(pf_launch(c->precision, c->model, c->ppt, c->pf_named, c->pf_general, c->pf_grid, c->pf_block, c->pf_smem,
-                     c->pl, s));
+  SMC2_TRY(ctx_pf_launch(c, c->pf_grid, c->pl, s));
   if (ev1) SMC2_TRY(cudaEventRecordWithFlags(ev1, s, cudaEventRecordExternal));
   SMC2_TRY(cudaStreamWaitEvent(s, c->ev_join, 0));
   SMC2_TRY(outer_weights(c->op, c->max_nblk, s));
@@ -672,11 +707,22 @@ smc2_status smc2_reset(smc2_ctx* c, uint64_t seed) {
 }
 
 static smc2_status pf_standalone(smc2_ctx* c, const double* theta, int n, int iteration, int dataset,
-                                 double* loglik, double* delta, int32_t* anc) {
+                                 double* loglik, double* delta, int32_t* anc, float* xtr = nullptr,
+                                 float* ltr = nullptr, uint64_t* qtr = nullptr) {
   if (!c || !theta || !loglik || n < 1 || n > SMC2_MAX_N || bad_ds(c, dataset) || iteration < 0 ||
       iteration >= (1 << 28))
     return SMC2_EINVAL;
+  const bool trace = xtr || ltr || qtr;
+  if (trace) {
+    if (!xtr || !ltr || !qtr) return SMC2_EINVAL;
+    // the traced instantiation of the one-group-per-CTA filter at the context's shape
+    int block = 0;
+    if (!(c->pf_fast || fast_shape_valid(c, c->ppt, &block))) return SMC2_EINVAL;
+  }
   PFJob job{};
+  job.xtr = xtr;
+  job.ltr = ltr;
+  job.qtr = qtr;
   job.theta = theta;
   job.ld = n;
   job.n = n;
@@ -698,11 +744,23 @@ static smc2_status pf_standalone(smc2_ctx* c, const double* theta, int n, int it
   L.wu_counter = nullptr;
   L.k_done = nullptr;
   L.k_imm = iteration;
-  const int occ =
-      std::max(1, pf_occupancy(c->precision, c->model, c->ppt, c->pf_named, c->pf_general, c->pf_block, c->pf_smem));
+  if (trace && !c->pf_fast) {  // the context runs pf_kernel: trace the FP32 filter at the same ppt
+    int block = 0;
+    fast_shape_valid(c, c->ppt, &block);
+    size_t smem = 0;
+    for (int m : c->M) smem = std::max(smem, pf_fast_smem_bytes(c->model, c->ppt, m));
+    SMC2_TRY(pf_fast_configure(c->model, c->ppt, true, smem));
+    L.fpc_single = 1;
+    L.n_wu = n;
+    const int occ = std::max(1, pf_fast_occupancy(c->model, c->ppt, true, block, smem));
+    SMC2_TRY(pf_fast_launch(c->model, c->ppt, true, std::min(n, occ * c->sms), block, smem, L, c->stream));
+    c->kernel_launches++;
+    return SMC2_OK;
+  }
+  if (trace) SMC2_TRY(pf_fast_configure(c->model, c->ppt, true, c->pf_smem));
+  const int occ = std::max(1, ctx_pf_occupancy(c, trace));
   const int grid = std::min(L.n_wu, occ * c->sms);
-  SMC2_TRY(pf_launch(c->precision, c->model, c->ppt, c->pf_named, c->pf_general, grid, c->pf_block, c->pf_smem, L,
-                     c->stream));
+  SMC2_TRY(ctx_pf_launch(c, grid, L, c->stream, trace));
   c->kernel_launches++;
   return SMC2_OK;
 }
@@ -715,6 +773,13 @@ smc2_status smc2_pf_loglik(smc2_ctx* c, const double* theta, int n, int iteratio
 smc2_status smc2_pf_trace(smc2_ctx* c, const double* theta, int n, int iteration, int dataset,
                           double* loglik, double* delta, int32_t* anc) {
   return pf_standalone(c, theta, n, iteration, dataset, loglik, delta, anc);
+}
+
+smc2_status smc2_pf_trace_states(smc2_ctx* c, const double* theta, int n, int iteration, int dataset,
+                                 double* loglik, double* delta, int32_t* anc, float* x, float* logw,
+                                 uint64_t* q) {
+  if (!x || !logw || !q) return SMC2_EINVAL;
+  return pf_standalone(c, theta, n, iteration, dataset, loglik, delta, anc, x, logw, q);
 }
 
 smc2_status smc2_run(smc2_ctx* c, int n_iter, smc2_iter_stats* stats_host) {
@@ -996,8 +1061,9 @@ smc2_status smc2_sync(smc2_ctx* c) {
   return sticky(c);
 }
 
-smc2_status smc2_get_launch_shape(smc2_ctx* c, int* ppt, int* cta_threads, int* grid) {
+smc2_status smc2_get_launch_shape(smc2_ctx* c, int* ppt, int* cta_threads, int* grid, int* one_group) {
   if (!c) return SMC2_EINVAL;
+  if (one_group) *one_group = c->pf_fast ? 1 : 0;
   if (ppt) *ppt = c->ppt;
   if (cta_threads) *cta_threads = c->pf_block;
   if (grid) *grid = c->pf_grid;

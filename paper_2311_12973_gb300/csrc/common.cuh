@@ -45,8 +45,9 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 key) {
   for (int round = 0; round < 10; ++round) {
     const uint32_t k0 = key.x + (uint32_t)round * 0x9E3779B9u;
     const uint32_t k1 = key.y + (uint32_t)round * 0xBB67AE85u;
-    const uint32_t hi0 = __umulhi(mult0, c.x), lo0 = mult0 * c.x;
-    const uint32_t hi1 = __umulhi(mult1, c.z), lo1 = mult1 * c.z;
+    const uint64_t p0 = (uint64_t)mult0 * c.x, p1 = (uint64_t)mult1 * c.z;  // one wide multiply each
+    const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
     c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
   }
   return c;

@@ -122,7 +122,15 @@ struct PFJob {
   const void* obs;     // R4 per step
   uint32_t c2hi;
   int pad;
+  // optional per-step trace of the FP32 filter (traced instantiations only): after the
+  // propagation of step t, by particle j, at [(i T + t - 1) M + j]: the state (LG x;
+  // SEIR S, E, I, log beta and the day's incidence) in xtr [..][kTraceState], the
+  // log-weight in ltr and the quantised weight in qtr
+  float* xtr;
+  float* ltr;
+  uint64_t* qtr;
 };
+constexpr int kTraceState = 5;  // floats per particle in a state trace
 
 struct PFModel {
   double npop, e0, i0, lambda_floor;
@@ -154,6 +162,17 @@ cudaError_t pf_launch(int precision, int model, int ppt, bool named, bool genera
                       size_t smem, const PFLaunch& L, cudaStream_t s);
 cudaError_t pf_configure(int precision, int model, int ppt, bool named, bool general, size_t smem);
 int pf_occupancy(int precision, int model, int ppt, bool named, bool general, int block, size_t smem);
+
+// The register-resident FP32 filter with one group per CTA (pf_fast.cuh): the
+// default filter (systematic resampling after every step) of the LG and SEIR
+// models in mixed precision, ppt 4, 8 or 16.  trace selects the instantiation
+// that writes the per-step trace of PFJob.
+bool pf_fast_eligible(int precision, int model, bool general, int ppt);
+size_t pf_fast_smem_bytes(int model, int ppt, int M);
+cudaError_t pf_fast_launch(int model, int ppt, bool trace, int grid, int block, size_t smem, const PFLaunch& L,
+                           cudaStream_t s);
+cudaError_t pf_fast_configure(int model, int ppt, bool trace, size_t smem);
+int pf_fast_occupancy(int model, int ppt, bool trace, int block, size_t smem);
 
 // Outer kernels (outer.cu).
 cudaError_t outer_obs_terms(int precision, int model, const double* y, int T, void* obs,

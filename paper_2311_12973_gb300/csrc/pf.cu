@@ -1,7 +1,7 @@
 // pf.cu -- host side of the particle-filter kernel: shapes, attributes, launches.
 #include <mutex>
 
-#include "pf_impl.cuh"
+#include "pf_fast.cuh"
 
 namespace smc2 {
 
@@ -56,6 +56,52 @@ int pf_occupancy(int precision, int model, int ppt, bool named, bool general, in
 cudaError_t pf_launch(int precision, int model, int ppt, bool named, bool general, int grid, int block,
                       size_t smem, const PFLaunch& L, cudaStream_t s) {
   const void* f = select_kernel(precision, model, ppt, named, general);
+  if (!f) return cudaErrorInvalidValue;
+  void* args[] = {const_cast<PFLaunch*>(&L)};
+  return cudaLaunchKernel(f, dim3(grid), dim3(block), args, smem, s);
+}
+
+// ---------------------------------------------------------------------------
+// the FP32 one-group-per-CTA filter (pf_fast.cuh)
+// ---------------------------------------------------------------------------
+bool pf_fast_eligible(int precision, int model, bool general, int ppt) {
+  return precision == SMC2_PREC_MIXED && (model == MODEL_LG || model == MODEL_SEIR) && !general &&
+         (ppt == 2 || ppt == 4 || ppt == 8);
+}
+
+size_t pf_fast_smem_bytes(int model, int ppt, int M) {
+  const int T = group_threads_for(ppt, M);
+  return fast_region_bytes(ppt * T, model == MODEL_LG ? 1 : 4);
+}
+
+static const void* select_fast(int model, int ppt, bool trace) {
+  if (model == MODEL_LG) return pf_fast_select_lg(ppt, trace);
+  if (model == MODEL_SEIR) return pf_fast_select_seir(ppt, trace);
+  return nullptr;
+}
+
+cudaError_t pf_fast_configure(int model, int ppt, bool trace, size_t smem) {
+  const void* f = select_fast(model, ppt, trace);
+  if (!f) return cudaErrorInvalidValue;
+  static std::mutex mu;  // only ever raised, as for pf_kernel
+  std::lock_guard<std::mutex> lock(mu);
+  cudaFuncAttributes a{};
+  const cudaError_t e = cudaFuncGetAttributes(&a, f);
+  if (e != cudaSuccess) return e;
+  if ((size_t)a.maxDynamicSharedSizeBytes >= smem) return cudaSuccess;
+  return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+int pf_fast_occupancy(int model, int ppt, bool trace, int block, size_t smem) {
+  const void* f = select_fast(model, ppt, trace);
+  int n = 0;
+  if (!f || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, block, smem) != cudaSuccess) return 0;
+  return n;
+}
+
+cudaError_t pf_fast_launch(int model, int ppt, bool trace, int grid, int block, size_t smem, const PFLaunch& L,
+                           cudaStream_t s) {
+  const void* f = select_fast(model, ppt, trace);
   if (!f) return cudaErrorInvalidValue;
   void* args[] = {const_cast<PFLaunch*>(&L)};
   return cudaLaunchKernel(f, dim3(grid), dim3(block), args, smem, s);

@@ -1,0 +1,421 @@
+// pf_fast.cuh -- the FP32 bootstrap particle filter (Sec. II) with one filter
+// per CTA and the particles held in registers.
+//
+// The same filter as pf_kernel's default (systematic resampling after every
+// step t < T, Eqs. 26-27 with Algorithm 1's output order; the mean-weight reset
+// of Eq. 13; the likelihood increment of Eq. 8), shaped for few instructions
+// per particle: each of the CTA's T threads owns PPT consecutive particles
+// (2, 4 or 8) and works on them in pairs with the packed two-wide FP32
+// instructions, and no step has a loop whose length differs between lanes.
+// Per step:
+//   1. propagate and log-weight every particle in registers (Eqs. 1, 2, 5);
+//   2. the group maximum of the log-weights (warp shuffles; one barrier when
+//      the CTA has several warps);
+//   3. q_j = floor(exp(l_j - max) 2^B) by integer operations on the float's
+//      exponent and significand (a float-to-u64 conversion instruction would run
+//      on the narrow FP64 pipe), a thread-local inclusive prefix, one warp scan
+//      and (several warps) one more barrier for the warp totals;
+//   4. the increment max + log(S 2^-B) - log M from the exact integer total S;
+//   5. resampling by marks: particle j fills the slots F(C_{j-1}) .. F(C_j) - 1,
+//      F(C) the number of thresholds tau_s = floor((s + u) S / M) below C (the
+//      slot counting of pf_kernel).  Each particle with copies writes its index,
+//      tagged with a step counter, at its first slot, and at the first slot of
+//      every thread whose slots its range covers; after a barrier the ancestor
+//      of slot s is the largest current tag at or before s within its thread's
+//      slots -- ancestors never decrease along the slots -- and the thread reads
+//      that particle's state.
+// Shared arrays indexed by a slot or a particle s keep it at row s % PPT, column
+// s / PPT, so that a warp reading one entry per thread touches consecutive words.
+#pragma once
+
+#include "pf_impl.cuh"
+
+namespace smc2 {
+
+// floor(v) for a float 0 <= v <= 2^52 as its two 32-bit halves: hi = floor(v 2^-32)
+// and lo = floor(v - hi 2^32).  Both steps are exact in float (v 2^-32 is a power-of-
+// two scaling; v - hi 2^32 = v mod 2^32 holds at most v's 24 significant bits), and
+// the two 32-bit conversions avoid the float-to-u64 one, which runs on the FP64 pipe.
+__device__ __forceinline__ uint64_t floor_to_u64(float v) {
+  const float hi = floorf(v * 0x1p-32f);
+  const float lo = fmaf(-hi, 0x1p32f, v);
+  return ((uint64_t)__float2uint_rz(hi) << 32) | (uint64_t)__float2uint_rz(lo);
+}
+
+// 2^x by the hardware approximation (relative error about 2^-22; 0 for -inf).
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 max2(float2 a, float b) { return make_float2(fmaxf(a.x, b), fmaxf(a.y, b)); }
+
+// The models' per-filter constants for pairs of particles (the SEIR-type
+// model's Euler day and Poisson log-weight, the AR(1) step and Gaussian
+// log-weight), computed as FilterParams computes them for one particle.
+template <int MODEL>
+struct PairModel;
+
+template <>
+struct PairModel<MODEL_LG> {
+  float2 phi, sx, inv_sy, c_obs;
+  __device__ explicit PairModel(const FilterParams<float, MODEL_LG>& f)
+      : phi(bc2(f.phi)), sx(bc2(f.sx)), inv_sy(bc2(f.inv_sy)), c_obs(bc2(f.c_obs)) {}
+  // x = phi x + sx z; l = c - (1/2) ((y - x) / sy)^2
+  __device__ __forceinline__ float2 step(float2* x, float2 z, const float4& ob, float2& lam) const {
+    x[0] = fma2(phi, x[0], mul2(sx, z));
+    const float2 r = mul2(fma2(x[0], bc2(-1.f), bc2(ob.x)), inv_sy);
+    lam = bc2(0.f);
+    return fma2(mul2(bc2(-0.5f), r), r, c_obs);
+  }
+};
+
+template <>
+struct PairModel<MODEL_SEIR> {
+  float2 srw, kappa, gamma, inv_npop, dt, ndt;
+  float lam_floor;
+  int n_sub;
+  __device__ explicit PairModel(const FilterParams<float, MODEL_SEIR>& f)
+      : srw(bc2(f.srw)), kappa(bc2(f.kappa)), gamma(bc2(f.gamma)), inv_npop(bc2(f.inv_npop)), dt(bc2(f.dt)),
+        ndt(bc2(-f.dt)), lam_floor(f.lam_floor), n_sub(f.n_sub) {}
+  __device__ __forceinline__ void substep(float2 beta, float2& S, float2& E, float2& I, float2& lam) const {
+    const float2 inf = mul2(mul2(mul2(beta, S), I), inv_npop);
+    const float2 onset = mul2(kappa, E);
+    const float2 recovery = mul2(gamma, I);
+    lam = fma2(dt, onset, lam);
+    S = max2(fma2(ndt, inf, S), 0.f);
+    E = max2(fma2(dt, fma2(onset, bc2(-1.f), inf), E), 0.f);       // E + dt (inf - onset)
+    I = max2(fma2(dt, fma2(recovery, bc2(-1.f), onset), I), 0.f);  // I + dt (onset - recovery)
+  }
+  // x = (S, E, I, log beta) of two particles; returns their log-weights, and lam the day's incidence
+  __device__ __forceinline__ float2 step(float2* x, float2 z, const float4& ob, float2& lam) const {
+    x[3] = fma2(srw, z, x[3]);
+    const float2 beta = make_float2(__expf(x[3].x), __expf(x[3].y));
+    float2 S = x[0], E = x[1], I = x[2];
+    lam = bc2(0.f);
+    if (n_sub == 2) {
+      substep(beta, S, E, I, lam);
+      substep(beta, S, E, I, lam);
+    } else {
+      for (int s = 0; s < n_sub; ++s) substep(beta, S, E, I, lam);
+    }
+    x[0] = S;
+    x[1] = E;
+    x[2] = I;
+    lam = max2(lam, lam_floor);
+    // Poisson log-pmf y (log1p(d) - d) + c_y, d = (lambda - y) / y (no cancellation near y)
+    if (ob.x > 0.f) {
+      const float2 d = mul2(add2(lam, bc2(-ob.x)), bc2(ob.y));
+      const float2 l1 = make_float2(log1pf(d.x), log1pf(d.y));
+      return fma2(bc2(ob.x), fma2(d, bc2(-1.f), l1), bc2(ob.z));
+    }
+    return mul2(lam, bc2(-1.f));
+  }
+};
+
+// Register budget per particles-per-thread shape of the FP32 filter.
+template <int PPT>
+struct FastRegCap {
+  static constexpr int value = PPT <= 2 ? 64 : (PPT == 4 ? 80 : 120);
+  static_assert(PPT == 2 || PPT == 4 || PPT == 8, "particles per thread");
+};
+
+// Shared memory of a CTA of T threads holding Mp = PPT T particles:
+//   Xo    float  [PPT][T][NS]   states after propagation, by particle
+//   Z     float2 [4][PPT/2][T]  the four normals of the current Philox counter of each slot pair
+//   mark  u32    [PPT][T]       step-tagged particle indices at the slots
+//   carry u32    [T]            the tagged ancestor of each thread's first slot
+//   wsum u64 [32], wmax float [32], sU u32 [8]
+__host__ __device__ constexpr size_t fast_region_bytes(int Mp, int ns) {
+  return (size_t)ns * Mp * 4 + (size_t)4 * Mp * 4 + (size_t)Mp * 4 + (size_t)(Mp / 2) * 4 + 32 * 8 + 32 * 4 + 32;
+}
+
+constexpr int kMarkBits = 12;  // particle index bits of a mark (M <= 4096)
+
+template <int MODEL, int PPT, bool TRACE>
+__device__ __forceinline__ void fast_filter(const PFJob& J, const PFModel& mdl, int i, unsigned char* smem,
+                                            uint2 key, uint32_t k, int t_cap, uint32_t& tag) {
+  constexpr int NS = ModelDims<MODEL>::NS;
+  constexpr int D = ModelDims<MODEL>::D;
+  constexpr int LOG2P = PPT == 2 ? 1 : (PPT == 4 ? 2 : 3);
+  constexpr int NP = PPT / 2;  // pairs per thread
+  const int T = blockDim.x, nw = T >> 5;
+  const int lt = threadIdx.x, lane = lt & 31, warp = lt >> 5;
+  const int M = J.M, TT = t_cap > 0 ? min(J.T, t_cap) : J.T;
+  const int Mp = PPT * T;
+  float* Xo = reinterpret_cast<float*>(smem);                           // [PPT][T][NS]
+  float2* Z = reinterpret_cast<float2*>(Xo + (size_t)NS * Mp);          // [4][NP][T]
+  uint32_t* mark = reinterpret_cast<uint32_t*>(Z + (size_t)2 * Mp);     // [PPT][T]
+  uint32_t* carry = mark + Mp;                                          // [T]
+  uint64_t* wsum = reinterpret_cast<uint64_t*>(carry + (Mp / 2));       // [32] (Mp / 2 >= T keeps 8-byte alignment)
+  float* wmax = reinterpret_cast<float*>(wsum + 32);                    // [32]
+  uint32_t* sU = reinterpret_cast<uint32_t*>(wmax + 32);                // [8]
+
+  double th[D];
+#pragma unroll
+  for (int d = 0; d < D; ++d) th[d] = J.theta[(size_t)d * J.ld + i];
+  FilterParams<float, MODEL> fp;
+  fp.load(th, mdl);
+  const PairModel<MODEL> pm(fp);
+
+  const uint32_t c2 = counter_c2((uint32_t)i, J.c2hi);
+  const uint32_t c3prop = counter_c3(TAG_PF_PROP, k);
+  const uint32_t c3res = counter_c3(TAG_PF_RES, k);
+  const int B = fixed_point_bits(M);
+  const float2 scaleB = bc2(ldexpf(1.f, B));
+  const double log_norm = -(double)B * kLn2 - log((double)M);
+  const float4* obs = reinterpret_cast<const float4*>(J.obs);
+
+  float2 x[NP][NS];  // particles 2p and 2p + 1 of the thread in x[p] (.x, .y)
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    float a[NS], b[NS];
+    float za = 0.f, zb = 0.f;
+    if constexpr (MODEL == MODEL_LG) {
+      float z[4];
+      normals4<float>(make_uint4((uint32_t)(lt * PPT + 2 * p), 0u, c2, counter_c3(TAG_PF_INIT, k)), key, z);
+      za = z[0];
+      normals4<float>(make_uint4((uint32_t)(lt * PPT + 2 * p + 1), 0u, c2, counter_c3(TAG_PF_INIT, k)), key, z);
+      zb = z[0];
+    }
+    fp.init(a, za, th);
+    fp.init(b, zb, th);
+#pragma unroll
+    for (int e = 0; e < NS; ++e) x[p][e] = make_float2(a[e], b[e]);
+  }
+
+  double loglik = 0.0;  // log p^(y_{1:t}) (Eq. 8), carried by thread 0
+  for (int t = 1; t <= TT; ++t) {
+    const int tm = (t - 1) & 3;
+    uint32_t* sUg = sU + 4 * (((t - 1) >> 2) & 1);
+    if (tm == 0) {  // one Philox call per slot every four steps; the normals wait in shared memory
+#pragma unroll 1
+      for (int p = 0; p < NP; ++p) {
+        float za[4], zb[4];
+        normals4<float>(make_uint4((uint32_t)(lt * PPT + 2 * p), (uint32_t)((t - 1) >> 2), c2, c3prop), key, za);
+        normals4<float>(make_uint4((uint32_t)(lt * PPT + 2 * p + 1), (uint32_t)((t - 1) >> 2), c2, c3prop), key, zb);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) Z[(e * NP + p) * T + lt] = make_float2(za[e], zb[e]);
+      }
+      if (lt < 4 && t + lt < TT) sUg[lt] = philox4x32_10(make_uint4(0u, (uint32_t)(t + lt), c2, c3res), key).x;
+      if (nw == 1) __syncwarp();  // the resampling words before the warp reads them
+    }
+    const float4 ob = obs[t - 1];
+    float ell[PPT];
+    float lmax = -INFINITY;
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      float2 lam;
+      const float2 l2 = pm.step(x[p], Z[(tm * NP + p) * T + lt], ob, lam);
+      const int j = lt * PPT + 2 * p;
+      const float la = (isnan(l2.x) || j >= M) ? -INFINITY : l2.x;
+      const float lb = (isnan(l2.y) || j + 1 >= M) ? -INFINITY : l2.y;
+      ell[2 * p] = la;
+      ell[2 * p + 1] = lb;
+      lmax = fmaxf(lmax, fmaxf(la, lb));
+      if constexpr (TRACE) {
+        if (J.xtr) {
+          const size_t row = ((size_t)i * J.T + (t - 1)) * M + j;
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            if (j + h >= M) continue;
+            float* xt = J.xtr + (row + h) * kTraceState;
+#pragma unroll
+            for (int e = 0; e < NS; ++e) xt[e] = h ? x[p][e].y : x[p][e].x;
+            if constexpr (MODEL == MODEL_SEIR) xt[NS] = h ? lam.y : lam.x;
+            J.ltr[row + h] = h ? lb : la;
+          }
+        }
+      }
+    }
+    // (2) group maximum
+    lmax = warp_max(lmax);
+    if (nw > 1) {
+      if (lane == 0) wmax[warp] = lmax;
+      __syncthreads();
+      for (int w = 0; w < nw; ++w) lmax = fmaxf(lmax, wmax[w]);
+    }
+    const float m = lmax;
+    if (!(m > -INFINITY)) {  // every weight vanished: the estimate is zero
+      loglik = -HUGE_VAL;
+      if (lt == 0 && J.delta)
+        for (int s = t; s <= J.T; ++s) J.delta[(size_t)i * J.T + (s - 1)] = -HUGE_VAL;
+      break;
+    }
+    // (3) quantise: v = 2^((l - max) log2 e) 2^B (0 for l = -inf), q = floor(v); the
+    // thread-local inclusive prefix (exact) and its float shadow
+    uint64_t c[PPT];
+    float cf[PPT];
+    uint64_t run = 0;
+    float runf = 0.f;
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      const float2 a = mul2(add2(make_float2(ell[2 * p], ell[2 * p + 1]), bc2(-m)), bc2(1.4426950408889634f));
+      const float2 v = mul2(make_float2(ex2_approx(a.x), ex2_approx(a.y)), scaleB);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const float vh = h ? v.y : v.x;
+        const uint64_t q = floor_to_u64(vh);
+        run += q;
+        runf += vh;
+        c[2 * p + h] = run;
+        cf[2 * p + h] = runf;
+        if constexpr (TRACE) {
+          if (J.qtr && lt * PPT + 2 * p + h < M) J.qtr[((size_t)i * J.T + (t - 1)) * M + lt * PPT + 2 * p + h] = q;
+        }
+      }
+    }
+    const uint64_t incl = warp_incl_scan_u64(run, lane);
+    const uint64_t excl = incl - run;
+    uint64_t S, base = 0;
+    if (nw > 1) {
+      if (lane == 31) wsum[warp] = incl;
+      __syncthreads();
+      S = 0;
+      for (int w = 0; w < nw; ++w) {
+        const uint64_t sw = wsum[w];
+        base += w < warp ? sw : 0ull;
+        S += sw;
+      }
+    } else {
+      S = __shfl_sync(0xffffffffu, incl, 31);
+    }
+    // (4) log-likelihood increment from the exact integer total (S >= 2^(B-1), B >= 51)
+    if (lt == 0) {
+      const int e = 63 - __clzll((long long)S);
+      const float mant = __uint2float_rn((uint32_t)(S >> (e - 31))) * 0x1p-31f;  // S / 2^e in [1, 2]
+      const double lmean = (double)m + ((double)e * kLn2 + (double)logf(mant)) + log_norm;
+      loglik += lmean;
+      if (J.delta) J.delta[(size_t)i * J.T + (t - 1)] = lmean;
+    }
+    // (5) systematic resampling by marks
+    if (t < TT) {
+      if (++tag == (1u << (32 - kMarkBits))) {  // the tags are spent: clear every mark, start again
+        for (int s = lt; s < Mp; s += T) mark[s] = 0u;
+        tag = 1;
+        if (nw > 1)
+          __syncthreads();
+        else
+          __syncwarp();
+      }
+      const uint32_t tg = tag << kMarkBits;
+      const SlotCount sc = slot_count_setup(sUg[tm], S, M);
+      const uint64_t C0 = base + excl;  // cumulative weight before the thread's first particle
+      const float C0f = u64_to_float(C0);
+      int start = slots_below(sc, C0, C0f);
+#pragma unroll
+      for (int p = 0; p < NP; ++p) {
+        float a[NS], b[NS];
+#pragma unroll
+        for (int e = 0; e < NS; ++e) {
+          a[e] = x[p][e].x;
+          b[e] = x[p][e].y;
+        }
+        StateVec<float, NS>::store(Xo + (size_t)((2 * p) * T + lt) * NS, 0, a);
+        StateVec<float, NS>::store(Xo + (size_t)((2 * p + 1) * T + lt) * NS, 0, b);
+      }
+#pragma unroll
+      for (int r = 0; r < PPT; ++r) {
+        const int end = slots_below(sc, C0 + c[r], C0f + cf[r]);
+        const uint32_t mk = tg | (uint32_t)(lt * PPT + r);
+        if (end > start) mark[(start & (PPT - 1)) * T + (start >> LOG2P)] = mk;
+        // the first slot of every thread inside [start, end): usually none or one
+        const int b0 = (start + PPT - 1) & ~(PPT - 1);
+        if (b0 < end) carry[b0 >> LOG2P] = mk;
+        if (end - b0 > PPT)
+          for (int b = b0 + PPT; b < end; b += PPT) carry[b >> LOG2P] = mk;
+        start = end;
+      }
+      if (nw > 1)
+        __syncthreads();
+      else
+        __syncwarp();
+      uint32_t a = carry[lt];
+#pragma unroll
+      for (int r = 0; r < PPT; ++r) {
+        if (lt * PPT + r >= M) continue;  // padding slots hold no particle
+        a = max(a, mark[r * T + lt]);
+        const int src = (int)(a & ((1u << kMarkBits) - 1));
+        if (J.anc) J.anc[((size_t)i * (J.T - 1) + (t - 1)) * M + lt * PPT + r] = src;
+        const float* xs = Xo + ((size_t)(src & (PPT - 1)) * T + (src >> LOG2P)) * NS;
+        float v[NS];
+        StateVec<float, NS>::load(xs, 0, v);
+#pragma unroll
+        for (int e = 0; e < NS; ++e) {
+          if (r & 1)
+            x[r >> 1][e].y = v[e];
+          else
+            x[r >> 1][e].x = v[e];
+        }
+      }
+      if (nw == 1) __syncwarp();  // every read done before the next step's writes
+    }
+  }
+  if (lt == 0) J.loglik[i] = loglik;
+}
+
+template <int MODEL, int PPT, bool TRACE>
+__global__ void __maxnreg__((FastRegCap<PPT>::value)) pf_fast_kernel(PFLaunch L) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_wu;
+  const uint32_t k = L.k_done ? (uint32_t)(*L.k_done + 1) : (uint32_t)L.k_imm;
+  const uint2 key = seed_key(L.seed);
+  uint32_t tag = 0;  // step tag of the marks, shared by every filter this CTA runs
+  bool cleared = false;
+  for (int it = 0;; ++it) {
+    int w;
+    if (L.wu_counter) {
+      __syncthreads();
+      if (threadIdx.x == 0) s_wu = atomicAdd(L.wu_counter, 1);
+      __syncthreads();
+      w = s_wu;
+    } else {
+      w = blockIdx.x + it * gridDim.x;
+    }
+    if (w >= L.n_wu) break;
+    int job, first, count;
+    if (L.wus) {
+      const int4 u = L.wus[w];
+      job = u.x;
+      first = u.y;
+      count = u.z;
+    } else {
+      job = 0;
+      first = w * L.fpc_single;
+      count = min(L.fpc_single, L.job0.n - first);
+    }
+    const PFJob J = L.jobs ? L.jobs[job] : L.job0;
+    if (!cleared) {  // the marks start untagged (tag 0)
+      const int Mp = PPT * (int)blockDim.x;
+      uint32_t* mark = reinterpret_cast<uint32_t*>(smem + (size_t)ModelDims<MODEL>::NS * Mp * 4 + (size_t)Mp * 16);
+      for (int s = threadIdx.x; s < Mp; s += blockDim.x) mark[s] = 0u;
+      cleared = true;
+    }
+    for (int f = 0; f < count; ++f) {  // one group per CTA: a unit's filters run in turn
+      __syncthreads();
+      fast_filter<MODEL, PPT, TRACE>(J, L.mdl, first + f, smem, key, k, L.t_cap, tag);
+    }
+    if (!L.wu_counter) __syncthreads();
+  }
+}
+
+template <int MODEL, bool TRACE>
+const void* pf_fast_select(int ppt) {
+  switch (ppt) {
+    case 2: return reinterpret_cast<const void*>(&pf_fast_kernel<MODEL, 2, TRACE>);
+    case 4: return reinterpret_cast<const void*>(&pf_fast_kernel<MODEL, 4, TRACE>);
+    case 8: return reinterpret_cast<const void*>(&pf_fast_kernel<MODEL, 8, TRACE>);
+    default: return nullptr;
+  }
+}
+
+// instantiated in pf_fast_lg.cu and pf_fast_seir.cu
+const void* pf_fast_select_lg(int ppt, bool trace);
+const void* pf_fast_select_seir(int ppt, bool trace);
+
+}  // namespace smc2

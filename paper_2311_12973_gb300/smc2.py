@@ -21,6 +21,7 @@ PREC_FP64, PREC_MIXED = 0, 1
 PROP_RW, PROP_MLP = 0, 1
 PF_SYSTEMATIC, PF_MULTINOMIAL = 0, 1
 PRIOR_GAUSS, PRIOR_UNIFORM = 0, 1
+PF_ANY, PF_GROUPS, PF_ONE_GROUP = 0, 1, 2
 LK_FORWARD, LK_GAUSS_OPT = 0, 1
 
 
@@ -35,7 +36,7 @@ class Config(C.Structure):
         ("ds_N", C.POINTER(C.c_int)), ("ds_M", C.POINTER(C.c_int)), ("ds_T", C.POINTER(C.c_int)),
         ("mlp_h", C.c_double), ("mlp_lr", C.c_double), ("mlp_steps", C.c_int), ("mlp_window", C.c_int),
         ("pf_ess_frac", C.c_double), ("pf_scheme", C.c_int), ("prior_kind", C.c_int),
-        ("prior_lo", C.c_double * MAX_D), ("prior_hi", C.c_double * MAX_D),
+        ("prior_lo", C.c_double * MAX_D), ("prior_hi", C.c_double * MAX_D), ("pf_family", C.c_int),
     ]
 
 
@@ -91,7 +92,9 @@ def _load() -> C.CDLL:
         "smc2_set_timing": ([ctx, C.c_int], st),
         "smc2_get_timing": ([ctx, C.POINTER(C.c_double), C.POINTER(C.c_int64),
                              C.POINTER(C.c_int64), C.c_int], st),
-        "smc2_get_launch_shape": ([ctx, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)], st),
+        "smc2_get_launch_shape": ([ctx, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                   C.POINTER(C.c_int)], st),
+        "smc2_pf_trace_states": ([ctx, dp, C.c_int, C.c_int, C.c_int, dp, dp, i32p, dp, dp, dp], st),
         "smc2_pf_loglik_noalloc": ([C.POINTER(Config), dp, dp, C.c_int, C.c_int, dp, vp], st),
         "smc2_mlp_loss_grad": ([C.c_int, dp, dp, dp, C.c_int, dp, dp, vp], st),
         "smc2_mlp_input_grad": ([C.c_int, dp, dp, C.c_int, dp, dp, vp], st),
@@ -160,6 +163,7 @@ def make_config(w, **over) -> Config:
     c.mlp_steps, c.mlp_window = get("mlp_steps", 0), get("mlp_window", 0)
     c.pf_ess_frac, c.pf_scheme = get("pf_ess_frac", 0.0), get("pf_scheme", PF_SYSTEMATIC)
     c.prior_kind = get("prior_kind", PRIOR_GAUSS)
+    c.pf_family = get("pf_family", PF_ANY)
     if c.prior_kind == PRIOR_UNIFORM:
         for d in range(c.D):
             c.prior_lo[d] = get("prior_lo")[d]
@@ -182,6 +186,8 @@ class SMC2:
             cfg.ds_N, cfg.ds_M, cfg.ds_T = (a.ctypes.data_as(C.POINTER(C.c_int)) for a in arrs)
         self.n_ds = max(1, cfg.n_datasets)
         self.Ns = [d[0] for d in datasets] if datasets is not None else [cfg.N]
+        self.Ms = [d[1] for d in datasets] if datasets is not None else [cfg.M]
+        self.Ts = [d[2] for d in datasets] if datasets is not None else [cfg.T]
         self.stream = _stream_handle(stream)
         y = self._host_or_device(y)
         self._ctx = C.c_void_p()
@@ -333,10 +339,29 @@ class SMC2:
         return ll, delta, anc
 
     def launch_shape(self):
-        a, b, c = C.c_int(), C.c_int(), C.c_int()
-        _check(lib.smc2_get_launch_shape(self._ctx, C.byref(a), C.byref(b), C.byref(c)),
+        a, b, c, f = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        _check(lib.smc2_get_launch_shape(self._ctx, C.byref(a), C.byref(b), C.byref(c), C.byref(f)),
                "smc2_get_launch_shape")
-        return {"ppt": a.value, "cta_threads": b.value, "grid": c.value}
+        return {"ppt": a.value, "cta_threads": b.value, "grid": c.value, "one_group_per_cta": bool(f.value)}
+
+    def pf_trace_states(self, theta_soa, iteration: int, dataset: int = 0):
+        """The FP32 filter's per-step trace: log-likelihoods [n], increments [n][T],
+        ancestors [n][T-1][M], post-propagation states [n][T][M][5], log-weights
+        [n][T][M] and quantised weights [n][T][M] (int64 storage of uint64)."""
+        import torch
+        n = theta_soa.shape[1]
+        M, T = self.Ms[dataset], self.Ts[dataset]
+        dev = theta_soa.device
+        ll = torch.empty(n, dtype=torch.float64, device=dev)
+        delta = torch.empty((n, T), dtype=torch.float64, device=dev)
+        anc = torch.empty((n, max(T - 1, 0), M), dtype=torch.int32, device=dev)
+        x = torch.empty((n, T, M, 5), dtype=torch.float32, device=dev)
+        lw = torch.empty((n, T, M), dtype=torch.float32, device=dev)
+        q = torch.empty((n, T, M), dtype=torch.int64, device=dev)
+        _check(lib.smc2_pf_trace_states(self._ctx, _ptr(theta_soa), n, int(iteration), dataset, _ptr(ll),
+                                        _ptr(delta), _ptr(anc), _ptr(x), _ptr(lw), _ptr(q)),
+               "smc2_pf_trace_states")
+        return ll, delta, anc, x, lw, q
 
     # -- timing -------------------------------------------------------------
     def set_timing(self, on: bool):
