@@ -168,7 +168,7 @@ __device__ __forceinline__ void fast_filter(const PFJob& J, const PFModel& mdl, 
   const uint32_t c3res = counter_c3(TAG_PF_RES, k);
   const int B = fixed_point_bits(M);
   const float2 scaleB = bc2(ldexpf(1.f, B));
-  const double log_norm = -(double)B * kLn2 - log((double)M);
+  const float logM = logf((float)M);
   const float4* obs = reinterpret_cast<const float4*>(J.obs);
 
   float2 x[NP][NS];  // particles 2p and 2p + 1 of the thread in x[p] (.x, .y)
@@ -189,7 +189,10 @@ __device__ __forceinline__ void fast_filter(const PFJob& J, const PFModel& mdl, 
     for (int e = 0; e < NS; ++e) x[p][e] = make_float2(a[e], b[e]);
   }
 
-  double loglik = 0.0;  // log p^(y_{1:t}) (Eq. 8), carried by thread 0
+  // log p^(y_{1:t}) (Eq. 8) = lsum_m + lsum_hi + lsum_lo, carried by thread 0
+  double lsum_m = 0.0;
+  float lsum_hi = 0.f, lsum_lo = 0.f;
+  bool dead = false;
   for (int t = 1; t <= TT; ++t) {
     const int tm = (t - 1) & 3;
     uint32_t* sUg = sU + 4 * (((t - 1) >> 2) & 1);
@@ -235,14 +238,14 @@ __device__ __forceinline__ void fast_filter(const PFJob& J, const PFModel& mdl, 
     }
     // (2) group maximum
     lmax = warp_max(lmax);
-    if (nw > 1) {
+    if (nw > 1) {  // lane w reads warp w's maximum; a shuffle reduction spreads the group's
       if (lane == 0) wmax[warp] = lmax;
       __syncthreads();
-      for (int w = 0; w < nw; ++w) lmax = fmaxf(lmax, wmax[w]);
+      lmax = warp_max(lane < nw ? wmax[lane] : -INFINITY);
     }
     const float m = lmax;
     if (!(m > -INFINITY)) {  // every weight vanished: the estimate is zero
-      loglik = -HUGE_VAL;
+      dead = true;
       if (lt == 0 && J.delta)
         for (int s = t; s <= J.T; ++s) J.delta[(size_t)i * J.T + (s - 1)] = -HUGE_VAL;
       break;
@@ -273,25 +276,34 @@ __device__ __forceinline__ void fast_filter(const PFJob& J, const PFModel& mdl, 
     const uint64_t incl = warp_incl_scan_u64(run, lane);
     const uint64_t excl = incl - run;
     uint64_t S, base = 0;
-    if (nw > 1) {
+    if (nw > 1) {  // lane w reads warp w's total; an inclusive shuffle scan gives S and the warp's base
       if (lane == 31) wsum[warp] = incl;
       __syncthreads();
-      S = 0;
-      for (int w = 0; w < nw; ++w) {
-        const uint64_t sw = wsum[w];
-        base += w < warp ? sw : 0ull;
-        S += sw;
+      uint64_t wp = lane < nw ? wsum[lane] : 0ull;
+      for (int o = 1; o < nw; o <<= 1) {
+        const uint64_t n = __shfl_up_sync(0xffffffffu, wp, o);
+        if (lane >= o) wp += n;
       }
+      S = __shfl_sync(0xffffffffu, wp, nw - 1);
+      const uint64_t b = __shfl_sync(0xffffffffu, wp, warp > 0 ? warp - 1 : 0);
+      base = warp > 0 ? b : 0ull;
     } else {
       S = __shfl_sync(0xffffffffu, incl, 31);
     }
-    // (4) log-likelihood increment from the exact integer total (S >= 2^(B-1), B >= 51)
+    // (4) log-likelihood increment from the exact integer total (S >= 2^(B-1), B >= 51):
+    // max + [(e - B) ln 2 + log(S 2^-e) - log M].  The maxima are summed in FP64 (exact for
+    // floats); the bracket, a few units in size, as an unevaluated float pair (hi, lo) by
+    // Knuth's TwoSum, which keeps the sum to about 2^-48, so that a step costs the narrow
+    // FP64 pipe two instructions.
     if (lt == 0) {
       const int e = 63 - __clzll((long long)S);
       const float mant = __uint2float_rn((uint32_t)(S >> (e - 31))) * 0x1p-31f;  // S / 2^e in [1, 2]
-      const double lmean = (double)m + ((double)e * kLn2 + (double)logf(mant)) + log_norm;
-      loglik += lmean;
-      if (J.delta) J.delta[(size_t)i * J.T + (t - 1)] = lmean;
+      const float small = fmaf((float)(e - B), (float)kLn2, logf(mant)) - logM;
+      lsum_m += (double)m;
+      const float sh = lsum_hi + small, bv = sh - lsum_hi;  // TwoSum: sh + err = lsum_hi + small exactly
+      lsum_lo += (lsum_hi - (sh - bv)) + (small - bv);
+      lsum_hi = sh;
+      if (J.delta) J.delta[(size_t)i * J.T + (t - 1)] = (double)m + (double)small;
     }
     // (5) systematic resampling by marks
     if (t < TT) {
@@ -356,7 +368,7 @@ __device__ __forceinline__ void fast_filter(const PFJob& J, const PFModel& mdl, 
       if (nw == 1) __syncwarp();  // every read done before the next step's writes
     }
   }
-  if (lt == 0) J.loglik[i] = loglik;
+  if (lt == 0) J.loglik[i] = dead ? -HUGE_VAL : lsum_m + ((double)lsum_hi + (double)lsum_lo);
 }
 
 template <int MODEL, int PPT, bool TRACE>

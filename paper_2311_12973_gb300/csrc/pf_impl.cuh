@@ -203,20 +203,18 @@ __device__ __forceinline__ SlotCount slot_count_setup(uint32_t U, uint64_t S, in
 // `margin`.  Away from an integer the estimate's ceiling is F; within the
 // margin of an integer n (clamped to [0, M - 1]), F is n or n + 1 and one exact
 // comparison, tau_n < C, says which.
+// Away from integers the estimate lies in (-1, M) (0 <= C <= S), so its ceiling is
+// already in [0, M]; only the exact branch clamps.
 __device__ __forceinline__ int slots_below(const SlotCount& sc, uint64_t C, float Cf) {
   const float est = fmaf(Cf, sc.scale, -sc.off);
   const float nf = rintf(est);
-  int n;
-  if (fabsf(est - nf) > sc.margin) {
-    n = (int)nf + (est > nf ? 1 : 0);
-  } else {
-    n = min(max((int)nf, 0), sc.M - 1);
-    const uint64_t a = ((uint64_t)n << 33) + sc.U21;
-    const uint64_t lh = __umul64hi(a, sc.S), ll = a * sc.S;
-    const uint64_t rh = __umul64hi(C, sc.M33), rl = C * sc.M33;
-    n += (lh < rh || (lh == rh && ll < rl)) ? 1 : 0;
-  }
-  return min(max(n, 0), sc.M);
+  if (fabsf(est - nf) > sc.margin) return (int)nf + (est > nf ? 1 : 0);
+  int n = min(max((int)nf, 0), sc.M - 1);
+  const uint64_t a = ((uint64_t)n << 33) + sc.U21;
+  const uint64_t lh = __umul64hi(a, sc.S), ll = a * sc.S;
+  const uint64_t rh = __umul64hi(C, sc.M33), rl = C * sc.M33;
+  n += (lh < rh || (lh == rh && ll < rl)) ? 1 : 0;
+  return n;
 }
 
 // exp in the working precision: the FP32 path uses the hardware exp2
