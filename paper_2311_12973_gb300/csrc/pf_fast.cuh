@@ -49,6 +49,17 @@ __device__ __forceinline__ float ex2_approx(float x) {
   return y;
 }
 
+__device__ __forceinline__ float rcp_approx(float x) {  // 1/x, hardware approximation (about 1 ulp)
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float lg2_approx(float x) {  // log2 x, hardware approximation
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 __device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
@@ -66,8 +77,12 @@ struct PairModel<MODEL_LG> {
   float2 phi, sx, inv_sy, c_obs;
   __device__ explicit PairModel(const FilterParams<float, MODEL_LG>& f)
       : phi(bc2(f.phi)), sx(bc2(f.sx)), inv_sy(bc2(f.inv_sy)), c_obs(bc2(f.c_obs)) {}
-  // x = phi x + sx z; l = c - (1/2) ((y - x) / sy)^2
-  __device__ __forceinline__ float2 step(float2* x, float2 z, const float4& ob, float2& lam) const {
+  // x = phi x + sx z; l = c - (1/2) ((y - x) / sy)^2 (no fix-up: far = 0)
+  __device__ __forceinline__ static float2 fix_far(float2 l, float2, int, const float4&) { return l; }
+  __device__ __forceinline__ float2 step(float2* x, float2 z, const float4& ob, float2& lam, float2& d,
+                                         int& far) const {
+    far = 0;
+    d = bc2(0.f);
     x[0] = fma2(phi, x[0], mul2(sx, z));
     const float2 r = mul2(fma2(x[0], bc2(-1.f), bc2(ob.x)), inv_sy);
     lam = bc2(0.f);
@@ -93,7 +108,8 @@ struct PairModel<MODEL_SEIR> {
     I = max2(fma2(dt, fma2(recovery, bc2(-1.f), onset), I), 0.f);  // I + dt (onset - recovery)
   }
   // x = (S, E, I, log beta) of two particles; returns their log-weights, and lam the day's incidence
-  __device__ __forceinline__ float2 step(float2* x, float2 z, const float4& ob, float2& lam) const {
+  __device__ __forceinline__ float2 step(float2* x, float2 z, const float4& ob, float2& lam, float2& d,
+                                         int& far) const {
     x[3] = fma2(srw, z, x[3]);
     const float2 beta = make_float2(__expf(x[3].x), __expf(x[3].y));
     float2 S = x[0], E = x[1], I = x[2];
@@ -108,20 +124,49 @@ struct PairModel<MODEL_SEIR> {
     x[1] = E;
     x[2] = I;
     lam = max2(lam, lam_floor);
-    // Poisson log-pmf y (log1p(d) - d) + c_y, d = (lambda - y) / y (no cancellation near y)
+    // Poisson log-pmf y (log1p(d) - d) + c_y, d = (lambda - y) / y (no cancellation near y);
+    // d is returned for the fix-up of the pairs whose |s| > 1/3 (see log1p_minus)
     if (ob.x > 0.f) {
-      const float2 d = mul2(add2(lam, bc2(-ob.x)), bc2(ob.y));
-      const float2 l1 = make_float2(log1pf(d.x), log1pf(d.y));
-      return fma2(bc2(ob.x), fma2(d, bc2(-1.f), l1), bc2(ob.z));
+      d = mul2(add2(lam, bc2(-ob.x)), bc2(ob.y));
+      return fma2(bc2(ob.x), log1p_minus(d, far), bc2(ob.z));
     }
+    far = 0;
     return mul2(lam, bc2(-1.f));
+  }
+  // the Poisson log-weights of a pair whose log1p_minus took the series outside its range
+  __device__ __forceinline__ static float2 fix_far(float2 l, float2 d, int far, const float4& ob) {
+    const float2 u = add2(d, bc2(1.f));
+    const float2 lg = make_float2(lg2_approx(u.x), lg2_approx(u.y));
+    const float2 r2 = fma2(bc2(ob.x), fma2(lg, bc2(0.69314718055994531f), mul2(d, bc2(-1.f))), bc2(ob.z));
+    return make_float2((far & 1) ? r2.x : l.x, (far & 2) ? r2.y : l.y);
+  }
+  // log1p(d) - d for two values.  With s = d / (2 + d), ln(1 + d) = 2 atanh s =
+  // 2 (s + s^3/3 + s^5/5 + ...) (Abramowitz and Stegun 4.1.27), and 2s - d = -s d, so
+  //   log1p(d) - d = -s d + 2 s^3 (1/3 + s^2/5 + s^4/7 + ... + s^10/13):
+  // for d < 0 both terms have one sign, for d > 0 the second is at most 2 s^2 / 3 <= 0.08 of
+  // the first, so no leading digits cancel.  For |s| <= 1/3 (-1/2 <= d <= 1) the omitted
+  // terms are below 10^-7 of the result.  Outside, |log1p(d) - d| >= 0.19 and
+  // ln(1 + d) from the hardware log2 (absolute error about 2^-22) serves; the warp takes
+  // that path (fix_far) only when one of its lanes needs it.
+  __device__ __forceinline__ static float2 log1p_minus(float2 d, int& far) {
+    const float2 den = add2(d, bc2(2.f));
+    const float2 sv = mul2(d, make_float2(rcp_approx(den.x), rcp_approx(den.y)));
+    const float2 s2 = mul2(sv, sv);
+    float2 p = fma2(s2, bc2(1.f / 13.f), bc2(1.f / 11.f));
+    p = fma2(s2, p, bc2(1.f / 9.f));
+    p = fma2(s2, p, bc2(1.f / 7.f));
+    p = fma2(s2, p, bc2(1.f / 5.f));
+    p = fma2(s2, p, bc2(1.f / 3.f));
+    const float2 t = mul2(mul2(s2, sv), bc2(2.f));                      // 2 s^3
+    far = (fabsf(sv.x) > (1.f / 3.f) ? 1 : 0) | (fabsf(sv.y) > (1.f / 3.f) ? 2 : 0);
+    return fma2(sv, mul2(d, bc2(-1.f)), mul2(t, p));  // -s d + 2 s^3 P(s^2)
   }
 };
 
 // Register budget per particles-per-thread shape of the FP32 filter.
 template <int PPT>
 struct FastRegCap {
-  static constexpr int value = PPT <= 2 ? 64 : (PPT == 4 ? 80 : 120);
+  static constexpr int value = PPT <= 2 ? 64 : (PPT == 4 ? 80 : 128);
   static_assert(PPT == 2 || PPT == 4 || PPT == 8, "particles per thread");
 };
 
@@ -136,6 +181,34 @@ __host__ __device__ constexpr size_t fast_region_bytes(int Mp, int ns) {
 }
 
 constexpr int kMarkBits = 12;  // particle index bits of a mark (M <= 4096)
+
+// Maximum over the warp in one reduction instruction: a float maps to an int
+// whose signed order is the float's (negative values have their magnitude bits
+// flipped), -inf included; no NaN reaches it.
+__device__ __forceinline__ float warp_max_redux(float v) {
+  const int b = __float_as_int(v);
+  const int key = b ^ ((b >> 31) & 0x7fffffff);
+  const int m = __reduce_max_sync(0xffffffffu, key);
+  return __int_as_float(m ^ ((m >> 31) & 0x7fffffff));
+}
+
+// slots_below split for a whole warp: the float estimate decides every crossing
+// point away from an integer (slots_estimate, which flags the others), and the
+// exact 128-bit comparison (slots_exact) settles the flagged ones.
+__device__ __forceinline__ int slots_estimate(const SlotCount& sc, float Cf, bool& near) {
+  const float est = fmaf(Cf, sc.scale, -sc.off);
+  const float nf = rintf(est);
+  near = !(fabsf(est - nf) > sc.margin);
+  return (int)nf + (est > nf ? 1 : 0);
+}
+__device__ __forceinline__ int slots_exact(const SlotCount& sc, uint64_t C, float Cf) {
+  const float est = fmaf(Cf, sc.scale, -sc.off);
+  int n = min(max((int)rintf(est), 0), sc.M - 1);
+  const uint64_t a = ((uint64_t)n << 33) + sc.U21;
+  const uint64_t lh = __umul64hi(a, sc.S), ll = a * sc.S;
+  const uint64_t rh = __umul64hi(C, sc.M33), rl = C * sc.M33;
+  return n + ((lh < rh || (lh == rh && ll < rl)) ? 1 : 0);
+}
 
 template <int MODEL, int PPT, bool TRACE>
 __device__ __forceinline__ void fast_filter(const PFJob& J, const PFModel& mdl, int i, unsigned char* smem,
@@ -213,8 +286,10 @@ __device__ __forceinline__ void fast_filter(const PFJob& J, const PFModel& mdl, 
     float lmax = -INFINITY;
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
-      float2 lam;
-      const float2 l2 = pm.step(x[p], Z[(tm * NP + p) * T + lt], ob, lam);
+      float2 lam, dp;
+      int far;
+      float2 l2 = pm.step(x[p], Z[(tm * NP + p) * T + lt], ob, lam, dp, far);
+      if (__any_sync(0xffffffffu, far != 0)) l2 = PairModel<MODEL>::fix_far(l2, dp, far, ob);  // rare
       const int j = lt * PPT + 2 * p;
       const float la = (isnan(l2.x) || j >= M) ? -INFINITY : l2.x;
       const float lb = (isnan(l2.y) || j + 1 >= M) ? -INFINITY : l2.y;
@@ -237,11 +312,11 @@ __device__ __forceinline__ void fast_filter(const PFJob& J, const PFModel& mdl, 
       }
     }
     // (2) group maximum
-    lmax = warp_max(lmax);
-    if (nw > 1) {  // lane w reads warp w's maximum; a shuffle reduction spreads the group's
+    lmax = warp_max_redux(lmax);
+    if (nw > 1) {  // lane w reads warp w's maximum; one more reduction spreads the group's
       if (lane == 0) wmax[warp] = lmax;
       __syncthreads();
-      lmax = warp_max(lane < nw ? wmax[lane] : -INFINITY);
+      lmax = warp_max_redux(lane < nw ? wmax[lane] : -INFINITY);
     }
     const float m = lmax;
     if (!(m > -INFINITY)) {  // every weight vanished: the estimate is zero
@@ -319,7 +394,22 @@ __device__ __forceinline__ void fast_filter(const PFJob& J, const PFModel& mdl, 
       const SlotCount sc = slot_count_setup(sUg[tm], S, M);
       const uint64_t C0 = base + excl;  // cumulative weight before the thread's first particle
       const float C0f = u64_to_float(C0);
-      int start = slots_below(sc, C0, C0f);
+      // the slot counts at the thread's cumulative weights, one vote for the exact comparisons
+      int ends[PPT + 1];
+      uint32_t near_mask = 0;
+#pragma unroll
+      for (int r = 0; r <= PPT; ++r) {
+        bool nr;
+        ends[r] = slots_estimate(sc, r == 0 ? C0f : C0f + cf[r - 1], nr);
+        near_mask |= nr ? (1u << r) : 0u;
+      }
+      if (__any_sync(0xffffffffu, near_mask != 0)) {
+#pragma unroll
+        for (int r = 0; r <= PPT; ++r)
+          if (near_mask & (1u << r))
+            ends[r] = slots_exact(sc, r == 0 ? C0 : C0 + c[r - 1], r == 0 ? C0f : C0f + cf[r - 1]);
+      }
+      int start = ends[0];
 #pragma unroll
       for (int p = 0; p < NP; ++p) {
         float a[NS], b[NS];
@@ -333,7 +423,7 @@ __device__ __forceinline__ void fast_filter(const PFJob& J, const PFModel& mdl, 
       }
 #pragma unroll
       for (int r = 0; r < PPT; ++r) {
-        const int end = slots_below(sc, C0 + c[r], C0f + cf[r]);
+        const int end = ends[r + 1];
         const uint32_t mk = tg | (uint32_t)(lt * PPT + r);
         if (end > start) mark[(start & (PPT - 1)) * T + (start >> LOG2P)] = mk;
         // the first slot of every thread inside [start, end): usually none or one
