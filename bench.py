@@ -6,9 +6,12 @@ L-kernel weights, ESS, outer resampling and recycling.  Inputs (observations)
 are resident on the device for `value`; `e2e` repeats the step through the C
 ABI with host buffers (observations copied in, recycled estimate copied out).
 
-Default workload: SEIR-type model, population 1e6, T=100, N=1024, M=512,
-K=20, FP32 particles with FP64 outer arithmetic.  `--impl reference` times
-the CPU oracle on a bounded sample of the same workload instead.
+Default workload: the largest single-GPU configuration, SEIR-type model,
+population 1e6, T=200, N=8192, M=1024, K=30, FP32 particles with FP64 outer
+arithmetic.  The accuracy comparison of the forms (mixed precision, the plain
+FP64 GPU form, the learned proposal) runs on the N=1024, M=512, T=100, K=20
+workload and is printed as extra keys.  `--impl reference` times the CPU
+oracle on a bounded sample of the workload instead.
 """
 from __future__ import annotations
 
@@ -62,9 +65,12 @@ def alg_ops(w) -> float:
                                 ALG_OPS_PER_PARTICLE_STEP[w.model])
 MODEL_NAMES = {0: "LG-AR(1)", 1: "SEIR-type", 2: "binomial SIR"}
 # DRAM bytes per particle-filter launch (dram__bytes_read.sum + dram__bytes_write.sum)
-# from one ncu capture of the SEIR-type workload N=1024, M=512, T=100, valid only for
-# the kernel source it was taken on (sha-256 prefixes of pf_impl.cuh and common.cuh).
-PF_TRAFFIC = {"bytes": 106496.0, "sources": {"pf_impl.cuh": "47574a10041971f0", "common.cuh": "4a6a88e11701ac7a"}}
+# from one ncu capture of a full-size launch of the workload, valid only for that
+# workload and the kernel source it was taken on (sha-256 prefixes of the sources).
+PF_TRAFFIC = {
+    "seir_t200_n8192": {"bytes": 462592.0, "sources": {"pf_fast.cuh": "c8fda16e3a150a2a", "pf_impl.cuh": "ed94a1cf40e60688",
+                                                       "common.cuh": "cb814bfa27b629ec"}},
+}
 
 
 def parse():
@@ -73,7 +79,9 @@ def parse():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="seir_t100_n1024")
+    p.add_argument("--workload", default="seir_t200_n8192")
+    p.add_argument("--forms-workload", default="seir_t100_n1024",
+                   help="workload of the accuracy comparison of the forms (extra keys of the line)")
     p.add_argument("--no-fp64-form", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-forms", action="store_true",
@@ -83,6 +91,8 @@ def parse():
                         "or the paper's (multinomial when the ESS falls below M/2)")
     p.add_argument("--ppt", type=int, default=0, help="pin particles per thread (0: tuner)")
     p.add_argument("--cta", type=int, default=0, help="pin threads per PF CTA (0: tuner)")
+    p.add_argument("--filters", type=int, default=0,
+                   help="run N parameter samples instead of the workload's (smaller cases for profiler captures)")
     return p.parse_args()
 
 
@@ -165,13 +175,16 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def pf_traffic_if_current():
+def pf_traffic_if_current(workload: str):
     import hashlib
+    rec = PF_TRAFFIC.get(workload)
+    if rec is None:
+        return None
     d = os.path.join(ROOT, "paper_2311_12973_gb300", "csrc")
-    for f, h in PF_TRAFFIC["sources"].items():
+    for f, h in rec["sources"].items():
         if hashlib.sha256(open(os.path.join(d, f), "rb").read()).hexdigest()[:16] != h:
             return None
-    return PF_TRAFFIC["bytes"]
+    return rec["bytes"]
 
 
 def measured_peaks() -> dict:
@@ -282,13 +295,18 @@ def time_runs(S, torch, ctx, w, steps, warmup, flush, rank_sync):
     return ms, ess_sums, pf_ms, pf_n, launches, wall
 
 
-def accuracy_forms(S, torch, I, wr, world, seeds=8):
+def accuracy_forms(S, torch, I, wr, world, seeds=96):
     """Posterior accuracy per unit time of three forms of the SMC^2 step on the
     same data: mixed precision with the random walk, the plain FP64 GPU form,
     and mixed precision with the learned proposal.  Accuracy is the mean
     squared error over `seeds` runs of the recycled posterior mean against a
-    reference pooled from four random-walk runs with 8x the samples; mse x
-    time is inversely proportional to accuracy per second."""
+    reference pooled from four FP64 random-walk runs with 8x the samples (the
+    FP64 form matches the oracle run for run); mse x time is inversely
+    proportional to accuracy per second.  The FP64 and mixed random-walk forms
+    run the same seeds, so their log-evidence estimates and squared errors are
+    compared pairwise.  The errors are heavy-tailed, so the line also carries
+    the median squared error and, per coordinate, the fraction of seeds in
+    which the mixed form is the worse of the pair."""
     import numpy as np
 
     def runs(w, seed_list, **over):
@@ -302,30 +320,43 @@ def accuracy_forms(S, torch, I, wr, world, seeds=8):
             a.record(stream)
             ctx.run(w.K, stats=False)
             b.record(stream)
-            mean, _, ess = ctx.estimate()
-            out.append((mean, ess, a.elapsed_time(b)))
+            mean, logz, ess = ctx.estimate()
+            out.append((mean, ess, a.elapsed_time(b), logz))
         ctx.close()
         return out
 
     base = 10_000 * (1 + wr.seed)
-    ref = runs(wr.with_(N=8 * wr.N, ppt=0, cta_threads=0), [base + i for i in range(4)], rw_scale=0.2)
+    ref_w = wr.with_(N=8 * wr.N, precision=I.PREC_FP64, ppt=0, cta_threads=0)
+    ref = runs(ref_w, [base + i for i in range(4)], rw_scale=0.2)
     ref_mean = np.mean([r[0] for r in ref], axis=0)
     forms = {"mixed_rw": wr.with_(ppt=0, cta_threads=0),
              "fp64_rw": wr.with_(precision=I.PREC_FP64, ppt=0, cta_threads=0),
              "mixed_learned": wr.with_(proposal=I.PROP_MLP, ppt=0, cta_threads=0)}
-    res = {}
+    res, logz, sqerr = {}, {}, {}
     for name, wf in forms.items():
         r = runs(wf, [base + 100 + i for i in range(seeds)])
         means = np.array([x[0] for x in r])
-        mse = ((means - ref_mean) ** 2).mean(axis=0)
+        sq = (means - ref_mean) ** 2
+        mse = sq.mean(axis=0)
         ms = float(np.mean([x[2] for x in r]))
+        logz[name] = np.array([x[3] for x in r])
+        sqerr[name] = sq
         res[name] = {"ms_per_run": ms, "ess_per_s": float(np.mean([x[1] for x in r])) * world / (ms * 1e-3),
-                     "rmse": [float(v) for v in np.sqrt(mse)], "mse_x_s": float(mse.mean() * ms * 1e-3)}
+                     "rmse": [float(v) for v in np.sqrt(mse)], "mse_x_s": float(mse.mean() * ms * 1e-3),
+                     "mse": float(mse.mean()), "median_sq_err": float(np.median(sq))}
     for name in ("fp64_rw", "mixed_learned"):
         res[name]["accuracy_per_s_vs_mixed_rw"] = res["mixed_rw"]["mse_x_s"] / res[name]["mse_x_s"]
     res["mixed_learned"]["accuracy_per_s_vs_fp64_rw"] = res["fp64_rw"]["mse_x_s"] / res["mixed_learned"]["mse_x_s"]
     res["mixed_learned"]["ess_per_s_vs_fp64_rw"] = res["mixed_learned"]["ess_per_s"] / res["fp64_rw"]["ess_per_s"]
-    res["reference"] = {"runs": 4, "N": 8 * wr.N, "rw_scale": 0.2, "seeds_per_form": seeds}
+    d = logz["mixed_rw"] - logz["fp64_rw"]   # same seeds: paired
+    res["mixed_minus_fp64_logz"] = {"mean": float(d.mean()), "se": float(d.std(ddof=1) / np.sqrt(len(d))),
+                                    "median_abs": float(np.median(np.abs(d))), "pairs": len(d),
+                                    "target_nats": 0.05}
+    res["mixed_over_fp64_mse"] = res["mixed_rw"]["mse"] / res["fp64_rw"]["mse"]
+    res["mixed_over_fp64_median_sq_err"] = res["mixed_rw"]["median_sq_err"] / res["fp64_rw"]["median_sq_err"]
+    res["mixed_worse_fraction"] = [float(v) for v in (sqerr["mixed_rw"] > sqerr["fp64_rw"]).mean(axis=0)]
+    res["reference"] = {"runs": 4, "N": ref_w.N, "precision": "fp64", "rw_scale": 0.2, "seeds_per_form": seeds,
+                        "workload": wr.name}
     return res
 
 
@@ -361,6 +392,8 @@ def main():
     rank, world, local = dist_env()
     from paper_2311_12973_gb300 import inputs as I
     w = I.workload(args.workload)
+    if args.filters:
+        w = w.with_(N=args.filters)
     if args.pf == "systematic":
         w = w.with_(pf_scheme=I.PF_SYSTEMATIC, pf_ess_frac=0.0)
     elif args.pf == "paper":
@@ -403,24 +436,24 @@ def main():
     value = job_throughput(units_per_step, world, step_ms)
     ess_per_s = statistics.mean(ess_sums) * world / (step_ms * 1e-3)
 
-    # end to end through the C ABI with host buffers
+    # end to end through the C ABI with host buffers, on the host clock: each step
+    # copies the observations in from pinned host memory, runs, and reads the
+    # recycled estimate back (which synchronises); L2 is flushed before each step,
+    # outside the timed region, as for `value`
     import numpy as np
     y_host = torch.tensor(wr.y, dtype=torch.float64).pin_memory()
-    stream = torch.cuda.current_stream()
     e2e_ms = []
     for s in range(args.warmup + args.steps):
+        flush.zero_()
         torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
+        t0 = time.perf_counter()
         ctx.set_observations(y_host)
         ctx.reset(wr.seed)
         ctx.run(wr.K, stats=False)
         mean, logz, ess = ctx.estimate()
-        b.record(stream)
-        b.synchronize()
         if s >= args.warmup:
-            e2e_ms.append(a.elapsed_time(b))
-    e2e_step = reduce_max_gpu(sum(e2e_ms) / len(e2e_ms))
+            e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    e2e_step = reduce_max(sum(e2e_ms) / len(e2e_ms), dist, "cuda")
     d2h = 8 * wr.D + 112 + 8 + 4
 
     # plain FP64 GPU form of the same workload
@@ -428,7 +461,7 @@ def main():
     if not args.no_fp64_form:
         w64 = wr.with_(precision=I.PREC_FP64, ppt=0, cta_threads=0)
         ctx64 = S.SMC2(S.make_config(w64), w64.y)
-        ms64, ess64, _, _, _, _ = time_runs(S, torch, ctx64, w64, max(2, args.steps // 3), 1, flush,
+        ms64, ess64, _, _, _, _ = time_runs(S, torch, ctx64, w64, max(2, args.steps // 5), 1, flush,
                                             rank_sync)
         st64 = reduce_max_gpu(sum(ms64) / len(ms64))
         fp64 = {"value": units_per_step * world / (st64 * 1e-3), "unit": UNIT,
@@ -437,7 +470,7 @@ def main():
 
     forms = None
     if not args.no_forms and wr.model == I.SEIR and wr.D <= 8:
-        forms = accuracy_forms(S, torch, I, wr, world)
+        forms = accuracy_forms(S, torch, I, replica_workload(I.workload(args.forms_workload), rank), world)
     paper_table = None
     if not args.no_forms and wr.model == I.SIR:
         paper_table = sir_paper_table(S, torch, I, wr)
@@ -463,9 +496,11 @@ def main():
         "ess_speedup_vs_fp64_form": (ess_per_s / fp64["ess_per_s"]) if fp64 else None,
         "forms": forms,
         "paper_table": paper_table,
-        "roofline": {"kernel": f"pf_kernel<float,{MODEL_NAMES[wr.model]}>", "bound": "alu", "achieved": achieved / 1e9,
+        "roofline": {"kernel": (f"pf_fast_kernel<{MODEL_NAMES[wr.model]}, {shape['ppt']}>"
+                                if shape["one_group_per_cta"] else f"pf_kernel<float, {MODEL_NAMES[wr.model]}, "
+                                f"{shape['ppt']}>"), "bound": "alu", "achieved": achieved / 1e9,
                      "peak": peak / 1e9, "unit": "Gop/s", "frac": achieved / peak,
-                     "traffic": pf_traffic_if_current() if wr.model == 1 else None,
+                     "traffic": pf_traffic_if_current(wr.name) if wr.N == I.workload(wr.name).N else None,
                      "ops_per_particle_step": ops_pps,
                      "pf_ms_per_launch": pf_avg_ms, "pf_launches": pf_n,
                      "pf_share_of_step": pf_ms / max(sum(ms), 1e-9),
@@ -478,7 +513,8 @@ def main():
                          "ms_per_step": step_ms,
                          "frac": 1e3 * units_per_step * ops_pps / peak / step_ms},
         "e2e": {"value": units_per_step * world / (e2e_step * 1e-3), "unit": UNIT,
-                "h2d_bytes_per_step": 8 * wr.T, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_step},
+                "h2d_bytes_per_step": 8 * wr.T, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_step,
+                "clock": "host (perf_counter), L2 flushed before each step"},
         "gpu_launches": launches,
         "clocks": clocks,
         "wall_s": wall,

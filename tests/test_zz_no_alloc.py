@@ -2,7 +2,9 @@
 device memory once running (a fixed budget, a framework-owned memory pool, or
 a loop that cannot pay for cudaMalloc's synchronisation): through the C ABI,
 two calls in a row must give what smc2_pf_loglik gives on the same inputs and
-launch shape, and repeated calls must leave the device's free memory as it was.
+launch shape (a context pinned to pf_kernel, the kernel the allocation-free
+entry point runs), and repeated calls must leave the device's free memory as
+it was.
 
 This file is collected last so that a run stopping at its first failure has
 already run every other test."""
@@ -39,7 +41,8 @@ def test_matches_context_entry_point_twice(S, precision, ppt, name, M, n, T):
     for bit; the mixed form within the FP32 stage bar (2e-5)."""
     w = I.workload(name, M=M, N=n, T=T, precision=precision)
     theta = _theta(w, n)
-    ctx = S.SMC2(S.make_config(w, ppt=ppt), w.y)
+    # the context pinned to the kernel the allocation-free entry point runs (pf_kernel)
+    ctx = S.SMC2(S.make_config(w, ppt=ppt, pf_family=S.PF_GROUPS), w.y)
     ref = ctx.pf_loglik(theta, iteration=3).cpu().numpy()
     ctx.close()
     y_dev = torch.tensor(w.y, dtype=torch.float64, device="cuda")
@@ -78,7 +81,7 @@ def test_a_smaller_call_does_not_shrink_a_context_launch(S):
     allocation-free call of the same kernel with a far smaller M."""
     w = I.workload("seir_t100_n1024", M=2048, N=40, T=30, precision=I.PREC_MIXED)
     theta = _theta(w, 40)
-    ctx = S.SMC2(S.make_config(w, ppt=4, cta_threads=512), w.y)
+    ctx = S.SMC2(S.make_config(w, ppt=4, cta_threads=512, pf_family=S.PF_GROUPS), w.y)
     before = ctx.pf_loglik(theta, iteration=2).cpu().numpy()
     ws = I.workload("seir_t100_n1024", M=32, N=40, T=30, precision=I.PREC_MIXED)
     y_dev = torch.tensor(ws.y, dtype=torch.float64, device="cuda")
