@@ -184,3 +184,38 @@ def test_full_size_batched_sampled_filters(S):
     assert abs(dd.mean()) < 4 * se
     ctx64.close()
     ctx32.close()
+
+
+def test_full_size_batched_fp64_iterations_against_oracle(S):
+    """The 64-dataset workload at full size in one FP64 context (every dataset
+    runs; 1.7e10 particle-steps per iteration): two whole SMC^2 iterations of
+    its three cheapest datasets (N = 256, M = 128, T = 218, 228, 259) against
+    the oracle's single-dataset runs with their dataset indices -- the
+    statistics of each iteration (Sec. IV: Eqs. 17, 20-22, 24-25, the
+    resampling decision) and the population after the second."""
+    ws = [w.with_(precision=I.PREC_FP64, K=2) for w in I.batched_workloads(64, K=2)]
+    shapes = [(w.N, w.M, w.T) for w in ws]
+    ctx = S.SMC2(S.make_config(ws[0]), np.concatenate([w.y for w in ws]), datasets=shapes)
+    t0 = time.perf_counter()
+    stats = ctx.run(2)
+    print(f"two FP64 iterations of the 64 datasets: {time.perf_counter() - t0:.1f} s")
+    for d in (24, 57, 1):
+        w = ws[d]
+        ref = O.SMC2(O.config_from(w), w.y).run(2)
+        fin = np.isfinite(ref.logw)
+        scale = max(10.0, float(np.max(np.abs(ref.logw[fin]))))
+        for k in range(2):
+            g, o = stats[k][d], ref.stats[k]
+            assert g["dataset"] == d and g["k"] == o["k"] and g["resampled"] == o["resampled"], (d, k, g, o)
+            for key in ("lse", "lse2", "logz"):
+                assert abs(g[key] - o[key]) <= 1e-12 * max(scale, abs(o[key])), (d, k, key, g[key], o[key])
+            assert abs(g["ess"] - o["ess"]) <= 1e-9 * o["ess"], (d, k, g["ess"], o["ess"])
+            assert np.max(np.abs(g["est"] - o["est"])) <= 1e-9 * max(1.0, float(np.max(np.abs(o["est"]))))
+        kk, th, lp, ll, lw = ctx.get_state(d)
+        assert kk == ref.k
+        assert np.max(np.abs(th - ref.theta)) <= 1e-10 * max(1.0, float(np.max(np.abs(ref.theta))))
+        assert np.array_equal(np.isfinite(lw), fin)
+        assert np.max(np.abs(ll[fin] - ref.loglik[fin])) <= 1e-12 * scale
+        assert np.max(np.abs(lw[fin] - ref.logw[fin])) <= 1e-12 * scale
+        print(f"dataset {d} (N={w.N}, M={w.M}, T={w.T}): two iterations equal the oracle's")
+    ctx.close()
