@@ -497,7 +497,7 @@ def main():
         "forms": forms,
         "paper_table": paper_table,
         "roofline": {"kernel": (f"pf_fast_kernel<{MODEL_NAMES[wr.model]}, {shape['ppt']}>"
-                                if shape["one_group_per_cta"] else f"pf_kernel<float, {MODEL_NAMES[wr.model]}, "
+                                if shape["fp32_filter"] else f"pf_kernel<float, {MODEL_NAMES[wr.model]}, "
                                 f"{shape['ppt']}>"), "bound": "alu", "achieved": achieved / 1e9,
                      "peak": peak / 1e9, "unit": "Gop/s", "frac": achieved / peak,
                      "traffic": pf_traffic_if_current(wr.name) if wr.N == I.workload(wr.name).N else None,

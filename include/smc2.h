@@ -64,7 +64,7 @@ enum { SMC2_PREC_FP64 = 0, SMC2_PREC_MIXED = 1 };   /* MIXED: FP32 particles, FP
 enum { SMC2_PROP_RW = 0, SMC2_PROP_MLP = 1 };
 enum { SMC2_LK_FORWARD = 0, SMC2_LK_GAUSS_OPT = 1 };
 enum { SMC2_PF_SYSTEMATIC = 0, SMC2_PF_MULTINOMIAL = 1 };
-enum { SMC2_PF_ANY = 0, SMC2_PF_GROUPS = 1, SMC2_PF_ONE_GROUP = 2 };
+enum { SMC2_PF_ANY = 0, SMC2_PF_GROUPS = 1, SMC2_PF_FP32 = 2 };
 
 #define SMC2_MAX_D 8
 #define SMC2_MAX_M 4096     /* particles per filter (see M in smc2_config) */
@@ -130,10 +130,11 @@ typedef struct smc2_ctx smc2_ctx; /* opaque; owns its device workspace */
  *   work list, prior draws of theta and min(T, 32) steps, during smc2_init.
  * pf_family: the particle-filter kernel the tuner may pick: 0 either,
  *   SMC2_PF_GROUPS pf_kernel only (filter groups of any width, several per
- *   CTA), SMC2_PF_ONE_GROUP the FP32 filter with one filter per CTA and 4, 8 or
- *   16 particles per thread (mixed precision, LG or SEIR model, the default
- *   filter, every dataset's group of the same width).  Both compute the same
- *   filter; they differ in speed only.
+ *   CTA), SMC2_PF_FP32 the register-resident FP32 filter with 2, 4 or 8
+ *   particles per thread (mixed precision, LG or SEIR model, the default
+ *   filter; one filter per CTA when every dataset's group has the same width,
+ *   else groups of unequal width sharing a CTA).  Both compute the same filter;
+ *   they differ in speed only.
  * n_datasets: number of independent datasets run together (<= 1: one).
  * ds_N, ds_M, ds_T: host arrays of n_datasets sizes (NULL when n_datasets <= 1). */
 typedef struct {
@@ -425,9 +426,11 @@ smc2_status smc2_get_timing(smc2_ctx* ctx, double* pf_ms, int64_t* pf_launches,
                             int64_t* kernel_launches, int reset);
 
 /* The particle-filter launch shape in use: particles per thread, threads per
- * CTA, CTAs per launch, and *one_group = 1 when the filter kernel is the FP32
- * one with one filter per CTA (host outputs, any may be NULL). */
-smc2_status smc2_get_launch_shape(smc2_ctx* ctx, int* ppt, int* cta_threads, int* grid, int* one_group);
+ * CTA, CTAs per launch, and the kernel family in *fp32_filter: 0 pf_kernel,
+ * 1 the register-resident FP32 filter with one filter per CTA, 2 the same with
+ * filter groups of unequal width sharing a CTA (host outputs, any may be
+ * NULL). */
+smc2_status smc2_get_launch_shape(smc2_ctx* ctx, int* ppt, int* cta_threads, int* grid, int* fp32_filter);
 
 /* Release the context and its device workspace (synchronises its stream). */
 void smc2_destroy(smc2_ctx* ctx);

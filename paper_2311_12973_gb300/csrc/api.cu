@@ -66,9 +66,9 @@ struct smc2_ctx {
   int* d_status = nullptr;
   unsigned* d_grid_ticket = nullptr;
   int ppt = 4, pf_block = 256, pf_grid = 1;
-  bool pf_named = false;
+  bool pf_named = false;    // pf_kernel: named-barrier groups; the FP32 filter: grouped instantiation
   bool pf_general = false;  // the paper's PF variants: multinomial slots, ESS-triggered resampling
-  bool pf_fast = false;     // the one-group-per-CTA FP32 filter (pf_fast.cuh) runs
+  bool pf_fast = false;     // the FP32 filter of pf_fast.cuh runs
   size_t pf_smem = 0;
   int k_host = 0;
   std::map<GraphKey, TimedGraph> graphs;
@@ -148,7 +148,7 @@ smc2_status validate(const smc2_config* c) {
   }
   if (c->ppt != 0 && c->ppt != 1 && c->ppt != 2 && c->ppt != 4 && c->ppt != 8 && c->ppt != 16)
     return SMC2_EINVAL;
-  if (c->pf_family < SMC2_PF_ANY || c->pf_family > SMC2_PF_ONE_GROUP) return SMC2_EINVAL;
+  if (c->pf_family < SMC2_PF_ANY || c->pf_family > SMC2_PF_FP32) return SMC2_EINVAL;
   if ((c->pf_scheme != SMC2_PF_SYSTEMATIC && c->pf_scheme != SMC2_PF_MULTINOMIAL) ||
       !(c->pf_ess_frac >= 0.0 && c->pf_ess_frac <= 1.0))
     return SMC2_EINVAL;
@@ -295,24 +295,33 @@ void build_work_units(smc2_ctx* c, std::vector<int4>& wus) {
 
 // The particle-filter launch of the context's shape, either kernel family.
 cudaError_t ctx_pf_launch(const smc2_ctx* c, int grid, const PFLaunch& L, cudaStream_t s, bool trace = false) {
-  if (c->pf_fast) return pf_fast_launch(c->model, c->ppt, trace, grid, c->pf_block, c->pf_smem, L, s);
+  if (c->pf_fast) return pf_fast_launch(c->model, c->ppt, trace, c->pf_named, grid, c->pf_block, c->pf_smem, L, s);
   return pf_launch(c->precision, c->model, c->ppt, c->pf_named, c->pf_general, grid, c->pf_block, c->pf_smem, L, s);
 }
 
 int ctx_pf_occupancy(const smc2_ctx* c, bool trace = false) {
-  if (c->pf_fast) return pf_fast_occupancy(c->model, c->ppt, trace, c->pf_block, c->pf_smem);
+  if (c->pf_fast) return pf_fast_occupancy(c->model, c->ppt, trace, c->pf_named, c->pf_block, c->pf_smem);
   return pf_occupancy(c->precision, c->model, c->ppt, c->pf_named, c->pf_general, c->pf_block, c->pf_smem);
 }
 
-// The one-group-per-CTA filter at ppt: every dataset's group has the CTA's width
-// (block threads), so no thread of a CTA idles on a narrower filter.
-bool fast_shape_valid(const smc2_ctx* c, int ppt, int* block) {
+// The FP32 filter of pf_fast.cuh at ppt.  When every dataset's filter group
+// has the same width, one group is the CTA; otherwise (grouped) the CTA is as
+// wide as the widest group and narrower groups share it: warps, or groups of
+// several warps on named barriers 1..15.
+bool fast_shape_valid(const smc2_ctx* c, int ppt, int* block, bool* grouped) {
   if (!pf_fast_eligible(c->precision, c->model, c->pf_general, ppt)) return false;
-  const int gt = pf_group_threads(ppt, c->M[0]);
-  for (int m : c->M)
-    if (pf_group_threads(ppt, m) != gt || pf_fast_smem_bytes(c->model, ppt, m) > 227 * 1024) return false;
-  if (gt > kPfMaxBlock || (c->cfg.cta_threads && gt != c->cfg.cta_threads)) return false;
-  *block = gt;
+  int b = 32;
+  bool gr = false;
+  for (int m : c->M) b = std::max(b, pf_group_threads(ppt, m));
+  for (int m : c->M) {
+    const int gt = pf_group_threads(ppt, m);
+    if (gt != b) gr = true;
+    if (b % gt || (gt > 32 && b / gt > 15)) return false;
+    if (pf_fast_smem_bytes(c->model, ppt, b, m) > 227 * 1024) return false;
+  }
+  if (b > kPfMaxBlock || (c->cfg.cta_threads && b != c->cfg.cta_threads)) return false;
+  *block = b;
+  *grouped = gr;
   return true;
 }
 
@@ -323,12 +332,12 @@ smc2_status apply_shape(smc2_ctx* c, int ppt, int block, bool named, bool upload
   c->pf_fast = fast;
   size_t smem = 0;
   for (int m : c->M)
-    smem = std::max(smem, fast ? pf_fast_smem_bytes(c->model, ppt, m)
+    smem = std::max(smem, fast ? pf_fast_smem_bytes(c->model, ppt, block, m)
                                : pf_smem_bytes(c->precision, c->model, ppt, c->pf_general, block, m));
   if (smem > 227 * 1024) return SMC2_EINVAL;
   c->pf_smem = smem;
   if (fast)
-    SMC2_TRY(pf_fast_configure(c->model, ppt, false, smem));
+    SMC2_TRY(pf_fast_configure(c->model, ppt, false, named, smem));
   else
     SMC2_TRY(pf_configure(c->precision, c->model, ppt, named, c->pf_general, smem));
   std::vector<int4> wus;
@@ -352,15 +361,17 @@ smc2_status choose_launch_shape(smc2_ctx* c) {
     bool named, fast;
   };
   std::vector<Shape> cand;
-  for (int ppt : {2, 4, 8}) {  // the one-group-per-CTA FP32 filter
+  for (int ppt : {2, 4, 8}) {  // the FP32 filter of pf_fast.cuh
     int block = 0;
-    if (c->cfg.pf_family != SMC2_PF_GROUPS && (!c->cfg.ppt || ppt == c->cfg.ppt) && fast_shape_valid(c, ppt, &block))
-      cand.push_back({ppt, block, false, true});
+    bool grouped = false;
+    if (c->cfg.pf_family != SMC2_PF_GROUPS && (!c->cfg.ppt || ppt == c->cfg.ppt) &&
+        fast_shape_valid(c, ppt, &block, &grouped))
+      cand.push_back({ppt, block, grouped, true});
   }
   for (int ppt : {1, 2, 4, 8, 16}) {
     if (c->cfg.ppt && ppt != c->cfg.ppt) continue;
     if ((c->pf_general || c->model == MODEL_SIR) && ppt > 4) continue;  // register-resident shapes only
-    if (c->cfg.pf_family == SMC2_PF_ONE_GROUP) break;
+    if (c->cfg.pf_family == SMC2_PF_FP32) break;
     for (int block = 32; block <= kPfMaxBlock; block += 32) {
       if (c->cfg.cta_threads && block != c->cfg.cta_threads) continue;
       if (!c->cfg.cta_threads && (block & (block - 1))) continue;  // powers of two when tuning
@@ -715,9 +726,7 @@ static smc2_status pf_standalone(smc2_ctx* c, const double* theta, int n, int it
   const bool trace = xtr || ltr || qtr;
   if (trace) {
     if (!xtr || !ltr || !qtr) return SMC2_EINVAL;
-    // the traced instantiation of the one-group-per-CTA filter at the context's shape
-    int block = 0;
-    if (!(c->pf_fast || fast_shape_valid(c, c->ppt, &block))) return SMC2_EINVAL;
+    if (!pf_fast_eligible(c->precision, c->model, c->pf_general, c->ppt)) return SMC2_EINVAL;
   }
   PFJob job{};
   job.xtr = xtr;
@@ -744,20 +753,17 @@ static smc2_status pf_standalone(smc2_ctx* c, const double* theta, int n, int it
   L.wu_counter = nullptr;
   L.k_done = nullptr;
   L.k_imm = iteration;
-  if (trace && !c->pf_fast) {  // the context runs pf_kernel: trace the FP32 filter at the same ppt
-    int block = 0;
-    fast_shape_valid(c, c->ppt, &block);
-    size_t smem = 0;
-    for (int m : c->M) smem = std::max(smem, pf_fast_smem_bytes(c->model, c->ppt, m));
-    SMC2_TRY(pf_fast_configure(c->model, c->ppt, true, smem));
+  if (trace) {  // the traced FP32 filter at the context's ppt, one filter group per CTA
+    const int block = pf_group_threads(c->ppt, job.M);
+    const size_t smem = pf_fast_smem_bytes(c->model, c->ppt, block, job.M);
+    SMC2_TRY(pf_fast_configure(c->model, c->ppt, true, false, smem));
     L.fpc_single = 1;
     L.n_wu = n;
-    const int occ = std::max(1, pf_fast_occupancy(c->model, c->ppt, true, block, smem));
-    SMC2_TRY(pf_fast_launch(c->model, c->ppt, true, std::min(n, occ * c->sms), block, smem, L, c->stream));
+    const int occ = std::max(1, pf_fast_occupancy(c->model, c->ppt, true, false, block, smem));
+    SMC2_TRY(pf_fast_launch(c->model, c->ppt, true, false, std::min(n, occ * c->sms), block, smem, L, c->stream));
     c->kernel_launches++;
     return SMC2_OK;
   }
-  if (trace) SMC2_TRY(pf_fast_configure(c->model, c->ppt, true, c->pf_smem));
   const int occ = std::max(1, ctx_pf_occupancy(c, trace));
   const int grid = std::min(L.n_wu, occ * c->sms);
   SMC2_TRY(ctx_pf_launch(c, grid, L, c->stream, trace));
@@ -1061,9 +1067,9 @@ smc2_status smc2_sync(smc2_ctx* c) {
   return sticky(c);
 }
 
-smc2_status smc2_get_launch_shape(smc2_ctx* c, int* ppt, int* cta_threads, int* grid, int* one_group) {
+smc2_status smc2_get_launch_shape(smc2_ctx* c, int* ppt, int* cta_threads, int* grid, int* fp32_filter) {
   if (!c) return SMC2_EINVAL;
-  if (one_group) *one_group = c->pf_fast ? 1 : 0;
+  if (fp32_filter) *fp32_filter = c->pf_fast ? (c->pf_named ? 2 : 1) : 0;
   if (ppt) *ppt = c->ppt;
   if (cta_threads) *cta_threads = c->pf_block;
   if (grid) *grid = c->pf_grid;

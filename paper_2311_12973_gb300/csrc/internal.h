@@ -163,16 +163,17 @@ cudaError_t pf_launch(int precision, int model, int ppt, bool named, bool genera
 cudaError_t pf_configure(int precision, int model, int ppt, bool named, bool general, size_t smem);
 int pf_occupancy(int precision, int model, int ppt, bool named, bool general, int block, size_t smem);
 
-// The register-resident FP32 filter with one group per CTA (pf_fast.cuh): the
-// default filter (systematic resampling after every step) of the LG and SEIR
-// models in mixed precision, ppt 4, 8 or 16.  trace selects the instantiation
-// that writes the per-step trace of PFJob.
+// The register-resident FP32 filter of pf_fast.cuh: the default filter
+// (systematic resampling after every step) of the LG and SEIR models in mixed
+// precision, ppt 2, 4 or 8, one filter group per CTA or several narrower ones
+// (named: groups of several warps sharing a CTA).  trace selects the
+// instantiation that writes the per-step trace of PFJob.
 bool pf_fast_eligible(int precision, int model, bool general, int ppt);
-size_t pf_fast_smem_bytes(int model, int ppt, int M);
-cudaError_t pf_fast_launch(int model, int ppt, bool trace, int grid, int block, size_t smem, const PFLaunch& L,
-                           cudaStream_t s);
-cudaError_t pf_fast_configure(int model, int ppt, bool trace, size_t smem);
-int pf_fast_occupancy(int model, int ppt, bool trace, int block, size_t smem);
+size_t pf_fast_smem_bytes(int model, int ppt, int block, int M);
+cudaError_t pf_fast_launch(int model, int ppt, bool trace, bool grouped, int grid, int block, size_t smem,
+                           const PFLaunch& L, cudaStream_t s);
+cudaError_t pf_fast_configure(int model, int ppt, bool trace, bool grouped, size_t smem);
+int pf_fast_occupancy(int model, int ppt, bool trace, bool grouped, int block, size_t smem);
 
 // Outer kernels (outer.cu).
 cudaError_t outer_obs_terms(int precision, int model, const double* y, int T, void* obs,

@@ -69,19 +69,21 @@ bool pf_fast_eligible(int precision, int model, bool general, int ppt) {
          (ppt == 2 || ppt == 4 || ppt == 8);
 }
 
-size_t pf_fast_smem_bytes(int model, int ppt, int M) {
+size_t pf_fast_smem_bytes(int model, int ppt, int block, int M) {
   const int T = group_threads_for(ppt, M);
-  return fast_region_bytes(ppt * T, model == MODEL_LG ? 1 : 4);
+  const size_t rb = (fast_region_bytes(ppt * T, model == MODEL_LG ? 1 : 4) + 15) & ~(size_t)15;
+  return (size_t)(block / T) * rb;
 }
 
-static const void* select_fast(int model, int ppt, bool trace) {
+static const void* select_fast(int model, int ppt, bool trace, bool grouped) {
+  if (grouped) return trace ? nullptr : pf_fast_select_grouped(model, ppt);
   if (model == MODEL_LG) return pf_fast_select_lg(ppt, trace);
   if (model == MODEL_SEIR) return pf_fast_select_seir(ppt, trace);
   return nullptr;
 }
 
-cudaError_t pf_fast_configure(int model, int ppt, bool trace, size_t smem) {
-  const void* f = select_fast(model, ppt, trace);
+cudaError_t pf_fast_configure(int model, int ppt, bool trace, bool grouped, size_t smem) {
+  const void* f = select_fast(model, ppt, trace, grouped);
   if (!f) return cudaErrorInvalidValue;
   static std::mutex mu;  // only ever raised, as for pf_kernel
   std::lock_guard<std::mutex> lock(mu);
@@ -92,16 +94,16 @@ cudaError_t pf_fast_configure(int model, int ppt, bool trace, size_t smem) {
   return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-int pf_fast_occupancy(int model, int ppt, bool trace, int block, size_t smem) {
-  const void* f = select_fast(model, ppt, trace);
+int pf_fast_occupancy(int model, int ppt, bool trace, bool grouped, int block, size_t smem) {
+  const void* f = select_fast(model, ppt, trace, grouped);
   int n = 0;
   if (!f || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, block, smem) != cudaSuccess) return 0;
   return n;
 }
 
-cudaError_t pf_fast_launch(int model, int ppt, bool trace, int grid, int block, size_t smem, const PFLaunch& L,
-                           cudaStream_t s) {
-  const void* f = select_fast(model, ppt, trace);
+cudaError_t pf_fast_launch(int model, int ppt, bool trace, bool grouped, int grid, int block, size_t smem,
+                           const PFLaunch& L, cudaStream_t s) {
+  const void* f = select_fast(model, ppt, trace, grouped);
   if (!f) return cudaErrorInvalidValue;
   void* args[] = {const_cast<PFLaunch*>(&L)};
   return cudaLaunchKernel(f, dim3(grid), dim3(block), args, smem, s);

@@ -163,10 +163,12 @@ struct PairModel<MODEL_SEIR> {
   }
 };
 
-// Register budget per particles-per-thread shape of the FP32 filter.
-template <int PPT>
+// Register budget per particles-per-thread shape of the FP32 filter (grouped
+// instantiations hold the group's width, index and region in registers too).
+template <int PPT, bool GROUPED>
 struct FastRegCap {
-  static constexpr int value = PPT <= 2 ? 64 : (PPT == 4 ? 80 : 128);
+  static constexpr int value = GROUPED ? (PPT <= 2 ? 72 : (PPT == 4 ? 96 : 128))
+                                       : (PPT <= 2 ? 64 : (PPT == 4 ? 80 : 128));
   static_assert(PPT == 2 || PPT == 4 || PPT == 8, "particles per thread");
 };
 
@@ -210,15 +212,32 @@ __device__ __forceinline__ int slots_exact(const SlotCount& sc, uint64_t C, floa
   return n + ((lh < rh || (lh == rh && ll < rl)) ? 1 : 0);
 }
 
-template <int MODEL, int PPT, bool TRACE>
+// Barrier of one filter group of T threads (group g of its CTA).  Ungrouped
+// instantiations run one group that is the whole CTA.  Grouped ones (datasets of
+// unequal width in one launch) let a warp synchronise alone, a group that fills
+// the CTA use the CTA barrier, and groups of several warps that share a CTA use
+// named barrier 1 + g.
+template <bool GROUPED>
+__device__ __forceinline__ void fast_group_sync(int T, int g) {
+  if (!GROUPED)
+    __syncthreads();
+  else if (T == 32)
+    __syncwarp();
+  else if (T != (int)blockDim.x)
+    named_barrier(1 + g, T);
+  else
+    __syncthreads();
+}
+
+template <int MODEL, int PPT, bool TRACE, bool GROUPED>
 __device__ __forceinline__ void fast_filter(const PFJob& J, const PFModel& mdl, int i, unsigned char* smem,
-                                            uint2 key, uint32_t k, int t_cap, uint32_t& tag) {
+                                            uint2 key, uint32_t k, int t_cap, int lt, int T, int g) {
   constexpr int NS = ModelDims<MODEL>::NS;
   constexpr int D = ModelDims<MODEL>::D;
   constexpr int LOG2P = PPT == 2 ? 1 : (PPT == 4 ? 2 : 3);
   constexpr int NP = PPT / 2;  // pairs per thread
-  const int T = blockDim.x, nw = T >> 5;
-  const int lt = threadIdx.x, lane = lt & 31, warp = lt >> 5;
+  const int nw = T >> 5;
+  const int lane = lt & 31, warp = lt >> 5;
   const int M = J.M, TT = t_cap > 0 ? min(J.T, t_cap) : J.T;
   const int Mp = PPT * T;
   float* Xo = reinterpret_cast<float*>(smem);                           // [PPT][T][NS]
@@ -228,6 +247,12 @@ __device__ __forceinline__ void fast_filter(const PFJob& J, const PFModel& mdl, 
   uint64_t* wsum = reinterpret_cast<uint64_t*>(carry + (Mp / 2));       // [32] (Mp / 2 >= T keeps 8-byte alignment)
   float* wmax = reinterpret_cast<float*>(wsum + 32);                    // [32]
   uint32_t* sU = reinterpret_cast<uint32_t*>(wmax + 32);                // [8]
+
+  // the marks start untagged for every filter: the region may have held another
+  // dataset's layout, and the step tag restarts at 1
+  for (int s = lt; s < Mp; s += T) mark[s] = 0u;
+  uint32_t tag = 0;
+  fast_group_sync<GROUPED>(T, g);
 
   double th[D];
 #pragma unroll
@@ -279,7 +304,7 @@ __device__ __forceinline__ void fast_filter(const PFJob& J, const PFModel& mdl, 
         for (int e = 0; e < 4; ++e) Z[(e * NP + p) * T + lt] = make_float2(za[e], zb[e]);
       }
       if (lt < 4 && t + lt < TT) sUg[lt] = philox4x32_10(make_uint4(0u, (uint32_t)(t + lt), c2, c3res), key).x;
-      if (nw == 1) __syncwarp();  // the resampling words before the warp reads them
+      if (nw == 1) __syncwarp();  // the resampling words before the warp reads them (wider groups: barriers below)
     }
     const float4 ob = obs[t - 1];
     float ell[PPT];
@@ -315,7 +340,7 @@ __device__ __forceinline__ void fast_filter(const PFJob& J, const PFModel& mdl, 
     lmax = warp_max_redux(lmax);
     if (nw > 1) {  // lane w reads warp w's maximum; one more reduction spreads the group's
       if (lane == 0) wmax[warp] = lmax;
-      __syncthreads();
+      fast_group_sync<GROUPED>(T, g);
       lmax = warp_max_redux(lane < nw ? wmax[lane] : -INFINITY);
     }
     const float m = lmax;
@@ -353,7 +378,7 @@ __device__ __forceinline__ void fast_filter(const PFJob& J, const PFModel& mdl, 
     uint64_t S, base = 0;
     if (nw > 1) {  // lane w reads warp w's total; an inclusive shuffle scan gives S and the warp's base
       if (lane == 31) wsum[warp] = incl;
-      __syncthreads();
+      fast_group_sync<GROUPED>(T, g);
       uint64_t wp = lane < nw ? wsum[lane] : 0ull;
       for (int o = 1; o < nw; o <<= 1) {
         const uint64_t n = __shfl_up_sync(0xffffffffu, wp, o);
@@ -385,10 +410,7 @@ __device__ __forceinline__ void fast_filter(const PFJob& J, const PFModel& mdl, 
       if (++tag == (1u << (32 - kMarkBits))) {  // the tags are spent: clear every mark, start again
         for (int s = lt; s < Mp; s += T) mark[s] = 0u;
         tag = 1;
-        if (nw > 1)
-          __syncthreads();
-        else
-          __syncwarp();
+        fast_group_sync<GROUPED>(T, g);
       }
       const uint32_t tg = tag << kMarkBits;
       const SlotCount sc = slot_count_setup(sUg[tm], S, M);
@@ -433,10 +455,7 @@ __device__ __forceinline__ void fast_filter(const PFJob& J, const PFModel& mdl, 
           for (int b = b0 + PPT; b < end; b += PPT) carry[b >> LOG2P] = mk;
         start = end;
       }
-      if (nw > 1)
-        __syncthreads();
-      else
-        __syncwarp();
+      fast_group_sync<GROUPED>(T, g);
       uint32_t a = carry[lt];
 #pragma unroll
       for (int r = 0; r < PPT; ++r) {
@@ -461,14 +480,12 @@ __device__ __forceinline__ void fast_filter(const PFJob& J, const PFModel& mdl, 
   if (lt == 0) J.loglik[i] = dead ? -HUGE_VAL : lsum_m + ((double)lsum_hi + (double)lsum_lo);
 }
 
-template <int MODEL, int PPT, bool TRACE>
-__global__ void __maxnreg__((FastRegCap<PPT>::value)) pf_fast_kernel(PFLaunch L) {
+template <int MODEL, int PPT, bool TRACE, bool GROUPED>
+__global__ void __maxnreg__((FastRegCap<PPT, GROUPED>::value)) pf_fast_kernel(PFLaunch L) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_wu;
   const uint32_t k = L.k_done ? (uint32_t)(*L.k_done + 1) : (uint32_t)L.k_imm;
   const uint2 key = seed_key(L.seed);
-  uint32_t tag = 0;  // step tag of the marks, shared by every filter this CTA runs
-  bool cleared = false;
   for (int it = 0;; ++it) {
     int w;
     if (L.wu_counter) {
@@ -492,32 +509,36 @@ __global__ void __maxnreg__((FastRegCap<PPT>::value)) pf_fast_kernel(PFLaunch L)
       count = min(L.fpc_single, L.job0.n - first);
     }
     const PFJob J = L.jobs ? L.jobs[job] : L.job0;
-    if (!cleared) {  // the marks start untagged (tag 0)
-      const int Mp = PPT * (int)blockDim.x;
-      uint32_t* mark = reinterpret_cast<uint32_t*>(smem + (size_t)ModelDims<MODEL>::NS * Mp * 4 + (size_t)Mp * 16);
-      for (int s = threadIdx.x; s < Mp; s += blockDim.x) mark[s] = 0u;
-      cleared = true;
-    }
-    for (int f = 0; f < count; ++f) {  // one group per CTA: a unit's filters run in turn
-      __syncthreads();
-      fast_filter<MODEL, PPT, TRACE>(J, L.mdl, first + f, smem, key, k, L.t_cap, tag);
+    if (!GROUPED) {  // one group, the whole CTA: a unit's filters run in turn
+      for (int f = 0; f < count; ++f) {
+        if (f) __syncthreads();
+        fast_filter<MODEL, PPT, TRACE, false>(J, L.mdl, first + f, smem, key, k, L.t_cap, threadIdx.x, blockDim.x, 0);
+      }
+    } else {  // groups of T threads, one filter each: warps, or named-barrier groups
+      const int T = group_threads_for(PPT, J.M);
+      const int g = threadIdx.x / T, lt = threadIdx.x - g * T;
+      const size_t rb = (fast_region_bytes(PPT * T, ModelDims<MODEL>::NS) + 15) & ~(size_t)15;
+      if (g < count && (g + 1) * T <= (int)blockDim.x)
+        fast_filter<MODEL, PPT, TRACE, true>(J, L.mdl, first + g, smem + g * rb, key, k, L.t_cap, lt, T, g);
     }
     if (!L.wu_counter) __syncthreads();
   }
 }
 
-template <int MODEL, bool TRACE>
+template <int MODEL, bool TRACE, bool GROUPED>
 const void* pf_fast_select(int ppt) {
   switch (ppt) {
-    case 2: return reinterpret_cast<const void*>(&pf_fast_kernel<MODEL, 2, TRACE>);
-    case 4: return reinterpret_cast<const void*>(&pf_fast_kernel<MODEL, 4, TRACE>);
-    case 8: return reinterpret_cast<const void*>(&pf_fast_kernel<MODEL, 8, TRACE>);
+    case 2: return reinterpret_cast<const void*>(&pf_fast_kernel<MODEL, 2, TRACE, GROUPED>);
+    case 4: return reinterpret_cast<const void*>(&pf_fast_kernel<MODEL, 4, TRACE, GROUPED>);
+    case 8: return reinterpret_cast<const void*>(&pf_fast_kernel<MODEL, 8, TRACE, GROUPED>);
     default: return nullptr;
   }
 }
 
-// instantiated in pf_fast_lg.cu and pf_fast_seir.cu
+// instantiated in pf_fast_lg.cu, pf_fast_seir.cu (one group per CTA) and
+// pf_fast_grouped.cu (groups of unequal width sharing a CTA, untraced)
 const void* pf_fast_select_lg(int ppt, bool trace);
 const void* pf_fast_select_seir(int ppt, bool trace);
+const void* pf_fast_select_grouped(int model, int ppt);
 
 }  // namespace smc2

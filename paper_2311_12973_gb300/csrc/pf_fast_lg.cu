@@ -3,6 +3,6 @@
 
 namespace smc2 {
 const void* pf_fast_select_lg(int ppt, bool trace) {
-  return trace ? pf_fast_select<MODEL_LG, true>(ppt) : pf_fast_select<MODEL_LG, false>(ppt);
+  return trace ? pf_fast_select<MODEL_LG, true, false>(ppt) : pf_fast_select<MODEL_LG, false, false>(ppt);
 }
 }  // namespace smc2

@@ -3,6 +3,6 @@
 
 namespace smc2 {
 const void* pf_fast_select_seir(int ppt, bool trace) {
-  return trace ? pf_fast_select<MODEL_SEIR, true>(ppt) : pf_fast_select<MODEL_SEIR, false>(ppt);
+  return trace ? pf_fast_select<MODEL_SEIR, true, false>(ppt) : pf_fast_select<MODEL_SEIR, false, false>(ppt);
 }
 }  // namespace smc2

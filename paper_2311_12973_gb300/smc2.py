@@ -21,7 +21,7 @@ PREC_FP64, PREC_MIXED = 0, 1
 PROP_RW, PROP_MLP = 0, 1
 PF_SYSTEMATIC, PF_MULTINOMIAL = 0, 1
 PRIOR_GAUSS, PRIOR_UNIFORM = 0, 1
-PF_ANY, PF_GROUPS, PF_ONE_GROUP = 0, 1, 2
+PF_ANY, PF_GROUPS, PF_FP32 = 0, 1, 2
 LK_FORWARD, LK_GAUSS_OPT = 0, 1
 
 
@@ -318,18 +318,22 @@ class SMC2:
     def pf_loglik(self, theta_soa, iteration: int, dataset: int = 0, out=None):
         """theta_soa: CUDA float64 tensor [D][n]; returns CUDA float64 [n]."""
         import torch
-        n = theta_soa.shape[1]
-        out = out if out is not None else torch.empty(n, dtype=torch.float64, device=theta_soa.device)
+        n = self._theta_n(theta_soa, "smc2_pf_loglik")
+        self._dataset_dims(dataset)
+        if out is None:
+            out = torch.empty(n, dtype=torch.float64, device=theta_soa.device)
+        elif not (out.is_cuda and out.dtype == torch.float64 and out.is_contiguous() and out.numel() >= n):
+            raise SMC2Error(EINVAL, "smc2_pf_loglik: out must be a contiguous CUDA float64 tensor of n values")
         _check(lib.smc2_pf_loglik(self._ctx, _ptr(theta_soa), n, int(iteration), dataset, _ptr(out)),
                "smc2_pf_loglik")
         return out
 
-    def pf_trace(self, theta_soa, iteration: int, dataset: int = 0, M: int | None = None,
-                 T: int | None = None):
+    def pf_trace(self, theta_soa, iteration: int, dataset: int = 0):
+        """Log-likelihoods [n], increments [n][T] and ancestors [n][T-1][M] of the
+        dataset's filters (T, M of that dataset)."""
         import torch
-        n = theta_soa.shape[1]
-        M = M or self.cfg.M
-        T = T or self.cfg.T
+        n = self._theta_n(theta_soa, "smc2_pf_trace")
+        M, T = self._dataset_dims(dataset)
         dev = theta_soa.device
         ll = torch.empty(n, dtype=torch.float64, device=dev)
         delta = torch.empty((n, T), dtype=torch.float64, device=dev)
@@ -338,19 +342,32 @@ class SMC2:
                                  _ptr(delta), _ptr(anc)), "smc2_pf_trace")
         return ll, delta, anc
 
+    def _theta_n(self, theta_soa, what: str) -> int:
+        """n of a [D][n] CUDA float64 parameter array, checked."""
+        import torch
+        if not (hasattr(theta_soa, "is_cuda") and theta_soa.is_cuda and theta_soa.dtype == torch.float64
+                and theta_soa.is_contiguous() and theta_soa.dim() == 2 and theta_soa.shape[0] == self.D):
+            raise SMC2Error(EINVAL, f"{what}: theta must be a contiguous CUDA float64 tensor [D][n]")
+        return theta_soa.shape[1]
+
+    def _dataset_dims(self, dataset: int):
+        if not 0 <= dataset < len(self.Ms):
+            raise SMC2Error(EINVAL, f"dataset {dataset} of {len(self.Ms)}")
+        return self.Ms[dataset], self.Ts[dataset]
+
     def launch_shape(self):
         a, b, c, f = C.c_int(), C.c_int(), C.c_int(), C.c_int()
         _check(lib.smc2_get_launch_shape(self._ctx, C.byref(a), C.byref(b), C.byref(c), C.byref(f)),
                "smc2_get_launch_shape")
-        return {"ppt": a.value, "cta_threads": b.value, "grid": c.value, "one_group_per_cta": bool(f.value)}
+        return {"ppt": a.value, "cta_threads": b.value, "grid": c.value, "fp32_filter": f.value}
 
     def pf_trace_states(self, theta_soa, iteration: int, dataset: int = 0):
         """The FP32 filter's per-step trace: log-likelihoods [n], increments [n][T],
         ancestors [n][T-1][M], post-propagation states [n][T][M][5], log-weights
         [n][T][M] and quantised weights [n][T][M] (int64 storage of uint64)."""
         import torch
-        n = theta_soa.shape[1]
-        M, T = self.Ms[dataset], self.Ts[dataset]
+        n = self._theta_n(theta_soa, "smc2_pf_trace")
+        M, T = self._dataset_dims(dataset)
         dev = theta_soa.device
         ll = torch.empty(n, dtype=torch.float64, device=dev)
         delta = torch.empty((n, T), dtype=torch.float64, device=dev)

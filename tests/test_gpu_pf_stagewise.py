@@ -50,19 +50,10 @@ CASES = [
 ]
 
 
-@pytest.mark.parametrize("name,M,T,n,ppt,fam", CASES)
-def test_fp32_filter_stagewise_against_oracle(S, name, M, T, n, ppt, fam):
-    w = I.workload(name, precision=I.PREC_MIXED).with_(M=M, T=T)
-    th = I.theta_near_prior(w, n, seed=23, spread=0.3)
-    if w.model == I.LG:
-        th[:, 0] = np.clip(th[:, 0], -0.95, 0.95)
-    ctx = S.SMC2(S.make_config(w, ppt=ppt, pf_family=fam), w.y)
-    shape = ctx.launch_shape()
-    if fam == 2:
-        assert shape["one_group_per_cta"] and shape["ppt"] == ppt, shape
-    k = 3
-    ll, delta, anc, xs, lw, q = (a.cpu().numpy() for a in ctx.pf_trace_states(soa(th), iteration=k))
-    ctx.close()
+def _check_stagewise(w, th, k, ll, delta, anc, xs, lw, q):
+    """Every step of every traced filter against the oracle (the bars of the
+    module docstring); returns the worst relative errors."""
+    M, T, n = w.M, w.T, th.shape[0]
     q = q.view(np.uint64)
     cfg = O.config_from(w)
     ns = 1 if w.model == I.LG else 4
@@ -106,4 +97,60 @@ def test_fp32_filter_stagewise_against_oracle(S, name, M, T, n, ppt, fam):
                 assert np.array_equal(anc[i, t - 1], a_or), (i, t, np.nonzero(anc[i, t - 1] != a_or)[0][:8])
                 x_pre = x_dev[anc[i, t - 1]]
         assert abs(ll[i] - np.sum(delta[i])) <= 1e-9 * max(1.0, abs(ll[i]))
+    return worst
+
+
+@pytest.mark.parametrize("name,M,T,n,ppt,fam", CASES)
+def test_fp32_filter_stagewise_against_oracle(S, name, M, T, n, ppt, fam):
+    w = I.workload(name, precision=I.PREC_MIXED).with_(M=M, T=T)
+    th = I.theta_near_prior(w, n, seed=23, spread=0.3)
+    if w.model == I.LG:
+        th[:, 0] = np.clip(th[:, 0], -0.95, 0.95)
+    ctx = S.SMC2(S.make_config(w, ppt=ppt, pf_family=fam), w.y)
+    shape = ctx.launch_shape()
+    if fam == 2:
+        assert shape["fp32_filter"] == 1 and shape["ppt"] == ppt, shape
+    k = 3
+    trace = [a.cpu().numpy() for a in ctx.pf_trace_states(soa(th), iteration=k)]
+    ctx.close()
+    worst = _check_stagewise(w, th, k, *trace)
     print(f"{name} M={M} ppt={ppt} family={fam}: worst relative errors {worst}")
+
+
+GROUPED = [
+    # (ppt, [(M, T)] of the datasets of one context): groups of one warp, of
+    # several warps on named barriers, and as wide as the CTA, with ragged M
+    (4, [(128, 40), (512, 60), (1024, 50), (250, 45)]),
+    (8, [(128, 40), (512, 60), (1024, 50), (250, 45)]),
+]
+
+
+@pytest.mark.parametrize("ppt,shapes", GROUPED)
+def test_grouped_fp32_filter_equals_one_group_per_cta(S, ppt, shapes):
+    """Datasets of unequal M in one context run the grouped instantiation of the
+    FP32 filter (filter groups of unequal width sharing a CTA).  The filter's
+    arithmetic does not depend on the group's width, so every dataset's
+    log-likelihoods, increments and ancestors equal bit for bit those of the
+    one-group-per-CTA instantiation on the same dataset (the traced run), and
+    the traced run of the ragged dataset is checked step by step against the
+    oracle."""
+    n = 5  # fewer filters than a unit of the narrowest groups holds
+    ws = [I.workload("seir_t100_n1024", precision=I.PREC_MIXED, N=n, M=m, T=t, dataset=d, data_seed=30 + d)
+          for d, (m, t) in enumerate(shapes)]
+    ctx = S.SMC2(S.make_config(ws[0], ppt=ppt, pf_family=S.PF_FP32), np.concatenate([w.y for w in ws]),
+                 datasets=[(n, m, t) for m, t in shapes])
+    shape = ctx.launch_shape()
+    assert shape["fp32_filter"] == 2 and shape["ppt"] == ppt, shape
+    k = 2
+    for d, w in enumerate(ws):
+        th = I.theta_near_prior(w, n, seed=40 + d, spread=0.3)
+        ll_g = ctx.pf_loglik(soa(th), iteration=k, dataset=d).cpu().numpy()
+        _, delta_g, anc_g = (a.cpu().numpy() for a in ctx.pf_trace(soa(th), iteration=k, dataset=d))
+        trace = [a.cpu().numpy() for a in ctx.pf_trace_states(soa(th), iteration=k, dataset=d)]
+        assert np.array_equal(ll_g, trace[0]), (d, ll_g, trace[0])
+        assert np.array_equal(delta_g, trace[1]), d
+        assert np.array_equal(anc_g, trace[2]), d
+        if w.M % ppt or (w.M // ppt) % 32:
+            worst = _check_stagewise(w, th[:2], k, *(a[:2] for a in trace))
+            print(f"dataset {d} (M={w.M}, T={w.T}) ppt={ppt}: worst relative errors {worst}")
+    ctx.close()

@@ -187,15 +187,20 @@ def test_batched_datasets_match_oracle(S, case):
     ctx.close()
 
 
-def test_batched_seir_mixed_runs(S):
+@pytest.mark.parametrize("family", ["groups", "fp32"])
+def test_batched_seir_mixed_runs(S, family):
     """Sixty-four SEIR-type datasets of uneven T, N and M in one mixed-precision
     context: every dataset's statistics are finite, and dataset 0 (whose random
     stream is that of a single-dataset context) equals a context holding it
-    alone, bit for bit, at the same launch shape."""
+    alone, bit for bit, with the same filter kernel: pf_kernel at the same
+    launch shape, or the FP32 filter (grouped in the batched context, one
+    filter per CTA alone)."""
     ws = I.batched_workloads(64, K=3)
     shapes = [(w.N, w.M, w.T) for w in ws]
-    shape = dict(ppt=4, cta_threads=256)
+    shape = dict(ppt=4, cta_threads=256, pf_family=S.PF_GROUPS) if family == "groups" else \
+        dict(ppt=4, pf_family=S.PF_FP32)
     ctx = S.SMC2(S.make_config(ws[0], **shape), np.concatenate([w.y for w in ws]), datasets=shapes)
+    assert ctx.launch_shape()["fp32_filter"] == (0 if family == "groups" else 2)
     stats = ctx.run(3)
     for k in range(3):
         for d in range(64):
