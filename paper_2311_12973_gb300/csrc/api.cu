@@ -353,6 +353,28 @@ smc2_status apply_shape(smc2_ctx* c, int ppt, int block, bool named, bool upload
   return SMC2_OK;
 }
 
+// With the learned proposal, the training cluster runs beside the particle
+// filter and holds part of its SMs (registers, shared memory and threads of one
+// CTA each).  A shape whose work units fit in one wave of the whole GPU but not
+// beside the cluster would run a second wave of whole filters every iteration,
+// so the tuner weighs its time by the ratio of waves with and without the
+// cluster.
+float training_wave_factor(const smc2_ctx* c) {
+  int ctas = 0, threads = 0, regs = 0;
+  size_t smem = 0;
+  if (mlp_train_footprint(&ctas, &threads, &regs, &smem) != cudaSuccess || ctas < 1) return 1.f;
+  const int occ = ctx_pf_occupancy(c);
+  const int beside = c->pf_fast ? pf_fast_blocks_beside(c->model, c->ppt, c->pf_named, c->pf_block, c->pf_smem,
+                                                        threads, regs, smem)
+                                : pf_blocks_beside(c->precision, c->model, c->ppt, c->pf_named, c->pf_general,
+                                                   c->pf_block, c->pf_smem, threads, regs, smem);
+  const long full = (long)occ * c->sms;
+  const long with = (long)occ * (c->sms - ctas) + (long)std::min(occ, beside) * ctas;
+  if (full < 1 || with < 1) return 1.f;
+  const long w_full = (c->n_wus + full - 1) / full, w_with = (c->n_wus + with - 1) / with;
+  return (float)w_with / (float)w_full;
+}
+
 // Launch-shape tuner: time every valid (particles per thread, CTA threads) pair
 // on the context's own work list (prior draws of theta, min(T, 32) steps).
 smc2_status choose_launch_shape(smc2_ctx* c) {
@@ -406,6 +428,7 @@ smc2_status choose_launch_shape(smc2_ctx* c) {
       c->kernel_launches++;
       if (ok && rep > 0) cand_best = std::min(cand_best, ms);
     }
+    if (ok && c->mlp.on) cand_best *= training_wave_factor(c);
     if (ok && cand_best < best) {
       best = cand_best;
       pick = cb;

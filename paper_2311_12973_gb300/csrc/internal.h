@@ -174,6 +174,13 @@ cudaError_t pf_fast_launch(int model, int ppt, bool trace, bool grouped, int gri
                            const PFLaunch& L, cudaStream_t s);
 cudaError_t pf_fast_configure(int model, int ppt, bool trace, bool grouped, size_t smem);
 int pf_fast_occupancy(int model, int ppt, bool trace, bool grouped, int block, size_t smem);
+// Particle-filter CTAs (the context's kernel, untraced) that fit on an SM beside
+// one resident CTA of another kernel (o_threads threads of o_regs registers,
+// o_smem bytes of shared memory).
+int pf_blocks_beside(int precision, int model, int ppt, bool named, bool general, int block, size_t smem,
+                     int o_threads, int o_regs, size_t o_smem);
+int pf_fast_blocks_beside(int model, int ppt, bool grouped, int block, size_t smem, int o_threads, int o_regs,
+                          size_t o_smem);
 
 // Outer kernels (outer.cu).
 cudaError_t outer_obs_terms(int precision, int model, const double* y, int T, void* obs,
@@ -196,6 +203,9 @@ cudaError_t mlp_step_launch(float* p, int D, const float* x, const float* y, int
                             float lr, cudaStream_t s);
 int mlp_train_cluster_size();  // CTAs of the training cluster (0: no cluster can be scheduled)
 size_t mlp_train_smem_bytes();
+// Per-SM footprint of the training cluster: its CTAs, and one CTA's threads,
+// registers per thread and shared memory.
+cudaError_t mlp_train_footprint(int* ctas, int* threads, int* regs, size_t* smem);
 cudaError_t mlp_train_steps_launch(float* p, float* m, float* v, int* step, float* x, float* y, int R,
                                    const int* R_dev, float* loss, int D, int steps, float lr, cudaStream_t s,
                                    const MlpDev* ring_of = nullptr);

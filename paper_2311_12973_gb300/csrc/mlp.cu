@@ -956,6 +956,17 @@ cudaError_t mlp_step_launch(float* p, int D, const float* x, const float* y, int
 
 size_t mlp_train_smem_bytes() { return sizeof(MlpTrainSmem); }
 
+cudaError_t mlp_train_footprint(int* ctas, int* threads, int* regs, size_t* smem) {
+  cudaFuncAttributes a{};
+  const cudaError_t e = cudaFuncGetAttributes(&a, mlp_train_kernel);
+  if (e != cudaSuccess) return e;
+  *ctas = mlp_train_cluster_size();
+  *threads = 32 * kTrainWarps;
+  *regs = a.numRegs;
+  *smem = sizeof(MlpTrainSmem) + a.sharedSizeBytes;
+  return cudaSuccess;
+}
+
 // Largest cluster (16, 8, 4, 2 or 1 CTAs) that the device can co-schedule with
 // this kernel's shared memory.
 int mlp_train_cluster_size() {

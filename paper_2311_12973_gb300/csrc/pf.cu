@@ -1,4 +1,5 @@
 // pf.cu -- host side of the particle-filter kernel: shapes, attributes, launches.
+#include <algorithm>
 #include <mutex>
 
 #include "pf_fast.cuh"
@@ -107,6 +108,45 @@ cudaError_t pf_fast_launch(int model, int ppt, bool trace, bool grouped, int gri
   if (!f) return cudaErrorInvalidValue;
   void* args[] = {const_cast<PFLaunch*>(&L)};
   return cudaLaunchKernel(f, dim3(grid), dim3(block), args, smem, s);
+}
+
+// CTAs of kernel f (block threads, smem bytes of dynamic shared memory) that fit
+// on one SM beside a resident CTA of another kernel (o_threads threads of o_regs
+// registers, o_smem bytes of shared memory): registers are allocated per warp
+// in units of 256, and every CTA reserves the device's per-block shared memory.
+static int blocks_beside(const void* f, int block, size_t smem, int o_threads, int o_regs, size_t o_smem) {
+  cudaFuncAttributes a{};
+  int dev = 0, regs_sm = 0, smem_sm = 0, resv = 0, thr_sm = 0, blk_sm = 0;
+  if (!f || cudaFuncGetAttributes(&a, f) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&blk_sm, cudaDevAttrMaxBlocksPerMultiprocessor, dev) != cudaSuccess)
+    return 0;
+  auto regs_of = [](int threads, int regs) {
+    return ((threads + 31) / 32) * (((regs * 32) + 255) / 256 * 256);
+  };
+  const long r_free = (long)regs_sm - regs_of(o_threads, o_regs);
+  const long s_free = (long)smem_sm - (long)(o_smem + resv);
+  const long t_free = (long)thr_sm - o_threads;
+  const long per_r = regs_of(block, a.numRegs), per_s = (long)(smem + a.sharedSizeBytes + resv);
+  if (r_free < 0 || s_free < 0 || t_free < 0) return 0;
+  long n = std::min<long>(blk_sm - 1, t_free / block);
+  n = std::min(n, r_free / per_r);
+  if (per_s > 0) n = std::min(n, s_free / per_s);
+  return (int)std::max<long>(n, 0);
+}
+
+int pf_blocks_beside(int precision, int model, int ppt, bool named, bool general, int block, size_t smem,
+                     int o_threads, int o_regs, size_t o_smem) {
+  return blocks_beside(select_kernel(precision, model, ppt, named, general), block, smem, o_threads, o_regs,
+                       o_smem);
+}
+
+int pf_fast_blocks_beside(int model, int ppt, bool grouped, int block, size_t smem, int o_threads, int o_regs,
+                          size_t o_smem) {
+  return blocks_beside(select_fast(model, ppt, false, grouped), block, smem, o_threads, o_regs, o_smem);
 }
 
 }  // namespace smc2
