@@ -68,7 +68,7 @@ MODEL_NAMES = {0: "LG-AR(1)", 1: "SEIR-type", 2: "binomial SIR"}
 # from one ncu capture of a full-size launch of the workload, valid only for that
 # workload and the kernel source it was taken on (sha-256 prefixes of the sources).
 PF_TRAFFIC = {
-    "seir_t200_n8192": {"bytes": 462592.0, "sources": {"pf_fast.cuh": "c8fda16e3a150a2a", "pf_impl.cuh": "ed94a1cf40e60688",
+    "seir_t200_n8192": {"bytes": 790528.0, "sources": {"pf_fast.cuh": "68b0361ca29cb26b", "pf_impl.cuh": "ed94a1cf40e60688",
                                                        "common.cuh": "cb814bfa27b629ec"}},
 }
 
@@ -84,6 +84,8 @@ def parse():
                    help="workload of the accuracy comparison of the forms (extra keys of the line)")
     p.add_argument("--no-fp64-form", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-batched", action="store_true",
+                   help="skip the 64-dataset workload (extra keys of the line)")
     p.add_argument("--no-forms", action="store_true",
                    help="skip the accuracy comparison of the random-walk, FP64 and learned forms")
     p.add_argument("--pf", default="workload", choices=["workload", "systematic", "paper"],
@@ -295,7 +297,30 @@ def time_runs(S, torch, ctx, w, steps, warmup, flush, rank_sync):
     return ms, ess_sums, pf_ms, pf_n, launches, wall
 
 
-def accuracy_forms(S, torch, I, wr, world, seeds=96):
+def batched_datasets(S, torch, I, flush, rank_sync, peak, steps=2):
+    """The 64-dataset SEIR-type workload (T in 50..400, N in {256, 1024, 4096},
+    M in {128, 512, 1024}, K = 10) in one mixed-precision context: particle-steps
+    per second of whole runs, and of its particle-filter launches against the
+    ALU issue peak."""
+    import numpy as np
+    ws = I.batched_workloads(64)
+    ctx = S.SMC2(S.make_config(ws[0]), np.concatenate([w.y for w in ws]),
+                 datasets=[(w.N, w.M, w.T) for w in ws])
+    shape = ctx.launch_shape()
+    ms, _, pf_ms, pf_n, launches, _ = time_runs(S, torch, ctx, ws[0], steps, 1, flush, rank_sync)
+    ctx.close()
+    per_iter = float(sum(w.N * w.M * w.T for w in ws))
+    run_ms = sum(ms) / len(ms)
+    pf_avg = pf_ms / max(pf_n, 1)
+    ops = alg_ops(ws[0]) * per_iter
+    return {"workload": "seir_batched_64", "datasets": 64, "K": ws[0].K, "particle_steps_per_iteration": per_iter,
+            "ms_per_run": run_ms, "value": per_iter * ws[0].K / (run_ms * 1e-3), "unit": UNIT,
+            "pf_ms_per_launch": pf_avg, "pf_particle_steps_per_s": per_iter / (pf_avg * 1e-3),
+            "pf_roofline_frac": ops / (pf_avg * 1e-3) / peak, "launch_shape": shape,
+            "gpu_launches_per_run": launches / max(len(ms), 1)}
+
+
+def accuracy_forms(S, torch, I, wr, world, seeds=384):
     """Posterior accuracy per unit time of three forms of the SMC^2 step on the
     same data: mixed precision with the random walk, the plain FP64 GPU form,
     and mixed precision with the learned proposal.  Accuracy is the mean
@@ -304,9 +329,11 @@ def accuracy_forms(S, torch, I, wr, world, seeds=96):
     FP64 form matches the oracle run for run); mse x time is inversely
     proportional to accuracy per second.  The FP64 and mixed random-walk forms
     run the same seeds, so their log-evidence estimates and squared errors are
-    compared pairwise.  The errors are heavy-tailed, so the line also carries
-    the median squared error and, per coordinate, the fraction of seeds in
-    which the mixed form is the worse of the pair."""
+    compared pairwise.  The errors are heavy-tailed (blocks of 96 seeds gave
+    worse-of-the-pair fractions from 0.40 to 0.68), so the line also carries
+    the median squared error, per coordinate the fraction of seeds in which
+    the mixed form is the worse of the pair, and the paired differences of the
+    posterior means with their standard errors."""
     import numpy as np
 
     def runs(w, seed_list, **over):
@@ -332,7 +359,7 @@ def accuracy_forms(S, torch, I, wr, world, seeds=96):
     forms = {"mixed_rw": wr.with_(ppt=0, cta_threads=0),
              "fp64_rw": wr.with_(precision=I.PREC_FP64, ppt=0, cta_threads=0),
              "mixed_learned": wr.with_(proposal=I.PROP_MLP, ppt=0, cta_threads=0)}
-    res, logz, sqerr = {}, {}, {}
+    res, logz, sqerr, post = {}, {}, {}, {}
     for name, wf in forms.items():
         r = runs(wf, [base + 100 + i for i in range(seeds)])
         means = np.array([x[0] for x in r])
@@ -341,6 +368,7 @@ def accuracy_forms(S, torch, I, wr, world, seeds=96):
         ms = float(np.mean([x[2] for x in r]))
         logz[name] = np.array([x[3] for x in r])
         sqerr[name] = sq
+        post[name] = means
         res[name] = {"ms_per_run": ms, "ess_per_s": float(np.mean([x[1] for x in r])) * world / (ms * 1e-3),
                      "rmse": [float(v) for v in np.sqrt(mse)], "mse_x_s": float(mse.mean() * ms * 1e-3),
                      "mse": float(mse.mean()), "median_sq_err": float(np.median(sq))}
@@ -355,6 +383,9 @@ def accuracy_forms(S, torch, I, wr, world, seeds=96):
     res["mixed_over_fp64_mse"] = res["mixed_rw"]["mse"] / res["fp64_rw"]["mse"]
     res["mixed_over_fp64_median_sq_err"] = res["mixed_rw"]["median_sq_err"] / res["fp64_rw"]["median_sq_err"]
     res["mixed_worse_fraction"] = [float(v) for v in (sqerr["mixed_rw"] > sqerr["fp64_rw"]).mean(axis=0)]
+    dm = post["mixed_rw"] - post["fp64_rw"]
+    res["mixed_minus_fp64_posterior_mean"] = {"mean": [float(v) for v in dm.mean(axis=0)],
+                                              "se": [float(v) for v in dm.std(axis=0, ddof=1) / np.sqrt(len(dm))]}
     res["reference"] = {"runs": 4, "N": ref_w.N, "precision": "fp64", "rw_scale": 0.2, "seeds_per_form": seeds,
                         "workload": wr.name}
     return res
@@ -474,6 +505,10 @@ def main():
     paper_table = None
     if not args.no_forms and wr.model == I.SIR:
         paper_table = sir_paper_table(S, torch, I, wr)
+    peak = alu_peak_ops(props.multi_processor_count, measured_peaks().get("sm_max_mhz", 2070.0))
+    batched = None
+    if not args.no_batched and wr.model == I.SEIR:
+        batched = batched_datasets(S, torch, I, flush, rank_sync, peak)
 
     if rank != 0:
         return
@@ -496,6 +531,7 @@ def main():
         "ess_speedup_vs_fp64_form": (ess_per_s / fp64["ess_per_s"]) if fp64 else None,
         "forms": forms,
         "paper_table": paper_table,
+        "batched": batched,
         "roofline": {"kernel": (f"pf_fast_kernel<{MODEL_NAMES[wr.model]}, {shape['ppt']}>"
                                 if shape["fp32_filter"] else f"pf_kernel<float, {MODEL_NAMES[wr.model]}, "
                                 f"{shape['ppt']}>"), "bound": "alu", "achieved": achieved / 1e9,
