@@ -746,11 +746,13 @@ static smc2_status pf_standalone(smc2_ctx* c, const double* theta, int n, int it
   if (!c || !theta || !loglik || n < 1 || n > SMC2_MAX_N || bad_ds(c, dataset) || iteration < 0 ||
       iteration >= (1 << 28))
     return SMC2_EINVAL;
-  const bool trace = xtr || ltr || qtr;
-  if (trace) {
+  const bool states = xtr || ltr || qtr;
+  if (states) {
     if (!xtr || !ltr || !qtr) return SMC2_EINVAL;
     if (!pf_fast_eligible(c->precision, c->model, c->pf_general, c->ppt)) return SMC2_EINVAL;
   }
+  // the FP32 filter writes increments and ancestors only in its traced instantiation
+  const bool trace = states || (c->pf_fast && (delta || anc));
   PFJob job{};
   job.xtr = xtr;
   job.ltr = ltr;

@@ -199,9 +199,8 @@ __device__ __forceinline__ float warp_max_redux(float v) {
 // exact 128-bit comparison (slots_exact) settles the flagged ones.
 __device__ __forceinline__ int slots_estimate(const SlotCount& sc, float Cf, bool& near) {
   const float est = fmaf(Cf, sc.scale, -sc.off);
-  const float nf = rintf(est);
-  near = !(fabsf(est - nf) > sc.margin);
-  return (int)nf + (est > nf ? 1 : 0);
+  near = !(fabsf(est - rintf(est)) > sc.margin);
+  return __float2int_ru(est);  // the ceiling, in one conversion
 }
 __device__ __forceinline__ int slots_exact(const SlotCount& sc, uint64_t C, float Cf) {
   const float est = fmaf(Cf, sc.scale, -sc.off);
@@ -251,6 +250,7 @@ __device__ __forceinline__ void fast_filter(const PFJob& J, const PFModel& mdl, 
   // the marks start untagged for every filter: the region may have held another
   // dataset's layout, and the step tag restarts at 1
   for (int s = lt; s < Mp; s += T) mark[s] = 0u;
+  carry[lt] = 0u;  // threads whose slots are all padding keep this valid ancestor (particle 0)
   uint32_t tag = 0;
   fast_group_sync<GROUPED>(T, g);
 
@@ -346,8 +346,10 @@ __device__ __forceinline__ void fast_filter(const PFJob& J, const PFModel& mdl, 
     const float m = lmax;
     if (!(m > -INFINITY)) {  // every weight vanished: the estimate is zero
       dead = true;
-      if (lt == 0 && J.delta)
-        for (int s = t; s <= J.T; ++s) J.delta[(size_t)i * J.T + (s - 1)] = -HUGE_VAL;
+      if constexpr (TRACE) {
+        if (lt == 0 && J.delta)
+          for (int s = t; s <= J.T; ++s) J.delta[(size_t)i * J.T + (s - 1)] = -HUGE_VAL;
+      }
       break;
     }
     // (3) quantise: v = 2^((l - max) log2 e) 2^B (0 for l = -inf), q = floor(v); the
@@ -403,7 +405,9 @@ __device__ __forceinline__ void fast_filter(const PFJob& J, const PFModel& mdl, 
       const float sh = lsum_hi + small, bv = sh - lsum_hi;  // TwoSum: sh + err = lsum_hi + small exactly
       lsum_lo += (lsum_hi - (sh - bv)) + (small - bv);
       lsum_hi = sh;
-      if (J.delta) J.delta[(size_t)i * J.T + (t - 1)] = (double)m + (double)small;
+      if constexpr (TRACE) {
+        if (J.delta) J.delta[(size_t)i * J.T + (t - 1)] = (double)m + (double)small;
+      }
     }
     // (5) systematic resampling by marks
     if (t < TT) {
@@ -459,10 +463,13 @@ __device__ __forceinline__ void fast_filter(const PFJob& J, const PFModel& mdl, 
       uint32_t a = carry[lt];
 #pragma unroll
       for (int r = 0; r < PPT; ++r) {
-        if (lt * PPT + r >= M) continue;  // padding slots hold no particle
+        // Padding slots (j >= M) take the last real particle's mark, or the
+        // cleared carry (particle 0): a valid state whose weight is never used.
         a = max(a, mark[r * T + lt]);
         const int src = (int)(a & ((1u << kMarkBits) - 1));
-        if (J.anc) J.anc[((size_t)i * (J.T - 1) + (t - 1)) * M + lt * PPT + r] = src;
+        if constexpr (TRACE) {
+          if (J.anc && lt * PPT + r < M) J.anc[((size_t)i * (J.T - 1) + (t - 1)) * M + lt * PPT + r] = src;
+        }
         const float* xs = Xo + ((size_t)(src & (PPT - 1)) * T + (src >> LOG2P)) * NS;
         float v[NS];
         StateVec<float, NS>::load(xs, 0, v);
