@@ -447,6 +447,7 @@ __device__ __forceinline__ void fast_filter(const PFJob& J, const PFModel& mdl, 
         StateVec<float, NS>::store(Xo + (size_t)((2 * p) * T + lt) * NS, 0, a);
         StateVec<float, NS>::store(Xo + (size_t)((2 * p + 1) * T + lt) * NS, 0, b);
       }
+      uint32_t longmask = 0;  // particles whose slots reach past a second thread's first slot
 #pragma unroll
       for (int r = 0; r < PPT; ++r) {
         const int end = ends[r + 1];
@@ -455,9 +456,20 @@ __device__ __forceinline__ void fast_filter(const PFJob& J, const PFModel& mdl, 
         // the first slot of every thread inside [start, end): usually none or one
         const int b0 = (start + PPT - 1) & ~(PPT - 1);
         if (b0 < end) carry[b0 >> LOG2P] = mk;
-        if (end - b0 > PPT)
-          for (int b = b0 + PPT; b < end; b += PPT) carry[b >> LOG2P] = mk;
+        longmask |= (end - b0 > PPT) ? (1u << r) : 0u;
         start = end;
+      }
+      if (__any_sync(0xffffffffu, longmask != 0)) {  // the further first slots, after the straight-line loop
+        start = ends[0];
+#pragma unroll
+        for (int r = 0; r < PPT; ++r) {
+          const int end = ends[r + 1];
+          if ((longmask >> r) & 1u) {
+            const uint32_t mk = tg | (uint32_t)(lt * PPT + r);
+            for (int b = ((start + PPT - 1) & ~(PPT - 1)) + PPT; b < end; b += PPT) carry[b >> LOG2P] = mk;
+          }
+          start = end;
+        }
       }
       fast_group_sync<GROUPED>(T, g);
       uint32_t a = carry[lt];
