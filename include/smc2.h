@@ -127,7 +127,9 @@ typedef struct smc2_ctx smc2_ctx; /* opaque; owns its device workspace */
  * cta_threads: threads per particle-filter CTA (0 = pick by the tuner;
  *   otherwise a multiple of 32 up to 512 that holds whole filter groups).
  *   The tuner times every valid (ppt, cta_threads) pair on the context's own
- *   work list, prior draws of theta and min(T, 32) steps, during smc2_init.
+ *   work list, prior draws of theta and min(T, 32) steps, then the shapes
+ *   within 15 % of the fastest five times each over min(T, 64) steps, during
+ *   smc2_init.
  * pf_family: the particle-filter kernel the tuner may pick: 0 either,
  *   SMC2_PF_GROUPS pf_kernel only (filter groups of any width, several per
  *   CTA), SMC2_PF_FP32 the register-resident FP32 filter with 2, 4 or 8

@@ -376,7 +376,8 @@ float training_wave_factor(const smc2_ctx* c) {
 }
 
 // Launch-shape tuner: time every valid (particles per thread, CTA threads) pair
-// on the context's own work list (prior draws of theta, min(T, 32) steps).
+// on the context's own work list (prior draws of theta, min(T, 32) steps), then
+// the few within 15 % of the fastest again, over min(T, 64) steps, in turn.
 smc2_status choose_launch_shape(smc2_ctx* c) {
   struct Shape {
     int ppt, block;
@@ -410,31 +411,69 @@ smc2_status choose_launch_shape(smc2_ctx* c) {
   cudaEvent_t e0, e1;
   SMC2_TRY(cudaEventCreate(&e0));
   SMC2_TRY(cudaEventCreate(&e1));
-  float best = 1e30f;
-  Shape pick = cand[0];
-  for (const auto& cb : cand) {
-    if (apply_shape(c, cb.ppt, cb.block, cb.named, true, cb.fast) != SMC2_OK) continue;
+  // one launch of the applied shape over t_cap steps; < 0 on failure
+  auto time_launch = [&](int t_cap) -> float {
     PFLaunch L = c->pl;
+    L.t_cap = t_cap;
     float ms = 0.f;
-    bool ok = true;
-    float cand_best = 1e30f;
-    for (int rep = 0; rep < 3 && ok; ++rep) {  // one warm-up launch, then the best of two
-      L.t_cap = rep == 0 ? 4 : 32;
-      ok = cudaMemsetAsync(c->d_wu_counter, 0, sizeof(int), s) == cudaSuccess &&
-           cudaEventRecord(e0, s) == cudaSuccess &&
-           ctx_pf_launch(c, c->pf_grid, L, s) == cudaSuccess &&
-           cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
-           cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
-      c->kernel_launches++;
-      if (ok && rep > 0) cand_best = std::min(cand_best, ms);
-    }
-    if (ok && c->mlp.on) cand_best *= training_wave_factor(c);
-    if (ok && cand_best < best) {
-      best = cand_best;
-      pick = cb;
-    }
+    const bool ok = cudaMemsetAsync(c->d_wu_counter, 0, sizeof(int), s) == cudaSuccess &&
+                    cudaEventRecord(e0, s) == cudaSuccess && ctx_pf_launch(c, c->pf_grid, L, s) == cudaSuccess &&
+                    cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+                    cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+    c->kernel_launches++;
     cudaGetLastError();
+    return ok ? ms : -1.f;
+  };
+  // first pass: one warm-up launch, then the best of two over 32 steps
+  std::vector<std::pair<float, size_t>> timed;
+  for (size_t ci = 0; ci < cand.size(); ++ci) {
+    const auto& cb = cand[ci];
+    if (apply_shape(c, cb.ppt, cb.block, cb.named, true, cb.fast) != SMC2_OK) continue;
+    float cand_best = 1e30f;
+    bool ok = time_launch(4) >= 0.f;
+    for (int rep = 0; rep < 2 && ok; ++rep) {
+      const float ms = time_launch(32);
+      ok = ms >= 0.f;
+      if (ok) cand_best = std::min(cand_best, ms);
+    }
+    if (!ok) continue;
+    if (c->mlp.on) cand_best *= training_wave_factor(c);
+    timed.push_back({cand_best, ci});
   }
+  if (timed.empty()) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return SMC2_EINVAL;
+  }
+  std::sort(timed.begin(), timed.end());
+  // second pass: the shapes within 15 % of the fastest, timed in turn over 64 steps
+  // five times each (interleaved, so that a clock ramp touches them alike); the
+  // smallest median wins
+  std::vector<size_t> fin;
+  for (const auto& tc : timed)
+    if (fin.size() < 3 && tc.first <= 1.15f * timed[0].first) fin.push_back(tc.second);
+  size_t pick_i = timed[0].second;
+  if (fin.size() > 1) {
+    std::vector<std::vector<float>> ts(fin.size());
+    for (int rep = 0; rep < 5; ++rep)
+      for (size_t f = 0; f < fin.size(); ++f) {
+        const auto& cb = cand[fin[f]];
+        if (apply_shape(c, cb.ppt, cb.block, cb.named, true, cb.fast) != SMC2_OK) continue;
+        const float ms = time_launch(64);
+        if (ms >= 0.f) ts[f].push_back(c->mlp.on ? ms * training_wave_factor(c) : ms);
+      }
+    float best = 1e30f;
+    for (size_t f = 0; f < fin.size(); ++f) {
+      if (ts[f].size() < 3) continue;
+      std::sort(ts[f].begin(), ts[f].end());
+      const float med = ts[f][ts[f].size() / 2];
+      if (med < best) {
+        best = med;
+        pick_i = fin[f];
+      }
+    }
+  }
+  const Shape pick = cand[pick_i];
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return apply_shape(c, pick.ppt, pick.block, pick.named, true, pick.fast);
