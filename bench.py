@@ -86,6 +86,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-batched", action="store_true",
                    help="skip the 64-dataset workload (extra keys of the line)")
+    p.add_argument("--batched-datasets", type=int, default=64,
+                   help="datasets of the batched workload (smaller cases for profiler captures)")
     p.add_argument("--no-forms", action="store_true",
                    help="skip the accuracy comparison of the random-walk, FP64 and learned forms")
     p.add_argument("--pf", default="workload", choices=["workload", "systematic", "paper"],
@@ -297,13 +299,13 @@ def time_runs(S, torch, ctx, w, steps, warmup, flush, rank_sync):
     return ms, ess_sums, pf_ms, pf_n, launches, wall
 
 
-def batched_datasets(S, torch, I, flush, rank_sync, peak, steps=2):
+def batched_datasets(S, torch, I, flush, rank_sync, peak, steps=2, n_datasets=64):
     """The 64-dataset SEIR-type workload (T in 50..400, N in {256, 1024, 4096},
     M in {128, 512, 1024}, K = 10) in one mixed-precision context: particle-steps
     per second of whole runs, and of its particle-filter launches against the
     ALU issue peak."""
     import numpy as np
-    ws = I.batched_workloads(64)
+    ws = I.batched_workloads(n_datasets)
     ctx = S.SMC2(S.make_config(ws[0]), np.concatenate([w.y for w in ws]),
                  datasets=[(w.N, w.M, w.T) for w in ws])
     shape = ctx.launch_shape()
@@ -313,7 +315,7 @@ def batched_datasets(S, torch, I, flush, rank_sync, peak, steps=2):
     run_ms = sum(ms) / len(ms)
     pf_avg = pf_ms / max(pf_n, 1)
     ops = alg_ops(ws[0]) * per_iter
-    return {"workload": "seir_batched_64", "datasets": 64, "K": ws[0].K, "particle_steps_per_iteration": per_iter,
+    return {"workload": f"seir_batched_{n_datasets}", "datasets": n_datasets, "K": ws[0].K, "particle_steps_per_iteration": per_iter,
             "ms_per_run": run_ms, "value": per_iter * ws[0].K / (run_ms * 1e-3), "unit": UNIT,
             "pf_ms_per_launch": pf_avg, "pf_particle_steps_per_s": per_iter / (pf_avg * 1e-3),
             "pf_roofline_frac": ops / (pf_avg * 1e-3) / peak, "launch_shape": shape,
@@ -508,7 +510,7 @@ def main():
     peak = alu_peak_ops(props.multi_processor_count, measured_peaks().get("sm_max_mhz", 2070.0))
     batched = None
     if not args.no_batched and wr.model == I.SEIR:
-        batched = batched_datasets(S, torch, I, flush, rank_sync, peak)
+        batched = batched_datasets(S, torch, I, flush, rank_sync, peak, n_datasets=args.batched_datasets)
 
     if rank != 0:
         return
