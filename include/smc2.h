@@ -213,22 +213,25 @@ smc2_status smc2_pf_loglik(smc2_ctx* ctx, const double* theta_dev, int n, int it
 /* As smc2_pf_loglik, and also writes the per-step increments
  * delta_dev[i * T + t] = log p^(y_{1:t+1}) - log p^(y_{1:t}) and the
  * ancestors anc_dev[(i * (T-1) + t) * M + j] of slot j after step t+1
- * (either may be NULL).  Diagnostic path for checking the filter. */
+ * (either may be NULL).  Diagnostic path for checking the filter; on a
+ * context whose filter is the FP32 one it runs that filter's traced
+ * instantiation, whose arithmetic equals the untraced one's. */
 smc2_status smc2_pf_trace(smc2_ctx* ctx, const double* theta_dev, int n, int iteration,
                           int dataset, double* loglik_dev, double* delta_dev, int32_t* anc_dev);
 
 /* As smc2_pf_trace, and also the per-step quantities of the FP32 filter that a
  * stage-wise check needs (mixed precision, LG or SEIR model, the default
- * filter; the context's ppt must be 4, 8 or 16): after the propagation of
+ * filter; the context's ppt must be 2, 4 or 8): after the propagation of
  * step t (0-based t < T), by particle j, at index (i T + t) M + j:
  * x_dev[.. * 5 + e] the state (LG: x in e = 0; SEIR: S, E, I, log beta and the
  * day's incidence lambda in e = 0..4), logw_dev the log-weight log g(y_t | x_t)
  * (Eq. 2; -inf for a NaN), q_dev the quantised weight floor(exp(logw - max)
  * 2^B) the resampling after step t used (Eqs. 26-27).  All outputs device
  * memory; delta_dev and anc_dev as in smc2_pf_trace (may be NULL).  It runs
- * the traced instantiation of the one-group-per-CTA FP32 filter, whose
- * arithmetic equals the untraced one's.  Errors: EINVAL (another precision,
- * model or filter, a ppt outside 4, 8, 16, a NULL trace pointer). */
+ * the traced instantiation of the FP32 filter with one filter per CTA, whose
+ * arithmetic equals the sampler's instantiations' (grouped or not).  Errors:
+ * EINVAL (another precision, model or filter, a ppt outside 2, 4, 8, a NULL
+ * trace pointer). */
 smc2_status smc2_pf_trace_states(smc2_ctx* ctx, const double* theta_dev, int n, int iteration, int dataset,
                                  double* loglik_dev, double* delta_dev, int32_t* anc_dev, float* x_dev,
                                  float* logw_dev, uint64_t* q_dev);

@@ -165,9 +165,10 @@ int pf_occupancy(int precision, int model, int ppt, bool named, bool general, in
 
 // The register-resident FP32 filter of pf_fast.cuh: the default filter
 // (systematic resampling after every step) of the LG and SEIR models in mixed
-// precision, ppt 2, 4 or 8, one filter group per CTA or several narrower ones
-// (named: groups of several warps sharing a CTA).  trace selects the
-// instantiation that writes the per-step trace of PFJob.
+// precision, ppt 2, 4 or 8, one filter group per CTA or (grouped) groups of
+// unequal width sharing a CTA.  trace selects the instantiation that writes the
+// per-step trace of PFJob (states, log-weights, integer weights, increments and
+// ancestors); the untraced ones write only the log-likelihoods.
 bool pf_fast_eligible(int precision, int model, bool general, int ppt);
 size_t pf_fast_smem_bytes(int model, int ppt, int block, int M);
 cudaError_t pf_fast_launch(int model, int ppt, bool trace, bool grouped, int grid, int block, size_t smem,

@@ -1,29 +1,32 @@
 // pf_fast.cuh -- the FP32 bootstrap particle filter (Sec. II) with one filter
-// per CTA and the particles held in registers.
+// per thread group and the particles held in registers: the group is the whole
+// CTA, or (the grouped instantiations, for datasets of unequal M) one of
+// several groups of unequal width that share it.
 //
 // The same filter as pf_kernel's default (systematic resampling after every
 // step t < T, Eqs. 26-27 with Algorithm 1's output order; the mean-weight reset
 // of Eq. 13; the likelihood increment of Eq. 8), shaped for few instructions
-// per particle: each of the CTA's T threads owns PPT consecutive particles
+// per particle: each of the group's T threads owns PPT consecutive particles
 // (2, 4 or 8) and works on them in pairs with the packed two-wide FP32
 // instructions, and no step has a loop whose length differs between lanes.
 // Per step:
 //   1. propagate and log-weight every particle in registers (Eqs. 1, 2, 5);
-//   2. the group maximum of the log-weights (warp shuffles; one barrier when
-//      the CTA has several warps);
-//   3. q_j = floor(exp(l_j - max) 2^B) by integer operations on the float's
-//      exponent and significand (a float-to-u64 conversion instruction would run
-//      on the narrow FP64 pipe), a thread-local inclusive prefix, one warp scan
-//      and (several warps) one more barrier for the warp totals;
+//   2. the group maximum of the log-weights (one warp reduction; one barrier
+//      when the group has several warps);
+//   3. q_j = floor(exp(l_j - max) 2^B) with the floor to u64 taken as two exact
+//      32-bit conversions (a float-to-u64 conversion instruction would run on
+//      the narrow FP64 pipe), a thread-local inclusive prefix, one warp scan and
+//      (several warps) one more barrier for the warp totals;
 //   4. the increment max + log(S 2^-B) - log M from the exact integer total S;
 //   5. resampling by marks: particle j fills the slots F(C_{j-1}) .. F(C_j) - 1,
 //      F(C) the number of thresholds tau_s = floor((s + u) S / M) below C (the
 //      slot counting of pf_kernel).  Each particle with copies writes its index,
 //      tagged with a step counter, at its first slot, and at the first slot of
-//      every thread whose slots its range covers; after a barrier the ancestor
-//      of slot s is the largest current tag at or before s within its thread's
-//      slots -- ancestors never decrease along the slots -- and the thread reads
-//      that particle's state.
+//      every thread whose slots its range covers (the rare ranges that cover
+//      more than one such slot after the loop, so that the loop has no branch);
+//      after a barrier the ancestor of slot s is the largest current tag at or
+//      before s within its thread's slots -- ancestors never decrease along the
+//      slots -- and the thread reads that particle's state.
 // Shared arrays indexed by a slot or a particle s keep it at row s % PPT, column
 // s / PPT, so that a warp reading one entry per thread touches consecutive words.
 #pragma once
