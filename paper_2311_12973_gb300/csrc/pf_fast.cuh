@@ -420,7 +420,15 @@ __device__ __forceinline__ void fast_filter(const PFJob& J, const PFModel& mdl, 
         fast_group_sync<GROUPED>(T, g);
       }
       const uint32_t tg = tag << kMarkBits;
-      const SlotCount sc = slot_count_setup(sUg[tm], S, M);
+      SlotCount sc = slot_count_setup(sUg[tm], S, M);
+      // The estimate below errs by at most 17 M u + 2 u + 8 M / S (u = 2^-24): S and
+      // C0 each reach float through two roundings (2 u), the approximate division
+      // M / S adds 2 ulp (4 u), the thread's running float sum 7 u of its own share
+      // (at most M) and its unfloored weights under 8 M / S, the sum C0 + share and
+      // the fma 1 u each, and the offset 2 u absolute.  A margin of M 2^-19 + 2^-20
+      // covers that 1.8 times over; the generic margin of slot_count_setup is
+      // wider, and each estimate inside the margin costs an exact test.
+      sc.margin = fmaf((float)M, 0x1p-19f, 0x1p-20f);
       const uint64_t C0 = base + excl;  // cumulative weight before the thread's first particle
       const float C0f = u64_to_float(C0);
       // the slot counts at the thread's cumulative weights, one vote for the exact comparisons
