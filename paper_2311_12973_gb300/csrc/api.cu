@@ -549,6 +549,7 @@ void fill_params(smc2_ctx* c) {
   L.fpc_single = 0;
   L.wu_counter = c->d_wu_counter;
   L.seed = c->cfg.seed;
+  philox_round_keys(c->cfg.seed, L.rk);
   L.k_done = c->d_k;
   L.k_imm = 0;
   L.status = c->d_status;

@@ -53,6 +53,29 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 key) {
   return c;
 }
 
+// The same generator with its round keys given: rk[2r] = key.x + r 0x9E3779B9,
+// rk[2r + 1] = key.y + r 0xBB67AE85 (philox_round_keys), so that a kernel can keep
+// them in its parameter block and fold them into the XORs as constants.
+__device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const uint32_t (&rk)[20]) {
+  const uint32_t mult0 = 0xD2511F53u, mult1 = 0xCD9E8D57u;
+#pragma unroll
+  for (int round = 0; round < 10; ++round) {
+    const uint64_t p0 = (uint64_t)mult0 * c.x, p1 = (uint64_t)mult1 * c.z;
+    const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    c = make_uint4(hi1 ^ c.y ^ rk[2 * round], lo1, hi0 ^ c.w ^ rk[2 * round + 1], lo0);
+  }
+  return c;
+}
+
+__host__ __device__ inline void philox_round_keys(uint64_t seed, uint32_t rk[20]) {
+  const uint32_t k0 = (uint32_t)(seed & 0xffffffffull), k1 = (uint32_t)(seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    rk[2 * r] = k0 + (uint32_t)r * 0x9E3779B9u;
+    rk[2 * r + 1] = k1 + (uint32_t)r * 0xBB67AE85u;
+  }
+}
+
 __device__ __forceinline__ uint2 seed_key(uint64_t seed) {
   return make_uint2((uint32_t)(seed & 0xffffffffull), (uint32_t)(seed >> 32));
 }

@@ -152,6 +152,7 @@ struct PFLaunch {
   PFModel mdl;
   int t_cap;           // > 0: run at most t_cap steps (launch-shape tuning)
   int pad;
+  uint32_t rk[20];     // Philox round keys of seed (philox_round_keys), read as constants
   PFJob job0;
 };
 

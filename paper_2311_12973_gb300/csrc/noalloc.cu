@@ -131,6 +131,7 @@ extern "C" smc2_status smc2_pf_loglik_noalloc(const smc2_config* cfg, const doub
   L.n_wu = (n + L.fpc_single - 1) / L.fpc_single;
   L.wu_counter = counter;
   L.seed = cfg->seed;
+  philox_round_keys(cfg->seed, L.rk);
   L.k_done = nullptr;
   L.k_imm = iteration;
   L.status = nullptr;

@@ -166,6 +166,14 @@ struct PairModel<MODEL_SEIR> {
   }
 };
 
+// Four normals from one Philox call with the round keys of the kernel's
+// parameter block (the same numbers as normals4 with the seed's key).
+__device__ __forceinline__ void normals4_rk(uint4 c, const uint32_t (&rk)[20], float z[4]) {
+  const uint4 w = philox4x32_10_rk(c, rk);
+  box_muller<float>(w.x, w.y, z[0], z[1]);
+  box_muller<float>(w.z, w.w, z[2], z[3]);
+}
+
 // Register budget per particles-per-thread shape of the FP32 filter (grouped
 // instantiations hold the group's width, index and region in registers too).
 template <int PPT, bool GROUPED>
@@ -233,7 +241,8 @@ __device__ __forceinline__ void fast_group_sync(int T, int g) {
 
 template <int MODEL, int PPT, bool TRACE, bool GROUPED>
 __device__ __forceinline__ void fast_filter(const PFJob& J, const PFModel& mdl, int i, unsigned char* smem,
-                                            uint2 key, uint32_t k, int t_cap, int lt, int T, int g) {
+                                            const uint32_t (&rk)[20], uint32_t k, int t_cap, int lt, int T,
+                                            int g) {
   constexpr int NS = ModelDims<MODEL>::NS;
   constexpr int D = ModelDims<MODEL>::D;
   constexpr int LOG2P = PPT == 2 ? 1 : (PPT == 4 ? 2 : 3);
@@ -279,9 +288,9 @@ __device__ __forceinline__ void fast_filter(const PFJob& J, const PFModel& mdl, 
     float za = 0.f, zb = 0.f;
     if constexpr (MODEL == MODEL_LG) {
       float z[4];
-      normals4<float>(make_uint4((uint32_t)(lt * PPT + 2 * p), 0u, c2, counter_c3(TAG_PF_INIT, k)), key, z);
+      normals4_rk(make_uint4((uint32_t)(lt * PPT + 2 * p), 0u, c2, counter_c3(TAG_PF_INIT, k)), rk, z);
       za = z[0];
-      normals4<float>(make_uint4((uint32_t)(lt * PPT + 2 * p + 1), 0u, c2, counter_c3(TAG_PF_INIT, k)), key, z);
+      normals4_rk(make_uint4((uint32_t)(lt * PPT + 2 * p + 1), 0u, c2, counter_c3(TAG_PF_INIT, k)), rk, z);
       zb = z[0];
     }
     fp.init(a, za, th);
@@ -301,12 +310,12 @@ __device__ __forceinline__ void fast_filter(const PFJob& J, const PFModel& mdl, 
 #pragma unroll 1
       for (int p = 0; p < NP; ++p) {
         float za[4], zb[4];
-        normals4<float>(make_uint4((uint32_t)(lt * PPT + 2 * p), (uint32_t)((t - 1) >> 2), c2, c3prop), key, za);
-        normals4<float>(make_uint4((uint32_t)(lt * PPT + 2 * p + 1), (uint32_t)((t - 1) >> 2), c2, c3prop), key, zb);
+        normals4_rk(make_uint4((uint32_t)(lt * PPT + 2 * p), (uint32_t)((t - 1) >> 2), c2, c3prop), rk, za);
+        normals4_rk(make_uint4((uint32_t)(lt * PPT + 2 * p + 1), (uint32_t)((t - 1) >> 2), c2, c3prop), rk, zb);
 #pragma unroll
         for (int e = 0; e < 4; ++e) Z[(e * NP + p) * T + lt] = make_float2(za[e], zb[e]);
       }
-      if (lt < 4 && t + lt < TT) sUg[lt] = philox4x32_10(make_uint4(0u, (uint32_t)(t + lt), c2, c3res), key).x;
+      if (lt < 4 && t + lt < TT) sUg[lt] = philox4x32_10_rk(make_uint4(0u, (uint32_t)(t + lt), c2, c3res), rk).x;
       if (nw == 1) __syncwarp();  // the resampling words before the warp reads them (wider groups: barriers below)
     }
     const float4 ob = obs[t - 1];
@@ -515,7 +524,6 @@ __global__ void __maxnreg__((FastRegCap<PPT, GROUPED>::value)) pf_fast_kernel(PF
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_wu;
   const uint32_t k = L.k_done ? (uint32_t)(*L.k_done + 1) : (uint32_t)L.k_imm;
-  const uint2 key = seed_key(L.seed);
   for (int it = 0;; ++it) {
     int w;
     if (L.wu_counter) {
@@ -542,14 +550,14 @@ __global__ void __maxnreg__((FastRegCap<PPT, GROUPED>::value)) pf_fast_kernel(PF
     if (!GROUPED) {  // one group, the whole CTA: a unit's filters run in turn
       for (int f = 0; f < count; ++f) {
         if (f) __syncthreads();
-        fast_filter<MODEL, PPT, TRACE, false>(J, L.mdl, first + f, smem, key, k, L.t_cap, threadIdx.x, blockDim.x, 0);
+        fast_filter<MODEL, PPT, TRACE, false>(J, L.mdl, first + f, smem, L.rk, k, L.t_cap, threadIdx.x, blockDim.x, 0);
       }
     } else {  // groups of T threads, one filter each: warps, or named-barrier groups
       const int T = group_threads_for(PPT, J.M);
       const int g = threadIdx.x / T, lt = threadIdx.x - g * T;
       const size_t rb = (fast_region_bytes(PPT * T, ModelDims<MODEL>::NS) + 15) & ~(size_t)15;
       if (g < count && (g + 1) * T <= (int)blockDim.x)
-        fast_filter<MODEL, PPT, TRACE, true>(J, L.mdl, first + g, smem + g * rb, key, k, L.t_cap, lt, T, g);
+        fast_filter<MODEL, PPT, TRACE, true>(J, L.mdl, first + g, smem + g * rb, L.rk, k, L.t_cap, lt, T, g);
     }
     if (!L.wu_counter) __syncthreads();
   }
