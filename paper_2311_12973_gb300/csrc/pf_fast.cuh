@@ -176,10 +176,12 @@ __device__ __forceinline__ void normals4_rk(uint4 c, const uint32_t (&rk)[20], f
 
 // Register budget per particles-per-thread shape of the FP32 filter (grouped
 // instantiations hold the group's width, index and region in registers too).
+// 64 at ppt 4 fits four 256-thread CTAs per SM without spills; at ppt 8, 96
+// registers (five 128-thread CTAs per SM, no spills) measured slower than 128.
 template <int PPT, bool GROUPED>
 struct FastRegCap {
   static constexpr int value = GROUPED ? (PPT <= 2 ? 72 : (PPT == 4 ? 96 : 128))
-                                       : (PPT <= 2 ? 64 : (PPT == 4 ? 80 : 128));
+                                       : (PPT <= 2 ? 64 : (PPT == 4 ? 64 : 128));
   static_assert(PPT == 2 || PPT == 4 || PPT == 8, "particles per thread");
 };
 
