@@ -11,12 +11,24 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.cuh"
 #include "internal.h"
 
 using namespace smc2;
 
 namespace {
+
+// Host-side trace ranges (NVTX) around the library's calls: a profiler that
+// attaches (ncu --nvtx, nsys) sees them and the kernels launched inside; with
+// none attached each range costs a few nanoseconds.
+struct TraceRange {
+  explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange&) = delete;
+  TraceRange& operator=(const TraceRange&) = delete;
+};
 
 // Learned proposal defaults: step h, Adam rate, Adam steps per iteration,
 // iterations of training pairs kept.
@@ -379,6 +391,7 @@ float training_wave_factor(const smc2_ctx* c) {
 // on the context's own work list (prior draws of theta, min(T, 32) steps), then
 // the few within 15 % of the fastest again, over min(T, 64) steps, in turn.
 smc2_status choose_launch_shape(smc2_ctx* c) {
+  const TraceRange range("smc2 launch-shape tuner");
   struct Shape {
     int ppt, block;
     bool named, fast;
@@ -682,6 +695,7 @@ const char* smc2_status_string(smc2_status s) {
 }
 
 smc2_status smc2_init(const smc2_config* cfg, const double* y, void* stream, smc2_ctx** out) {
+  const TraceRange range("smc2_init");
   if (!out || !y) return SMC2_EINVAL;
   smc2_status st = validate(cfg);
   if (st != SMC2_OK) return st;
@@ -783,6 +797,7 @@ smc2_status smc2_reset(smc2_ctx* c, uint64_t seed) {
 static smc2_status pf_standalone(smc2_ctx* c, const double* theta, int n, int iteration, int dataset,
                                  double* loglik, double* delta, int32_t* anc, float* xtr = nullptr,
                                  float* ltr = nullptr, uint64_t* qtr = nullptr) {
+  const TraceRange range("smc2 particle filter");
   if (!c || !theta || !loglik || n < 1 || n > SMC2_MAX_N || bad_ds(c, dataset) || iteration < 0 ||
       iteration >= (1 << 28))
     return SMC2_EINVAL;
@@ -854,6 +869,7 @@ smc2_status smc2_pf_trace_states(smc2_ctx* c, const double* theta, int n, int it
 }
 
 smc2_status smc2_run(smc2_ctx* c, int n_iter, smc2_iter_stats* stats_host) {
+  const TraceRange range("smc2_run");
   if (!c || n_iter < 1) return SMC2_EINVAL;
   if (c->k_host + n_iter > c->K) return SMC2_ESTATE;
   TimedGraph* g = nullptr;
