@@ -154,3 +154,28 @@ def test_grouped_fp32_filter_equals_one_group_per_cta(S, ppt, shapes):
             worst = _check_stagewise(w, th[:2], k, *(a[:2] for a in trace))
             print(f"dataset {d} (M={w.M}, T={w.T}) ppt={ppt}: worst relative errors {worst}")
     ctx.close()
+
+
+@pytest.mark.parametrize("name,M,T", [("seir_t100_n1024", 512, 80), ("seir_t100_n1024", 300, 40), ("lg_t50_n64", 256, 50)])
+def test_fp32_filter_results_do_not_depend_on_the_launch_shape(S, name, M, T):
+    """The tuner may pick any particles-per-thread shape, and the sampler's
+    results must not change with it: per particle the arithmetic is the same,
+    the slot counts are exact whatever the thread's float running sum, and S
+    and the increment come from exact integer totals.  Log-likelihoods and
+    increments at ppt 2, 4 and 8 agree bit for bit."""
+    w = I.workload(name, precision=I.PREC_MIXED).with_(M=M, T=T)
+    th = I.theta_near_prior(w, 40, seed=29, spread=0.5)
+    if w.model == I.LG:
+        th[:, 0] = np.clip(th[:, 0], -0.95, 0.95)
+    out = {}
+    for ppt in (2, 4, 8):
+        ctx = S.SMC2(S.make_config(w, ppt=ppt, pf_family=S.PF_FP32), w.y)
+        assert ctx.launch_shape()["fp32_filter"] == 1
+        ll = ctx.pf_loglik(soa(th), iteration=5).cpu().numpy()
+        _, delta, anc = (a.cpu().numpy() for a in ctx.pf_trace(soa(th), iteration=5))
+        ctx.close()
+        out[ppt] = (ll, delta, anc)
+    for ppt in (4, 8):
+        assert np.array_equal(out[ppt][0], out[2][0]), (ppt, out[ppt][0][:4], out[2][0][:4])
+        assert np.array_equal(out[ppt][1], out[2][1]), ppt
+        assert np.array_equal(out[ppt][2], out[2][2]), ppt
