@@ -185,7 +185,8 @@ struct FastRegCap {
   static_assert(PPT == 2 || PPT == 4 || PPT == 8, "particles per thread");
 };
 
-// Shared memory of a CTA of T threads holding Mp = PPT T particles:
+// Shared memory of one filter group of T threads holding Mp = PPT T particles
+// (the whole CTA's, or one of the grouped instantiation's regions):
 //   Xo    float  [PPT][T][NS]   states after propagation, by particle
 //   Z     float2 [4][PPT/2][T]  the four normals of the current Philox counter of each slot pair
 //   mark  u32    [PPT][T]       step-tagged particle indices at the slots
