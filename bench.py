@@ -95,6 +95,8 @@ def parse():
                         "or the paper's (multinomial when the ESS falls below M/2)")
     p.add_argument("--ppt", type=int, default=0, help="pin particles per thread (0: tuner)")
     p.add_argument("--cta", type=int, default=0, help="pin threads per PF CTA (0: tuner)")
+    p.add_argument("--pf-family", default="any", choices=["any", "groups", "fp32"],
+                   help="particle-filter kernel family: the tuner's pick, pf_kernel, or the FP32 filter")
     p.add_argument("--filters", type=int, default=0,
                    help="run N parameter samples instead of the workload's (smaller cases for profiler captures)")
     return p.parse_args()
@@ -107,9 +109,9 @@ def dist_env():
     return rank, world, local
 
 
-def replica_workload(w, rank: int, ppt: int = 0, cta: int = 0):
+def replica_workload(w, rank: int, ppt: int = 0, cta: int = 0, pf_family: int = 0):
     """Rank `rank`'s independent replica of the workload: same data, own seed."""
-    return w.with_(seed=w.seed + 1000 * rank, ppt=ppt, cta_threads=cta)
+    return w.with_(seed=w.seed + 1000 * rank, ppt=ppt, cta_threads=cta, pf_family=pf_family)
 
 
 def reduce_max(x: float, dist=None, device: str = "cpu") -> float:
@@ -454,7 +456,7 @@ def main():
     from paper_2311_12973_gb300 import smc2 as S
 
     # each rank runs an independent replica (its own seed): weak scaling
-    wr = replica_workload(w, rank, args.ppt, args.cta)
+    wr = replica_workload(w, rank, args.ppt, args.cta, {"any": 0, "groups": 1, "fp32": 2}[args.pf_family])
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     ctx = S.SMC2(S.make_config(wr), wr.y)
     shape = ctx.launch_shape()
@@ -492,7 +494,7 @@ def main():
     # plain FP64 GPU form of the same workload
     fp64 = None
     if not args.no_fp64_form:
-        w64 = wr.with_(precision=I.PREC_FP64, ppt=0, cta_threads=0)
+        w64 = wr.with_(precision=I.PREC_FP64, ppt=0, cta_threads=0, pf_family=0)
         ctx64 = S.SMC2(S.make_config(w64), w64.y)
         ms64, ess64, _, _, _, _ = time_runs(S, torch, ctx64, w64, max(2, args.steps // 5), 1, flush,
                                             rank_sync)

@@ -70,6 +70,7 @@ class Workload:
     pf_ess_frac: float = 0.0
     ppt: int = 0            # particle-filter launch shape (0: the library's tuner)
     cta_threads: int = 0
+    pf_family: int = 0      # particle-filter kernel family the tuner may pick (0: either)
     y: np.ndarray | None = None
 
     @property
