@@ -68,7 +68,7 @@ MODEL_NAMES = {0: "LG-AR(1)", 1: "SEIR-type", 2: "binomial SIR"}
 # from one ncu capture of a full-size launch of the workload, valid only for that
 # workload and the kernel source it was taken on (sha-256 prefixes of the sources).
 PF_TRAFFIC = {
-    "seir_t200_n8192": {"bytes": 459776.0, "sources": {"pf_fast.cuh": "547248935ef74261", "pf_impl.cuh": "ed94a1cf40e60688",
+    "seir_t200_n8192": {"bytes": 748800.0, "sources": {"pf_fast.cuh": "bde90cf5170865a6", "pf_impl.cuh": "ed94a1cf40e60688",
                                                        "common.cuh": "e78c60dc197c7ed7"}},
 }
 

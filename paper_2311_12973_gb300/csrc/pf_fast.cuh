@@ -432,31 +432,66 @@ __device__ __forceinline__ void fast_filter(const PFJob& J, const PFModel& mdl, 
         fast_group_sync<GROUPED>(T, g);
       }
       const uint32_t tg = tag << kMarkBits;
-      SlotCount sc = slot_count_setup(sUg[tm], S, M);
-      // The estimate below errs by at most 17 M u + 2 u + 8 M / S (u = 2^-24): S and
-      // C0 each reach float through two roundings (2 u), the approximate division
-      // M / S adds 2 ulp (4 u), the thread's running float sum 7 u of its own share
-      // (at most M) and its unfloored weights under 8 M / S, the sum C0 + share and
-      // the fma 1 u each, and the offset 2 u absolute.  A margin of M 2^-19 + 2^-20
-      // covers that 1.8 times over; the generic margin of slot_count_setup is
-      // wider, and each estimate inside the margin costs an exact test.
-      sc.margin = fmaf((float)M, 0x1p-19f, 0x1p-20f);
+      const SlotCount sc = slot_count_setup(sUg[tm], S, M);
       const uint64_t C0 = base + excl;  // cumulative weight before the thread's first particle
       const float C0f = u64_to_float(C0);
-      // the slot counts at the thread's cumulative weights, one vote for the exact comparisons
       int ends[PPT + 1];
-      uint32_t near_mask = 0;
+      if constexpr (PPT < 8) {
+        // Few particles per thread: every crossing from the float estimate, whose
+        // error is under 17 M u + 2 u + 8 M / S (u = 2^-24): S and C0 each reach float
+        // through two roundings (2 u), the approximate division M / S adds 2 ulp (4 u),
+        // the thread's running float sum 7 u of its own share (at most M) and its
+        // unfloored weights under 8 M / S, the sum C0 + share and the fma 1 u each, and
+        // the offset 2 u absolute.  A margin of M 2^-19 + 2^-20 covers that 1.8 times.
+        SlotCount sm = sc;
+        sm.margin = fmaf((float)M, 0x1p-19f, 0x1p-20f);
+        uint32_t near_mask = 0;
 #pragma unroll
-      for (int r = 0; r <= PPT; ++r) {
-        bool nr;
-        ends[r] = slots_estimate(sc, r == 0 ? C0f : C0f + cf[r - 1], nr);
-        near_mask |= nr ? (1u << r) : 0u;
-      }
-      if (__any_sync(0xffffffffu, near_mask != 0)) {
+        for (int r = 0; r <= PPT; ++r) {
+          bool nr;
+          ends[r] = slots_estimate(sm, r == 0 ? C0f : C0f + cf[r - 1], nr);
+          near_mask |= nr ? (1u << r) : 0u;
+        }
+        if (__any_sync(0xffffffffu, near_mask != 0)) {
 #pragma unroll
-        for (int r = 0; r <= PPT; ++r)
-          if (near_mask & (1u << r))
-            ends[r] = slots_exact(sc, r == 0 ? C0 : C0 + c[r - 1], r == 0 ? C0f : C0f + cf[r - 1]);
+          for (int r = 0; r <= PPT; ++r)
+            if (near_mask & (1u << r))
+              ends[r] = slots_exact(sm, r == 0 ? C0 : C0 + c[r - 1], r == 0 ? C0f : C0f + cf[r - 1]);
+        }
+      } else {
+        // Eight particles per thread, where one exact test per thread costs less than
+        // the near crossings' tests: the thread's first crossing exactly, n0 from the
+        // float estimate (its error, under 17 M u, is far below 1/2), then
+        // E = C0 M 2^33 - (2^33 n0 + 2U + 1) S, which is S 2^33 (x0 - n0) for the crossing
+        // point x0 = C0 M / S - (2U + 1) 2^-33 of Eq. (27): F(C0) = n0 + [E > 0], and
+        // e0 = x0 - n0 = E 2^-33 / S to about 9 u.  |x0 - n0| < 1 and S <= 2^63 keep
+        // E 2^-33 inside 64 bits.
+        const int n0 = min(max((int)rintf(fmaf(C0f, sc.scale, -sc.off)), 0), M - 1);
+        const uint64_t a0 = ((uint64_t)n0 << 33) + sc.U21;
+        const uint64_t p_lo = a0 * sc.S, p_hi = __umul64hi(a0, sc.S);
+        const uint64_t q_lo = C0 * sc.M33, q_hi = __umul64hi(C0, sc.M33);
+        const uint64_t e_lo = q_lo - p_lo, e_hi = q_hi - p_hi - (q_lo < p_lo ? 1ull : 0ull);
+        const long long e33 = (long long)((e_hi << 31) | (e_lo >> 33));
+        const float e0 = fmaf((float)(int)(e33 >> 32), 0x1p32f, (float)(uint32_t)e33) * sc.scale / (float)M;
+        // The later crossings x0 + s_r M / S, s_r the thread's share of the weight
+        // before particle r: its float sum errs by 7 u of itself, M / S by 6 u and the
+        // product by 1 u, so y = e0 + s_r M / S errs by under 15 u s_r M / S + 10 u.  A
+        // margin of 2^-19 (s_r M / S + 1) covers that twice; crossings inside it (rare:
+        // the margin follows the share, not M) take the exact test.
+        ends[0] = n0 + (((long long)e_hi > 0 || (e_hi == 0 && e_lo != 0)) ? 1 : 0);
+        uint32_t near_mask = 0;
+#pragma unroll
+        for (int r = 1; r <= PPT; ++r) {
+          const float inc = cf[r - 1] * sc.scale;
+          const float y = e0 + inc;
+          near_mask |= !(fabsf(y - rintf(y)) > fmaf(inc, 0x1p-19f, 0x1p-19f)) ? (1u << r) : 0u;
+          ends[r] = n0 + __float2int_ru(y);
+        }
+        if (__any_sync(0xffffffffu, near_mask != 0)) {
+#pragma unroll
+          for (int r = 1; r <= PPT; ++r)
+            if (near_mask & (1u << r)) ends[r] = slots_exact(sc, C0 + c[r - 1], C0f + cf[r - 1]);
+        }
       }
       int start = ends[0];
 #pragma unroll
